@@ -1,0 +1,218 @@
+/*
+ * dlx.h - C ABI of the GB300 (sm_103a) differentiable-optics hot path.
+ *
+ * The library evaluates, on one GPU, the forward model and gradient of
+ * arXiv:2406.08703 (Sec. 3-4):
+ *
+ *   OPD   = OPD_fixed + sum_j c_j Z_j + OPD_pix                   (Sec. 3, BasisOptic + mask)
+ *   P     = T_hat exp(i 2 pi / lambda (OPD + x th_x + y th_y))       (Sec. 3, normalise=True)
+ *   E     = A(lambda) P A(lambda)^T                                   (Sec. 3, two-sided MFT)
+ *           A[k][n] = sqrt(dx du / lambda) exp(-2 pi i x_n u_k / lambda)
+ *   I_e   = sum_s F_s sum_l w_l |E_{l,s,e}|^2    (w normalised to sum 1)
+ *   m_e   = FF * (os x os block sums of I_e)                          (Sec. 3, pixel response)
+ *   L     = sum_e sum_p (m - d ln m)                                  (Sec. 4, Poisson likelihood)
+ *
+ * and the gradient of L with respect to the Zernike coefficients, the pixel
+ * OPD map, the flat field, the source fluxes and the source positions (the
+ * parameter groups of Sec. 3-4).
+ *
+ * Grids are pixel-centred: x_n = (n - (N-1)/2) D/N_pupil, u_k = (k - (No-1)/2)
+ * pixscale/oversample with No = n_det * oversample.  A source at +theta lands
+ * at u = +theta.  Arrays are row-major [y][x], float32, contiguous, on the
+ * plan's device unless stated otherwise.  Angles are radians.
+ *
+ * Ownership: the caller owns every array it passes and the CUDA stream; the
+ * library owns plans (MFT matrices + workspaces) and servers.  Device-pointer
+ * calls are asynchronous on the given stream (NULL = legacy default stream):
+ * outputs are valid once the stream has completed.  Every call returns a
+ * dlx_status; no exception crosses the ABI.  dlx_last_error() gives a
+ * thread-local message for the last failing call on the calling thread.
+ */
+#ifndef DLX_H
+#define DLX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DLX_OK = 0,
+    DLX_PENDING = 1,             /* dlx_poll: request not finished yet */
+    DLX_ERR_INVALID_ARG = -1,    /* bad pointer, size, or enum value */
+    DLX_ERR_NOMEM = -2,          /* device allocation or admission budget failed */
+    DLX_ERR_CUDA = -3,           /* a CUDA runtime call failed (message has the CUDA error) */
+    DLX_ERR_NONFINITE = -4,      /* loss or gradient is NaN/Inf (server path) */
+    DLX_ERR_TIMEOUT = -5,        /* dlx_poll deadline, or a device-side bounded wait expired */
+    DLX_ERR_RANGE = -6,          /* size beyond a supported maximum */
+    DLX_ERR_UNSUPPORTED = -7     /* precision form not available for this shape or device */
+} dlx_status;
+
+/* Arithmetic form of the four MFT contractions (Sec. 3 "two-sided MFT").
+ * All forms accumulate in FP32; phase arguments are reduced in FP64 and the
+ * loss and gradient reductions are FP64. */
+typedef enum {
+    DLX_FP32_SIMT = 0, /* FP32 FMA on CUDA cores */
+    DLX_TF32X3 = 1,    /* tcgen05 kind::tf32, operands split hi + lo, 3 products */
+    DLX_BF16X3 = 2,    /* tcgen05 kind::f16 (BF16), operands split hi + lo, 3 products */
+    DLX_BF16 = 3       /* tcgen05 kind::f16 (BF16), hi only */
+} dlx_prec;
+
+typedef struct dlx_plan dlx_plan;
+typedef struct dlx_server dlx_server;
+
+/* Shape of one optical model (Sec. 3, Listing 1: AngularOpticalSystem(wf_npix,
+ * diameter, layers, det_npix, det_pixsize) over a set of wavelengths). */
+typedef struct {
+    int n_pupil;             /* pupil samples per side, Ni >= 2 */
+    double diameter_m;       /* aperture diameter D; pupil spacing dx = D / Ni */
+    int n_det;               /* detector pixels per side, Nd >= 1 */
+    double pixscale_rad;     /* detector pixel scale p; MFT spacing du = p / oversample */
+    int oversample;          /* os >= 1; MFT output No = Nd * os */
+    int n_lambda;            /* number of wavelengths, >= 1 */
+    const double *lambda_m;  /* HOST array [n_lambda], metres; copied */
+    int n_src;               /* point sources, >= 1 */
+    int n_exp;               /* exposures (known dithers), >= 1 */
+    int n_zern;              /* Zernike basis terms, >= 0 */
+    int precision;           /* dlx_prec */
+    int psf_chunk;           /* PSFs per adjoint pass (per-wavelength recomputation batch);
+                                0 = automatic from workspace_limit_bytes */
+    size_t workspace_limit_bytes; /* 0 = no limit; bounds the adjoint workspace */
+} dlx_mft_desc;
+
+/* Parameters and fixed inputs of one evaluation.  Device pointers. */
+typedef struct {
+    const float *transmission; /* [Ni][Ni] aperture transmission T (>= 0) */
+    const float *opd_fixed;    /* [Ni][Ni] fixed OPD (mask), metres; NULL = 0 */
+    const float *zern_basis;   /* [n_zern][Ni][Ni] basis images; NULL iff n_zern == 0 */
+    const float *zern_coeff;   /* [n_zern] coefficients, metres RMS; NULL iff n_zern == 0 */
+    const float *opd_pix;      /* [Ni][Ni] free pixel OPD map, metres; NULL = not a parameter */
+    const float *weights;      /* [n_lambda] spectral weights (normalised internally) */
+    const float *flux;         /* [n_src] photons per source per exposure */
+    const float *pos;          /* [n_src][2] (theta_x, theta_y), rad */
+    const float *dither;       /* [n_exp][2] known offsets added to every source, rad; NULL = 0 */
+    const float *flat;         /* [Nd][Nd] pixel response FF */
+} dlx_params;
+
+/* Gradient outputs (device, caller-owned).  Any pointer may be NULL to skip it. */
+typedef struct {
+    float *d_zern;    /* [n_zern]   dL/dc_j */
+    float *d_opd_pix; /* [Ni][Ni]   dL/dOPD_pix */
+    float *d_flat;    /* [Nd][Nd]   dL/dFF */
+    float *d_flux;    /* [n_src]    dL/dF_s */
+    float *d_pos;     /* [n_src][2] dL/dtheta */
+} dlx_grads;
+
+typedef struct {
+    int n_pupil, n_det, oversample, n_out, n_lambda, n_src, n_exp, n_zern, n_psf;
+    int precision;
+    int psf_chunk;             /* PSFs per adjoint pass */
+    size_t workspace_bytes;    /* device memory held by the plan */
+    double flop_forward;       /* algorithmic MFT FLOP of one forward (8 per complex MAC) */
+    double flop_loss_grad;     /* algorithmic MFT FLOP of one loss+gradient incl. recomputation */
+    int gemm_tiles_stage2;     /* output tiles of the dominant contraction */
+} dlx_plan_info;
+
+/* Build a plan: validates the shape, allocates the MFT matrices A(lambda) and
+ * A(lambda)^H for every wavelength in the chosen operand form (phase arguments
+ * x_n u_k / lambda reduced in FP64 before sin/cos) and the workspaces, on
+ * `device`.  Synchronous.  Errors: INVALID_ARG (bad shape), UNSUPPORTED
+ * (tensor-core form on a device that is not sm_103), NOMEM, CUDA. */
+int dlx_make_mft(const dlx_mft_desc *desc, int device, dlx_plan **out);
+int dlx_destroy_plan(dlx_plan *plan);
+int dlx_plan_get_info(const dlx_plan *plan, dlx_plan_info *out);
+
+/* Forward model (Sec. 3): model[e][py][px] = FF * bin_os(sum_s F_s sum_l w_l |E|^2).
+ * `model` is device [n_exp][Nd][Nd]. */
+int dlx_forward(dlx_plan *plan, const dlx_params *params, float *model, void *cuda_stream);
+
+/* The flux-weighted oversampled intensity before binning and flat field,
+ * psf_os[e][ky][kx] = sum_s F_s sum_l w_l |E_{l,s,e}|^2, device [n_exp][No][No]. */
+int dlx_psf(dlx_plan *plan, const dlx_params *params, float *psf_os, void *cuda_stream);
+
+/* Loss and gradient (Sec. 4): *loss (device, one double) = sum (m - d ln max(m, 1e-30)),
+ * gradients into `grads`, and the model into `model_opt` ([n_exp][Nd][Nd], may be NULL).
+ * `data` is device int32 [n_exp][Nd][Nd] photon counts.  The adjoint recomputes
+ * each PSF's field from the stored first-stage product instead of storing all
+ * complex fields, psf_chunk PSFs at a time. */
+int dlx_loss_grad(dlx_plan *plan, const dlx_params *params, const int32_t *data, double *loss,
+                  const dlx_grads *grads, float *model_opt, void *cuda_stream);
+
+/* Synchronous diagnostics of the last evaluation on this plan: pixels whose
+ * model was clamped at 1e-30 before the log, and the device error flag (non-zero
+ * when a device-side bounded wait expired; the flag is cleared by this call). */
+int dlx_plan_diagnostics(dlx_plan *plan, int64_t *clamped, int32_t *device_error);
+
+/* Adam update (Kingma & Ba; the optimiser of Sec. 4) of n parameters in place:
+ * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; theta -= lr mhat / (sqrt(vhat) + eps),
+ * with bias correction for 1-based step `t`.  All arrays device float32. */
+int dlx_adam(float *theta, const float *grad, float *m, float *v, size_t n, float lr, float beta1, float beta2,
+             float eps, int t, void *cuda_stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* One fit request: the model shape, host copies of the fixed inputs, a starting
+ * point, the data, and K Adam steps (K = 0: one loss+gradient evaluation). */
+typedef struct {
+    dlx_mft_desc desc;          /* desc.precision selects the form; lambda_m is host */
+    const float *transmission;  /* host [Ni][Ni] */
+    const float *opd_fixed;     /* host [Ni][Ni] or NULL */
+    const float *zern_basis;    /* host [n_zern][Ni][Ni] or NULL iff n_zern == 0 */
+    const float *weights;       /* host [n_lambda] */
+    const float *dither;        /* host [n_exp][2] or NULL */
+    const float *zern_coeff;    /* host [n_zern] start */
+    const float *opd_pix;       /* host [Ni][Ni] start, or NULL (not fitted) */
+    const float *flux;          /* host [n_src] start */
+    const float *pos;           /* host [n_src][2] start */
+    const float *flat;          /* host [Nd][Nd] start */
+    const int32_t *data;        /* host [n_exp][Nd][Nd] */
+    int n_steps;                /* K Adam steps */
+    float lr[5];                /* learning rates: zern, opd_pix, flat, flux, pos (0 freezes a group) */
+} dlx_request;
+
+/* Result of a finished request, copied into caller-owned HOST buffers (any may be NULL). */
+typedef struct {
+    double loss;                /* loss at the final parameters' last evaluation */
+    float *zern_coeff, *opd_pix, *flux, *pos, *flat;          /* final parameters */
+    float *g_zern, *g_opd_pix, *g_flux, *g_pos, *g_flat;      /* gradient of the last evaluation */
+    double queued_s, latency_s; /* submit -> admit, submit -> done */
+    int steps_done;
+} dlx_result;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, rejected;
+    int active, queued;
+    size_t hbm_in_use, hbm_budget;
+    uint64_t evals, graph_launches, grouped_launches;
+} dlx_server_stats;
+
+/* Create a continuous-batching fit server on `device` with its own stream and
+ * scheduler thread.  `hbm_budget` bounds the device memory of admitted
+ * requests (0 = 90% of free memory); `max_slots` bounds concurrent fits. */
+int dlx_server_create(int device, size_t hbm_budget, int max_slots, dlx_server **out);
+int dlx_server_destroy(dlx_server *server);
+
+/* Non-blocking: copies the request's host inputs and queues it.  Returns
+ * NOMEM if the request alone exceeds the budget, INVALID_ARG on a bad shape. */
+int dlx_submit(dlx_server *server, const dlx_request *request, uint64_t *ticket);
+
+/* Wait up to timeout_s (0 = just test) for a ticket.  Returns OK and fills
+ * `out` once, PENDING while running, TIMEOUT if the deadline passed, or the
+ * request's error status (NONFINITE, NOMEM, CUDA...).  A finished ticket is
+ * released after a successful poll. */
+int dlx_poll(dlx_server *server, uint64_t ticket, double timeout_s, dlx_result *out);
+int dlx_server_get_stats(dlx_server *server, dlx_server_stats *out);
+
+/* Host-side fault injection for tests: 1 = fail the next admission with NOMEM,
+ * 2 = poison the next admitted request's first gradient with NaN. */
+int dlx_server_inject_fault(dlx_server *server, int kind);
+
+const char *dlx_last_error(void);
+const char *dlx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DLX_H */

@@ -50,6 +50,7 @@ def lib():
         _lib.orc_loss.restype = C.c_double
         _lib.orc_loss_grad.argtypes = [C.POINTER(_Problem), cp, cp, cp, cp, cp, cp, cp, cp]
         _lib.orc_loss_grad.restype = C.c_long
+        _lib.orc_model_at.argtypes = [C.POINTER(_Problem), C.c_int, cp, cp, cp]
     return _lib
 
 
@@ -170,6 +171,16 @@ def loss_grad(p, data):
                                   _ptr(out["opd_pix"]), _ptr(out["flat"]), _ptr(out["flux"]), _ptr(out["pos"]))
     out["loss"] = float(L[0])
     out["clamped"] = int(clamped)
+    return out
+
+
+def model_at(p, e_idx, p_idx):
+    """Model values at (exposure, flat pixel index) pairs, each by direct sums."""
+    m = _Marshalled(p)
+    e = np.ascontiguousarray(e_idx, dtype=np.int32)
+    q = np.ascontiguousarray(p_idx, dtype=np.int32)
+    out = np.zeros(len(e))
+    lib().orc_model_at(m.ref(), len(e), _ptr(e), _ptr(q), _ptr(out))
     return out
 
 

@@ -441,3 +441,55 @@ long orc_loss_grad(const orc_problem *q, const int *data, double *loss, double *
     free_mats(q, mats);
     return clamped;
 }
+
+/* The model at selected detector pixels only, for sizes where the full image
+ * is out of reach: for exposure e_idx[i] and pixel p_idx[i],
+ * out[i] = FF[p] sum_s F_s sum_l w_l sum_{q in the os x os block of p} |E_{l,s,e}[q]|^2,
+ * with each E[q] a direct sum sum_ny A[ky][ny] sum_nx P[ny][nx] A[kx][nx]. */
+void orc_model_at(const orc_problem *q, int n_pix, const int *e_idx, const int *p_idx, double *out) {
+    int n = q->n_pupil, nd = q->n_det, os = q->oversample, no = nd * os;
+    size_t npx = (size_t)n * n;
+    double dx = q->diameter / n, du = q->pixscale / os, wn = weight_norm(q);
+    double *opd = (double *)malloc(npx * sizeof(double));
+    cplx *P = (cplx *)malloc(npx * sizeof(cplx));
+    cplx *ax = (cplx *)malloc((size_t)n * sizeof(cplx)), *ay = (cplx *)malloc((size_t)n * sizeof(cplx));
+    orc_opd(q, opd);
+    for (int i = 0; i < n_pix; ++i) out[i] = 0;
+    for (int e = 0; e < q->n_exp; ++e)
+        for (int s = 0; s < q->n_src; ++s)
+            for (int l = 0; l < q->n_lambda; ++l) {
+                int any = 0;
+                for (int i = 0; i < n_pix; ++i) any |= (e_idx[i] == e);
+                if (!any) continue;
+                double lam = q->lambdas[l], sc = sqrt(dx * du / lam), w = q->weights[l] / wn;
+                orc_phasor(q, opd, l, s, e, P);
+                for (int i = 0; i < n_pix; ++i) {
+                    if (e_idx[i] != e) continue;
+                    int py = p_idx[i] / nd, px = p_idx[i] % nd;
+                    double acc = 0;
+                    for (int a = 0; a < os; ++a)
+                        for (int b = 0; b < os; ++b) {
+                            int ky = py * os + a, kx = px * os + b;
+                            for (int t = 0; t < n; ++t) {
+                                double phx = -TWO_PI * coord(t, n, dx) * coord(kx, no, du) / lam;
+                                double phy = -TWO_PI * coord(t, n, dx) * coord(ky, no, du) / lam;
+                                ax[t] = sc * (cos(phx) + I * sin(phx));
+                                ay[t] = sc * (cos(phy) + I * sin(phy));
+                            }
+                            cplx E = 0;
+                            for (int ny = 0; ny < n; ++ny) {
+                                cplx row = 0;
+                                for (int nx = 0; nx < n; ++nx) row += P[(size_t)ny * n + nx] * ax[nx];
+                                E += ay[ny] * row;
+                            }
+                            acc += creal(E) * creal(E) + cimag(E) * cimag(E);
+                        }
+                    out[i] += q->flux[s] * w * acc;
+                }
+            }
+    for (int i = 0; i < n_pix; ++i) out[i] *= q->flat[p_idx[i]];
+    free(opd);
+    free(P);
+    free(ax);
+    free(ay);
+}

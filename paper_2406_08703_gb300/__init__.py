@@ -1,0 +1,278 @@
+"""GB300 (sm_103a) differentiable-optics hot path of arXiv:2406.08703.
+
+Thin Python binding of the C ABI in include/dlx.h.  Every step of the path
+(MFT matrices, OPD, phasor, the four MFT contractions, intensity, binning,
+flat field, Poisson NLL, gradient reductions, Adam) runs in the library's
+CUDA kernels; this module only marshals torch tensors (device memory and
+streams) into the ABI structs.  The functions carry the ABI's names.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _native as N
+from ._native import DLX_BF16, DLX_BF16X3, DLX_FP32_SIMT, DLX_TF32X3, PRECISIONS, DlxError  # noqa: F401
+
+PARAM_KEYS = ("transmission", "opd_fixed", "zern_basis", "zern_coeff", "opd_pix", "weights", "flux", "pos", "dither",
+              "flat")
+GRAD_KEYS = ("d_zern", "d_opd_pix", "d_flat", "d_flux", "d_pos")
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def load():
+    """Load (building if needed) the CUDA library; raises if it is unavailable."""
+    return N.load()
+
+
+@dataclasses.dataclass
+class MftDesc:
+    n_pupil: int
+    diameter_m: float
+    n_det: int
+    pixscale_rad: float
+    oversample: int
+    lambdas: Sequence[float]
+    n_src: int
+    n_exp: int = 1
+    n_zern: int = 0
+    precision: int = DLX_BF16X3
+    psf_chunk: int = 0
+    workspace_limit_bytes: int = 0
+
+    def to_c(self):
+        lam = (C.c_double * len(self.lambdas))(*[float(x) for x in self.lambdas])
+        d = N.MftDesc(self.n_pupil, self.diameter_m, self.n_det, self.pixscale_rad, self.oversample,
+                      len(self.lambdas), C.cast(lam, C.POINTER(C.c_double)), self.n_src, self.n_exp, self.n_zern,
+                      int(self.precision), self.psf_chunk, self.workspace_limit_bytes)
+        return d, lam
+
+
+class Plan:
+    """Owns a dlx_plan (MFT matrices + workspaces on one device)."""
+
+    def __init__(self, handle: int, desc: MftDesc, device: int):
+        self.handle = C.c_void_p(handle)
+        self.desc = desc
+        self.device = device
+        self.info = dlx_plan_get_info(self)
+
+    def close(self):
+        if self.handle:
+            N.check(load().dlx_destroy_plan(self.handle), "dlx_destroy_plan")
+            self.handle = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def desc_from_problem(p, precision=DLX_BF16X3, **kw) -> MftDesc:
+    """MftDesc of a workloads.Problem-like object (duck-typed)."""
+    return MftDesc(n_pupil=p.n_pupil, diameter_m=p.diameter, n_det=p.n_det, pixscale_rad=p.pixscale,
+                   oversample=p.oversample, lambdas=list(p.lambdas), n_src=len(p.flux), n_exp=len(p.dither),
+                   n_zern=len(p.coeff), precision=precision, **kw)
+
+
+def params_from_problem(p, device="cuda") -> dict:
+    """float32 device tensors of a workloads.Problem-like object's arrays."""
+    torch = _torch()
+
+    def t(a):
+        return None if a is None else torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device)
+
+    out = {k: t(getattr(p, k)) for k in ("transmission", "opd_fixed", "opd_pix", "weights", "flux", "pos", "dither",
+                                         "flat")}
+    out["zern_basis"] = t(p.basis) if len(p.coeff) else None
+    out["zern_coeff"] = t(p.coeff) if len(p.coeff) else None
+    return out
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check_tensor(name, t, shape, dtype, device):
+    torch = _torch()
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name}: expected a contiguous {dtype} CUDA tensor")
+    if t.device.index != device:
+        raise ValueError(f"{name}: tensor on cuda:{t.device.index}, plan on cuda:{device}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(t.shape)} != {tuple(shape)}")
+
+
+def _param_shapes(plan: Plan):
+    i = plan.info
+    ni, nd = i.n_pupil, i.n_det
+    return dict(transmission=(ni, ni), opd_fixed=(ni, ni), zern_basis=(i.n_zern, ni, ni), zern_coeff=(i.n_zern,),
+                opd_pix=(ni, ni), weights=(i.n_lambda,), flux=(i.n_src,), pos=(i.n_src, 2), dither=(i.n_exp, 2),
+                flat=(nd, nd))
+
+
+def _params_c(plan: Plan, params: dict):
+    torch = _torch()
+    shapes = _param_shapes(plan)
+    for k in PARAM_KEYS:
+        _check_tensor(k, params.get(k), shapes[k], torch.float32, plan.device)
+    return N.Params(*[_ptr(params.get(k)) for k in PARAM_KEYS])
+
+
+def _stream(plan: Plan, stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream(plan.device)
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ------------------------------------------------------------------ ABI-named calls
+
+def dlx_make_mft(desc: MftDesc, device: int = 0) -> Plan:
+    d, keep = desc.to_c()
+    h = C.c_void_p()
+    N.check(load().dlx_make_mft(C.byref(d), device, C.byref(h)), "dlx_make_mft")
+    del keep
+    return Plan(h.value, desc, device)
+
+
+def dlx_destroy_plan(plan: Plan) -> None:
+    plan.close()
+
+
+def dlx_plan_get_info(plan: Plan):
+    info = N.PlanInfo()
+    N.check(load().dlx_plan_get_info(plan.handle, C.byref(info)), "dlx_plan_get_info")
+    return info
+
+
+def dlx_forward(plan: Plan, params: dict, model=None, stream=None):
+    torch = _torch()
+    i = plan.info
+    if model is None:
+        model = torch.empty((i.n_exp, i.n_det, i.n_det), dtype=torch.float32, device=f"cuda:{plan.device}")
+    _check_tensor("model", model, (i.n_exp, i.n_det, i.n_det), torch.float32, plan.device)
+    prm = _params_c(plan, params)
+    N.check(load().dlx_forward(plan.handle, C.byref(prm), _ptr(model), _stream(plan, stream)), "dlx_forward")
+    return model
+
+
+def dlx_psf(plan: Plan, params: dict, out=None, stream=None):
+    torch = _torch()
+    i = plan.info
+    if out is None:
+        out = torch.empty((i.n_exp, i.n_out, i.n_out), dtype=torch.float32, device=f"cuda:{plan.device}")
+    _check_tensor("psf_os", out, (i.n_exp, i.n_out, i.n_out), torch.float32, plan.device)
+    prm = _params_c(plan, params)
+    N.check(load().dlx_psf(plan.handle, C.byref(prm), _ptr(out), _stream(plan, stream)), "dlx_psf")
+    return out
+
+
+def empty_grads(plan: Plan, which=GRAD_KEYS) -> dict:
+    torch = _torch()
+    i = plan.info
+    shapes = dict(d_zern=(i.n_zern,), d_opd_pix=(i.n_pupil, i.n_pupil), d_flat=(i.n_det, i.n_det),
+                  d_flux=(i.n_src,), d_pos=(i.n_src, 2))
+    dev = f"cuda:{plan.device}"
+    return {k: (torch.empty(shapes[k], dtype=torch.float32, device=dev) if k in which else None) for k in GRAD_KEYS}
+
+
+def dlx_loss_grad(plan: Plan, params: dict, data, loss=None, grads: Optional[dict] = None, model=None, stream=None):
+    """Returns (loss[1] float64 tensor, grads dict, model or None); asynchronous on the stream."""
+    torch = _torch()
+    i = plan.info
+    _check_tensor("data", data, (i.n_exp, i.n_det, i.n_det), torch.int32, plan.device)
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float64, device=f"cuda:{plan.device}")
+    _check_tensor("loss", loss, (1,), torch.float64, plan.device)
+    if grads is None:
+        grads = empty_grads(plan)
+    gshapes = dict(d_zern=(i.n_zern,), d_opd_pix=(i.n_pupil, i.n_pupil), d_flat=(i.n_det, i.n_det),
+                   d_flux=(i.n_src,), d_pos=(i.n_src, 2))
+    for k in GRAD_KEYS:
+        _check_tensor(k, grads.get(k), gshapes[k], torch.float32, plan.device)
+    if model is not None:
+        _check_tensor("model", model, (i.n_exp, i.n_det, i.n_det), torch.float32, plan.device)
+    prm = _params_c(plan, params)
+    g = N.Grads(*[_ptr(grads.get(k)) for k in GRAD_KEYS])
+    N.check(load().dlx_loss_grad(plan.handle, C.byref(prm), _ptr(data), _ptr(loss), C.byref(g), _ptr(model),
+                                 _stream(plan, stream)), "dlx_loss_grad")
+    return loss, grads, model
+
+
+def dlx_plan_diagnostics(plan: Plan):
+    c = C.c_int64()
+    e = C.c_int32()
+    N.check(load().dlx_plan_diagnostics(plan.handle, C.byref(c), C.byref(e)), "dlx_plan_diagnostics")
+    return dict(clamped=c.value, device_error=e.value)
+
+
+def dlx_adam(theta, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    torch = _torch()
+    for name, x in (("theta", theta), ("grad", grad), ("m", m), ("v", v)):
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.numel() != theta.numel():
+            raise TypeError(f"{name}: contiguous float32 CUDA tensor of theta's size expected")
+    st = torch.cuda.current_stream(theta.device) if stream is None else stream
+    N.check(load().dlx_adam(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), theta.numel(), lr, beta1, beta2, eps, t,
+                            C.c_void_p(st.cuda_stream)), "dlx_adam")
+
+
+# ------------------------------------------------------------------ autograd
+
+def _autograd_fn():
+    torch = _torch()
+
+    class DlxPSFLoss(torch.autograd.Function):
+        """Poisson NLL of the optical model with the library's hand-written adjoint.
+
+        forward(plan, data, fixed, zern_coeff, opd_pix, flat, flux, pos) -> loss (float64 scalar);
+        `fixed` holds transmission, opd_fixed, zern_basis, weights and dither.  The gradient
+        of every differentiable input is computed in the same dlx_loss_grad call.
+        """
+
+        @staticmethod
+        def forward(ctx, plan, data, fixed, zern_coeff, opd_pix, flat, flux, pos):
+            params = dict(fixed, zern_coeff=zern_coeff, opd_pix=opd_pix, flat=flat, flux=flux, pos=pos)
+            which = ["d_flat", "d_flux", "d_pos"] + (["d_zern"] if zern_coeff is not None else []) + (
+                ["d_opd_pix"] if opd_pix is not None else [])
+            grads = empty_grads(plan, which)
+            loss, grads, _ = dlx_loss_grad(plan, params, data, grads=grads)
+            ctx.save_for_backward(*[grads[k] if grads[k] is not None else torch.empty(0) for k in
+                                    ("d_zern", "d_opd_pix", "d_flat", "d_flux", "d_pos")])
+            ctx.has = (zern_coeff is not None, opd_pix is not None)
+            return loss[0]
+
+        @staticmethod
+        def backward(ctx, gout):
+            dz, dpix, dflat, dflux, dpos = ctx.saved_tensors
+            s = gout.to(torch.float32)
+            return (None, None, None, s * dz if ctx.has[0] else None, s * dpix if ctx.has[1] else None, s * dflat,
+                    s * dflux, s * dpos)
+
+    return DlxPSFLoss
+
+
+_DlxPSFLoss = None
+
+
+def psf_loss(plan: Plan, data, fixed: dict, zern_coeff, opd_pix, flat, flux, pos):
+    """Differentiable loss: torch.autograd.Function over dlx_loss_grad."""
+    global _DlxPSFLoss
+    if _DlxPSFLoss is None:
+        _DlxPSFLoss = _autograd_fn()
+    return _DlxPSFLoss.apply(plan, data, fixed, zern_coeff, opd_pix, flat, flux, pos)
+
+
+from .server import Server, dlx_poll, dlx_server_create, dlx_submit  # noqa: E402,F401

@@ -1,0 +1,384 @@
+// C ABI entry points (include/dlx.h): plan creation, forward, loss + gradient,
+// Adam, diagnostics.  Orchestration only; every step of the path is one of
+// the kernels in k_elem.cu, k_gemm_simt.cu and k_gemm_tc.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dlx_common.cuh"
+
+static thread_local std::string g_last_error;
+
+void dlx_set_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
+
+// Makes the plan's device current for the duration of a call and restores the caller's.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(int code, const std::string &msg) {
+    dlx_set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+    return fail(DLX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define DLX_CU(call, where)                              \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(_e, where); \
+    } while (0)
+
+int round8(int x) { return (x + 7) / 8 * 8; }
+
+template <class T>
+cudaError_t plan_alloc(dlx_plan *p, T **ptr, size_t bytes) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    p->allocs.push_back(q);
+    p->workspace += bytes;
+    *ptr = (T *)q;
+    return cudaSuccess;
+}
+
+void plan_free(dlx_plan *p) {
+    for (void *q : p->allocs) cudaFree(q);
+    p->allocs.clear();
+}
+
+int validate_params(const dlx_plan *p, const dlx_params *prm) {
+    if (!prm) return fail(DLX_ERR_INVALID_ARG, "params is NULL");
+    if (!prm->transmission || !prm->weights || !prm->flux || !prm->pos || !prm->flat)
+        return fail(DLX_ERR_INVALID_ARG, "transmission, weights, flux, pos and flat are required");
+    if (p->nz > 0 && (!prm->zern_basis || !prm->zern_coeff))
+        return fail(DLX_ERR_INVALID_ARG, "n_zern > 0 needs zern_basis and zern_coeff");
+    return DLX_OK;
+}
+
+}  // namespace
+
+namespace dlx {
+
+void free_plan(dlx_plan *p) {
+    if (!p) return;
+    plan_free(p);
+    delete p;
+}
+
+int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
+    if (!d || !out) return fail(DLX_ERR_INVALID_ARG, "desc/out is NULL");
+    *out = nullptr;
+    if (d->n_pupil < 2 || d->n_det < 1 || d->oversample < 1 || d->n_lambda < 1 || d->n_src < 1 || d->n_exp < 1 ||
+        d->n_zern < 0 || R_max < 1)
+        return fail(DLX_ERR_INVALID_ARG, "sizes must be positive (n_pupil >= 2)");
+    if (!(d->diameter_m > 0) || !(d->pixscale_rad > 0)) return fail(DLX_ERR_INVALID_ARG, "diameter and pixscale > 0");
+    if (!d->lambda_m) return fail(DLX_ERR_INVALID_ARG, "lambda_m is NULL");
+    for (int l = 0; l < d->n_lambda; ++l)
+        if (!(d->lambda_m[l] > 0) || !std::isfinite(d->lambda_m[l]))
+            return fail(DLX_ERR_INVALID_ARG, "wavelengths must be finite and > 0");
+    if (d->precision < DLX_FP32_SIMT || d->precision > DLX_BF16) return fail(DLX_ERR_INVALID_ARG, "bad precision");
+    if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 8 sources per plan");
+    const long long no_ll = (long long)d->n_det * d->oversample;
+    if (d->n_pupil > 8192 || no_ll > 16384) return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and n_det*oversample <= 16384");
+
+    DeviceGuard guard(device);
+    cudaDeviceProp prop;
+    DLX_CU(cudaGetDeviceProperties(&prop, device), "cudaGetDeviceProperties");
+
+    dlx_plan *p = new dlx_plan();
+    p->desc = *d;
+    p->lambdas.assign(d->lambda_m, d->lambda_m + d->n_lambda);
+    p->desc.lambda_m = p->lambdas.data();
+    p->device = device;
+    p->R_max = R_max;
+    p->sm_count = prop.multiProcessorCount;
+    p->cc_major = prop.major;
+    p->cc_minor = prop.minor;
+    p->ni = d->n_pupil;
+    p->nd = d->n_det;
+    p->os = d->oversample;
+    p->no = (int)no_ll;
+    p->nl = d->n_lambda;
+    p->ns = d->n_src;
+    p->ne = d->n_exp;
+    p->nz = d->n_zern;
+    p->nse = p->ns * p->ne;
+    p->B = p->nl * p->nse;
+    p->ldi = round8(p->ni);
+    p->ldo = round8(p->no);
+    p->prec = d->precision;
+    p->fmt = fmt_of_prec(p->prec);
+    p->planes = fmt_planes(p->fmt);
+    p->esz = fmt_esize(p->fmt);
+    p->dx = d->diameter_m / p->ni;
+    p->du = d->pixscale_rad / p->os;
+
+    if (p->prec != DLX_FP32_SIMT) {
+        std::string why;
+        if (!(p->cc_major == 10 && p->cc_minor == 3)) {
+            delete p;
+            return fail(DLX_ERR_UNSUPPORTED, "tensor-core forms are built for sm_103a only");
+        }
+        if (!tc_supported(p, &why)) {
+            delete p;
+            return fail(DLX_ERR_UNSUPPORTED, why);
+        }
+    }
+
+    const int Bt = p->B * R_max;
+    // adjoint chunk: the per-wavelength recomputation batch
+    const size_t per_psf = (size_t)p->planes * p->esz * ((size_t)p->no * p->ldo + (size_t)p->ni * p->ldo);
+    int chunk = Bt;
+    if (d->psf_chunk > 0)
+        chunk = std::min(d->psf_chunk, Bt);
+    else if (d->workspace_limit_bytes > 0)
+        chunk = (int)std::max<size_t>(1, std::min<size_t>(Bt, d->workspace_limit_bytes / per_psf));
+    p->chunk = chunk;
+
+    // wavelength groups of the intensity contraction: enough independent output
+    // tiles to cover every SM.
+    {
+        int tile = (p->prec == DLX_FP32_SIMT) ? 64 : 128;
+        long units = (long)((p->no + tile - 1) / tile) * ((p->no + tile - 1) / tile) * p->nse;
+        long want = (p->prec == DLX_FP32_SIMT) ? 2L * p->sm_count : (long)p->sm_count;
+        p->G = (int)std::min<long>(p->nl, std::max<long>(1, (want + units - 1) / units));
+    }
+
+    cudaError_t e = cudaSuccess;
+    auto op_alloc = [&](Operand &o, int batch, int rows, int ld) {
+        o.batch = batch;
+        o.rows = rows;
+        o.ld = ld;
+        o.bytes = (size_t)batch * p->planes * rows * ld * p->esz;
+        if (e == cudaSuccess) e = plan_alloc(p, &o.ptr, o.bytes);
+        if (e == cudaSuccess) e = cudaMemset(o.ptr, 0, o.bytes);
+    };
+    op_alloc(p->amat, p->nl, p->no, p->ldi);
+    op_alloc(p->amatH, p->nl, p->ni, p->ldo);
+    op_alloc(p->P, Bt, p->ni, p->ldi);
+    op_alloc(p->T1t, Bt, p->no, p->ldi);
+    op_alloc(p->GEt, p->chunk, p->no, p->ldo);
+    op_alloc(p->GT1, p->chunk, p->ni, p->ldo);
+    const size_t npx = (size_t)p->ni * p->ni, np = (size_t)p->nd * p->nd, nq = (size_t)p->no * p->no;
+    p->red_blocks = std::max(1, std::min((int)((np + 255) / 256), std::max(1, p->sm_count * 2 / R_max)));
+    if (e == cudaSuccess) e = plan_alloc(p, &p->lam_d, sizeof(double) * p->nl);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->wnorm, sizeof(float) * p->nl * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->pscale, sizeof(double) * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->tilt, sizeof(float2) * Bt * 2 * p->ni);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->opd, sizeof(float) * npx * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->Is, sizeof(float) * (size_t)p->G * p->nse * R_max * nq);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->GI, sizeof(float) * p->ne * np * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->model_tmp, sizeof(float) * p->ne * np * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(double) * npx * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->err, sizeof(int32_t));
+    if (e == cudaSuccess) e = plan_alloc(p, &p->clamped, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemset(p->clamped, 0, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(p->lam_d, p->lambdas.data(), sizeof(double) * p->nl, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_mft_matrices(p, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        int code = (e == cudaErrorMemoryAllocation) ? DLX_ERR_NOMEM : DLX_ERR_CUDA;
+        std::string msg = std::string("plan setup: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        free_plan(p);
+        return fail(code, msg);
+    }
+    if (p->prec != DLX_FP32_SIMT) {
+        std::string why;
+        if (!tc_make_maps(p, &why)) {
+            free_plan(p);
+            return fail(DLX_ERR_CUDA, "tensor maps: " + why);
+        }
+    }
+    *out = p;
+    return DLX_OK;
+}
+
+int eval_forward(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
+    DLX_CU(launch_prologue(p, prm, R, st), "prologue");
+    if (p->prec == DLX_FP32_SIMT) {
+        DLX_CU(simt_forward(p, R, st), "simt forward");
+    } else {
+        DLX_CU(tc_forward(p, R, st), "tensor-core forward");
+    }
+    return DLX_OK;
+}
+
+int eval_loss_grad(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride, double *loss,
+                   const DevGrads *g, float *model, size_t model_stride, cudaStream_t st) {
+    int rc = eval_forward(p, prm, R, st);
+    if (rc) return rc;
+    if (!model) {
+        model = p->model_tmp;
+        model_stride = (size_t)p->ne * p->nd * p->nd;
+    }
+    DLX_CU(launch_bin_nll(p, prm, R, data, data_stride, model, model_stride, g, st), "bin+nll");
+    DLX_CU(launch_finalize_loss(p, R, loss, g, st), "loss");
+    const bool pupil = g && (g->p[GZERN] || g->p[GPIX] || g->p[GPOS]);
+    if (pupil) {
+        const int Bt = R * p->B;
+        for (int b0 = 0; b0 < Bt; b0 += p->chunk) {
+            int nb = std::min(p->chunk, Bt - b0);
+            if (p->prec == DLX_FP32_SIMT) {
+                DLX_CU(simt_adjoint_chunk(p, prm, b0, nb, st), "simt adjoint");
+            } else {
+                DLX_CU(tc_adjoint_chunk(p, prm, b0, nb, st), "tensor-core adjoint");
+            }
+        }
+        DLX_CU(launch_grad_reduce(p, prm, R, g, st), "gradient reductions");
+    }
+    return DLX_OK;
+}
+
+}  // namespace dlx
+
+namespace {
+
+dlx::DevParams dev_params(const dlx_params *q) {
+    dlx::DevParams d{};
+    d.p[dlx::PT] = q->transmission;
+    d.p[dlx::POPDF] = q->opd_fixed;
+    d.p[dlx::PBASIS] = q->zern_basis;
+    d.p[dlx::PCOEFF] = q->zern_coeff;
+    d.p[dlx::POPDPIX] = q->opd_pix;
+    d.p[dlx::PW] = q->weights;
+    d.p[dlx::PFLUX] = q->flux;
+    d.p[dlx::PPOS] = q->pos;
+    d.p[dlx::PDITHER] = q->dither;
+    d.p[dlx::PFLAT] = q->flat;
+    return d;
+}
+
+dlx::DevGrads dev_grads(const dlx_grads *g) {
+    dlx::DevGrads d{};
+    if (!g) return d;
+    d.p[dlx::GZERN] = g->d_zern;
+    d.p[dlx::GPIX] = g->d_opd_pix;
+    d.p[dlx::GFLAT] = g->d_flat;
+    d.p[dlx::GFLUX] = g->d_flux;
+    d.p[dlx::GPOS] = g->d_pos;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dlx_last_error(void) { return g_last_error.c_str(); }
+
+const char *dlx_version(void) { return "dlx 0.1 (sm_103a)"; }
+
+int dlx_make_mft(const dlx_mft_desc *d, int device, dlx_plan **out) { return dlx::make_plan(d, device, 1, out); }
+
+int dlx_destroy_plan(dlx_plan *p) {
+    if (!p) return DLX_OK;
+    DeviceGuard guard(p->device);
+    cudaDeviceSynchronize();
+    dlx::free_plan(p);
+    return DLX_OK;
+}
+
+int dlx_plan_get_info(const dlx_plan *p, dlx_plan_info *o) {
+    if (!p || !o) return fail(DLX_ERR_INVALID_ARG, "NULL argument");
+    memset(o, 0, sizeof(*o));
+    o->n_pupil = p->ni;
+    o->n_det = p->nd;
+    o->oversample = p->os;
+    o->n_out = p->no;
+    o->n_lambda = p->nl;
+    o->n_src = p->ns;
+    o->n_exp = p->ne;
+    o->n_zern = p->nz;
+    o->n_psf = p->B;
+    o->precision = p->prec;
+    o->psf_chunk = p->chunk;
+    o->workspace_bytes = p->workspace;
+    const double ni = p->ni, no = p->no;
+    const double s1 = 8.0 * no * ni * ni, s2 = 8.0 * no * no * ni;
+    o->flop_forward = p->B * (s1 + s2);
+    // forward (s1 + s2) + recomputed field (s2) + adjoint stage 2^T (s2) + adjoint stage 1^T (s1)
+    o->flop_loss_grad = p->B * (2 * s1 + 3 * s2);
+    int t = (p->prec == DLX_FP32_SIMT) ? 64 : 128;
+    o->gemm_tiles_stage2 = ((p->no + t - 1) / t) * ((p->no + t - 1) / t) * p->nse * p->G;
+    return DLX_OK;
+}
+
+int dlx_forward(dlx_plan *p, const dlx_params *prm, float *model, void *stream) {
+    if (!p || !model) return fail(DLX_ERR_INVALID_ARG, "plan/model is NULL");
+    int rc = validate_params(p, prm);
+    if (rc) return rc;
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const dlx::DevParams d = dev_params(prm);
+    if ((rc = dlx::eval_forward(p, d, 1, st))) return rc;
+    DLX_CU(dlx::launch_bin_nll(p, d, 1, nullptr, 0, model, 0, nullptr, st), "bin");
+    return DLX_OK;
+}
+
+int dlx_psf(dlx_plan *p, const dlx_params *prm, float *psf_os, void *stream) {
+    if (!p || !psf_os) return fail(DLX_ERR_INVALID_ARG, "plan/psf is NULL");
+    int rc = validate_params(p, prm);
+    if (rc) return rc;
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const dlx::DevParams d = dev_params(prm);
+    if ((rc = dlx::eval_forward(p, d, 1, st))) return rc;
+    DLX_CU(dlx::launch_psf_out(p, d, psf_os, st), "psf");
+    return DLX_OK;
+}
+
+int dlx_loss_grad(dlx_plan *p, const dlx_params *prm, const int32_t *data, double *loss, const dlx_grads *g,
+                  float *model_opt, void *stream) {
+    if (!p || !data || !loss) return fail(DLX_ERR_INVALID_ARG, "plan/data/loss is NULL");
+    int rc = validate_params(p, prm);
+    if (rc) return rc;
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    DLX_CU(cudaMemsetAsync(p->clamped, 0, sizeof(unsigned long long), st), "memset");
+    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevGrads dg = dev_grads(g);
+    return dlx::eval_loss_grad(p, d, 1, data, 0, loss, g ? &dg : nullptr, model_opt, 0, st);
+}
+
+int dlx_plan_diagnostics(dlx_plan *p, int64_t *clamped, int32_t *device_error) {
+    if (!p) return fail(DLX_ERR_INVALID_ARG, "plan is NULL");
+    DeviceGuard guard(p->device);
+    DLX_CU(cudaDeviceSynchronize(), "synchronize");
+    unsigned long long c = 0;
+    int32_t err = 0;
+    DLX_CU(cudaMemcpy(&c, p->clamped, sizeof(c), cudaMemcpyDeviceToHost), "copy");
+    DLX_CU(cudaMemcpy(&err, p->err, sizeof(err), cudaMemcpyDeviceToHost), "copy");
+    DLX_CU(cudaMemset(p->err, 0, sizeof(int32_t)), "memset");
+    if (clamped) *clamped = (int64_t)c;
+    if (device_error) *device_error = err;
+    return DLX_OK;
+}
+
+int dlx_adam(float *theta, const float *grad, float *m, float *v, size_t n, float lr, float beta1, float beta2,
+             float eps, int t, void *stream) {
+    if (n && (!theta || !grad || !m || !v)) return fail(DLX_ERR_INVALID_ARG, "NULL array");
+    if (t < 1) return fail(DLX_ERR_INVALID_ARG, "Adam step t is 1-based");
+    DLX_CU(dlx::launch_adam(theta, grad, m, v, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream), "adam");
+    return DLX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal declarations of the dlx CUDA library (sm_103a).
+//
+// Operand layout.  Every complex matrix that feeds a contraction is stored as
+// P planes of a row-major [rows][ld] array, plane-major, where ld is the
+// contraction length rounded up to a multiple of 8 (16-byte rows for the
+// tensor-memory-access engine; padding columns stay zero).  The planes depend
+// on the arithmetic form:
+//   F32    : re, im                   (float)           -- CUDA-core FP32 form
+//   BF16X3 : re_hi, re_lo, im_hi, im_lo (bf16)           -- split, 3 products
+//   BF16   : re, im                   (bf16)            -- hi only
+//   TF32X3 : re_hi, re_lo, im_hi, im_lo (tf32 in fp32)   -- split, 3 products
+// hi = round(x), lo = round(x - hi); the lo*lo product is dropped.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/dlx.h"
+
+namespace dlx {
+
+enum Fmt { FMT_F32 = 0, FMT_BF16X4 = 1, FMT_BF16X2 = 2, FMT_TF32X4 = 3 };
+
+__host__ __device__ constexpr int fmt_planes(int f) { return (f == FMT_BF16X4 || f == FMT_TF32X4) ? 4 : 2; }
+__host__ __device__ constexpr int fmt_esize(int f) { return (f == FMT_BF16X4 || f == FMT_BF16X2) ? 2 : 4; }
+
+inline int fmt_of_prec(int prec) {
+    switch (prec) {
+        case DLX_FP32_SIMT: return FMT_F32;
+        case DLX_TF32X3: return FMT_TF32X4;
+        case DLX_BF16X3: return FMT_BF16X4;
+        default: return FMT_BF16X2;
+    }
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// Store one complex value at element `idx` of a plane-major operand whose
+// planes are `pstride` elements apart.
+template <int F>
+__device__ __forceinline__ void store_cplx(void *base, size_t pstride, size_t idx, float re, float im) {
+    if constexpr (F == FMT_F32) {
+        float *p = (float *)base;
+        p[idx] = re;
+        p[pstride + idx] = im;
+    } else if constexpr (F == FMT_BF16X4) {
+        __nv_bfloat16 *p = (__nv_bfloat16 *)base;
+        __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+        p[idx] = rh;
+        p[pstride + idx] = __float2bfloat16_rn(re - __bfloat162float(rh));
+        p[2 * pstride + idx] = ih;
+        p[3 * pstride + idx] = __float2bfloat16_rn(im - __bfloat162float(ih));
+    } else if constexpr (F == FMT_BF16X2) {
+        __nv_bfloat16 *p = (__nv_bfloat16 *)base;
+        p[idx] = __float2bfloat16_rn(re);
+        p[pstride + idx] = __float2bfloat16_rn(im);
+    } else {
+        float *p = (float *)base;
+        float rh = tf32_round(re), ih = tf32_round(im);
+        p[idx] = rh;
+        p[pstride + idx] = tf32_round(re - rh);
+        p[2 * pstride + idx] = ih;
+        p[3 * pstride + idx] = tf32_round(im - ih);
+    }
+}
+
+// Read back the value an operand represents (hi + lo).
+template <int F>
+__device__ __forceinline__ float2 load_cplx(const void *base, size_t pstride, size_t idx) {
+    if constexpr (F == FMT_F32) {
+        const float *p = (const float *)base;
+        return make_float2(p[idx], p[pstride + idx]);
+    } else if constexpr (F == FMT_BF16X4) {
+        const __nv_bfloat16 *p = (const __nv_bfloat16 *)base;
+        return make_float2(__bfloat162float(p[idx]) + __bfloat162float(p[pstride + idx]),
+                           __bfloat162float(p[2 * pstride + idx]) + __bfloat162float(p[3 * pstride + idx]));
+    } else if constexpr (F == FMT_BF16X2) {
+        const __nv_bfloat16 *p = (const __nv_bfloat16 *)base;
+        return make_float2(__bfloat162float(p[idx]), __bfloat162float(p[pstride + idx]));
+    } else {
+        const float *p = (const float *)base;
+        return make_float2(p[idx] + p[pstride + idx], p[2 * pstride + idx] + p[3 * pstride + idx]);
+    }
+}
+
+#define DLX_FMT_DISPATCH(fmt, F, ...)                                   \
+    switch (fmt) {                                                      \
+        case FMT_F32: { constexpr int F = FMT_F32; __VA_ARGS__; } break;     \
+        case FMT_BF16X4: { constexpr int F = FMT_BF16X4; __VA_ARGS__; } break; \
+        case FMT_BF16X2: { constexpr int F = FMT_BF16X2; __VA_ARGS__; } break; \
+        default: { constexpr int F = FMT_TF32X4; __VA_ARGS__; } break;         \
+    }
+
+// One operand tensor (plane-major [batch][planes][rows][ld]) and its TMA map.
+struct Operand {
+    void *ptr = nullptr;
+    int batch = 0, rows = 0, ld = 0;  // ld = padded contraction length
+    size_t bytes = 0;
+    CUtensorMap tmap;                 // valid when the plan uses a tensor-core form
+};
+
+// Parameters of R independent same-shape models ("slots"): array k of slot r
+// starts at p[k] + r * s[k] (s[k] = 0 shares one array between slots).
+enum { PT = 0, POPDF, PBASIS, PCOEFF, POPDPIX, PW, PFLUX, PPOS, PDITHER, PFLAT, NPARAM };
+struct DevParams {
+    const float *p[NPARAM];
+    size_t s[NPARAM];
+};
+enum { GZERN = 0, GPIX, GFLAT, GFLUX, GPOS, NGRAD };
+struct DevGrads {
+    float *p[NGRAD];
+    size_t s[NGRAD];
+};
+
+__device__ __forceinline__ const float *slot_ptr(const DevParams &P, int k, int r) {
+    return P.p[k] ? P.p[k] + (size_t)r * P.s[k] : nullptr;
+}
+
+}  // namespace dlx
+
+// A plan holds the MFT matrices of one shape and wavelength set and the
+// workspaces for up to R_max slots.  PSF index: bg = r * B + l * nse + s * ne + e.
+struct dlx_plan {
+    dlx_mft_desc desc;
+    std::vector<double> lambdas;
+    int device = 0, sm_count = 0, cc_major = 0, cc_minor = 0;
+    int R_max = 1;
+    int ni, nd, os, no, nl, ns, ne, nz, B, nse, ldi, ldo;
+    int prec, fmt, planes, esz;
+    double dx, du;
+    int G = 1;       // wavelength groups of the intensity contraction (partial planes)
+    int chunk = 1;   // PSFs per adjoint pass
+    dlx::Operand amat, amatH, P, T1t, GEt, GT1;
+    double *lam_d = nullptr;   // [nl]
+    float *wnorm = nullptr;    // [R][nl] weights / sum(weights)
+    double *pscale = nullptr;  // [R] 1/sqrt(sum T^2)
+    float2 *tilt = nullptr;    // [R*B][2][ni]
+    float *opd = nullptr;      // [R][ni*ni]
+    float *Is = nullptr;       // [G][R*nse][no][no] per-source intensity partials
+    float *GI = nullptr;       // [R][ne][nd*nd] FF * dL/dm
+    float *model_tmp = nullptr;// [R][ne][nd*nd]
+    float *gphi = nullptr;     // [R*B][ni*ni] (2 pi / lambda) dL/dphase
+    double *gopd = nullptr;    // [R][ni*ni]
+    double *red = nullptr;     // [R][red_blocks][1 + 8] reduction partials
+    int red_blocks = 0;
+    double *pos_part = nullptr;// [R*B][2]
+    int32_t *err = nullptr;    // device error flag
+    unsigned long long *clamped = nullptr;
+    size_t workspace = 0;
+    std::vector<void *> allocs;
+};
+
+namespace dlx {
+
+constexpr int kMaxSrc = 8;
+
+// ---- plan construction (dlx_api.cu)
+int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out);
+void free_plan(dlx_plan *p);
+
+// ---- launchers (k_elem.cu); R = number of active slots (<= R_max)
+cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st);
+cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st);  // norms, OPD, tilt, phasor
+// binning + flat field (+ Poisson NLL and its partials when data != NULL)
+cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride,
+                           float *model, size_t model_stride, const DevGrads *g, cudaStream_t st);
+cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaStream_t st);
+cudaError_t launch_finalize_loss(dlx_plan *p, int R, double *loss, const DevGrads *g, cudaStream_t st);
+cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st);
+cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, size_t n, float lr, float b1, float b2,
+                        float eps, int t, cudaStream_t st);
+// Adam over R packed slots of n parameters each; group k of a slot is
+// [off[k], off[k+1]) with learning rate lr[r][k]; step[r] is 1-based.
+cudaError_t launch_adam_slots(float *theta, const float *grad, float *m, float *v, size_t n, int R, const int *off,
+                              const float *lr, const int *step, float b1, float b2, float eps, cudaStream_t st);
+
+// ---- contractions (k_gemm_simt.cu / k_gemm_tc.cu) over global PSF indices
+// stage 1:  T1t[bg] = A(l) . P[bg]^T                   (rows kx, cols ny)
+// stage 2:  Is[g][r nse + se] = sum_{l in g} w_l |A(l) . T1t[bg]^T|^2
+// adjoint:  GEt[z] = 2 w_l F_s GI o (T1t[bg] . A(l)^T),  GT1[z] = AH(l) . GEt[z]^T,
+//           gphi[bg] = (2 pi/lambda) Im((GT1[z] . AH(l)^T) conj P[bg]),   z = bg - b0
+cudaError_t simt_forward(dlx_plan *p, int R, cudaStream_t st);
+cudaError_t simt_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st);
+cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st);
+cudaError_t tc_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st);
+int tc_supported(const dlx_plan *p, std::string *why);
+int tc_make_maps(dlx_plan *p, std::string *why);
+
+// ---- whole evaluations (dlx_api.cu), asynchronous on st
+int eval_forward(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st);
+int eval_loss_grad(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride, double *loss,
+                   const DevGrads *g, float *model, size_t model_stride, cudaStream_t st);
+
+}  // namespace dlx
+
+// error reporting (dlx_api.cu)
+void dlx_set_error(const std::string &msg);

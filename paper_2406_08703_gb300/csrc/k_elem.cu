@@ -1,0 +1,427 @@
+// Memory-bound stages of the path: MFT matrix generation, OPD, tilt tables,
+// phasor build, binning + flat field + Poisson NLL, the FP64 gradient
+// reductions and Adam.  Each is a coalesced grid-stride kernel over all
+// active slots; every reduction is a fixed-order block tree in FP64 (no
+// floating-point atomics), so results do not depend on scheduling or on
+// which other slots share the launch.
+#include <algorithm>
+
+#include "dlx_common.cuh"
+
+namespace dlx {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sums of NV doubles per thread in a fixed order; valid in warp 0.
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double *sh /* [32][NV] */) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sh[wid * NV + i] = v[i];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = warp_sum(lane < nw ? sh[lane * NV + i] : 0.0);
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// MFT matrices (Sec. 3, two-sided MFT): A[l][k][n] = sqrt(c) exp(-2 pi i t),
+// t = (n - (Ni-1)/2)(k - (No-1)/2) c, c = dx du / lambda_l.  The argument is
+// formed and reduced to r = t - rint(t) in FP64 before sin/cos, so the phase
+// error does not grow with |t|.  AH[l][n][k] = conj(A[l][k][n]).
+template <int F>
+__global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, int nl, int ni, int no, int ldi, int ldo,
+                               double dx, double du) {
+    const int P = fmt_planes(F), es = fmt_esize(F);
+    const size_t per = (size_t)no * ni, total = per * nl;
+    const double cN = 0.5 * (ni - 1), cO = 0.5 * (no - 1);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int l = (int)(i / per);
+        int k = (int)((i % per) / ni), n = (int)(i % ni);
+        double c = dx * du / lam[l];
+        double t = ((double)n - cN) * ((double)k - cO) * c;
+        double r = t - rint(t);
+        double s, co;
+        sincospi(2.0 * r, &s, &co);
+        double sc = sqrt(c);
+        float re = (float)(sc * co), im = (float)(-sc * s);
+        char *a = (char *)amat + (size_t)l * P * no * ldi * es;
+        store_cplx<F>(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im);
+        char *ah = (char *)amatH + (size_t)l * P * ni * ldo * es;
+        store_cplx<F>(ah, (size_t)ni * ldo, (size_t)n * ldo + k, re, -im);
+    }
+}
+
+cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
+    size_t total = (size_t)p->nl * p->no * p->ni;
+    int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
+    DLX_FMT_DISPATCH(p->fmt, F,
+                     k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->nl, p->ni,
+                                                               p->no, p->ldi, p->ldo, p->dx, p->du));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per slot: pupil normalisation of BasisOptic(normalise=True), 1/sqrt(sum T^2),
+// and the normalised spectral weights w_l / sum w.  One block per slot.
+__global__ void k_norms(DevParams prm, int npx, int nl, double *pscale, float *wnorm) {
+    __shared__ double sh[32];
+    const int r = blockIdx.x;
+    const float *T = slot_ptr(prm, PT, r), *w = slot_ptr(prm, PW, r);
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < npx; i += blockDim.x) v[0] += (double)T[i] * (double)T[i];
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) pscale[r] = 1.0 / sqrt(v[0]);
+    double ws = 0;
+    for (int l = 0; l < nl; ++l) ws += (double)w[l];
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) wnorm[(size_t)r * nl + l] = (float)((double)w[l] / ws);
+}
+
+// OPD = OPD_fixed + sum_j c_j Z_j + OPD_pix (Sec. 3: BasisOptic coefficients on a
+// Zernike basis, the fixed mask, and the free per-pixel map).  grid.y = slot.
+__global__ void k_opd(DevParams prm, int nz, int npx, float *__restrict__ opd) {
+    extern __shared__ float c_sh[];
+    const int r = blockIdx.y;
+    const float *fixed = slot_ptr(prm, POPDF, r), *basis = slot_ptr(prm, PBASIS, r);
+    const float *coeff = slot_ptr(prm, PCOEFF, r), *pix = slot_ptr(prm, POPDPIX, r);
+    for (int j = threadIdx.x; j < nz; j += blockDim.x) c_sh[j] = coeff[j];
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npx; i += gridDim.x * blockDim.x) {
+        float v = fixed ? fixed[i] : 0.f;
+        for (int j = 0; j < nz; ++j) v = fmaf(c_sh[j], __ldg(basis + (size_t)j * npx + i), v);
+        if (pix) v += pix[i];
+        opd[(size_t)r * npx + i] = v;
+    }
+}
+
+// Separable tilt factors exp(i 2 pi x_n theta / lambda) per PSF and axis, with
+// the argument reduced in FP64.  theta = pos[s] + dither[e].
+__global__ void k_tilt(DevParams prm, const double *lam, int nbt, int B, int nse, int ne, int ni, double dx,
+                       float2 *tilt) {
+    const double cN = 0.5 * (ni - 1);
+    const size_t total = (size_t)nbt * 2 * ni;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int bg = (int)(i / (2 * ni)), ax = (int)((i / ni) % 2), n = (int)(i % ni);
+        int r = bg / B, bl = bg % B, l = bl / nse, se = bl % nse, s = se / ne, e = se % ne;
+        const float *pos = slot_ptr(prm, PPOS, r), *dith = slot_ptr(prm, PDITHER, r);
+        double th = (double)pos[2 * s + ax] + (dith ? (double)dith[2 * e + ax] : 0.0);
+        double t = ((double)n - cN) * dx * th / lam[l];
+        double rr = t - rint(t);
+        float sn, cs;
+        sincospif((float)(2.0 * rr), &sn, &cs);
+        tilt[i] = make_float2(cs, sn);
+    }
+}
+
+// Pupil phasor P = T_hat exp(i 2 pi OPD / lambda) ex[nx] ey[ny] (Sec. 3), written
+// in the operand form of the contractions.
+template <int F>
+__global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
+                         const double *__restrict__ lam, const double *__restrict__ pscale, int nbt, int B, int nse,
+                         int ni, int ldi, void *P) {
+    const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F);
+    const size_t total = (size_t)nbt * npx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int bg = (int)(i / npx), n = (int)(i % npx);
+        int r = bg / B, l = (bg % B) / nse, ny = n / ni, nx = n % ni;
+        float t = slot_ptr(prm, PT, r)[n] * (float)pscale[r];
+        float re = 0.f, im = 0.f;
+        if (t != 0.f) {
+            float ph = opd[(size_t)r * npx + n] * (float)(1.0 / lam[l]);
+            ph -= rintf(ph);
+            float sn, cs;
+            sincospif(2.f * ph, &sn, &cs);
+            float2 ex = tilt[(size_t)bg * 2 * ni + nx], ey = tilt[(size_t)bg * 2 * ni + ni + ny];
+            float xr = ex.x * ey.x - ex.y * ey.y, xi = ex.x * ey.y + ex.y * ey.x;
+            re = t * (cs * xr - sn * xi);
+            im = t * (cs * xi + sn * xr);
+        }
+        char *base = (char *)P + (size_t)bg * Pl * ni * ldi * es;
+        store_cplx<F>(base, (size_t)ni * ldi, (size_t)ny * ldi + nx, re, im);
+    }
+}
+
+cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
+    const int npx = p->ni * p->ni, nbt = R * p->B;
+    k_norms<<<R, 1024, 0, st>>>(prm, npx, p->nl, p->pscale, p->wnorm);
+    int blocks = std::max(1, std::min((npx + 255) / 256, p->sm_count * 8 / R));
+    k_opd<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(prm, p->nz, npx, p->opd);
+    size_t tt = (size_t)nbt * 2 * p->ni;
+    int tb = (int)std::min<size_t>((tt + 255) / 256, (size_t)p->sm_count * 8);
+    k_tilt<<<tb, 256, 0, st>>>(prm, p->lam_d, nbt, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt);
+    size_t total = (size_t)nbt * npx;
+    int pb = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
+    DLX_FMT_DISPATCH(p->fmt, F,
+                     k_phasor<F><<<pb, 256, 0, st>>>(prm, p->opd, p->tilt, p->lam_d, p->pscale, nbt, p->B, p->nse,
+                                                     p->ni, p->ldi, p->P.ptr));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Binning, flat field and Poisson NLL (Sec. 3 pixel response, Sec. 4 likelihood).
+// One thread per detector pixel p of slot r = blockIdx.y:
+//   B_{e,s}[p] = sum over the os x os block and the wavelength-group planes,
+//   m = FF sum_s F_s B_{e,s};  L += m - d ln max(m, 1e-30);
+//   g_m = 1 - d / max(m, 1e-30);  GI = FF g_m;  dL/dFF[p] = sum_e g_m B_e;
+//   flux partials sum_p FF g_m B_{e,s}.
+// Per-block FP64 partials go to red[r][blk][1 + kMaxSrc].
+__global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os,
+                          int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
+                          float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
+                          unsigned long long *clamped) {
+    __shared__ double sh[32 * (1 + kMaxSrc)];
+    const int np = nd * nd, r = blockIdx.y;
+    const float *flux = slot_ptr(prm, PFLUX, r), *flat = slot_ptr(prm, PFLAT, r);
+    const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
+    float *mod = model + (size_t)r * mstride;
+    float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
+    double acc[1 + kMaxSrc];
+#pragma unroll
+    for (int i = 0; i < 1 + kMaxSrc; ++i) acc[i] = 0.0;
+    unsigned long long nclamp = 0;
+    const size_t plane = (size_t)no * no;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        const int py = p / nd, px = p % nd;
+        const float ff = flat[p];
+        float dff = 0.f;
+        for (int e = 0; e < ne; ++e) {
+            float bs[kMaxSrc];
+            float btot = 0.f;
+#pragma unroll
+            for (int s = 0; s < kMaxSrc; ++s) {
+                bs[s] = 0.f;
+                if (s < ns) {
+                    const int rse = r * nse + s * ne + e;
+                    float v = 0.f;
+                    for (int gg = 0; gg < G; ++gg) {
+                        const float *src = Is + ((size_t)gg * Rnse + rse) * plane;
+                        for (int a = 0; a < os; ++a) {
+                            const float *row = src + (size_t)(py * os + a) * no + (size_t)px * os;
+                            for (int c = 0; c < os; ++c) v += row[c];
+                        }
+                    }
+                    bs[s] = v;
+                    btot = fmaf(flux[s], v, btot);
+                }
+            }
+            const float m = ff * btot;
+            mod[(size_t)e * np + p] = m;
+            if (dat) {
+                const float d = (float)dat[(size_t)e * np + p];
+                float mc = m;
+                if (!(mc >= 1e-30f)) {
+                    mc = 1e-30f;
+                    ++nclamp;
+                }
+                acc[0] += (double)m - (double)d * (double)logf(mc);
+                const float gm = 1.f - d / mc;
+                GI[((size_t)r * ne + e) * np + p] = ff * gm;
+                dff = fmaf(gm, btot, dff);
+#pragma unroll
+                for (int s = 0; s < kMaxSrc; ++s)
+                    if (s < ns) acc[1 + s] += (double)(ff * gm) * (double)bs[s];
+            }
+        }
+        if (dat && dflat) dflat[p] = dff;
+    }
+    block_sum<1 + kMaxSrc>(acc, sh);
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 1 + kMaxSrc; ++i) red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = acc[i];
+    if (dat && nclamp) atomicAdd(clamped, nclamp);  // integer count: order-independent
+}
+
+cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride,
+                           float *model, size_t model_stride, const DevGrads *g, cudaStream_t st) {
+    DevGrads gg{};
+    if (g) gg = *g;
+    k_bin_nll<<<dim3(p->red_blocks, R), 256, 0, st>>>(p->Is, p->G, R * p->nse, p->nse, p->ns, p->ne, p->nd, p->os,
+                                                        p->no, prm, data, data_stride, model, model_stride, p->GI, gg,
+                                                        p->red, p->clamped);
+    return cudaGetLastError();
+}
+
+__global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, int ne, size_t plane,
+                          const float *__restrict__ flux, float *__restrict__ psf) {
+    size_t total = (size_t)ne * plane;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        int e = (int)(i / plane);
+        size_t q = i % plane;
+        float v = 0.f;
+        for (int s = 0; s < ns; ++s) {
+            float vs = 0.f;
+            for (int gg = 0; gg < G; ++gg) vs += Is[((size_t)gg * nse + s * ne + e) * plane + q];
+            v = fmaf(flux[s], vs, v);
+        }
+        psf[i] = v;
+    }
+}
+
+cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaStream_t st) {
+    size_t plane = (size_t)p->no * p->no, total = plane * p->ne;
+    int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
+    k_psf_out<<<blocks, 256, 0, st>>>(p->Is, p->G, p->nse, p->ns, p->ne, plane, prm.p[PFLUX], psf);
+    return cudaGetLastError();
+}
+
+// Fixed-order sum of the per-block partials of slot r = blockIdx.x: loss[r] and dL/dF_s.
+__global__ void k_finalize_loss(const double *red, int nblk, int ns, double *loss, DevGrads g) {
+    __shared__ double sh[32 * (1 + kMaxSrc)];
+    const int r = blockIdx.x;
+    double v[1 + kMaxSrc];
+    for (int i = 0; i < 1 + kMaxSrc; ++i) v[i] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+        for (int i = 0; i < 1 + ns; ++i) v[i] += red[((size_t)r * nblk + b) * (1 + kMaxSrc) + i];
+    block_sum<1 + kMaxSrc>(v, sh);
+    if (threadIdx.x == 0) {
+        if (loss) loss[r] = v[0];
+        if (g.p[GFLUX])
+            for (int s = 0; s < ns; ++s) g.p[GFLUX][(size_t)r * g.s[GFLUX] + s] = (float)v[1 + s];
+    }
+}
+
+cudaError_t launch_finalize_loss(dlx_plan *p, int R, double *loss, const DevGrads *g, cudaStream_t st) {
+    DevGrads gg{};
+    if (g) gg = *g;
+    k_finalize_loss<<<R, 256, 0, st>>>(p->red, p->red_blocks, p->ns, loss, gg);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Gradient reductions (FP64).  gphi[bg][n] already carries 2 pi / lambda_l.
+// g_OPD[r][n] = sum_{b in slot r} gphi[b][n];  dL/dOPD_pix = g_OPD.
+__global__ void k_gopd(const float *__restrict__ gphi, int R, int B, int npx, double *__restrict__ gopd, DevGrads g) {
+    const size_t total = (size_t)R * npx;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / npx), n = (int)(i % npx);
+        double acc = 0.0;
+        for (int b = 0; b < B; ++b) acc += (double)gphi[((size_t)r * B + b) * npx + n];
+        gopd[i] = acc;
+        if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = (float)acc;
+    }
+}
+
+// Per-PSF position moments: sum_n gphi[bg][n] x_n and y_n.  One block per PSF.
+__global__ void k_pos_moments(const float *__restrict__ gphi, int ni, double dx, double *part) {
+    __shared__ double sh[64];
+    const int b = blockIdx.x, npx = ni * ni;
+    const double cN = 0.5 * (ni - 1);
+    double v[2] = {0.0, 0.0};
+    for (int n = threadIdx.x; n < npx; n += blockDim.x) {
+        double gv = (double)gphi[(size_t)b * npx + n];
+        v[0] += gv * (((double)(n % ni) - cN) * dx);
+        v[1] += gv * (((double)(n / ni) - cN) * dx);
+    }
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        part[2 * (size_t)b] = v[0];
+        part[2 * (size_t)b + 1] = v[1];
+    }
+}
+
+// dL/dtheta_s = sum over wavelengths and exposures of the moments of source s (slot r = blockIdx.x).
+__global__ void k_pos_final(const double *part, int B, int nl, int ns, int ne, DevGrads g) {
+    const int s = threadIdx.x, r = blockIdx.x;
+    if (s >= ns) return;
+    double ax = 0, ay = 0;
+    for (int l = 0; l < nl; ++l)
+        for (int e = 0; e < ne; ++e) {
+            size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
+            ax += part[2 * b];
+            ay += part[2 * b + 1];
+        }
+    float *d = g.p[GPOS] + (size_t)r * g.s[GPOS];
+    d[2 * s] = (float)ax;
+    d[2 * s + 1] = (float)ay;
+}
+
+// dL/dc_j = <Z_j, g_OPD>.  grid (n_zern, R).
+__global__ void k_zern_grad(DevParams prm, const double *__restrict__ gopd, int npx, DevGrads g) {
+    __shared__ double sh[32];
+    const int j = blockIdx.x, r = blockIdx.y;
+    const float *basis = slot_ptr(prm, PBASIS, r) + (size_t)j * npx;
+    const double *go = gopd + (size_t)r * npx;
+    double v[1] = {0.0};
+    for (int n = threadIdx.x; n < npx; n += blockDim.x) v[0] += (double)basis[n] * go[n];
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) g.p[GZERN][(size_t)r * g.s[GZERN] + j] = (float)v[0];
+}
+
+cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st) {
+    const int npx = p->ni * p->ni;
+    DevGrads gg{};
+    if (g) gg = *g;
+    int blocks = (int)std::min<size_t>(((size_t)R * npx + 255) / 256, (size_t)p->sm_count * 8);
+    k_gopd<<<blocks, 256, 0, st>>>(p->gphi, R, p->B, npx, p->gopd, gg);
+    if (gg.p[GPOS]) {
+        k_pos_moments<<<R * p->B, 256, 0, st>>>(p->gphi, p->ni, p->dx, p->pos_part);
+        k_pos_final<<<R, 32 * ((p->ns + 31) / 32), 0, st>>>(p->pos_part, p->B, p->nl, p->ns, p->ne, gg);
+    }
+    if (gg.p[GZERN] && p->nz > 0) k_zern_grad<<<dim3(p->nz, R), 256, 0, st>>>(prm, p->gopd, npx, gg);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Adam (Kingma & Ba 2014), the optimiser of Sec. 4.
+__global__ void k_adam(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                       size_t n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        float gi = g[i];
+        float mi = b1 * m[i] + (1.f - b1) * gi;
+        float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, size_t n, float lr, float b1, float b2,
+                        float eps, int t, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_adam<<<blocks, 256, 0, st>>>(theta, grad, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+// Adam over packed slots: element i of slot r belongs to group k with
+// off[k] <= i < off[k+1]; a zero learning rate freezes the group.
+__global__ void k_adam_slots(float *__restrict__ th, const float *__restrict__ g, float *__restrict__ m,
+                             float *__restrict__ v, size_t n, int R, const int *__restrict__ off,
+                             const float *__restrict__ lr, const int *__restrict__ step, float b1, float b2,
+                             float eps) {
+    const size_t total = (size_t)R * n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(i / n);
+        const int j = (int)(i % n);
+        int k = 0;
+        while (k < 4 && j >= off[k + 1]) ++k;
+        const float a = lr[r * 5 + k];
+        if (a == 0.f) continue;
+        const int t = step[r];
+        const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        th[i] -= a * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+cudaError_t launch_adam_slots(float *theta, const float *grad, float *m, float *v, size_t n, int R, const int *off,
+                              const float *lr, const int *step, float b1, float b2, float eps, cudaStream_t st) {
+    if (n == 0 || R == 0) return cudaSuccess;
+    int blocks = (int)std::min<size_t>(((size_t)R * n + 255) / 256, 8192);
+    k_adam_slots<<<blocks, 256, 0, st>>>(theta, grad, m, v, n, R, off, lr, step, b1, b2, eps);
+    return cudaGetLastError();
+}
+
+}  // namespace dlx

@@ -1,0 +1,258 @@
+// FP32 CUDA-core form of the four MFT contractions (Sec. 3, two-sided MFT).
+//
+// Every contraction is C[m][n] = sum_k A[m][k] B[n][k] over complex operands
+// stored as re/im FP32 planes with both operands contiguous in k.  A 256-thread
+// block owns a 64 x 64 output tile; each thread holds a 4 x 4 complex
+// register tile (rows ty + 16 i, columns tx + 16 j) so that stores of
+// neighbouring threads are contiguous.  Operand tiles of 16 k are staged in
+// shared memory transposed to [k][row] (padded by one word against bank
+// conflicts).  The epilogues are the same as in the tensor-core form.
+#include "dlx_common.cuh"
+
+namespace dlx {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+struct SimtSmem {
+    float ar[BK][BM + 1], ai[BK][BM + 1], br[BK][BN + 1], bi[BK][BN + 1];
+};
+
+// Accumulates the tile (m0, n0) of A . B^T into (cr, ci).
+__device__ __forceinline__ void simt_tile(const float *__restrict__ A, size_t a_ps, int lda, int M,
+                                          const float *__restrict__ Bm, size_t b_ps, int ldb, int N, int K, int m0,
+                                          int n0, float (&cr)[4][4], float (&ci)[4][4], SimtSmem &sm) {
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+        for (int r = 0; r < (BM * BK) / NT; ++r) {
+            int idx = tid + r * NT, row = idx / BK, kk = idx % BK, gk = k0 + kk;
+            float vr = 0.f, vi = 0.f, wr = 0.f, wi = 0.f;
+            int gm = m0 + row, gn = n0 + row;
+            if (gm < M && gk < K) {
+                size_t o = (size_t)gm * lda + gk;
+                vr = A[o];
+                vi = A[a_ps + o];
+            }
+            if (gn < N && gk < K) {
+                size_t o = (size_t)gn * ldb + gk;
+                wr = Bm[o];
+                wi = Bm[b_ps + o];
+            }
+            sm.ar[kk][row] = vr;
+            sm.ai[kk][row] = vi;
+            sm.br[kk][row] = wr;
+            sm.bi[kk][row] = wi;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float a_r[4], a_i[4], b_r[4], b_i[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                a_r[i] = sm.ar[kk][ty + 16 * i];
+                a_i[i] = sm.ai[kk][ty + 16 * i];
+                b_r[i] = sm.br[kk][tx + 16 * i];
+                b_i[i] = sm.bi[kk][tx + 16 * i];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cr[i][j] = fmaf(a_r[i], b_r[j], cr[i][j]);
+                    cr[i][j] = fmaf(-a_i[i], b_i[j], cr[i][j]);
+                    ci[i][j] = fmaf(a_r[i], b_i[j], ci[i][j]);
+                    ci[i][j] = fmaf(a_i[i], b_r[j], ci[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ void zero(float (&c)[4][4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) c[i][j] = 0.f;
+}
+
+// Stage 1: T1t[b][kx][ny] = sum_nx A(l)[kx][nx] P[b][ny][nx].
+__global__ void __launch_bounds__(NT) k_simt_stage1(const float *amat, const float *P, float *T1t, int ni, int no,
+                                                    int ldi, int nse, int B) {
+    __shared__ SimtSmem sm;
+    const int b = blockIdx.z, l = (b % B) / nse, m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    float cr[4][4], ci[4][4];
+    zero(cr);
+    zero(ci);
+    const size_t aps = (size_t)no * ldi, pps = (size_t)ni * ldi;
+    simt_tile(amat + (size_t)l * 2 * aps, aps, ldi, no, P + (size_t)b * 2 * pps, pps, ldi, ni, ni, m0, n0, cr, ci, sm);
+    float *out = T1t + (size_t)b * 2 * aps;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < no && n < ni) {
+                out[(size_t)m * ldi + n] = cr[i][j];
+                out[aps + (size_t)m * ldi + n] = ci[i][j];
+            }
+        }
+}
+
+// Stage 2 + intensity: Is[g][r nse + se][ky][kx] = sum_{l in group g} w_l |sum_ny A(l)[ky][ny] T1t[b][kx][ny]|^2.
+__global__ void __launch_bounds__(NT) k_simt_stage2(const float *amat, const float *T1t, const float *wnorm, float *Is,
+                                                    int ni, int no, int ldi, int nse, int nl, int G, int tiles_n,
+                                                    int B) {
+    __shared__ SimtSmem sm;
+    const int rse = blockIdx.y, r = rse / nse, se = rse % nse, g = blockIdx.z;
+    const int m0 = (blockIdx.x / tiles_n) * BM, n0 = (blockIdx.x % tiles_n) * BN;
+    const int l0 = (int)((long)g * nl / G), l1 = (int)((long)(g + 1) * nl / G);
+    const size_t aps = (size_t)no * ldi;
+    float acc[4][4];
+    zero(acc);
+    for (int l = l0; l < l1; ++l) {
+        float cr[4][4], ci[4][4];
+        zero(cr);
+        zero(ci);
+        const int b = r * B + l * nse + se;
+        simt_tile(amat + (size_t)l * 2 * aps, aps, ldi, no, T1t + (size_t)b * 2 * aps, aps, ldi, no, ni, m0, n0, cr,
+                  ci, sm);
+        const float w = wnorm[(size_t)r * nl + l];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(w, cr[i][j] * cr[i][j] + ci[i][j] * ci[i][j], acc[i][j]);
+    }
+    float *out = Is + ((size_t)g * gridDim.y + rse) * no * no;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < no && n < no) out[(size_t)m * no + n] = acc[i][j];
+        }
+}
+
+// Adjoint, recomputed field: E^T[kx][ky] = sum_ny T1t[b][kx][ny] A(l)[ky][ny];
+// GEt[z][kx][ky] = 2 w_l F_s GI[e][bin(ky,kx)] E^T[kx][ky]  (dL/dRe E + i dL/dIm E).
+__global__ void __launch_bounds__(NT) k_simt_grad_field(const float *amat, const float *T1t, const float *wnorm,
+                                                        DevParams prm, const float *GI, float *GEt, int ni, int no,
+                                                        int ldi, int ldo, int nl, int nse, int ne, int nd, int os,
+                                                        int B, int b0, int tiles_n) {
+    __shared__ SimtSmem sm;
+    const int z = blockIdx.y, b = b0 + z, r = b / B, bl = b % B, l = bl / nse, se = bl % nse, s = se / ne,
+              e = se % ne;
+    const int m0 = (blockIdx.x / tiles_n) * BM, n0 = (blockIdx.x % tiles_n) * BN;
+    const size_t aps = (size_t)no * ldi;
+    float cr[4][4], ci[4][4];
+    zero(cr);
+    zero(ci);
+    simt_tile(T1t + (size_t)b * 2 * aps, aps, ldi, no, amat + (size_t)l * 2 * aps, aps, ldi, no, ni, m0, n0, cr, ci,
+              sm);
+    const float c = 2.f * wnorm[(size_t)r * nl + l] * slot_ptr(prm, PFLUX, r)[s];
+    const float *gi = GI + ((size_t)r * ne + e) * nd * nd;
+    const size_t gps = (size_t)no * ldo;
+    float *out = GEt + (size_t)z * 2 * gps;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int kx = m0 + ty + 16 * i, ky = n0 + tx + 16 * j;
+            if (kx < no && ky < no) {
+                float f = c * gi[(ky / os) * nd + kx / os];
+                out[(size_t)kx * ldo + ky] = f * cr[i][j];
+                out[gps + (size_t)kx * ldo + ky] = f * ci[i][j];
+            }
+        }
+}
+
+// Adjoint stage 2^T: GT1[z][ny][kx] = sum_ky AH(l)[ny][ky] GEt[z][kx][ky].
+__global__ void __launch_bounds__(NT) k_simt_adj2(const float *amatH, const float *GEt, float *GT1, int ni, int no,
+                                                  int ldo, int nse, int B, int b0) {
+    __shared__ SimtSmem sm;
+    const int z = blockIdx.z, b = b0 + z, l = (b % B) / nse, m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const size_t hps = (size_t)ni * ldo, gps = (size_t)no * ldo;
+    float cr[4][4], ci[4][4];
+    zero(cr);
+    zero(ci);
+    simt_tile(amatH + (size_t)l * 2 * hps, hps, ldo, ni, GEt + (size_t)z * 2 * gps, gps, ldo, no, no, m0, n0, cr, ci,
+              sm);
+    float *out = GT1 + (size_t)z * 2 * hps;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            if (m < ni && n < no) {
+                out[(size_t)m * ldo + n] = cr[i][j];
+                out[hps + (size_t)m * ldo + n] = ci[i][j];
+            }
+        }
+}
+
+// Adjoint stage 1^T + phase gradient: G_P[ny][nx] = sum_kx GT1[z][ny][kx] AH(l)[nx][kx];
+// gphi[b][ny][nx] = (2 pi / lambda_l) Im(G_P conj(P[b][ny][nx])).
+__global__ void __launch_bounds__(NT) k_simt_adj1(const float *amatH, const float *GT1, const float *P,
+                                                  const double *lam, float *gphi, int ni, int no, int ldi, int ldo,
+                                                  int nse, int B, int b0) {
+    __shared__ SimtSmem sm;
+    const int z = blockIdx.z, b = b0 + z, l = (b % B) / nse, m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const size_t hps = (size_t)ni * ldo, pps = (size_t)ni * ldi;
+    float cr[4][4], ci[4][4];
+    zero(cr);
+    zero(ci);
+    simt_tile(GT1 + (size_t)z * 2 * hps, hps, ldo, ni, amatH + (size_t)l * 2 * hps, hps, ldo, ni, no, m0, n0, cr, ci,
+              sm);
+    const float k2 = (float)(6.283185307179586476925286766559 / lam[l]);
+    const float *pb = P + (size_t)b * 2 * pps;
+    float *out = gphi + (size_t)b * ni * ni;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int ny = m0 + ty + 16 * i, nx = n0 + tx + 16 * j;
+            if (ny < ni && nx < ni) {
+                float pr = pb[(size_t)ny * ldi + nx], pi = pb[pps + (size_t)ny * ldi + nx];
+                out[(size_t)ny * ni + nx] = k2 * (ci[i][j] * pr - cr[i][j] * pi);
+            }
+        }
+}
+
+inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+cudaError_t simt_forward(dlx_plan *p, int R, cudaStream_t st) {
+    const float *amat = (const float *)p->amat.ptr;
+    dim3 g1(cdiv(p->no, BM), cdiv(p->ni, BN), R * p->B);
+    k_simt_stage1<<<g1, NT, 0, st>>>(amat, (const float *)p->P.ptr, (float *)p->T1t.ptr, p->ni, p->no, p->ldi, p->nse,
+                                     p->B);
+    int tn = cdiv(p->no, BN);
+    dim3 g2(cdiv(p->no, BM) * tn, R * p->nse, p->G);
+    k_simt_stage2<<<g2, NT, 0, st>>>(amat, (const float *)p->T1t.ptr, p->wnorm, p->Is, p->ni, p->no, p->ldi, p->nse,
+                                     p->nl, p->G, tn, p->B);
+    return cudaGetLastError();
+}
+
+cudaError_t simt_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st) {
+    const float *amat = (const float *)p->amat.ptr, *amatH = (const float *)p->amatH.ptr;
+    int tn = cdiv(p->no, BN);
+    dim3 ge(cdiv(p->no, BM) * tn, nb);
+    k_simt_grad_field<<<ge, NT, 0, st>>>(amat, (const float *)p->T1t.ptr, p->wnorm, prm, p->GI, (float *)p->GEt.ptr,
+                                         p->ni, p->no, p->ldi, p->ldo, p->nl, p->nse, p->ne, p->nd, p->os, p->B, b0,
+                                         tn);
+    dim3 g2(cdiv(p->ni, BM), cdiv(p->no, BN), nb);
+    k_simt_adj2<<<g2, NT, 0, st>>>(amatH, (const float *)p->GEt.ptr, (float *)p->GT1.ptr, p->ni, p->no, p->ldo, p->nse,
+                                   p->B, b0);
+    dim3 g1(cdiv(p->ni, BM), cdiv(p->ni, BN), nb);
+    k_simt_adj1<<<g1, NT, 0, st>>>(amatH, (const float *)p->GT1.ptr, (const float *)p->P.ptr, p->lam_d, p->gphi, p->ni,
+                                   p->no, p->ldi, p->ldo, p->nse, p->B, b0);
+    return cudaGetLastError();
+}
+
+}  // namespace dlx

@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element
+by element, on seeded inputs -- tiny, ragged (tile edges), a reduced and the
+full binary-star workload, and sampled outputs plus exact identities at the
+million-parameter calibration size."""
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import TOL, compare, fit_problem, gpu_eval, oracle_eval, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FORMS = ["fp32", "bf16x3", "tf32x3", "bf16"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2406_08703_gb300 as P
+
+    P.load()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    truth, data, start = fit_problem("tiny")
+    return start, data, oracle_eval(start, data)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_tiny_workload(tiny, form):
+    """64^2 pupil -> 256^2 oversampled grid, one wavelength, one star (the tiny workload)."""
+    start, data, ref = tiny
+    out = gpu_eval(start, data, form)
+    err = compare(out, ref, form)
+    print(form, err)
+
+
+RAGGED = [
+    dict(n_pupil=17, n_det=9, oversample=3, n_lambda=2, n_src=2, n_exp=2, dither_px=0.5, obscuration=0.2,
+         grating=True, n_zern_max=6, opd_pix_rms=3e-9),
+    dict(n_pupil=40, n_det=50, oversample=2, n_lambda=3, n_src=1, n_exp=1, n_zern_max=4),
+    dict(n_pupil=136, n_det=35, oversample=4, n_lambda=2, n_src=3, n_exp=1, obscuration=0.2, grating=True,
+         n_zern_max=10, opd_pix_rms=5e-9),
+]
+
+
+@pytest.mark.parametrize("case", range(len(RAGGED)))
+@pytest.mark.parametrize("form", FORMS)
+def test_ragged_shapes(case, form):
+    """Sizes that are not multiples of any tile: partial tiles in every dimension."""
+    _, data, start = fit_problem("custom", seed=10 + case, **RAGGED[case])
+    out = gpu_eval(start, data, form)
+    compare(out, oracle_eval(start, data), form)
+
+
+@pytest.fixture(scope="module")
+def binary_reduced():
+    truth, data, start = fit_problem("binary", n_lambda=4)
+    return start, data, oracle_eval(start, data)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_binary_reduced(binary_reduced, form):
+    """Binary-star workload (256^2 pupil, 1024^2 grid, 2 stars) with 4 of its 32 wavelengths."""
+    start, data, ref = binary_reduced
+    compare(gpu_eval(start, data, form), ref, form)
+
+
+@pytest.fixture(scope="module")
+def binary_full():
+    truth, data, start = fit_problem("binary")
+    return start, data, oracle_eval(start, data)
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "tf32x3"])
+def test_binary_full_size(binary_full, form):
+    """The full binary-star workload: 32 wavelengths x 2 stars = 64 PSFs of 1024^2."""
+    start, data, ref = binary_full
+    err = compare(gpu_eval(start, data, form, want_psf=False), ref, form)
+    print(form, err)
+
+
+def test_adjoint_chunking_is_bitwise_identical():
+    """Per-wavelength recomputation in chunks of 1, 3 or all PSFs gives identical bits."""
+    _, data, start = fit_problem("custom", seed=5, **RAGGED[0])
+    outs = [gpu_eval(start, data, "fp32", psf_chunk=c, want_psf=False) for c in (1, 3, 0)]
+    for o in outs[1:]:
+        assert o["loss"] == outs[0]["loss"]
+        for k in o["grads"]:
+            assert np.array_equal(o["grads"][k], outs[0]["grads"][k]), k
+
+
+def test_repeat_is_deterministic():
+    _, data, start = fit_problem("custom", seed=6, **RAGGED[2])
+    a = gpu_eval(start, data, "bf16x3", want_psf=False)
+    b = gpu_eval(start, data, "bf16x3", want_psf=False)
+    assert a["loss"] == b["loss"]
+    for k in a["grads"]:
+        assert np.array_equal(a["grads"][k], b["grads"][k])
+
+
+@pytest.fixture(scope="module")
+def calib_full():
+    """The million-parameter calibration workload at full size, hard-edged pupil so
+    the Z2/Z3 identities hold exactly; data from an analytic image."""
+    p = W.make_problem("calib")
+    p = W.perturbed_start(p, 41)
+    p.transmission = W.aperture(p.n_pupil, p.diameter, 0.0, oversample=1)
+    p.coeff = 10e-9 * np.random.default_rng(3).standard_normal(p.n_zern)
+    data = W.synthetic_counts((p.n_exp, p.n_det, p.n_det), 1e9, np.zeros((1, 2)), 12.0, 44)
+    return p, data
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_calib_full_size_sampled(calib_full, form):
+    """512^2 pupil, 16 wavelengths x 8 exposures, 2048^2 grid: sampled model pixels
+    against direct sums, and identities that hold at any size."""
+    p, data = calib_full
+    out = gpu_eval(p, data, form, want_psf=False)
+    m = out["model"]
+    rng = np.random.default_rng(0)
+    e_idx = list(rng.integers(0, p.n_exp, 16))
+    q_idx = list(rng.integers(0, p.n_det**2, 16))
+    e0, q0 = np.unravel_index(np.argmax(m.reshape(p.n_exp, -1)), (p.n_exp, p.n_det**2))
+    e_idx.append(int(e0))
+    q_idx.append(int(q0))
+    ref = oracle.model_at(p, e_idx, q_idx)
+    got = m.reshape(p.n_exp, -1)[e_idx, q_idx]
+    assert np.max(np.abs(got - ref)) <= TOL[form]["psf"] * ref[-1]
+    g = out["grads"]
+    s_m = float(np.sum(m - data))
+    assert np.dot(p.flux, g["d_flux"]) == pytest.approx(s_m, rel=1e-4)
+    assert np.sum(p.flat * g["d_flat"]) == pytest.approx(s_m, rel=1e-4)
+    assert np.all(g["d_opd_pix"][p.transmission == 0] == 0)
+    assert p.noll[:2] == [2, 3]
+    for ax in (0, 1):
+        lhs, rhs = np.sum(g["d_pos"][:, ax]), p.diameter / 4 * g["d_zern"][ax]
+        assert abs(lhs - rhs) <= 2e-3 * max(abs(rhs), 1e-30)
+    assert out["diag"]["device_error"] == 0
+
+
+def test_autograd_function_matches_loss_grad():
+    import torch
+
+    import paper_2406_08703_gb300 as P
+
+    _, data, start = fit_problem("custom", seed=8, **RAGGED[1])
+    plan = P.dlx_make_mft(P.desc_from_problem(start, P.DLX_FP32_SIMT))
+    prm = P.params_from_problem(start)
+    fixed = {k: prm[k] for k in ("transmission", "opd_fixed", "zern_basis", "weights", "dither")}
+    leaves = {k: prm[k].clone().requires_grad_(True) for k in ("zern_coeff", "flat", "flux", "pos")}
+    dt = torch.as_tensor(data, device="cuda")
+    L = P.psf_loss(plan, dt, fixed, leaves["zern_coeff"], None, leaves["flat"], leaves["flux"], leaves["pos"])
+    (2.0 * L).backward()
+    loss, grads, _ = P.dlx_loss_grad(plan, prm, dt)
+    torch.cuda.synchronize()
+    assert L.item() == loss.item()
+    for k, gk in (("zern_coeff", "d_zern"), ("flat", "d_flat"), ("flux", "d_flux"), ("pos", "d_pos")):
+        assert torch.allclose(leaves[k].grad, 2.0 * grads[gk], rtol=1e-6, atol=0)
+
+
+def test_adam_matches_numpy():
+    import torch
+
+    import paper_2406_08703_gb300 as P
+
+    rng = np.random.default_rng(1)
+    n = 10007
+    th, m, v = rng.standard_normal(n), np.zeros(n), np.zeros(n)
+    T = {k: torch.tensor(a, dtype=torch.float32, device="cuda") for k, a in (("th", th), ("m", m), ("v", v))}
+    lr, b1, b2, eps = 1e-2, 0.9, 0.999, 1e-8
+    for t in range(1, 6):
+        g = rng.standard_normal(n)
+        P.dlx_adam(T["th"], torch.tensor(g, dtype=torch.float32, device="cuda"), T["m"], T["v"], lr, t)
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        th = th - lr * (m / (1 - b1**t)) / (np.sqrt(v / (1 - b2**t)) + eps)
+    torch.cuda.synchronize()
+    assert rel_l2(T["th"].cpu().numpy(), th) < 1e-6

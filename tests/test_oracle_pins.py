@@ -365,3 +365,14 @@ def test_zernike_basis_orthonormal():
     Z2 = W.zernike_basis([2], npix, D)[0]
     xx = np.meshgrid(c, c)[0]
     assert np.allclose(Z2[inside], 4 * xx[inside] / D)
+
+
+def test_sampled_model_equals_full_forward(oracle_lib, fit_case):
+    """The per-pixel direct-sum model equals the full forward at the sampled pixels."""
+    p, _ = fit_case
+    m = oracle_lib.forward(p)
+    rng = np.random.default_rng(9)
+    e = rng.integers(0, p.n_exp, 12)
+    q = rng.integers(0, p.n_det * p.n_det, 12)
+    got = oracle_lib.model_at(p, e, q)
+    assert np.allclose(got, m.reshape(p.n_exp, -1)[e, q], rtol=1e-12, atol=0)
