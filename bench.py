@@ -1,0 +1,383 @@
+"""Benchmark: fwd+grad evaluations per second of the differentiable-optics model.
+
+One step = one dlx_loss_grad over the whole model (every wavelength x source x
+exposure PSF: phasor, two-sided MFT, intensity, binning, flat field, Poisson
+NLL, and the full adjoint to the Zernike, pixel-OPD, flat-field, flux and
+position gradients).  The default workload is the binary-star polychromatic
+fit: 256^2 pupil, 32 wavelengths x 2 stars = 64 PSFs onto a 1024^2 oversampled
+grid (256^2 detector, oversample 4), synthetic seeded inputs.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form bf16x3] [--impl reference]
+
+Prints one JSON line (rank 0).  `value` is device-timed (CUDA events on the
+launching stream, inputs resident); `e2e` times the same call with host inputs
+copied in from pinned memory and the loss and gradients copied back.  The
+reference arm (--impl reference) times the FP64 CPU oracle on a bounded sample
+of the same workload on this host's cores.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+grad PSF evals/s & tensor-pipe % at ≤1e-5 rel err; p50/p99 latency"
+WORKLOAD = "binary-star polychromatic fit: 256^2 pupil (0.2 D obstruction, 0/pi grating), 32 wavelengths 530-640 nm x 2 stars, 256^2 detector oversample 4 (1024^2 MFT per PSF), fwd + full gradient"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "tf32x3", "bf16", "fp32"])
+    ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
+    ap.add_argument("--workload", default="binary")
+    ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side FP32 / other-form lines")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, local):
+    if world <= 1:
+        return None
+    import torch
+    import torch.distributed as dist
+
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(workload, seed_offset=0):
+    """Seeded synthetic inputs: the workload's truth, a perturbed starting point and
+    Poisson data of an analytic image with the workload's total flux."""
+    import workloads as W
+
+    truth = W.make_problem(workload)
+    start = W.perturbed_start(truth, 100 + seed_offset)
+    total = float(np.sum(truth.flux)) * truth.n_exp
+    pix = truth.pixscale
+    centres = truth.pos / pix
+    data = W.synthetic_counts((truth.n_exp, truth.n_det, truth.n_det), total, centres, 6.0, 200 + seed_offset)
+    return truth, start, data
+
+
+class Clocks:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def run_form(P, torch, workload, form, steps, warmup, device, timing=True):
+    """Device-timed fwd+grad steps of one arithmetic form; returns a dict."""
+    truth, start, data = make_inputs(workload)
+    plan = P.dlx_make_mft(P.desc_from_problem(start, P.PRECISIONS[form]), device=device)
+    prm = P.params_from_problem(start, device=f"cuda:{device}")
+    dt = torch.as_tensor(data, device=f"cuda:{device}")
+    grads = P.empty_grads(plan)
+    loss = torch.empty(1, dtype=torch.float64, device=f"cuda:{device}")
+    model = torch.empty((start.n_exp, start.n_det, start.n_det), device=f"cuda:{device}")
+    stream = torch.cuda.current_stream(device)
+    for _ in range(warmup):
+        P.dlx_loss_grad(plan, prm, dt, loss=loss, grads=grads, model=model, stream=stream)
+    torch.cuda.synchronize(device)
+    P.dlx_plan_get_timing(plan)  # reset counters
+    if timing:
+        P.dlx_plan_set_timing(plan, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize(device)
+    for i in range(steps):
+        ev[i][0].record(stream)
+        P.dlx_loss_grad(plan, prm, dt, loss=loss, grads=grads, model=model, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(device)
+    times = np.array([a.elapsed_time(b) for a, b in ev])
+    kt = P.dlx_plan_get_timing(plan)
+    P.dlx_plan_set_timing(plan, False)
+    diag = P.dlx_plan_diagnostics(plan)
+    info = plan.info
+    out = dict(form=form, ms=times, kt=kt, info=info, diag=diag, loss=float(loss.item()), plan=plan, prm=prm,
+               start=start, data=data)
+    return out
+
+
+def e2e_run(P, torch, r, steps, device):
+    """Same call through the public API with host inputs: H2D of the step's inputs
+    from pinned memory, the evaluation, D2H of loss and gradients, per step."""
+    plan, start, data = r["plan"], r["start"], r["data"]
+    host = {k: (None if v is None else v.cpu().pin_memory()) for k, v in r["prm"].items()}
+    dev = {k: (None if v is None else torch.empty_like(v)) for k, v in r["prm"].items()}
+    hdata = torch.as_tensor(data).pin_memory()
+    ddata = torch.empty_like(hdata, device=f"cuda:{device}")
+    grads = P.empty_grads(plan)
+    hgrads = {k: (None if v is None else torch.empty(v.shape, dtype=v.dtype).pin_memory()) for k, v in grads.items()}
+    loss = torch.empty(1, dtype=torch.float64, device=f"cuda:{device}")
+    hloss = torch.empty(1, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream(device)
+    h2d = sum(v.numel() * v.element_size() for v in host.values() if v is not None) + hdata.numel() * 4
+    d2h = 8 + sum(v.numel() * v.element_size() for v in hgrads.values() if v is not None)
+
+    def step():
+        for k, v in host.items():
+            if v is not None:
+                dev[k].copy_(v, non_blocking=True)
+        ddata.copy_(hdata, non_blocking=True)
+        P.dlx_loss_grad(plan, dev, ddata, loss=loss, grads=grads, stream=stream)
+        hloss.copy_(loss, non_blocking=True)
+        for k, v in grads.items():
+            if v is not None:
+                hgrads[k].copy_(v, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize(device)
+    dt = (time.perf_counter() - t0) / steps
+    return dict(s_per_step=dt, h2d=h2d, d2h=d2h)
+
+
+def cpu_baseline(workload, budget_s=20.0):
+    """The FP64 oracle as it stands, on this host's cores, on a bounded sample of the
+    workload: the same model restricted to its first few wavelengths (all sources and
+    exposures); evals/s scaled by the sampled share of the PSFs."""
+    import oracle
+
+    truth, start, data = make_inputs(workload)
+    nsub = 2
+    sub = start.copy()
+    sub.lambdas, sub.weights = start.lambdas[:nsub], start.weights[:nsub]
+    oracle.lib()
+    oracle.loss_grad(sub, data)  # warm (thread pool, page-in)
+    t0, n = time.perf_counter(), 0
+    while True:
+        oracle.loss_grad(sub, data)
+        n += 1
+        if time.perf_counter() - t0 > budget_s or n >= 20:
+            break
+    dt = (time.perf_counter() - t0) / n
+    frac = nsub / start.n_lambda
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(value=frac / dt, unit="evals/s", cores=cores, kind="oracle",
+                sample=f"{nsub} of {start.n_lambda} wavelengths (all sources and exposures), {n} runs, "
+                       f"{dt:.2f} s each; value scaled by {frac:.4f} of the PSFs")
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the FP64 CPU oracle timed on this host, rank 0 only."""
+    if rank != 0:
+        return
+    import oracle
+
+    truth, start, data = make_inputs(args.workload)
+    nsub = 1
+    sub = start.copy()
+    sub.lambdas, sub.weights = start.lambdas[:nsub], start.weights[:nsub]
+    oracle.lib()
+    for _ in range(args.warmup):
+        oracle.loss_grad(sub, data)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.loss_grad(sub, data)
+    dt = (time.perf_counter() - t0) / args.steps
+    frac = nsub / start.n_lambda
+    value = frac / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = dict(impl="reference", metric=METRIC, value=value, unit="evals/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * dt / frac, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=WORKLOAD, sample=f"{nsub} of {start.n_lambda} wavelengths per step"),
+                cpu_baseline=dict(value=value, unit="evals/s", cores=cores, kind="oracle",
+                                  sample=f"each step: {nsub} of {start.n_lambda} wavelengths x all sources; "
+                                         f"value scaled by {frac:.4f}"),
+                e2e=dict(value=value, unit="evals/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import torch
+
+    import paper_2406_08703_gb300 as P
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    dist = init_dist(world, local)
+    device = local if world > 1 else 0
+    torch.cuda.set_device(device)
+    P.load()
+    peaks = measured_peaks()
+
+    clocks = Clocks(device)
+    barrier(dist)
+    torch.cuda.synchronize(device)
+    clocks.start()
+    t_wall = time.perf_counter()
+    r = run_form(P, torch, args.workload, args.form, args.steps, args.warmup, device)
+    torch.cuda.synchronize(device)
+    barrier(dist)
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    ms = r["ms"]
+    total_ms = max_over_ranks(dist, float(ms.sum()))
+    info = r["info"]
+    evals_per_s = world * args.steps / (total_ms / 1e3)
+    ms_step = total_ms / args.steps
+
+    # roofline of the dominant kernel class (device time measured with events in the timed region)
+    kt = r["kt"]
+    classes = {k: v for k, v in kt.items() if isinstance(v, dict)}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    ni, no, B = info.n_pupil, info.n_out, info.n_psf
+    alg = {  # algorithmic FLOP per launch (8 per complex MAC), one launch per class per eval
+        "stage1": 8.0 * B * no * ni * ni, "stage2_intensity": 8.0 * B * no * no * ni,
+        "adjoint_field": 8.0 * B * no * no * ni, "adjoint_stage2T": 8.0 * B * ni * no * no,
+        "adjoint_stage1T": 8.0 * B * ni * ni * no,
+    }
+    split = {"bf16x3": 3.0, "tf32x3": 3.0, "bf16": 1.0, "fp32": 1.0}[args.form]
+    nom_ratio = {"bf16x3": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
+    roof = None
+    if dom in alg:
+        per_launch_ms = classes[dom]["ms"] / max(classes[dom]["events"], 1)
+        achieved = alg[dom] / (per_launch_ms / 1e3) / 1e12
+        if args.form == "fp32":
+            peak = 152 * 128 * 2 * (clk["sm_mhz"] or 1920.0) * 1e6 / 1e12
+            roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                        traffic=None, kernel=dom, peak_source="152 SMs x 128 FP32 lanes x 2 x median SM clock")
+        else:
+            base = peaks.get("bf16_tflops_sustained", 1707.9)
+            peak = base * nom_ratio[args.form]
+            roof = dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                        traffic=None, kernel=dom,
+                        executed_tflops=achieved * split, executed_frac=achieved * split / peak,
+                        peak_source="MEASURED_PEAKS.json bf16_tflops_sustained" +
+                                    (" x nominal tf32/bf16 ratio 1.1/2.25" if args.form == "tf32x3" else "") +
+                                    " (of measured)")
+
+    line = dict(metric=METRIC, value=evals_per_s, unit="evals/s", n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype={"bf16x3": "bf16x3 split (fp32 accumulate)", "tf32x3": "tf32x3 split (fp32 accumulate)",
+                       "bf16": "bf16 (fp32 accumulate)", "fp32": "f32"}[args.form],
+                data="synthetic",
+                config=dict(workload=WORKLOAD, form=args.form, psfs_per_eval=B, pupil=ni, mft_out=no,
+                            parallelism="replicas" if world > 1 else "single",
+                            l2="no flush: per-step working set > 129 MB L2",
+                            working_set_mb=round(info.workspace_bytes / 2**20)),
+                psf_evals_per_s=evals_per_s * B,
+                latency_ms=dict(p50=float(np.percentile(ms, 50)), p99=float(np.percentile(ms, 99))),
+                tflops_algorithmic=evals_per_s / world * info.flop_loss_grad / 1e12,
+                gpu_launches=int(kt["total_launches"]), clocks=clk, roofline=roof,
+                kernels={k: round(v["ms"] / args.steps, 4) for k, v in classes.items() if v["ms"] > 0},
+                wall_s=wall, device_error=r["diag"]["device_error"])
+
+    # e2e through the public API with host buffers
+    e = e2e_run(P, torch, r, max(3, args.steps // 3), device)
+    line["e2e"] = dict(value=world / max_over_ranks(dist, e["s_per_step"]), unit="evals/s",
+                       h2d_bytes_per_step=e["h2d"], d2h_bytes_per_step=e["d2h"])
+    r["plan"].close()
+
+    if not args.no_forms and rank == 0:
+        forms = {}
+        for f in ("fp32", "tf32x3", "bf16"):
+            if f == args.form:
+                continue
+            try:
+                rf = run_form(P, torch, args.workload, f, max(5, args.steps // 3), 2, device, timing=False)
+                forms[f] = dict(value=1e3 / float(rf["ms"].mean()), p50_ms=float(np.percentile(rf["ms"], 50)),
+                                p99_ms=float(np.percentile(rf["ms"], 99)))
+                rf["plan"].close()
+            except Exception as ex:  # report, do not hide
+                forms[f] = dict(error=str(ex))
+        line["forms"] = forms
+
+    if not args.no_cpu and rank == 0 and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -145,6 +145,22 @@ int dlx_loss_grad(dlx_plan *plan, const dlx_params *params, const int32_t *data,
  * when a device-side bounded wait expired; the flag is cleared by this call). */
 int dlx_plan_diagnostics(dlx_plan *plan, int64_t *clamped, int32_t *device_error);
 
+/* Per-kernel-class device time of the evaluations issued on this plan while
+ * timing is enabled: CUDA events are recorded on the launching stream around
+ * each class of launch (so the times include no host gaps), and every kernel
+ * launch is counted whether timing is on or not.  dlx_plan_get_timing is
+ * synchronous and resets the accumulators and counters. */
+typedef struct {
+    int n_classes;
+    const char *name[16];   /* e.g. "stage2_intensity", "adjoint_field" */
+    double ms[16];          /* total device milliseconds (0 when timing was off) */
+    int64_t events[16];     /* timed scopes (one per launch or launch group) */
+    int64_t launches[16];   /* kernel launches */
+    int64_t total_launches;
+} dlx_kernel_times;
+int dlx_plan_set_timing(dlx_plan *plan, int enable);
+int dlx_plan_get_timing(dlx_plan *plan, dlx_kernel_times *out);
+
 /* Adam update (Kingma & Ba; the optimiser of Sec. 4) of n parameters in place:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; theta -= lr mhat / (sqrt(vhat) + eps),
  * with bias correction for 1-based step `t`.  All arrays device float32. */

@@ -219,6 +219,20 @@ def dlx_plan_diagnostics(plan: Plan):
     return dict(clamped=c.value, device_error=e.value)
 
 
+def dlx_plan_set_timing(plan: Plan, enable: bool = True) -> None:
+    N.check(load().dlx_plan_set_timing(plan.handle, 1 if enable else 0), "dlx_plan_set_timing")
+
+
+def dlx_plan_get_timing(plan: Plan) -> dict:
+    """{class: dict(ms, events, launches)} plus 'total_launches'; synchronous, resets."""
+    t = N.KernelTimes()
+    N.check(load().dlx_plan_get_timing(plan.handle, C.byref(t)), "dlx_plan_get_timing")
+    out = {t.name[i].decode(): dict(ms=t.ms[i], events=t.events[i], launches=t.launches[i])
+           for i in range(t.n_classes)}
+    out["total_launches"] = t.total_launches
+    return out
+
+
 def dlx_adam(theta, grad, m, v, lr, t, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     torch = _torch()
     for name, x in (("theta", theta), ("grad", grad), ("m", m), ("v", v)):

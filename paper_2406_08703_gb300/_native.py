@@ -45,6 +45,11 @@ class PlanInfo(C.Structure):
         ("gemm_tiles_stage2", C.c_int)]
 
 
+class KernelTimes(C.Structure):
+    _fields_ = [("n_classes", C.c_int), ("name", C.c_char_p * 16), ("ms", C.c_double * 16),
+                ("events", C.c_int64 * 16), ("launches", C.c_int64 * 16), ("total_launches", C.c_int64)]
+
+
 class Request(C.Structure):
     _fields_ = [("desc", MftDesc)] + [(k, C.c_void_p) for k in (
         "transmission", "opd_fixed", "zern_basis", "weights", "dither", "zern_coeff", "opd_pix", "flux", "pos",
@@ -74,6 +79,8 @@ SIGNATURES = {
     "dlx_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p, C.POINTER(Grads),
                                 C.c_void_p, C.c_void_p]),
     "dlx_plan_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    "dlx_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "dlx_plan_get_timing": (C.c_int, [C.c_void_p, C.POINTER(KernelTimes)]),
     "dlx_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_float, C.c_float,
                            C.c_float, C.c_float, C.c_int, C.c_void_p]),
     "dlx_server_create": (C.c_int, [C.c_int, C.c_size_t, C.c_int, C.POINTER(C.c_void_p)]),

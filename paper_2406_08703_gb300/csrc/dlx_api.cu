@@ -74,8 +74,40 @@ int validate_params(const dlx_plan *p, const dlx_params *prm) {
 
 namespace dlx {
 
+static const char *kClassNames[KC_N] = {"mft_matrices", "prologue",      "stage1",          "stage2_intensity",
+                                        "bin_nll",      "loss",          "adjoint_field",   "adjoint_stage2T",
+                                        "adjoint_stage1T", "grad_reduce", "adam"};
+
+static cudaEvent_t pool_get(dlx_plan *p) {
+    if (p->pool_next < p->pool.size()) return p->pool[p->pool_next++];
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    p->pool.push_back(e);
+    p->pool_next++;
+    return e;
+}
+
+KScope::KScope(dlx_plan *p_, int c, int n_, cudaStream_t s) : p(p_), cls(c), n(n_), st(s) {
+    if (p->timing) {
+        cudaEvent_t a = pool_get(p);
+        b = pool_get(p);
+        cudaEventRecord(a, st);
+        p->recs.push_back({cls, a, b});
+    }
+}
+
+KScope::~KScope() {
+    p->launches[cls] += n;
+    if (b) {
+        cudaEventRecord(b, st);
+        p->events[cls]++;
+    }
+}
+
 void free_plan(dlx_plan *p) {
     if (!p) return;
+    for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
+    p->pool.clear();
     plan_free(p);
     delete p;
 }
@@ -370,6 +402,34 @@ int dlx_plan_diagnostics(dlx_plan *p, int64_t *clamped, int32_t *device_error) {
     DLX_CU(cudaMemset(p->err, 0, sizeof(int32_t)), "memset");
     if (clamped) *clamped = (int64_t)c;
     if (device_error) *device_error = err;
+    return DLX_OK;
+}
+
+int dlx_plan_set_timing(dlx_plan *p, int enable) {
+    if (!p) return fail(DLX_ERR_INVALID_ARG, "plan is NULL");
+    p->timing = enable != 0;
+    return DLX_OK;
+}
+
+int dlx_plan_get_timing(dlx_plan *p, dlx_kernel_times *out) {
+    if (!p || !out) return fail(DLX_ERR_INVALID_ARG, "NULL argument");
+    DeviceGuard guard(p->device);
+    DLX_CU(cudaDeviceSynchronize(), "synchronize");
+    memset(out, 0, sizeof(*out));
+    out->n_classes = dlx::KC_N;
+    for (int c = 0; c < dlx::KC_N; ++c) {
+        out->name[c] = dlx::kClassNames[c];
+        out->launches[c] = p->launches[c];
+        out->events[c] = p->events[c];
+        out->total_launches += p->launches[c];
+    }
+    for (const auto &r : p->recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) out->ms[r.cls] += ms;
+    }
+    p->recs.clear();
+    p->pool_next = 0;
+    for (int c = 0; c < 16; ++c) p->launches[c] = p->events[c] = 0;
     return DLX_OK;
 }
 

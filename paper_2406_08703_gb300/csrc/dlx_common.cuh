@@ -155,11 +155,36 @@ struct dlx_plan {
     unsigned long long *clamped = nullptr;
     size_t workspace = 0;
     std::vector<void *> allocs;
+    // per-kernel-class timing (events on the launching stream) and launch counts
+    struct TimedRec {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    bool timing = false;
+    std::vector<TimedRec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_next = 0;
+    int64_t launches[16] = {};
+    int64_t events[16] = {};
 };
 
 namespace dlx {
 
 constexpr int kMaxSrc = 8;
+
+enum KClass { KC_MATRICES = 0, KC_PROLOGUE, KC_STAGE1, KC_STAGE2, KC_BIN, KC_LOSS, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1,
+              KC_GRAD, KC_ADAM, KC_N };
+
+// Scope around one class of launches on stream st: counts the `n` kernels it
+// launches and, when the plan's timing is on, records events around them.
+struct KScope {
+    dlx_plan *p;
+    int cls, n;
+    cudaStream_t st;
+    cudaEvent_t b = nullptr;
+    KScope(dlx_plan *p, int cls, int n, cudaStream_t st);
+    ~KScope();
+};
 
 // ---- plan construction (dlx_api.cu)
 int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out);

@@ -63,6 +63,7 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, int n
 cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
     size_t total = (size_t)p->nl * p->no * p->ni;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
+    KScope ks(p, KC_MATRICES, 1, st);
     DLX_FMT_DISPATCH(p->fmt, F,
                      k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->nl, p->ni,
                                                                p->no, p->ldi, p->ldo, p->dx, p->du));
@@ -151,6 +152,7 @@ __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const flo
 
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
     const int npx = p->ni * p->ni, nbt = R * p->B;
+    KScope ks(p, KC_PROLOGUE, 4, st);
     k_norms<<<R, 1024, 0, st>>>(prm, npx, p->nl, p->pscale, p->wnorm);
     int blocks = std::max(1, std::min((npx + 255) / 256, p->sm_count * 8 / R));
     k_opd<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(prm, p->nz, npx, p->opd);
@@ -242,6 +244,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
                            float *model, size_t model_stride, const DevGrads *g, cudaStream_t st) {
     DevGrads gg{};
     if (g) gg = *g;
+    KScope ks(p, KC_BIN, 1, st);
     k_bin_nll<<<dim3(p->red_blocks, R), 256, 0, st>>>(p->Is, p->G, R * p->nse, p->nse, p->ns, p->ne, p->nd, p->os,
                                                         p->no, prm, data, data_stride, model, model_stride, p->GI, gg,
                                                         p->red, p->clamped);
@@ -267,6 +270,7 @@ __global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, 
 cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaStream_t st) {
     size_t plane = (size_t)p->no * p->no, total = plane * p->ne;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
+    KScope ks(p, KC_BIN, 1, st);
     k_psf_out<<<blocks, 256, 0, st>>>(p->Is, p->G, p->nse, p->ns, p->ne, plane, prm.p[PFLUX], psf);
     return cudaGetLastError();
 }
@@ -290,6 +294,7 @@ __global__ void k_finalize_loss(const double *red, int nblk, int ns, double *los
 cudaError_t launch_finalize_loss(dlx_plan *p, int R, double *loss, const DevGrads *g, cudaStream_t st) {
     DevGrads gg{};
     if (g) gg = *g;
+    KScope ks(p, KC_LOSS, 1, st);
     k_finalize_loss<<<R, 256, 0, st>>>(p->red, p->red_blocks, p->ns, loss, gg);
     return cudaGetLastError();
 }
@@ -359,6 +364,7 @@ cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const D
     DevGrads gg{};
     if (g) gg = *g;
     int blocks = (int)std::min<size_t>(((size_t)R * npx + 255) / 256, (size_t)p->sm_count * 8);
+    KScope ks(p, KC_GRAD, 1 + (gg.p[GPOS] ? 2 : 0) + ((gg.p[GZERN] && p->nz > 0) ? 1 : 0), st);
     k_gopd<<<blocks, 256, 0, st>>>(p->gphi, R, p->B, npx, p->gopd, gg);
     if (gg.p[GPOS]) {
         k_pos_moments<<<R * p->B, 256, 0, st>>>(p->gphi, p->ni, p->dx, p->pos_part);

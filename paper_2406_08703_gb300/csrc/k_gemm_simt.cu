@@ -230,10 +230,14 @@ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 cudaError_t simt_forward(dlx_plan *p, int R, cudaStream_t st) {
     const float *amat = (const float *)p->amat.ptr;
     dim3 g1(cdiv(p->no, BM), cdiv(p->ni, BN), R * p->B);
+    {
+    KScope ks(p, KC_STAGE1, 1, st);
     k_simt_stage1<<<g1, NT, 0, st>>>(amat, (const float *)p->P.ptr, (float *)p->T1t.ptr, p->ni, p->no, p->ldi, p->nse,
                                      p->B);
+    }
     int tn = cdiv(p->no, BN);
     dim3 g2(cdiv(p->no, BM) * tn, R * p->nse, p->G);
+    KScope ks(p, KC_STAGE2, 1, st);
     k_simt_stage2<<<g2, NT, 0, st>>>(amat, (const float *)p->T1t.ptr, p->wnorm, p->Is, p->ni, p->no, p->ldi, p->nse,
                                      p->nl, p->G, tn, p->B);
     return cudaGetLastError();
@@ -243,13 +247,20 @@ cudaError_t simt_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb
     const float *amat = (const float *)p->amat.ptr, *amatH = (const float *)p->amatH.ptr;
     int tn = cdiv(p->no, BN);
     dim3 ge(cdiv(p->no, BM) * tn, nb);
+    {
+    KScope ks(p, KC_ADJ_FIELD, 1, st);
     k_simt_grad_field<<<ge, NT, 0, st>>>(amat, (const float *)p->T1t.ptr, p->wnorm, prm, p->GI, (float *)p->GEt.ptr,
                                          p->ni, p->no, p->ldi, p->ldo, p->nl, p->nse, p->ne, p->nd, p->os, p->B, b0,
                                          tn);
+    }
     dim3 g2(cdiv(p->ni, BM), cdiv(p->no, BN), nb);
+    {
+    KScope ks(p, KC_ADJ2, 1, st);
     k_simt_adj2<<<g2, NT, 0, st>>>(amatH, (const float *)p->GEt.ptr, (float *)p->GT1.ptr, p->ni, p->no, p->ldo, p->nse,
                                    p->B, b0);
+    }
     dim3 g1(cdiv(p->ni, BM), cdiv(p->ni, BN), nb);
+    KScope ks(p, KC_ADJ1, 1, st);
     k_simt_adj1<<<g1, NT, 0, st>>>(amatH, (const float *)p->GT1.ptr, (const float *)p->P.ptr, p->lam_d, p->gphi, p->ni,
                                    p->no, p->ldi, p->ldo, p->nse, p->B, b0);
     return cudaGetLastError();

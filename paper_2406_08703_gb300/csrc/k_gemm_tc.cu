@@ -1,8 +1,691 @@
-// Tensor-core (tcgen05) form of the MFT contractions -- placeholder until the kernel lands.
+// Tensor-core form of the four MFT contractions (Sec. 3, two-sided MFT) on
+// sm_103a: TMA -> shared memory -> tcgen05.mma -> tensor memory -> epilogue.
+//
+// Every contraction is C[m][n] = sum_k A[m][k] B[n][k] over complex operands
+// held as bf16 (or tf32) planes, both K-major.  One CTA (320 threads) owns a
+// 128 x 128 complex output tile per job and runs persistently over jobs:
+//   warp 8  : TMA producer (one lane) -- 4-D tensor maps {k, row, plane, batch},
+//             64-byte swizzled boxes of every plane of A and B per stage;
+//   warp 9  : MMA issuer (one lane) and tensor-memory owner -- per 16-wide k
+//             step it issues the complex product as real products into two
+//             FP32 accumulators Er, Ei (128 columns each, double-buffered):
+//               split forms: Er += Ar_h Br_h + Ar_h Br_l + Ar_l Br_h - (Ai_h Bi_h + Ai_h Bi_l + Ai_l Bi_h)
+//                            Ei += Ar_h Bi_h + Ar_h Bi_l + Ar_l Bi_h + Ai_h Br_h + Ai_h Br_l + Ai_l Br_h
+//               (the minus is the instruction descriptor's negate-A bit);
+//   warps 0-7: epilogue -- tcgen05.ld of a 32-lane quarter and a 64-column
+//             half of Er/Ei, then the stage's fused epilogue (operand split
+//             store, |E|^2 spectral accumulation, dL/dE scaling, or the
+//             phase-gradient product with conj(P)).
+// Every mbarrier wait is bounded (globaltimer, 1 s): on expiry the CTA raises
+// a shared abort flag and the plan's device error flag, waits (bounded) for
+// its own copies and MMAs in flight, frees its tensor memory and returns.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
 #include "dlx_common.cuh"
+
 namespace dlx {
-int tc_supported(const dlx_plan *, std::string *why) { *why = "tensor-core form not built yet"; return 0; }
-int tc_make_maps(dlx_plan *, std::string *why) { *why = "not built"; return 0; }
-cudaError_t tc_forward(dlx_plan *, int, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t tc_adjoint_chunk(dlx_plan *, const DevParams &, int, int, cudaStream_t) { return cudaErrorNotSupported; }
+namespace {
+
+constexpr int BM = 128, BN = 128, NTHREADS = 320, EPI_WARPS = 8, PRODUCER_WARP = 8, MMA_WARP = 9;
+constexpr int PLANE_BYTES = 128 * 64;  // one 128-row x 64-byte swizzled box
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+constexpr uint32_t TMEM_COLS = 512;
+
+enum Kind { KS1 = 0, KS2 = 1, KGE = 2, KGT1 = 3, KGP = 4 };
+
+template <int F>
+struct Cfg {
+    static constexpr int PL = fmt_planes(F);
+    static constexpr int ES = fmt_esize(F);
+    static constexpr int KB = 64 / ES;  // k elements per stage (64 bytes per row)
+    static constexpr int STAGE_BYTES = 2 * PL * PLANE_BYTES;
+    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
+    static constexpr int KSTEP = (F == FMT_TF32X4) ? 8 : 16;  // k per MMA instruction (32 bytes)
+    static constexpr int NKSTEP = KB / KSTEP;
+    static constexpr uint32_t AB_FMT = (F == FMT_TF32X4) ? 2u : 1u;  // TF32 : BF16
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+// Arguments of one launch.  Per-job operand coordinates come from decode().
+struct TcArgs {
+    int kind;
+    int M, N, K;   // per-job contraction sizes (complex)
+    int tm, tn;    // 128-tiles along M and N
+    int units;
+    int nl, nse, B, ne, nd, os, ni, no, ldi, ldo, G, Rnse, b0;
+    const float *wnorm;
+    const float *GI;
+    DevParams prm;
+    float *Is;
+    void *out;        // operand output base (KS1, KGE, KGT1)
+    int out_ld;
+    size_t out_ps;    // plane stride (elements)
+    const void *P;    // phasor operand (KGP)
+    const double *lam;
+    float *gphi;
+    int32_t *err;
+};
+
+struct Job {
+    int a_batch, a_row, b_batch, b_row;
+    int m0, n0;
+    int b;       // global PSF index
+    int z;       // chunk-local index
+    int l, r, se;
+};
+
+__device__ __forceinline__ int decode_unit_jobs(const TcArgs &a, int u, int &g, int &rse, int &tile) {
+    if (a.kind != KS2) return 1;
+    tile = u % (a.tm * a.tn);
+    int rest = u / (a.tm * a.tn);
+    g = rest % a.G;
+    rse = rest / a.G;
+    int l0 = (int)((long)g * a.nl / a.G), l1 = (int)((long)(g + 1) * a.nl / a.G);
+    return l1 - l0;
 }
+
+__device__ __forceinline__ Job decode(const TcArgs &a, int u, int j) {
+    Job J;
+    const int tt = a.tm * a.tn;
+    int tile = u % tt;
+    J.m0 = (tile / a.tn) * BM;
+    J.n0 = (tile % a.tn) * BN;
+    if (a.kind == KS2) {
+        int rest = u / tt, g = rest % a.G, rse = rest / a.G;
+        int l0 = (int)((long)g * a.nl / a.G);
+        J.l = l0 + j;
+        J.r = rse / a.nse;
+        J.se = rse % a.nse;
+        J.b = J.r * a.B + J.l * a.nse + J.se;
+        J.z = 0;
+        J.a_batch = J.l;
+        J.b_batch = J.b;
+    } else {
+        int z = u / tt;
+        J.z = z;
+        J.b = (a.kind == KS1) ? z : a.b0 + z;
+        J.r = J.b / a.B;
+        J.l = (J.b % a.B) / a.nse;
+        J.se = (J.b % a.B) % a.nse;
+        switch (a.kind) {
+            case KS1: J.a_batch = J.l; J.b_batch = J.b; break;   // A(l) . P[b]^T
+            case KGE: J.a_batch = J.b; J.b_batch = J.l; break;   // T1t[b] . A(l)^T
+            case KGT1: J.a_batch = J.l; J.b_batch = J.z; break;  // AH(l) . GEt[z]^T
+            default: J.a_batch = J.z; J.b_batch = J.l; break;    // GT1[z] . AH(l)^T
+        }
+    }
+    J.a_row = J.m0;
+    J.b_row = J.n0;
+    return J;
+}
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait.  Returns false when the limit expired (raising the abort flag and
+// the device error) or when another role already aborted (unless `ignore_abort`).
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag, int32_t *err, int code,
+                          bool ignore_abort = false, uint64_t limit = WAIT_LIMIT_NS) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    for (uint32_t i = 1;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63) == 0) {
+            if (!ignore_abort && *abort_flag) return false;
+            if (gtimer() - t0 > limit) {
+                *abort_flag = 1;
+                atomicCAS(err, 0, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                          uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// K-major operand in a 64-byte swizzled layout: rows of 64 bytes, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(512 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
+}
+
+template <int F>
+__device__ __forceinline__ uint32_t idesc(bool negA) {
+    return (1u << 4) | (Cfg<F>::AB_FMT << 7) | (Cfg<F>::AB_FMT << 10) | ((negA ? 1u : 0u) << 13) |
+           ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+template <int F>
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    if constexpr (F == FMT_TF32X4) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::
+                "r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::
+                "r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 32 consecutive FP32 columns from tensor memory, waited on in the same asm.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ epilogue stores
+// Store 32 consecutive complex values of one row into a plane-major operand.
+template <int F>
+__device__ __forceinline__ void store_row32(void *base, size_t ps, size_t off, const float (&re)[32],
+                                            const float (&im)[32], int nvalid) {
+    if (nvalid == 32) {
+        if constexpr (F == FMT_BF16X4 || F == FMT_BF16X2) {
+            __nv_bfloat16 *p = (__nv_bfloat16 *)base + off;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    float x = re[8 * q + i], y = im[8 * q + i];
+                    rh[i] = __float2bfloat16_rn(x);
+                    ih[i] = __float2bfloat16_rn(y);
+                    rl[i] = __float2bfloat16_rn(x - __bfloat162float(rh[i]));
+                    il[i] = __float2bfloat16_rn(y - __bfloat162float(ih[i]));
+                }
+                if constexpr (F == FMT_BF16X4) {
+                    *(uint4 *)(p + 8 * q) = *(uint4 *)rh;
+                    *(uint4 *)(p + ps + 8 * q) = *(uint4 *)rl;
+                    *(uint4 *)(p + 2 * ps + 8 * q) = *(uint4 *)ih;
+                    *(uint4 *)(p + 3 * ps + 8 * q) = *(uint4 *)il;
+                } else {
+                    *(uint4 *)(p + 8 * q) = *(uint4 *)rh;
+                    *(uint4 *)(p + ps + 8 * q) = *(uint4 *)ih;
+                }
+            }
+        } else {
+            float *p = (float *)base + off;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float4 h, l, hi, li;
+                float *hp = &h.x, *lp = &l.x, *hip = &hi.x, *lip = &li.x;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float x = re[4 * q + i], y = im[4 * q + i];
+                    hp[i] = tf32_round(x);
+                    lp[i] = tf32_round(x - hp[i]);
+                    hip[i] = tf32_round(y);
+                    lip[i] = tf32_round(y - hip[i]);
+                }
+                *(float4 *)(p + 4 * q) = h;
+                *(float4 *)(p + ps + 4 * q) = l;
+                *(float4 *)(p + 2 * ps + 4 * q) = hi;
+                *(float4 *)(p + 3 * ps + 4 * q) = li;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < nvalid) store_cplx<F>(base, ps, off + i, re[i], im[i]);
+    }
+}
+
+// ------------------------------------------------------------------ the kernel
+template <int F>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+    using C = Cfg<F>;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *bars = (uint64_t *)(smem + C::STAGES * C::STAGE_BYTES);
+    // bars: full[S], empty[S], tfull[2], tempty[2], drain
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::STAGES, tfull0 = empty0 + 8 * C::STAGES,
+                   tempty0 = tfull0 + 16, drain = tempty0 + 16;
+    volatile int *abort_flag = (volatile int *)(bars + 2 * C::STAGES + 5);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * C::STAGES + 6);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, EPI_WARPS);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tmem_slot;
+    const int nk = (a.K + C::KB - 1) / C::KB;
+
+    if (warp == PRODUCER_WARP) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+                int g, rse, tile;
+                const int nj = decode_unit_jobs(a, u, g, rse, tile);
+                for (int j = 0; j < nj && ok; ++j) {
+                    const Job J = decode(a, u, j);
+                    for (int kb = 0; kb < nk; ++kb, ++it) {
+                        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+                        if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort_flag, a.err, 1)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
+                        mbar_expect_tx(full0 + 8 * s, C::STAGE_BYTES);
+                        tma_load4(st, &mapA, kb * C::KB, J.a_row, 0, J.a_batch, full0 + 8 * s);
+                        tma_load4(st + C::PL * PLANE_BYTES, &mapB, kb * C::KB, J.b_row, 0, J.b_batch, full0 + 8 * s);
+                    }
+                }
+            }
+            if (!ok) {
+                // let the copies already issued land before the CTA exits
+                const uint32_t n = it < (uint32_t)C::STAGES ? it : (uint32_t)C::STAGES;
+                for (uint32_t q = 0; q < n; ++q) {
+                    const uint32_t k = it - 1 - q, s = k % C::STAGES, ph = (k / C::STAGES) & 1;
+                    mbar_wait(full0 + 8 * s, ph, abort_flag, a.err, 2, true, 100000000ull);
+                }
+            }
+        }
+    } else if (warp == MMA_WARP) {
+        if (lane == 0) {
+            uint32_t it = 0, jt = 0;
+            bool ok = true;
+            const uint32_t id_pos = idesc<F>(false), id_neg = idesc<F>(true);
+            for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+                int g, rse, tile;
+                const int nj = decode_unit_jobs(a, u, g, rse, tile);
+                for (int j = 0; j < nj && ok; ++j, ++jt) {
+                    const uint32_t buf = jt & 1, tph = (jt >> 1) & 1;
+                    if (!mbar_wait(tempty0 + 8 * buf, tph ^ 1, abort_flag, a.err, 3)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dr = tbase + buf * 256, di = dr + 128;
+                    for (int kb = 0; kb < nk; ++kb, ++it) {
+                        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+                        if (!mbar_wait(full0 + 8 * s, ph, abort_flag, a.err, 4)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES), sb = sa + C::PL * PLANE_BYTES;
+#pragma unroll
+                        for (int ks = 0; ks < C::NKSTEP; ++ks) {
+                            const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
+                            const uint32_t ko = ks * 32;
+                            auto A = [&](int p) { return sdesc(sa + p * PLANE_BYTES + ko); };
+                            auto Bd = [&](int p) { return sdesc(sb + p * PLANE_BYTES + ko); };
+                            if constexpr (C::PL == 4) {
+                                // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
+                                mma<F>(dr, A(0), Bd(0), id_pos, first);
+                                mma<F>(dr, A(0), Bd(1), id_pos, 1);
+                                mma<F>(dr, A(1), Bd(0), id_pos, 1);
+                                mma<F>(dr, A(2), Bd(2), id_neg, 1);
+                                mma<F>(dr, A(2), Bd(3), id_neg, 1);
+                                mma<F>(dr, A(3), Bd(2), id_neg, 1);
+                                mma<F>(di, A(0), Bd(2), id_pos, first);
+                                mma<F>(di, A(0), Bd(3), id_pos, 1);
+                                mma<F>(di, A(1), Bd(2), id_pos, 1);
+                                mma<F>(di, A(2), Bd(0), id_pos, 1);
+                                mma<F>(di, A(2), Bd(1), id_pos, 1);
+                                mma<F>(di, A(3), Bd(0), id_pos, 1);
+                            } else {
+                                // planes: 0 re, 1 im
+                                mma<F>(dr, A(0), Bd(0), id_pos, first);
+                                mma<F>(dr, A(1), Bd(1), id_neg, 1);
+                                mma<F>(di, A(0), Bd(1), id_pos, first);
+                                mma<F>(di, A(1), Bd(0), id_pos, 1);
+                            }
+                        }
+                        mma_commit(empty0 + 8 * s);  // frees the stage once these MMAs have read it
+                    }
+                    if (!ok) break;
+                    mma_commit(tfull0 + 8 * buf);  // accumulators ready for the epilogue
+                }
+            }
+            // drain: every MMA issued by this thread has completed before tensor memory is freed
+            mma_commit(drain);
+            mbar_wait(drain, 0, abort_flag, a.err, 5, true, 100000000ull);
+        }
+    } else {
+        // ---------------- epilogue warps 0..7
+        const int q = warp & 3, h = warp >> 2;
+        const int row = 32 * q + lane;
+        uint32_t jt = 0;
+        bool ok = true;
+        float acc[64];
+#pragma unroll
+        for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+        for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+            int g = 0, rse = 0, tile = 0;
+            const int nj = decode_unit_jobs(a, u, g, rse, tile);
+            Job J{};
+            for (int j = 0; j < nj; ++j, ++jt) {
+                J = decode(a, u, j);
+                const uint32_t buf = jt & 1, tph = (jt >> 1) & 1;
+                // every lane waits; the warp proceeds only if all lanes saw the phase,
+                // so the warp-collective tensor-memory loads never diverge
+                const bool got = mbar_wait(tfull0 + 8 * buf, tph, abort_flag, a.err, 6);
+                if (!__all_sync(0xffffffffu, got)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const int m = J.m0 + row;
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int c0 = 64 * h + 32 * cc;
+                    const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + c0;
+                    float er[32], ei[32];
+                    tmem_ld32(ta, er);
+                    tmem_ld32(ta + 128, ei);
+                    const int n0 = J.n0 + c0;
+                    const int nvalid = min(32, a.N - n0);
+                    if (a.kind == KS2) {
+                        const float w = a.wnorm[(size_t)J.r * a.nl + J.l];
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) acc[32 * cc + i] = fmaf(w, er[i] * er[i] + ei[i] * ei[i], acc[32 * cc + i]);
+                    } else if (m < a.M && nvalid > 0) {
+                        if (a.kind == KGE) {
+                            // rows kx, columns ky: scale by 2 w_l F_s GI[e][bin(ky, kx)]
+                            const int s = J.se / a.ne, e = J.se % a.ne;
+                            const float c = 2.f * a.wnorm[(size_t)J.r * a.nl + J.l] * slot_ptr(a.prm, PFLUX, J.r)[s];
+                            const float *gi = a.GI + ((size_t)J.r * a.ne + e) * a.nd * a.nd + m / a.os;
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                const int ky = min(n0 + i, a.N - 1);
+                                const float f = c * gi[(ky / a.os) * a.nd];
+                                er[i] *= f;
+                                ei[i] *= f;
+                            }
+                        }
+                        if (a.kind == KGP) {
+                            // rows ny, columns nx: gphi = (2 pi / lambda) Im(G_P conj P)
+                            const float k2 = (float)(6.283185307179586476925286766559 / a.lam[J.l]);
+                            const size_t pps = (size_t)a.ni * a.ldi;
+                            const char *pb = (const char *)a.P + (size_t)J.b * C::PL * pps * C::ES;
+                            float *o = a.gphi + (size_t)J.b * a.ni * a.ni + (size_t)m * a.ni + n0;
+#pragma unroll
+                            for (int i = 0; i < 32; ++i) {
+                                if (i < nvalid) {
+                                    const float2 pv = load_cplx<F>(pb, pps, (size_t)m * a.ldi + n0 + i);
+                                    o[i] = k2 * (ei[i] * pv.x - er[i] * pv.y);
+                                }
+                            }
+                        } else {
+                            const int zb = (a.kind == KS1) ? J.b : J.z;
+                            char *ob = (char *)a.out + (size_t)zb * C::PL * a.out_ps * C::ES;
+                            store_row32<F>(ob, a.out_ps, (size_t)m * a.out_ld + n0, er, ei, nvalid);
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+            }
+            if (!ok) break;
+            if (a.kind == KS2) {
+                const int m = J.m0 + row;
+                if (m < a.M) {
+                    float *o = a.Is + ((size_t)g * a.Rnse + rse) * a.no * a.no + (size_t)m * a.no;
+#pragma unroll
+                    for (int i = 0; i < 64; ++i) {
+                        const int n = J.n0 + 64 * h + i;
+                        if (n < a.N) o[n] = acc[i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == MMA_WARP) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+bool make_map(dlx_plan *p, Operand &o, std::string *why) {
+    auto enc = get_encoder();
+    if (!enc) {
+        *why = "cuTensorMapEncodeTiled unavailable";
+        return false;
+    }
+    const int es = p->esz, PL = p->planes;
+    cuuint64_t dims[4] = {(cuuint64_t)o.ld, (cuuint64_t)o.rows, (cuuint64_t)PL, (cuuint64_t)o.batch};
+    cuuint64_t strides[3] = {(cuuint64_t)o.ld * es, (cuuint64_t)o.rows * o.ld * es,
+                             (cuuint64_t)PL * o.rows * o.ld * es};
+    cuuint32_t box[4] = {(cuuint32_t)(64 / es), 128u, (cuuint32_t)PL, 1u};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUtensorMapDataType dt =
+        (p->fmt == FMT_TF32X4) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUresult r = enc(&o.tmap, dt, 4, o.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+        return false;
+    }
+    return true;
+}
+
+template <int F>
+cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, TcArgs &a, cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<F>::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    a.err = p->err;
+    a.nl = p->nl;
+    a.nse = p->nse;
+    a.B = p->B;
+    a.ne = p->ne;
+    a.nd = p->nd;
+    a.os = p->os;
+    a.ni = p->ni;
+    a.no = p->no;
+    a.ldi = p->ldi;
+    a.ldo = p->ldo;
+    a.G = p->G;
+    a.wnorm = p->wnorm;
+    a.lam = p->lam_d;
+    a.tm = (a.M + BM - 1) / BM;
+    a.tn = (a.N + BN - 1) / BN;
+    if (a.units <= 0) return cudaSuccess;
+    const int grid = std::min(a.units, p->sm_count);
+    static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
+    KScope ks(p, cls_of[a.kind], 1, st);
+    k_tc_gemm<F><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, a);
+    return cudaGetLastError();
+}
+
+template <int F>
+cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
+    TcArgs a{};
+    // stage 1: T1t[b] = A(l) . P[b]^T   (M = No rows kx, N = Ni cols ny, K = Ni)
+    a.kind = KS1;
+    a.M = p->no;
+    a.N = p->ni;
+    a.K = p->ni;
+    a.out = p->T1t.ptr;
+    a.out_ld = p->ldi;
+    a.out_ps = (size_t)p->no * p->ldi;
+    a.units = R * p->B * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
+    cudaError_t e = launch<F>(p, p->amat, p->P, a, st);
+    if (e != cudaSuccess) return e;
+    // stage 2 + intensity: Is[g][rse] = sum_l w |A(l) . T1t[b]^T|^2  (M = N = No, K = Ni)
+    TcArgs c{};
+    c.kind = KS2;
+    c.M = p->no;
+    c.N = p->no;
+    c.K = p->ni;
+    c.Is = p->Is;
+    c.Rnse = R * p->nse;
+    c.units = c.Rnse * p->G * ((p->no + BM - 1) / BM) * ((p->no + BN - 1) / BN);
+    return launch<F>(p, p->amat, p->T1t, c, st);
+}
+
+template <int F>
+cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st) {
+    const int tmo = (p->no + BM - 1) / BM, tmi = (p->ni + BM - 1) / BM;
+    TcArgs a{};
+    // recomputed field and dL/dE: GEt[z][kx][ky] = 2 w F GI o (T1t[b] . A(l)^T)
+    a.kind = KGE;
+    a.M = p->no;
+    a.N = p->no;
+    a.K = p->ni;
+    a.b0 = b0;
+    a.prm = prm;
+    a.GI = p->GI;
+    a.out = p->GEt.ptr;
+    a.out_ld = p->ldo;
+    a.out_ps = (size_t)p->no * p->ldo;
+    a.units = nb * tmo * tmo;
+    cudaError_t e = launch<F>(p, p->T1t, p->amat, a, st);
+    if (e != cudaSuccess) return e;
+    // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No)
+    TcArgs b{};
+    b.kind = KGT1;
+    b.M = p->ni;
+    b.N = p->no;
+    b.K = p->no;
+    b.b0 = b0;
+    b.out = p->GT1.ptr;
+    b.out_ld = p->ldo;
+    b.out_ps = (size_t)p->ni * p->ldo;
+    b.units = nb * tmi * tmo;
+    e = launch<F>(p, p->amatH, p->GEt, b, st);
+    if (e != cudaSuccess) return e;
+    // adjoint stage 1^T + phase gradient: gphi[b] = (2 pi/lambda) Im((GT1[z] . AH(l)^T) conj P[b])
+    TcArgs c{};
+    c.kind = KGP;
+    c.M = p->ni;
+    c.N = p->ni;
+    c.K = p->no;
+    c.b0 = b0;
+    c.P = p->P.ptr;
+    c.gphi = p->gphi;
+    c.units = nb * tmi * tmi;
+    return launch<F>(p, p->GT1, p->amatH, c, st);
+}
+
+}  // namespace
+
+int tc_supported(const dlx_plan *p, std::string *why) {
+    if (p->fmt == FMT_F32) {
+        *why = "FP32 form runs on CUDA cores";
+        return 0;
+    }
+    return 1;
+}
+
+int tc_make_maps(dlx_plan *p, std::string *why) {
+    return make_map(p, p->amat, why) && make_map(p, p->amatH, why) && make_map(p, p->P, why) &&
+           make_map(p, p->T1t, why) && make_map(p, p->GEt, why) && make_map(p, p->GT1, why);
+}
+
+cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st) {
+    switch (p->fmt) {
+        case FMT_BF16X4: return forward_impl<FMT_BF16X4>(p, R, st);
+        case FMT_BF16X2: return forward_impl<FMT_BF16X2>(p, R, st);
+        case FMT_TF32X4: return forward_impl<FMT_TF32X4>(p, R, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t tc_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st) {
+    switch (p->fmt) {
+        case FMT_BF16X4: return adjoint_impl<FMT_BF16X4>(p, prm, b0, nb, st);
+        case FMT_BF16X2: return adjoint_impl<FMT_BF16X2>(p, prm, b0, nb, st);
+        case FMT_TF32X4: return adjoint_impl<FMT_TF32X4>(p, prm, b0, nb, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace dlx
