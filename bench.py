@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "tf32x3", "bf16", "fp32"])
+    ap.add_argument("--form", default="bf16x4", choices=["bf16x4", "bf16x3", "tf32x3", "bf16", "fp32"])
     ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
     ap.add_argument("--workload", default="binary")
     ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side FP32 / other-form lines")
@@ -315,8 +315,10 @@ def main():
         "adjoint_field": 8.0 * B * no * no * ni, "adjoint_stage2T": 8.0 * B * ni * no * no,
         "adjoint_stage1T": 8.0 * B * ni * ni * no,
     }
-    split = {"bf16x3": 3.0, "tf32x3": 3.0, "bf16": 1.0, "fp32": 1.0}[args.form]
-    nom_ratio = {"bf16x3": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
+    # tensor instructions per algorithmic product: forward contractions of BF16x4 take 4, its adjoint 3
+    split = {"bf16x4": 3.0 if dom.startswith("adjoint") else 4.0, "bf16x3": 3.0, "tf32x3": 3.0, "bf16": 1.0,
+             "fp32": 1.0}[args.form]
+    nom_ratio = {"bf16x4": 1.0, "bf16x3": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
     roof = None
     if dom in alg:
         per_launch_ms = classes[dom]["ms"] / max(classes[dom]["events"], 1)
@@ -337,7 +339,8 @@ def main():
 
     line = dict(metric=METRIC, value=evals_per_s, unit="evals/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype={"bf16x3": "bf16x3 split (fp32 accumulate)", "tf32x3": "tf32x3 split (fp32 accumulate)",
+                dtype={"bf16x4": "bf16x4 split (fp32 accumulate)", "bf16x3": "bf16x3 split (fp32 accumulate)",
+                       "tf32x3": "tf32x3 split (fp32 accumulate)",
                        "bf16": "bf16 (fp32 accumulate)", "fp32": "f32"}[args.form],
                 data="synthetic",
                 config=dict(workload=WORKLOAD, form=args.form, psfs_per_eval=B, pupil=ni, mft_out=no,
@@ -359,7 +362,7 @@ def main():
 
     if not args.no_forms and rank == 0:
         forms = {}
-        for f in ("fp32", "tf32x3", "bf16"):
+        for f in ("fp32", "bf16x3", "tf32x3", "bf16"):
             if f == args.form:
                 continue
             try:

@@ -123,7 +123,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     for (int l = 0; l < d->n_lambda; ++l)
         if (!(d->lambda_m[l] > 0) || !std::isfinite(d->lambda_m[l]))
             return fail(DLX_ERR_INVALID_ARG, "wavelengths must be finite and > 0");
-    if (d->precision < DLX_FP32_SIMT || d->precision > DLX_BF16) return fail(DLX_ERR_INVALID_ARG, "bad precision");
+    if (d->precision < DLX_FP32_SIMT || d->precision > DLX_BF16X4) return fail(DLX_ERR_INVALID_ARG, "bad precision");
     if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 8 sources per plan");
     const long long no_ll = (long long)d->n_det * d->oversample;
     if (d->n_pupil > 8192 || no_ll > 16384) return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and n_det*oversample <= 16384");
@@ -210,21 +210,29 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->red_blocks = std::max(1, std::min((int)((np + 255) / 256), std::max(1, p->sm_count * 2 / R_max)));
     if (e == cudaSuccess) e = plan_alloc(p, &p->lam_d, sizeof(double) * p->nl);
     if (e == cudaSuccess) e = plan_alloc(p, &p->wnorm, sizeof(float) * p->nl * R_max);
-    if (e == cudaSuccess) e = plan_alloc(p, &p->pscale, sizeof(double) * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->pscale, sizeof(float) * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->invlam, sizeof(float) * p->nl);
     if (e == cudaSuccess) e = plan_alloc(p, &p->tilt, sizeof(float2) * Bt * 2 * p->ni);
     if (e == cudaSuccess) e = plan_alloc(p, &p->opd, sizeof(float) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->Is, sizeof(float) * (size_t)p->G * p->nse * R_max * nq);
     if (e == cudaSuccess) e = plan_alloc(p, &p->GI, sizeof(float) * p->ne * np * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->model_tmp, sizeof(float) * p->ne * np * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx);
-    if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(double) * npx * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(float2) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
-    if (e == cudaSuccess) e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt);
+    const size_t nslice = (npx + 2047) / 2048;  // slices of the sliced gradient reductions
+    if (e == cudaSuccess) e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * nslice);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->zpart, sizeof(double) * R_max * std::max(1, p->nz) * nslice);
     if (e == cudaSuccess) e = plan_alloc(p, &p->err, sizeof(int32_t));
     if (e == cudaSuccess) e = plan_alloc(p, &p->clamped, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMemset(p->clamped, 0, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemcpy(p->lam_d, p->lambdas.data(), sizeof(double) * p->nl, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<float> inv(p->nl);
+        for (int l = 0; l < p->nl; ++l) inv[l] = (float)(1.0 / p->lambdas[l]);
+        e = cudaMemcpy(p->invlam, inv.data(), sizeof(float) * p->nl, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = launch_mft_matrices(p, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {

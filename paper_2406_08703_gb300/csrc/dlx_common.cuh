@@ -32,6 +32,7 @@ inline int fmt_of_prec(int prec) {
         case DLX_FP32_SIMT: return FMT_F32;
         case DLX_TF32X3: return FMT_TF32X4;
         case DLX_BF16X3: return FMT_BF16X4;
+        case DLX_BF16X4: return FMT_BF16X4;
         default: return FMT_BF16X2;
     }
 }
@@ -140,17 +141,19 @@ struct dlx_plan {
     dlx::Operand amat, amatH, P, T1t, GEt, GT1;
     double *lam_d = nullptr;   // [nl]
     float *wnorm = nullptr;    // [R][nl] weights / sum(weights)
-    double *pscale = nullptr;  // [R] 1/sqrt(sum T^2)
+    float *pscale = nullptr;   // [R] 1/sqrt(sum T^2)
+    float *invlam = nullptr;   // [nl] 1/lambda (FP32)
     float2 *tilt = nullptr;    // [R*B][2][ni]
     float *opd = nullptr;      // [R][ni*ni]
     float *Is = nullptr;       // [G][R*nse][no][no] per-source intensity partials
     float *GI = nullptr;       // [R][ne][nd*nd] FF * dL/dm
     float *model_tmp = nullptr;// [R][ne][nd*nd]
     float *gphi = nullptr;     // [R*B][ni*ni] (2 pi / lambda) dL/dphase
-    double *gopd = nullptr;    // [R][ni*ni]
+    float2 *gopd = nullptr;    // [R][ni*ni] g_OPD as a compensated (hi, lo) FP32 pair
     double *red = nullptr;     // [R][red_blocks][1 + 8] reduction partials
     int red_blocks = 0;
-    double *pos_part = nullptr;// [R*B][2]
+    double *pos_part = nullptr;// [R*B][slices][2] position-moment partials
+    double *zpart = nullptr;   // [R][n_zern][slices] Zernike-gradient partials
     int32_t *err = nullptr;    // device error flag
     unsigned long long *clamped = nullptr;
     size_t workspace = 0;

@@ -1,23 +1,57 @@
 // Memory-bound stages of the path: MFT matrix generation, OPD, tilt tables,
-// phasor build, binning + flat field + Poisson NLL, the FP64 gradient
-// reductions and Adam.  Each is a coalesced grid-stride kernel over all
-// active slots; every reduction is a fixed-order block tree in FP64 (no
-// floating-point atomics), so results do not depend on scheduling or on
-// which other slots share the launch.
+// phasor build, binning + flat field + Poisson NLL, the gradient reductions
+// and Adam.  Each is a coalesced grid-stride kernel over all active slots.
+//
+// Reductions.  FP64 arithmetic on this GPU runs at a small fraction of the
+// FP32 rate, so per-element work stays in FP32 and long sums are carried as
+// compensated (hi, lo) FP32 pairs ("double-float": every addition is an exact
+// two-sum, about 44 significant bits); FP64 is used only to combine the few
+// per-block partials and in the phase-argument reductions, where an FP32
+// argument would lose accuracy.  Every reduction has a fixed order (no
+// floating-point atomics), so results do not depend on scheduling or on which
+// other slots share the launch.
 #include <algorithm>
 
 #include "dlx_common.cuh"
 
 namespace dlx {
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// ---------------------------------------------------------------------------
+// compensated FP32 pairs
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    const float s = a.hi + b.hi, bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ df df_add(df a, float b) {
+    const float s = a.hi + b, bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b - bb);
+    e += a.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df warp_sum(df v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        df w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = df_add(v, w);
+    }
     return v;
 }
 
-// Block-wide sums of NV doubles per thread in a fixed order; valid in warp 0.
+// Block-wide sums of NV compensated pairs in a fixed order; valid in warp 0.
 template <int NV>
-__device__ void block_sum(double (&v)[NV], double *sh /* [32][NV] */) {
+__device__ void block_sum(df (&v)[NV], df *sh /* [32][NV] */) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
@@ -27,7 +61,7 @@ __device__ void block_sum(double (&v)[NV], double *sh /* [32][NV] */) {
     __syncthreads();
     if (wid == 0) {
 #pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] = warp_sum(lane < nw ? sh[lane * NV + i] : 0.0);
+        for (int i = 0; i < NV; ++i) v[i] = warp_sum(lane < nw ? sh[lane * NV + i] : df{0.f, 0.f});
     }
     __syncthreads();
 }
@@ -36,7 +70,8 @@ __device__ void block_sum(double (&v)[NV], double *sh /* [32][NV] */) {
 // MFT matrices (Sec. 3, two-sided MFT): A[l][k][n] = sqrt(c) exp(-2 pi i t),
 // t = (n - (Ni-1)/2)(k - (No-1)/2) c, c = dx du / lambda_l.  The argument is
 // formed and reduced to r = t - rint(t) in FP64 before sin/cos, so the phase
-// error does not grow with |t|.  AH[l][n][k] = conj(A[l][k][n]).
+// error does not grow with |t|.  AH[l][n][k] = conj(A[l][k][n]).  Built once
+// per plan.
 template <int F>
 __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, int nl, int ni, int no, int ldi, int ldo,
                                double dx, double du) {
@@ -73,17 +108,30 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // Per slot: pupil normalisation of BasisOptic(normalise=True), 1/sqrt(sum T^2),
 // and the normalised spectral weights w_l / sum w.  One block per slot.
-__global__ void k_norms(DevParams prm, int npx, int nl, double *pscale, float *wnorm) {
-    __shared__ double sh[32];
+__global__ void k_norms(DevParams prm, int npx, int nl, float *pscale, float *wnorm) {
+    __shared__ df sh[32];
     const int r = blockIdx.x;
     const float *T = slot_ptr(prm, PT, r), *w = slot_ptr(prm, PW, r);
-    double v[1] = {0.0};
-    for (int i = threadIdx.x; i < npx; i += blockDim.x) v[0] += (double)T[i] * (double)T[i];
+    df v[1] = {{0.f, 0.f}};
+    int i = threadIdx.x;
+    for (; i + 7 * (int)blockDim.x < npx; i += 8 * blockDim.x) {
+        float t[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) t[q] = __ldg(T + i + q * blockDim.x);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[0] = df_add(v[0], t[q] * t[q]);
+    }
+    for (; i < npx; i += blockDim.x) v[0] = df_add(v[0], T[i] * T[i]);
     block_sum<1>(v, sh);
-    if (threadIdx.x == 0) pscale[r] = 1.0 / sqrt(v[0]);
-    double ws = 0;
-    for (int l = 0; l < nl; ++l) ws += (double)w[l];
-    for (int l = threadIdx.x; l < nl; l += blockDim.x) wnorm[(size_t)r * nl + l] = (float)((double)w[l] / ws);
+    __shared__ float s_scale;
+    if (threadIdx.x == 0) {
+        s_scale = (float)(1.0 / sqrt(df_to_double(v[0])));
+        pscale[r] = s_scale;
+    }
+    df ws{0.f, 0.f};
+    for (int l = 0; l < nl; ++l) ws = df_add(ws, w[l]);
+    const float wsum = ws.hi + ws.lo;
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) wnorm[(size_t)r * nl + l] = w[l] / wsum;
 }
 
 // OPD = OPD_fixed + sum_j c_j Z_j + OPD_pix (Sec. 3: BasisOptic coefficients on a
@@ -104,7 +152,7 @@ __global__ void k_opd(DevParams prm, int nz, int npx, float *__restrict__ opd) {
 }
 
 // Separable tilt factors exp(i 2 pi x_n theta / lambda) per PSF and axis, with
-// the argument reduced in FP64.  theta = pos[s] + dither[e].
+// the argument reduced in FP64 (B * 2 * Ni values).  theta = pos[s] + dither[e].
 __global__ void k_tilt(DevParams prm, const double *lam, int nbt, int B, int nse, int ne, int ni, double dx,
                        float2 *tilt) {
     const double cN = 0.5 * (ni - 1);
@@ -123,20 +171,21 @@ __global__ void k_tilt(DevParams prm, const double *lam, int nbt, int B, int nse
 }
 
 // Pupil phasor P = T_hat exp(i 2 pi OPD / lambda) ex[nx] ey[ny] (Sec. 3), written
-// in the operand form of the contractions.
+// in the operand form of the contractions.  OPD / lambda is below one cycle for
+// the aberrations of interest, so FP32 is exact enough there.
 template <int F>
 __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
-                         const double *__restrict__ lam, const double *__restrict__ pscale, int nbt, int B, int nse,
+                         const float *__restrict__ invlam, const float *__restrict__ pscale, int nbt, int B, int nse,
                          int ni, int ldi, void *P) {
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F);
     const size_t total = (size_t)nbt * npx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         int bg = (int)(i / npx), n = (int)(i % npx);
         int r = bg / B, l = (bg % B) / nse, ny = n / ni, nx = n % ni;
-        float t = slot_ptr(prm, PT, r)[n] * (float)pscale[r];
+        float t = slot_ptr(prm, PT, r)[n] * pscale[r];
         float re = 0.f, im = 0.f;
         if (t != 0.f) {
-            float ph = opd[(size_t)r * npx + n] * (float)(1.0 / lam[l]);
+            float ph = opd[(size_t)r * npx + n] * invlam[l];
             ph -= rintf(ph);
             float sn, cs;
             sincospif(2.f * ph, &sn, &cs);
@@ -162,7 +211,7 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     size_t total = (size_t)nbt * npx;
     int pb = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
     DLX_FMT_DISPATCH(p->fmt, F,
-                     k_phasor<F><<<pb, 256, 0, st>>>(prm, p->opd, p->tilt, p->lam_d, p->pscale, nbt, p->B, p->nse,
+                     k_phasor<F><<<pb, 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->pscale, nbt, p->B, p->nse,
                                                      p->ni, p->ldi, p->P.ptr));
     return cudaGetLastError();
 }
@@ -174,20 +223,20 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
 //   m = FF sum_s F_s B_{e,s};  L += m - d ln max(m, 1e-30);
 //   g_m = 1 - d / max(m, 1e-30);  GI = FF g_m;  dL/dFF[p] = sum_e g_m B_e;
 //   flux partials sum_p FF g_m B_{e,s}.
-// Per-block FP64 partials go to red[r][blk][1 + kMaxSrc].
+// Per-block partials (converted to FP64 once) go to red[r][blk][1 + kMaxSrc].
 __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os,
                           int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped) {
-    __shared__ double sh[32 * (1 + kMaxSrc)];
+    __shared__ df sh[32 * (1 + kMaxSrc)];
     const int np = nd * nd, r = blockIdx.y;
     const float *flux = slot_ptr(prm, PFLUX, r), *flat = slot_ptr(prm, PFLAT, r);
     const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
     float *mod = model + (size_t)r * mstride;
     float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
-    double acc[1 + kMaxSrc];
+    df acc[1 + kMaxSrc];
 #pragma unroll
-    for (int i = 0; i < 1 + kMaxSrc; ++i) acc[i] = 0.0;
+    for (int i = 0; i < 1 + kMaxSrc; ++i) acc[i] = {0.f, 0.f};
     unsigned long long nclamp = 0;
     const size_t plane = (size_t)no * no;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
@@ -223,20 +272,22 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                     mc = 1e-30f;
                     ++nclamp;
                 }
-                acc[0] += (double)m - (double)d * (double)logf(mc);
+                acc[0] = df_add(acc[0], m);
+                acc[0] = df_add(acc[0], -d * logf(mc));
                 const float gm = 1.f - d / mc;
                 GI[((size_t)r * ne + e) * np + p] = ff * gm;
                 dff = fmaf(gm, btot, dff);
 #pragma unroll
                 for (int s = 0; s < kMaxSrc; ++s)
-                    if (s < ns) acc[1 + s] += (double)(ff * gm) * (double)bs[s];
+                    if (s < ns) acc[1 + s] = df_add(acc[1 + s], (ff * gm) * bs[s]);
             }
         }
         if (dat && dflat) dflat[p] = dff;
     }
     block_sum<1 + kMaxSrc>(acc, sh);
     if (threadIdx.x == 0)
-        for (int i = 0; i < 1 + kMaxSrc; ++i) red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = acc[i];
+        for (int i = 0; i < 1 + kMaxSrc; ++i)
+            red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = df_to_double(acc[i]);
     if (dat && nclamp) atomicAdd(clamped, nclamp);  // integer count: order-independent
 }
 
@@ -275,19 +326,19 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
     return cudaGetLastError();
 }
 
-// Fixed-order sum of the per-block partials of slot r = blockIdx.x: loss[r] and dL/dF_s.
+// Fixed-order sum of the per-block partials of slot r = blockIdx.x: loss[r] and
+// dL/dF_s.  One warp per quantity; FP64 over a few hundred partials.
 __global__ void k_finalize_loss(const double *red, int nblk, int ns, double *loss, DevGrads g) {
-    __shared__ double sh[32 * (1 + kMaxSrc)];
-    const int r = blockIdx.x;
-    double v[1 + kMaxSrc];
-    for (int i = 0; i < 1 + kMaxSrc; ++i) v[i] = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x)
-        for (int i = 0; i < 1 + ns; ++i) v[i] += red[((size_t)r * nblk + b) * (1 + kMaxSrc) + i];
-    block_sum<1 + kMaxSrc>(v, sh);
-    if (threadIdx.x == 0) {
-        if (loss) loss[r] = v[0];
-        if (g.p[GFLUX])
-            for (int s = 0; s < ns; ++s) g.p[GFLUX][(size_t)r * g.s[GFLUX] + s] = (float)v[1 + s];
+    const int r = blockIdx.x, i = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (i > ns) return;
+    double v = 0.0;
+    for (int b = lane; b < nblk; b += 32) v += red[((size_t)r * nblk + b) * (1 + kMaxSrc) + i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane != 0) return;
+    if (i == 0) {
+        if (loss) loss[r] = v;
+    } else if (g.p[GFLUX]) {
+        g.p[GFLUX][(size_t)r * g.s[GFLUX] + (i - 1)] = (float)v;
     }
 }
 
@@ -295,82 +346,131 @@ cudaError_t launch_finalize_loss(dlx_plan *p, int R, double *loss, const DevGrad
     DevGrads gg{};
     if (g) gg = *g;
     KScope ks(p, KC_LOSS, 1, st);
-    k_finalize_loss<<<R, 256, 0, st>>>(p->red, p->red_blocks, p->ns, loss, gg);
+    k_finalize_loss<<<R, 32 * (1 + p->ns), 0, st>>>(p->red, p->red_blocks, p->ns, loss, gg);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
-// Gradient reductions (FP64).  gphi[bg][n] already carries 2 pi / lambda_l.
-// g_OPD[r][n] = sum_{b in slot r} gphi[b][n];  dL/dOPD_pix = g_OPD.
-__global__ void k_gopd(const float *__restrict__ gphi, int R, int B, int npx, double *__restrict__ gopd, DevGrads g) {
+// Gradient reductions.  gphi[bg][n] already carries 2 pi / lambda_l.  Loads are
+// issued eight at a time ahead of the compensated additions, and long sums are
+// split over many blocks (slices of RED_SLICE pupil pixels), so no kernel waits
+// on one memory latency per element.
+constexpr int RED_SLICE = 2048;  // pupil pixels per block in the sliced reductions (256 threads x 8)
+
+// g_OPD[r][n] = sum_{b in slot r} gphi[b][n] (compensated);  dL/dOPD_pix = g_OPD.
+__global__ void k_gopd(const float *__restrict__ gphi, int R, int B, int npx, float2 *__restrict__ gopd, DevGrads g) {
     const size_t total = (size_t)R * npx;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int r = (int)(i / npx), n = (int)(i % npx);
-        double acc = 0.0;
-        for (int b = 0; b < B; ++b) acc += (double)gphi[((size_t)r * B + b) * npx + n];
-        gopd[i] = acc;
-        if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = (float)acc;
+        const float *src = gphi + (size_t)r * B * npx + n;
+        df acc{0.f, 0.f};
+        int b = 0;
+        for (; b + 8 <= B; b += 8) {
+            float v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __ldg(src + (size_t)(b + q) * npx);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc = df_add(acc, v[q]);
+        }
+        for (; b < B; ++b) acc = df_add(acc, __ldg(src + (size_t)b * npx));
+        gopd[i] = make_float2(acc.hi, acc.lo);
+        if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = acc.hi + acc.lo;
     }
 }
 
-// Per-PSF position moments: sum_n gphi[bg][n] x_n and y_n.  One block per PSF.
-__global__ void k_pos_moments(const float *__restrict__ gphi, int ni, double dx, double *part) {
-    __shared__ double sh[64];
-    const int b = blockIdx.x, npx = ni * ni;
-    const double cN = 0.5 * (ni - 1);
-    double v[2] = {0.0, 0.0};
-    for (int n = threadIdx.x; n < npx; n += blockDim.x) {
-        double gv = (double)gphi[(size_t)b * npx + n];
-        v[0] += gv * (((double)(n % ni) - cN) * dx);
-        v[1] += gv * (((double)(n / ni) - cN) * dx);
+// Position moments of one PSF over one slice of the pupil: sum_n gphi[bg][n] x_n
+// and y_n.  grid (n_slices, R * B); partials in part[bg][slice][2].
+__global__ void k_pos_moments(const float *__restrict__ gphi, int ni, float dx, double *part) {
+    __shared__ df sh[64];
+    const int slice = blockIdx.x, b = blockIdx.y, npx = ni * ni;
+    const float cN = 0.5f * (ni - 1);
+    df v[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    const int n0 = slice * RED_SLICE;
+    float gv[8];
+    int nn[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        nn[q] = n0 + q * 256 + threadIdx.x;
+        gv[q] = nn[q] < npx ? __ldg(gphi + (size_t)b * npx + nn[q]) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int ny = nn[q] / ni, nx = nn[q] - ny * ni;
+        v[0] = df_add(v[0], gv[q] * (((float)nx - cN) * dx));
+        v[1] = df_add(v[1], gv[q] * (((float)ny - cN) * dx));
     }
     block_sum<2>(v, sh);
     if (threadIdx.x == 0) {
-        part[2 * (size_t)b] = v[0];
-        part[2 * (size_t)b + 1] = v[1];
+        double *o = part + ((size_t)b * gridDim.x + slice) * 2;
+        o[0] = df_to_double(v[0]);
+        o[1] = df_to_double(v[1]);
     }
 }
 
-// dL/dtheta_s = sum over wavelengths and exposures of the moments of source s (slot r = blockIdx.x).
-__global__ void k_pos_final(const double *part, int B, int nl, int ns, int ne, DevGrads g) {
-    const int s = threadIdx.x, r = blockIdx.x;
-    if (s >= ns) return;
-    double ax = 0, ay = 0;
-    for (int l = 0; l < nl; ++l)
-        for (int e = 0; e < ne; ++e) {
-            size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
-            ax += part[2 * b];
-            ay += part[2 * b + 1];
-        }
-    float *d = g.p[GPOS] + (size_t)r * g.s[GPOS];
-    d[2 * s] = (float)ax;
-    d[2 * s + 1] = (float)ay;
+// dL/dtheta_s = sum over wavelengths, exposures and slices of the moments of
+// source s.  One warp per (slot, source, axis); fixed order.
+__global__ void k_pos_final(const double *part, int nslice, int B, int nl, int ns, int ne, DevGrads g) {
+    const int r = blockIdx.x, s = blockIdx.y, ax = blockIdx.z, lane = threadIdx.x;
+    const int nt = nl * ne * nslice;
+    double v = 0.0;
+    for (int t = lane; t < nt; t += 32) {
+        const int sl = t % nslice, le = t / nslice, l = le / ne, e = le % ne;
+        const size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
+        v += part[(b * nslice + sl) * 2 + ax];
+    }
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + ax] = (float)v;
 }
 
-// dL/dc_j = <Z_j, g_OPD>.  grid (n_zern, R).
-__global__ void k_zern_grad(DevParams prm, const double *__restrict__ gopd, int npx, DevGrads g) {
-    __shared__ double sh[32];
-    const int j = blockIdx.x, r = blockIdx.y;
+// dL/dc_j = <Z_j, g_OPD> over one slice of the pupil.  grid (n_slices, n_zern, R);
+// partials in zpart[r][j][slice].
+__global__ void k_zern_partial(DevParams prm, const float2 *__restrict__ gopd, int npx, double *zpart) {
+    __shared__ df sh[32];
+    const int slice = blockIdx.x, j = blockIdx.y, r = blockIdx.z;
     const float *basis = slot_ptr(prm, PBASIS, r) + (size_t)j * npx;
-    const double *go = gopd + (size_t)r * npx;
-    double v[1] = {0.0};
-    for (int n = threadIdx.x; n < npx; n += blockDim.x) v[0] += (double)basis[n] * go[n];
+    const float2 *go = gopd + (size_t)r * npx;
+    const int n0 = slice * RED_SLICE;
+    float z[8];
+    float2 gv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int n = n0 + q * 256 + threadIdx.x;
+        z[q] = n < npx ? __ldg(basis + n) : 0.f;
+        gv[q] = n < npx ? go[n] : make_float2(0.f, 0.f);
+    }
+    df v[1] = {{0.f, 0.f}};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        v[0] = df_add(v[0], z[q] * gv[q].x);
+        v[0] = df_add(v[0], z[q] * gv[q].y);
+    }
     block_sum<1>(v, sh);
-    if (threadIdx.x == 0) g.p[GZERN][(size_t)r * g.s[GZERN] + j] = (float)v[0];
+    if (threadIdx.x == 0) zpart[((size_t)r * gridDim.y + j) * gridDim.x + slice] = df_to_double(v[0]);
+}
+
+__global__ void k_zern_final(const double *zpart, int nslice, int nz, DevGrads g) {
+    const int j = blockIdx.x, r = blockIdx.y, lane = threadIdx.x;
+    double v = 0.0;
+    for (int t = lane; t < nslice; t += 32) v += zpart[((size_t)r * nz + j) * nslice + t];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) g.p[GZERN][(size_t)r * g.s[GZERN] + j] = (float)v;
 }
 
 cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st) {
-    const int npx = p->ni * p->ni;
+    const int npx = p->ni * p->ni, nslice = (npx + RED_SLICE - 1) / RED_SLICE;
     DevGrads gg{};
     if (g) gg = *g;
     int blocks = (int)std::min<size_t>(((size_t)R * npx + 255) / 256, (size_t)p->sm_count * 8);
-    KScope ks(p, KC_GRAD, 1 + (gg.p[GPOS] ? 2 : 0) + ((gg.p[GZERN] && p->nz > 0) ? 1 : 0), st);
+    KScope ks(p, KC_GRAD, 1 + (gg.p[GPOS] ? 2 : 0) + ((gg.p[GZERN] && p->nz > 0) ? 2 : 0), st);
     k_gopd<<<blocks, 256, 0, st>>>(p->gphi, R, p->B, npx, p->gopd, gg);
     if (gg.p[GPOS]) {
-        k_pos_moments<<<R * p->B, 256, 0, st>>>(p->gphi, p->ni, p->dx, p->pos_part);
-        k_pos_final<<<R, 32 * ((p->ns + 31) / 32), 0, st>>>(p->pos_part, p->B, p->nl, p->ns, p->ne, gg);
+        k_pos_moments<<<dim3(nslice, R * p->B), 256, 0, st>>>(p->gphi, p->ni, (float)p->dx, p->pos_part);
+        k_pos_final<<<dim3(R, p->ns, 2), 32, 0, st>>>(p->pos_part, nslice, p->B, p->nl, p->ns, p->ne, gg);
     }
-    if (gg.p[GZERN] && p->nz > 0) k_zern_grad<<<dim3(p->nz, R), 256, 0, st>>>(prm, p->gopd, npx, gg);
+    if (gg.p[GZERN] && p->nz > 0) {
+        k_zern_partial<<<dim3(nslice, p->nz, R), 256, 0, st>>>(prm, p->gopd, npx, p->zpart);
+        k_zern_final<<<dim3(p->nz, R), 32, 0, st>>>(p->zpart, nslice, p->nz, gg);
+    }
     return cudaGetLastError();
 }
 

@@ -284,10 +284,21 @@ __device__ __forceinline__ void store_row32(void *base, size_t ps, size_t off, c
 }
 
 // ------------------------------------------------------------------ the kernel
-template <int F>
+// Accumulation modes.  FAST: two accumulators (Er, Ei), double-buffered, three
+// split products.  SPLIT3 / SPLIT4: the hi*hi products and the small correction
+// products go to separate accumulators (Er_hh, Ei_hh, Er_c, Ei_c; one buffer),
+// so the accumulator that carries the large values takes two instructions per
+// 16-wide k step instead of six -- the tensor core's FP32 accumulation loses a
+// fraction of an ulp towards zero per instruction, and at a PSF peak those
+// losses add up coherently.  SPLIT4 also adds the lo*lo product, whose omission
+// biases coherent sums of conjugate pairs upwards by about 2^-16.
+enum AccMode { FAST = 0, SPLIT3 = 1, SPLIT4 = 2 };
+
+template <int F, int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
     using C = Cfg<F>;
+    constexpr uint32_t NBUF = (MODE == FAST) ? 2 : 1;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *bars = (uint64_t *)(smem + C::STAGES * C::STAGE_BYTES);
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 int g, rse, tile;
                 const int nj = decode_unit_jobs(a, u, g, rse, tile);
                 for (int j = 0; j < nj && ok; ++j, ++jt) {
-                    const uint32_t buf = jt & 1, tph = (jt >> 1) & 1;
+                    const uint32_t buf = jt % NBUF, tph = (jt / NBUF) & 1;
                     if (!mbar_wait(tempty0 + 8 * buf, tph ^ 1, abort_flag, a.err, 3)) {
                         ok = false;
                         break;
@@ -384,7 +395,29 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             const uint32_t ko = ks * 32;
                             auto A = [&](int p) { return sdesc(sa + p * PLANE_BYTES + ko); };
                             auto Bd = [&](int p) { return sdesc(sb + p * PLANE_BYTES + ko); };
-                            if constexpr (C::PL == 4) {
+                            if constexpr (MODE != FAST) {
+                                // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo; dr/di hold the hi*hi
+                                // products, cr/ci the corrections
+                                const uint32_t cr = tbase + 256, ci = tbase + 384;
+                                mma<F>(dr, A(0), Bd(0), id_pos, first);
+                                mma<F>(dr, A(2), Bd(2), id_neg, 1);
+                                mma<F>(di, A(0), Bd(2), id_pos, first);
+                                mma<F>(di, A(2), Bd(0), id_pos, 1);
+                                mma<F>(cr, A(0), Bd(1), id_pos, first);
+                                mma<F>(cr, A(1), Bd(0), id_pos, 1);
+                                mma<F>(cr, A(2), Bd(3), id_neg, 1);
+                                mma<F>(cr, A(3), Bd(2), id_neg, 1);
+                                mma<F>(ci, A(0), Bd(3), id_pos, first);
+                                mma<F>(ci, A(1), Bd(2), id_pos, 1);
+                                mma<F>(ci, A(2), Bd(1), id_pos, 1);
+                                mma<F>(ci, A(3), Bd(0), id_pos, 1);
+                                if constexpr (MODE == SPLIT4) {
+                                    mma<F>(cr, A(1), Bd(1), id_pos, 1);
+                                    mma<F>(cr, A(3), Bd(3), id_neg, 1);
+                                    mma<F>(ci, A(1), Bd(3), id_pos, 1);
+                                    mma<F>(ci, A(3), Bd(1), id_pos, 1);
+                                }
+                            } else if constexpr (C::PL == 4) {
                                 // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo
                                 mma<F>(dr, A(0), Bd(0), id_pos, first);
                                 mma<F>(dr, A(0), Bd(1), id_pos, 1);
@@ -431,7 +464,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             Job J{};
             for (int j = 0; j < nj; ++j, ++jt) {
                 J = decode(a, u, j);
-                const uint32_t buf = jt & 1, tph = (jt >> 1) & 1;
+                const uint32_t buf = jt % NBUF, tph = (jt / NBUF) & 1;
                 // every lane waits; the warp proceeds only if all lanes saw the phase,
                 // so the warp-collective tensor-memory loads never diverge
                 const bool got = mbar_wait(tfull0 + 8 * buf, tph, abort_flag, a.err, 6);
@@ -448,6 +481,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     float er[32], ei[32];
                     tmem_ld32(ta, er);
                     tmem_ld32(ta + 128, ei);
+                    if constexpr (MODE != FAST) {
+                        float t[32];
+                        tmem_ld32(ta + 256, t);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) er[i] += t[i];
+                        tmem_ld32(ta + 384, t);
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) ei[i] += t[i];
+                    }
                     const int n0 = J.n0 + c0;
                     const int nvalid = min(32, a.N - n0);
                     if (a.kind == KS2) {
@@ -553,11 +595,12 @@ bool make_map(dlx_plan *p, Operand &o, std::string *why) {
     return true;
 }
 
-template <int F>
+template <int F, int MODE = FAST>
 cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, TcArgs &a, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<F>::SMEM);
+        cudaError_t e =
+            cudaFuncSetAttribute(k_tc_gemm<F, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<F>::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -581,11 +624,11 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, TcArgs &a, c
     const int grid = std::min(a.units, p->sm_count);
     static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
     KScope ks(p, cls_of[a.kind], 1, st);
-    k_tc_gemm<F><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, a);
+    k_tc_gemm<F, MODE><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, a);
     return cudaGetLastError();
 }
 
-template <int F>
+template <int F, int MODE>
 cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     TcArgs a{};
     // stage 1: T1t[b] = A(l) . P[b]^T   (M = No rows kx, N = Ni cols ny, K = Ni)
@@ -597,7 +640,7 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     a.out_ld = p->ldi;
     a.out_ps = (size_t)p->no * p->ldi;
     a.units = R * p->B * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
-    cudaError_t e = launch<F>(p, p->amat, p->P, a, st);
+    cudaError_t e = launch<F, MODE>(p, p->amat, p->P, a, st);
     if (e != cudaSuccess) return e;
     // stage 2 + intensity: Is[g][rse] = sum_l w |A(l) . T1t[b]^T|^2  (M = N = No, K = Ni)
     TcArgs c{};
@@ -608,7 +651,7 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     c.Is = p->Is;
     c.Rnse = R * p->nse;
     c.units = c.Rnse * p->G * ((p->no + BM - 1) / BM) * ((p->no + BN - 1) / BN);
-    return launch<F>(p, p->amat, p->T1t, c, st);
+    return launch<F, MODE>(p, p->amat, p->T1t, c, st);
 }
 
 template <int F>
@@ -672,9 +715,11 @@ int tc_make_maps(dlx_plan *p, std::string *why) {
 
 cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st) {
     switch (p->fmt) {
-        case FMT_BF16X4: return forward_impl<FMT_BF16X4>(p, R, st);
-        case FMT_BF16X2: return forward_impl<FMT_BF16X2>(p, R, st);
-        case FMT_TF32X4: return forward_impl<FMT_TF32X4>(p, R, st);
+        case FMT_BF16X4:
+            return p->prec == DLX_BF16X4 ? forward_impl<FMT_BF16X4, SPLIT4>(p, R, st)
+                                         : forward_impl<FMT_BF16X4, FAST>(p, R, st);
+        case FMT_BF16X2: return forward_impl<FMT_BF16X2, FAST>(p, R, st);
+        case FMT_TF32X4: return forward_impl<FMT_TF32X4, SPLIT3>(p, R, st);
         default: return cudaErrorNotSupported;
     }
 }

@@ -1,0 +1,155 @@
+"""GPU tests of the continuous-batching fit server: a request's result is the
+same alone and in a mix of concurrent requests, it agrees with the direct
+loss/gradient call and with a manual Adam loop, admission respects the HBM
+budget, and host-side faults (admission refusal, a NaN input, a poll
+deadline) come back as error statuses."""
+
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+LR = dict(zern=2e-9, opd_pix=1e-9, flat=1e-3, flux=1e3, pos=1e-8)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2406_08703_gb300 as P
+
+    P.load()
+    return P
+
+
+def _request(seed, **over):
+    truth = W.make_problem("custom", seed=seed, **over)
+    data = W.poisson_counts(oracle.forward(truth), seed + 1)
+    start = W.perturbed_start(truth, seed + 2)
+    return start, data
+
+
+SHAPE_A = dict(n_pupil=64, n_det=32, oversample=2, n_lambda=3, n_src=2, n_zern_max=6, opd_pix_rms=3e-9)
+SHAPE_B = dict(n_pupil=48, n_det=24, oversample=4, n_lambda=2, n_src=1, n_zern_max=4)
+
+
+def _serve(P, reqs, n_steps=3, max_slots=8, budget=0, form="bf16x4"):
+    from paper_2406_08703_gb300.server import result_shapes
+
+    srv = P.dlx_server_create(0, budget, max_slots)
+    tickets = [srv.submit(p, d, n_steps=n_steps, lr=LR, precision=P.PRECISIONS[form]) for p, d in reqs]
+    out = [srv.poll(t, timeout_s=120.0, shapes=result_shapes(p)) for t, (p, _) in zip(tickets, reqs)]
+    stats = srv.stats()
+    srv.close()
+    return out, stats
+
+
+def test_same_result_alone_and_in_the_mix(P):
+    a = _request(31, **SHAPE_A)
+    alone, _ = _serve(P, [a])
+    mix = [_request(40 + i, **SHAPE_A) for i in range(3)] + [_request(50, **SHAPE_B), _request(51, **SHAPE_B)]
+    mixed, stats = _serve(P, mix[:2] + [a] + mix[2:])
+    x, y = alone[0], mixed[2]
+    assert stats["grouped_launches"] > 0  # same-shape requests shared launches
+    assert x["loss"] == pytest.approx(y["loss"], rel=1e-9)
+    for k in ("zern_coeff", "opd_pix", "flux", "pos", "flat", "g_zern", "g_flat", "g_pos"):
+        assert rel_l2(y[k], x[k]) < 1e-6, k
+
+
+def test_single_evaluation_matches_direct_call(P):
+    import torch
+
+    p, d = _request(60, **SHAPE_A)
+    res, _ = _serve(P, [(p, d)], n_steps=0)
+    plan = P.dlx_make_mft(P.desc_from_problem(p, P.DLX_BF16X4))
+    loss, grads, _ = P.dlx_loss_grad(plan, P.params_from_problem(p), torch.as_tensor(d, device="cuda"))
+    torch.cuda.synchronize()
+    assert res[0]["loss"] == pytest.approx(loss.item(), rel=1e-9)
+    assert rel_l2(res[0]["g_zern"], grads["d_zern"].cpu().numpy()) < 1e-6
+    assert rel_l2(res[0]["g_flat"], grads["d_flat"].cpu().numpy()) < 1e-6
+    assert res[0]["steps_done"] == 1
+
+
+def test_adam_steps_match_manual_loop(P):
+    import torch
+
+    p, d = _request(70, **SHAPE_A)
+    res, _ = _serve(P, [(p, d)], n_steps=4)
+    plan = P.dlx_make_mft(P.desc_from_problem(p, P.DLX_BF16X4))
+    prm = P.params_from_problem(p)
+    dt = torch.as_tensor(d, device="cuda")
+    groups = [("zern_coeff", "d_zern", LR["zern"]), ("opd_pix", "d_opd_pix", LR["opd_pix"]),
+              ("flat", "d_flat", LR["flat"]), ("flux", "d_flux", LR["flux"]), ("pos", "d_pos", LR["pos"])]
+    state = {k: (torch.zeros_like(prm[k]), torch.zeros_like(prm[k])) for k, _, _ in groups}
+    for t in range(1, 5):
+        _, grads, _ = P.dlx_loss_grad(plan, prm, dt)
+        for k, gk, lr in groups:
+            P.dlx_adam(prm[k], grads[gk], state[k][0], state[k][1], lr, t)
+    torch.cuda.synchronize()
+    for k, _, _ in groups:
+        assert rel_l2(res[0][k], prm[k].cpu().numpy()) < 1e-5, k
+
+
+def test_admission_respects_budget_and_all_complete(P):
+    reqs = [_request(80 + i, **(SHAPE_A if i % 2 else SHAPE_B)) for i in range(6)]
+    from paper_2406_08703_gb300.server import result_shapes
+
+    budget = 1 << 30
+    srv = P.dlx_server_create(0, budget, 2)
+    tickets = [srv.submit(p, d, n_steps=5, lr=LR) for p, d in reqs]
+    peak = 0
+    done = {}
+    t0 = time.time()
+    while len(done) < len(tickets) and time.time() - t0 < 120:
+        s = srv.stats()
+        peak = max(peak, s["hbm_in_use"])
+        for t, (p, _) in zip(tickets, reqs):
+            if t not in done:
+                r = srv.poll(t, 0.0, result_shapes(p))
+                if r is not None:
+                    done[t] = r
+        time.sleep(0.005)
+    stats = srv.stats()
+    srv.close()
+    assert len(done) == len(tickets)
+    assert peak <= budget
+    assert stats["completed"] == len(tickets) and stats["rejected"] == 0
+    assert all(np.isfinite(r["loss"]) for r in done.values())
+
+
+def test_host_side_faults_return_status(P):
+    from paper_2406_08703_gb300._native import DlxError
+
+    p, d = _request(90, **SHAPE_B)
+    srv = P.dlx_server_create(0, 0, 4)
+    srv.inject_fault(1)  # next admission refused
+    t = srv.submit(p, d, n_steps=1, lr=LR)
+    with pytest.raises(DlxError) as e:
+        srv.poll(t, 60.0)
+    assert e.value.code == -2  # NOMEM
+    srv.inject_fault(2)  # next admitted request gets a NaN input
+    t = srv.submit(p, d, n_steps=1, lr=LR)
+    with pytest.raises(DlxError) as e:
+        srv.poll(t, 60.0)
+    assert e.value.code == -4  # NONFINITE
+    t = srv.submit(p, d, n_steps=200, lr=LR)
+    with pytest.raises(DlxError) as e:
+        srv.poll(t, 1e-3)
+    assert e.value.code == -5  # TIMEOUT
+    assert srv.poll(t, 120.0) is not None
+    srv.close()
+
+
+def test_request_larger_than_budget_is_rejected(P):
+    from paper_2406_08703_gb300._native import DlxError
+
+    p, d = _request(95, **SHAPE_A)
+    srv = P.dlx_server_create(0, 1 << 20, 2)
+    with pytest.raises(DlxError) as e:
+        srv.submit(p, d, n_steps=1, lr=LR)
+    assert e.value.code == -2
+    srv.close()
