@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--form", default="bf16x4", choices=["bf16x4", "bf16x3", "tf32x3", "bf16", "fp32"])
     ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
     ap.add_argument("--workload", default="binary")
+    ap.add_argument("--lambdas", type=int, default=0,
+                    help="use only this many of the workload's wavelengths (same per-PSF shapes; profiling captures)")
     ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side FP32 / other-form lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -83,12 +85,15 @@ def max_over_ranks(dist, x):
     return float(t.item())
 
 
+N_LAMBDAS = 0  # set from --lambdas
+
+
 def make_inputs(workload, seed_offset=0):
     """Seeded synthetic inputs: the workload's truth, a perturbed starting point and
     Poisson data of an analytic image with the workload's total flux."""
     import workloads as W
 
-    truth = W.make_problem(workload)
+    truth = W.make_problem(workload, **({"n_lambda": N_LAMBDAS} if N_LAMBDAS else {}))
     start = W.perturbed_start(truth, 100 + seed_offset)
     total = float(np.sum(truth.flux)) * truth.n_exp
     pix = truth.pixscale
@@ -273,7 +278,9 @@ def reference_arm(args, rank, world):
 
 
 def main():
+    global N_LAMBDAS
     args = parse()
+    N_LAMBDAS = args.lambdas
     rank, world, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, rank, world)

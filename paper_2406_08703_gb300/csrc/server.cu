@@ -118,7 +118,9 @@ struct Bucket {
     dlx::DevGrads grads() const {
         dlx::DevGrads g{};
         g.p[dlx::GZERN] = nz ? grad + off[0] : nullptr;
-        g.p[dlx::GPIX] = grad + off[1];  // always computed: g_OPD feeds the Zernike gradient
+        // the pixel-OPD gradient has a slot region only when the map is fitted (the
+        // Zernike gradient is reduced from the plan's own g_OPD buffer either way)
+        g.p[dlx::GPIX] = has_pix ? grad + off[1] : nullptr;
         g.p[dlx::GFLAT] = grad + off[2];
         g.p[dlx::GFLUX] = grad + off[3];
         g.p[dlx::GPOS] = grad + off[4];
