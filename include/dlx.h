@@ -131,6 +131,28 @@ int dlx_plan_get_info(const dlx_plan *plan, dlx_plan_info *out);
  * `model` is device [n_exp][Nd][Nd]. */
 int dlx_forward(dlx_plan *plan, const dlx_params *params, float *model, void *cuda_stream);
 
+/* The paper has no counterpart of this entry point; it exists for callers that
+ * cannot allocate device memory -- host applications that reserve all of the
+ * GPU's memory through their own allocator at start-up and forbid further
+ * allocation at run time (for example an instrument-control or real-time
+ * reduction loop that must never stall or fail on an allocation).
+ * It computes the same model as dlx_forward in the FP32 CUDA-core form
+ * (desc->precision is ignored) without a plan and without calling cudaMalloc,
+ * cudaFree or any allocating routine: all working memory comes from one
+ * file-scope device array of 16 MiB that every GPU loading the library holds
+ * until the process exits.  Arguments are dlx_forward's, with `desc` in place
+ * of a plan (desc->lambda_m is host memory, read during the call).
+ * Limits: at most 8 sources and 256 wavelengths, and the working memory of
+ *   8*nl + 8*nl + 8*B*Ni + 4*Ni^2 + 8*nl*No*Ni8 + 8*nl*Ni*No8 + 8*B*Ni*Ni8
+ *   + 8*B*No*Ni8 + 4*nS*nE*No^2 + reduction partials   (bytes, Ni8/No8 = sizes rounded up to 8)
+ * must fit in 16 MiB; larger shapes return DLX_ERR_RANGE with the byte count.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  Every call on a device shares the array and overwrites
+ * it, so calls whose work overlaps on the GPU (other streams or threads) race:
+ * serialise them.  Asynchronous on the stream like dlx_forward. */
+int dlx_forward_noalloc(const dlx_mft_desc *desc, const dlx_params *params, float *model, void *cuda_stream);
+
 /* The flux-weighted oversampled intensity before binning and flat field,
  * psf_os[e][ky][kx] = sum_s F_s sum_l w_l |E_{l,s,e}|^2, device [n_exp][No][No]. */
 int dlx_psf(dlx_plan *plan, const dlx_params *params, float *psf_os, void *cuda_stream);

@@ -169,6 +169,30 @@ def dlx_forward(plan: Plan, params: dict, model=None, stream=None):
     return model
 
 
+def dlx_forward_noalloc(desc: MftDesc, params: dict, model, device: int = 0, stream=None):
+    """dlx_forward in the FP32 form without a plan and without any device
+    allocation (working memory from the library's fixed 16 MiB device array);
+    for callers that cannot allocate.  `model` is the caller's output buffer."""
+    torch = _torch()
+    i = dict(n_pupil=desc.n_pupil, n_det=desc.n_det, n_zern=desc.n_zern, n_lambda=len(desc.lambdas),
+             n_src=desc.n_src, n_exp=desc.n_exp)
+    shapes = dict(transmission=(i["n_pupil"],) * 2, opd_fixed=(i["n_pupil"],) * 2,
+                  zern_basis=(i["n_zern"], i["n_pupil"], i["n_pupil"]), zern_coeff=(i["n_zern"],),
+                  opd_pix=(i["n_pupil"],) * 2, weights=(i["n_lambda"],), flux=(i["n_src"],), pos=(i["n_src"], 2),
+                  dither=(i["n_exp"], 2), flat=(i["n_det"],) * 2)
+    for k in PARAM_KEYS:
+        _check_tensor(k, params.get(k), shapes[k], torch.float32, device)
+    _check_tensor("model", model, (i["n_exp"], i["n_det"], i["n_det"]), torch.float32, device)
+    prm = N.Params(*[_ptr(params.get(k)) for k in PARAM_KEYS])
+    d, keep = desc.to_c()
+    st = torch.cuda.current_stream(device) if stream is None else stream
+    with torch.cuda.device(device):
+        N.check(load().dlx_forward_noalloc(C.byref(d), C.byref(prm), _ptr(model), C.c_void_p(st.cuda_stream)),
+                "dlx_forward_noalloc")
+    del keep
+    return model
+
+
 def dlx_psf(plan: Plan, params: dict, out=None, stream=None):
     torch = _torch()
     i = plan.info

@@ -76,6 +76,7 @@ SIGNATURES = {
     "dlx_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),
     "dlx_forward": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p]),
     "dlx_psf": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p]),
+    "dlx_forward_noalloc": (C.c_int, [C.POINTER(MftDesc), C.POINTER(Params), C.c_void_p, C.c_void_p]),
     "dlx_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p, C.POINTER(Grads),
                                 C.c_void_p, C.c_void_p]),
     "dlx_plan_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
