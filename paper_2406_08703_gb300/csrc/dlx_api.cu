@@ -217,11 +217,19 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->Is, sizeof(float) * (size_t)p->G * p->nse * R_max * nq);
     if (e == cudaSuccess) e = plan_alloc(p, &p->GI, sizeof(float) * p->ne * np * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->model_tmp, sizeof(float) * p->ne * np * R_max);
-    if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx);
+    if (p->prec != DLX_FP32_SIMT) {
+        // split the long-K adjoint 1^T contraction until its 128-tiles fill the SMs a few times over
+        const long units = (long)p->chunk * ((p->ni + 127) / 128) * ((p->ni + 127) / 128);
+        const int kblocks = (p->no + 31) / 32;
+        int s = 1;
+        while (s < 8 && units * s < 4L * p->sm_count && kblocks / (2 * s) >= 4) s *= 2;
+        p->gsplit = s;
+    }
+    if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx * p->gsplit);
     if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(float2) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
     const size_t nslice = (npx + 2047) / 2048;  // slices of the sliced gradient reductions
-    if (e == cudaSuccess) e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * nslice);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * p->gsplit * nslice);
     if (e == cudaSuccess) e = plan_alloc(p, &p->zpart, sizeof(double) * R_max * std::max(1, p->nz) * nslice);
     if (e == cudaSuccess) e = plan_alloc(p, &p->err, sizeof(int32_t));
     if (e == cudaSuccess) e = plan_alloc(p, &p->clamped, sizeof(unsigned long long));

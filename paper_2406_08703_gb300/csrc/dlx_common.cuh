@@ -138,6 +138,7 @@ struct dlx_plan {
     double dx, du;
     int G = 1;       // wavelength groups of the intensity contraction (partial planes)
     int chunk = 1;   // PSFs per adjoint pass
+    int gsplit = 1;  // K splits of the adjoint 1^T contraction: gphi holds [R*B][gsplit][ni*ni]
     dlx::Operand amat, amatH, P, T1t, GEt, GT1;
     double *lam_d = nullptr;   // [nl]
     float *wnorm = nullptr;    // [R][nl] weights / sum(weights)

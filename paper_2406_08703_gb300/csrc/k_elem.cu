@@ -177,25 +177,29 @@ template <int F>
 __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
                          const float *__restrict__ invlam, const float *__restrict__ pscale, int nbt, int B, int nse,
                          int ni, int ldi, void *P) {
+    // grid: x over pupil pixels, y over PSFs (no 64-bit index arithmetic)
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F);
-    const size_t total = (size_t)nbt * npx;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        int bg = (int)(i / npx), n = (int)(i % npx);
-        int r = bg / B, l = (bg % B) / nse, ny = n / ni, nx = n % ni;
-        float t = slot_ptr(prm, PT, r)[n] * pscale[r];
+    const int bg = blockIdx.y, r = bg / B, l = (bg % B) / nse;
+    const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
+    const float sc = pscale[r], il = invlam[l];
+    const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
+    char *base = (char *)P + (size_t)bg * Pl * ni * ldi * es;
+    const size_t ps = (size_t)ni * ldi;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npx; n += gridDim.x * blockDim.x) {
+        const int ny = n / ni, nx = n - ny * ni;
+        const float t = T[n] * sc;
         float re = 0.f, im = 0.f;
         if (t != 0.f) {
-            float ph = opd[(size_t)r * npx + n] * invlam[l];
+            float ph = op[n] * il;
             ph -= rintf(ph);
             float sn, cs;
             sincospif(2.f * ph, &sn, &cs);
-            float2 ex = tilt[(size_t)bg * 2 * ni + nx], ey = tilt[(size_t)bg * 2 * ni + ni + ny];
-            float xr = ex.x * ey.x - ex.y * ey.y, xi = ex.x * ey.y + ex.y * ey.x;
+            const float2 ex = tx[nx], ey = ty[ny];
+            const float xr = ex.x * ey.x - ex.y * ey.y, xi = ex.x * ey.y + ex.y * ey.x;
             re = t * (cs * xr - sn * xi);
             im = t * (cs * xi + sn * xr);
         }
-        char *base = (char *)P + (size_t)bg * Pl * ni * ldi * es;
-        store_cplx<F>(base, (size_t)ni * ldi, (size_t)ny * ldi + nx, re, im);
+        store_cplx<F>(base, ps, (size_t)ny * ldi + nx, re, im);
     }
 }
 
@@ -208,11 +212,10 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     size_t tt = (size_t)nbt * 2 * p->ni;
     int tb = (int)std::min<size_t>((tt + 255) / 256, (size_t)p->sm_count * 8);
     k_tilt<<<tb, 256, 0, st>>>(prm, p->lam_d, nbt, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt);
-    size_t total = (size_t)nbt * npx;
-    int pb = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
+    const int px = std::max(1, std::min((npx + 255) / 256, (p->sm_count * 16 + nbt - 1) / nbt));
     DLX_FMT_DISPATCH(p->fmt, F,
-                     k_phasor<F><<<pb, 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->pscale, nbt, p->B, p->nse,
-                                                     p->ni, p->ldi, p->P.ptr));
+                     k_phasor<F><<<dim3(px, nbt), 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->pscale, nbt,
+                                                                p->B, p->nse, p->ni, p->ldi, p->P.ptr));
     return cudaGetLastError();
 }
 
@@ -358,65 +361,75 @@ cudaError_t launch_finalize_loss(dlx_plan *p, int R, double *loss, const DevGrad
 constexpr int RED_SLICE = 2048;  // pupil pixels per block in the sliced reductions (256 threads x 8)
 
 // g_OPD[r][n] = sum_{b in slot r} gphi[b][n] (compensated);  dL/dOPD_pix = g_OPD.
+// A block covers 64 pupil pixels with 4 threads per pixel, each summing every
+// 4th entry (8 loads in flight); the 4 partial sums are combined in a fixed order.
 __global__ void k_gopd(const float *__restrict__ gphi, int R, int B, int npx, float2 *__restrict__ gopd, DevGrads g) {
-    const size_t total = (size_t)R * npx;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        const int r = (int)(i / npx), n = (int)(i % npx);
+    __shared__ df sh[4][64];
+    const int r = blockIdx.y, px = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int n = blockIdx.x * 64 + px;
+    df acc{0.f, 0.f};
+    if (n < npx) {
         const float *src = gphi + (size_t)r * B * npx + n;
-        df acc{0.f, 0.f};
-        int b = 0;
-        for (; b + 8 <= B; b += 8) {
+        int b = grp;
+        for (; b + 28 < B; b += 32) {
             float v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = __ldg(src + (size_t)(b + q) * npx);
+            for (int q = 0; q < 8; ++q) v[q] = __ldg(src + (size_t)(b + 4 * q) * npx);
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc = df_add(acc, v[q]);
         }
-        for (; b < B; ++b) acc = df_add(acc, __ldg(src + (size_t)b * npx));
-        gopd[i] = make_float2(acc.hi, acc.lo);
-        if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = acc.hi + acc.lo;
+        for (; b < B; b += 4) acc = df_add(acc, __ldg(src + (size_t)b * npx));
+    }
+    sh[grp][px] = acc;
+    __syncthreads();
+    if (grp == 0 && n < npx) {
+        df t = df_add(df_add(sh[0][px], sh[1][px]), df_add(sh[2][px], sh[3][px]));
+        gopd[(size_t)r * npx + n] = make_float2(t.hi, t.lo);
+        if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = t.hi + t.lo;
     }
 }
 
-// Position moments of one PSF over one slice of the pupil: sum_n gphi[bg][n] x_n
-// and y_n.  grid (n_slices, R * B); partials in part[bg][slice][2].
+// Position moments of one PSF entry over the whole pupil: sum_n gphi[e][n] x_n
+// and y_n.  One block per entry (PSF x K split), 8 loads in flight per thread.
 __global__ void k_pos_moments(const float *__restrict__ gphi, int ni, float dx, double *part) {
     __shared__ df sh[64];
-    const int slice = blockIdx.x, b = blockIdx.y, npx = ni * ni;
+    const int b = blockIdx.x, npx = ni * ni;
     const float cN = 0.5f * (ni - 1);
+    const float *src = gphi + (size_t)b * npx;
     df v[2] = {{0.f, 0.f}, {0.f, 0.f}};
-    const int n0 = slice * RED_SLICE;
-    float gv[8];
-    int nn[8];
+    for (int n0 = 0; n0 < npx; n0 += 8 * 256) {
+        float gv[8];
+        int nn[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        nn[q] = n0 + q * 256 + threadIdx.x;
-        gv[q] = nn[q] < npx ? __ldg(gphi + (size_t)b * npx + nn[q]) : 0.f;
-    }
+        for (int q = 0; q < 8; ++q) {
+            nn[q] = n0 + q * 256 + threadIdx.x;
+            gv[q] = nn[q] < npx ? __ldg(src + nn[q]) : 0.f;
+        }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int ny = nn[q] / ni, nx = nn[q] - ny * ni;
-        v[0] = df_add(v[0], gv[q] * (((float)nx - cN) * dx));
-        v[1] = df_add(v[1], gv[q] * (((float)ny - cN) * dx));
+        for (int q = 0; q < 8; ++q) {
+            const int ny = nn[q] / ni, nx = nn[q] - ny * ni;
+            v[0] = df_add(v[0], gv[q] * (((float)nx - cN) * dx));
+            v[1] = df_add(v[1], gv[q] * (((float)ny - cN) * dx));
+        }
     }
     block_sum<2>(v, sh);
     if (threadIdx.x == 0) {
-        double *o = part + ((size_t)b * gridDim.x + slice) * 2;
-        o[0] = df_to_double(v[0]);
-        o[1] = df_to_double(v[1]);
+        part[2 * (size_t)b] = df_to_double(v[0]);
+        part[2 * (size_t)b + 1] = df_to_double(v[1]);
     }
 }
 
-// dL/dtheta_s = sum over wavelengths, exposures and slices of the moments of
+// dL/dtheta_s = sum over wavelengths, exposures and K splits of the moments of
 // source s.  One warp per (slot, source, axis); fixed order.
-__global__ void k_pos_final(const double *part, int nslice, int B, int nl, int ns, int ne, DevGrads g) {
+__global__ void k_pos_final(const double *part, int nsplit, int B, int nl, int ns, int ne, DevGrads g) {
     const int r = blockIdx.x, s = blockIdx.y, ax = blockIdx.z, lane = threadIdx.x;
-    const int nt = nl * ne * nslice;
+    const int nt = nl * ne * nsplit;
     double v = 0.0;
     for (int t = lane; t < nt; t += 32) {
-        const int sl = t % nslice, le = t / nslice, l = le / ne, e = le % ne;
+        const int sp = t % nsplit, le = t / nsplit;
+        const int l = le / ne, e = le % ne;
         const size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
-        v += part[(b * nslice + sl) * 2 + ax];
+        v += part[(b * nsplit + sp) * 2 + ax];
     }
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + ax] = (float)v;
@@ -460,12 +473,12 @@ cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const D
     const int npx = p->ni * p->ni, nslice = (npx + RED_SLICE - 1) / RED_SLICE;
     DevGrads gg{};
     if (g) gg = *g;
-    int blocks = (int)std::min<size_t>(((size_t)R * npx + 255) / 256, (size_t)p->sm_count * 8);
     KScope ks(p, KC_GRAD, 1 + (gg.p[GPOS] ? 2 : 0) + ((gg.p[GZERN] && p->nz > 0) ? 2 : 0), st);
-    k_gopd<<<blocks, 256, 0, st>>>(p->gphi, R, p->B, npx, p->gopd, gg);
+    // gphi holds gsplit partial planes per PSF; they are summed with the PSFs
+    k_gopd<<<dim3((npx + 63) / 64, R), 256, 0, st>>>(p->gphi, R, p->B * p->gsplit, npx, p->gopd, gg);
     if (gg.p[GPOS]) {
-        k_pos_moments<<<dim3(nslice, R * p->B), 256, 0, st>>>(p->gphi, p->ni, (float)p->dx, p->pos_part);
-        k_pos_final<<<dim3(R, p->ns, 2), 32, 0, st>>>(p->pos_part, nslice, p->B, p->nl, p->ns, p->ne, gg);
+        k_pos_moments<<<R * p->B * p->gsplit, 256, 0, st>>>(p->gphi, p->ni, (float)p->dx, p->pos_part);
+        k_pos_final<<<dim3(R, p->ns, 2), 32, 0, st>>>(p->pos_part, p->gsplit, p->B, p->nl, p->ns, p->ne, gg);
     }
     if (gg.p[GZERN] && p->nz > 0) {
         k_zern_partial<<<dim3(nslice, p->nz, R), 256, 0, st>>>(prm, p->gopd, npx, p->zpart);

@@ -7,15 +7,16 @@
 //   warp 8  : TMA producer (one lane) -- 4-D tensor maps {k, row, plane, batch},
 //             64-byte swizzled boxes of every plane of A and B per stage;
 //   warp 9  : MMA issuer (one lane) and tensor-memory owner -- per 16-wide k
-//             step it issues the complex product as real products into two
-//             FP32 accumulators Er, Ei (128 columns each, double-buffered):
-//               split forms: Er += Ar_h Br_h + Ar_h Br_l + Ar_l Br_h - (Ai_h Bi_h + Ai_h Bi_l + Ai_l Bi_h)
-//                            Ei += Ar_h Bi_h + Ar_h Bi_l + Ar_l Bi_h + Ai_h Br_h + Ai_h Br_l + Ai_l Br_h
-//               (the minus is the instruction descriptor's negate-A bit);
+//             step it issues the complex product as real products into FP32
+//             accumulators in tensor memory (the subtraction in Re(AB) is the
+//             instruction descriptor's negate-A bit);
 //   warps 0-7: epilogue -- tcgen05.ld of a 32-lane quarter and a 64-column
-//             half of Er/Ei, then the stage's fused epilogue (operand split
-//             store, |E|^2 spectral accumulation, dL/dE scaling, or the
-//             phase-gradient product with conj(P)).
+//             half of the accumulators, 16 columns at a time, then the
+//             contraction's fused epilogue (operand split store, spectral
+//             |E|^2 accumulation, dL/dE scaling, or the phase-gradient product
+//             with conj(P)).
+// The kernel is specialised per contraction kind, arithmetic form and
+// accumulation mode, so each instance carries only its own epilogue.
 // Every mbarrier wait is bounded (globaltimer, 1 s): on expiry the CTA raises
 // a shared abort flag and the plan's device error flag, waits (bounded) for
 // its own copies and MMAs in flight, frees its tensor memory and returns.
@@ -32,8 +33,19 @@ constexpr int BM = 128, BN = 128, NTHREADS = 320, EPI_WARPS = 8, PRODUCER_WARP =
 constexpr int PLANE_BYTES = 128 * 64;  // one 128-row x 64-byte swizzled box
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
 constexpr uint32_t TMEM_COLS = 512;
+constexpr int CW = 16;  // epilogue columns per tensor-memory load
 
 enum Kind { KS1 = 0, KS2 = 1, KGE = 2, KGT1 = 3, KGP = 4 };
+
+// Accumulation modes.  FAST: two accumulators (Er, Ei), double-buffered, three
+// split products.  SPLIT3 / SPLIT4: the hi*hi products and the small correction
+// products go to separate accumulators (Er_hh, Ei_hh, Er_c, Ei_c; one buffer),
+// so the accumulator that carries the large values takes two instructions per
+// 16-wide k step instead of six -- the tensor core's FP32 accumulation loses a
+// fraction of an ulp towards zero per instruction, and at a PSF peak those
+// losses add up coherently.  SPLIT4 also adds the lo*lo product, whose omission
+// biases coherent sums of conjugate pairs upwards by about 2^-16.
+enum AccMode { FAST = 0, SPLIT3 = 1, SPLIT4 = 2 };
 
 template <int F>
 struct Cfg {
@@ -50,10 +62,11 @@ struct Cfg {
 
 // Arguments of one launch.  Per-job operand coordinates come from decode().
 struct TcArgs {
-    int kind;
     int M, N, K;   // per-job contraction sizes (complex)
     int tm, tn;    // 128-tiles along M and N
     int units;
+    int ksplit;    // K splits of the adjoint 1^T contraction (gphi planes per PSF)
+    int KB;        // k elements per pipeline stage
     int nl, nse, B, ne, nd, os, ni, no, ldi, ldo, G, Rnse, b0;
     const float *wnorm;
     const float *GI;
@@ -74,50 +87,78 @@ struct Job {
     int b;       // global PSF index
     int z;       // chunk-local index
     int l, r, se;
+    int kb0, kb1;  // k-block range of this job (split-K for the adjoint 1^T contraction)
+    int split;
 };
 
-__device__ __forceinline__ int decode_unit_jobs(const TcArgs &a, int u, int &g, int &rse, int &tile) {
-    if (a.kind != KS2) return 1;
-    tile = u % (a.tm * a.tn);
-    int rest = u / (a.tm * a.tn);
-    g = rest % a.G;
-    rse = rest / a.G;
-    int l0 = (int)((long)g * a.nl / a.G), l1 = (int)((long)(g + 1) * a.nl / a.G);
-    return l1 - l0;
+template <int KIND>
+__device__ __forceinline__ int decode_unit_jobs(const TcArgs &a, int u, int &g, int &rse) {
+    if constexpr (KIND != KS2) {
+        return 1;
+    } else {
+        const int rest = u / (a.tm * a.tn);
+        g = rest % a.G;
+        rse = rest / a.G;
+        const int l0 = (int)((long)g * a.nl / a.G), l1 = (int)((long)(g + 1) * a.nl / a.G);
+        return l1 - l0;
+    }
 }
 
+template <int KIND>
 __device__ __forceinline__ Job decode(const TcArgs &a, int u, int j) {
     Job J;
     const int tt = a.tm * a.tn;
     int tile = u % tt;
-    J.m0 = (tile / a.tn) * BM;
-    J.n0 = (tile % a.tn) * BN;
-    if (a.kind == KS2) {
-        int rest = u / tt, g = rest % a.G, rse = rest / a.G;
-        int l0 = (int)((long)g * a.nl / a.G);
+    J.split = 0;
+    if constexpr (KIND == KS2) {
+        const int rest = u / tt, g = rest % a.G, rse = rest / a.G;
+        const int l0 = (int)((long)g * a.nl / a.G);
         J.l = l0 + j;
         J.r = rse / a.nse;
         J.se = rse % a.nse;
         J.b = J.r * a.B + J.l * a.nse + J.se;
         J.z = 0;
-        J.a_batch = J.l;
+        J.a_batch = J.l;  // A(l) . T1t[b]^T
         J.b_batch = J.b;
     } else {
         int z = u / tt;
+        if constexpr (KIND == KGP) {  // units are (z, tile, split) with the split fastest
+            J.split = u % a.ksplit;
+            const int rest = u / a.ksplit;
+            tile = rest % tt;
+            z = rest / tt;
+        }
         J.z = z;
-        J.b = (a.kind == KS1) ? z : a.b0 + z;
+        J.b = (KIND == KS1) ? z : a.b0 + z;
         J.r = J.b / a.B;
         J.l = (J.b % a.B) / a.nse;
         J.se = (J.b % a.B) % a.nse;
-        switch (a.kind) {
-            case KS1: J.a_batch = J.l; J.b_batch = J.b; break;   // A(l) . P[b]^T
-            case KGE: J.a_batch = J.b; J.b_batch = J.l; break;   // T1t[b] . A(l)^T
-            case KGT1: J.a_batch = J.l; J.b_batch = J.z; break;  // AH(l) . GEt[z]^T
-            default: J.a_batch = J.z; J.b_batch = J.l; break;    // GT1[z] . AH(l)^T
+        if constexpr (KIND == KS1) {  // A(l) . P[b]^T
+            J.a_batch = J.l;
+            J.b_batch = J.b;
+        } else if constexpr (KIND == KGE) {  // T1t[b] . A(l)^T
+            J.a_batch = J.b;
+            J.b_batch = J.l;
+        } else if constexpr (KIND == KGT1) {  // AH(l) . GEt[z]^T
+            J.a_batch = J.l;
+            J.b_batch = J.z;
+        } else {  // GT1[z] . AH(l)^T
+            J.a_batch = J.z;
+            J.b_batch = J.l;
         }
     }
+    J.m0 = (tile / a.tn) * BM;
+    J.n0 = (tile % a.tn) * BN;
     J.a_row = J.m0;
     J.b_row = J.n0;
+    const int nkb = (a.K + a.KB - 1) / a.KB;
+    if constexpr (KIND == KGP) {
+        J.kb0 = (int)((long)J.split * nkb / a.ksplit);
+        J.kb1 = (int)((long)(J.split + 1) * nkb / a.ksplit);
+    } else {
+        J.kb0 = 0;
+        J.kb1 = nkb;
+    }
     return J;
 }
 
@@ -210,37 +251,35 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 lanes x 32 consecutive FP32 columns from tensor memory, waited on in the same asm.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
+// 32 lanes x 16 consecutive FP32 columns from tensor memory, waited on in the same asm.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
         "tcgen05.wait::ld.sync.aligned;\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr)
         : "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// ------------------------------------------------------------------ epilogue stores
-// Store 32 consecutive complex values of one row into a plane-major operand.
+// ------------------------------------------------------------------ epilogue row I/O
+// Store CW consecutive complex values of one row into a plane-major operand.
 template <int F>
-__device__ __forceinline__ void store_row32(void *base, size_t ps, size_t off, const float (&re)[32],
-                                            const float (&im)[32], int nvalid) {
-    if (nvalid == 32) {
+__device__ __forceinline__ void store_row(void *base, size_t ps, size_t off, const float (&re)[CW],
+                                          const float (&im)[CW], int nvalid) {
+    if (nvalid == CW) {
         if constexpr (F == FMT_BF16X4 || F == FMT_BF16X2) {
             __nv_bfloat16 *p = (__nv_bfloat16 *)base + off;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < CW / 8; ++q) {
                 __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    float x = re[8 * q + i], y = im[8 * q + i];
+                    const float x = re[8 * q + i], y = im[8 * q + i];
                     rh[i] = __float2bfloat16_rn(x);
                     ih[i] = __float2bfloat16_rn(y);
                     rl[i] = __float2bfloat16_rn(x - __bfloat162float(rh[i]));
@@ -259,12 +298,12 @@ __device__ __forceinline__ void store_row32(void *base, size_t ps, size_t off, c
         } else {
             float *p = (float *)base + off;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < CW / 4; ++q) {
                 float4 h, l, hi, li;
                 float *hp = &h.x, *lp = &l.x, *hip = &hi.x, *lip = &li.x;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    float x = re[4 * q + i], y = im[4 * q + i];
+                    const float x = re[4 * q + i], y = im[4 * q + i];
                     hp[i] = tf32_round(x);
                     lp[i] = tf32_round(x - hp[i]);
                     hip[i] = tf32_round(y);
@@ -278,23 +317,71 @@ __device__ __forceinline__ void store_row32(void *base, size_t ps, size_t off, c
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
+        for (int i = 0; i < CW; ++i)
             if (i < nvalid) store_cplx<F>(base, ps, off + i, re[i], im[i]);
     }
 }
 
-// ------------------------------------------------------------------ the kernel
-// Accumulation modes.  FAST: two accumulators (Er, Ei), double-buffered, three
-// split products.  SPLIT3 / SPLIT4: the hi*hi products and the small correction
-// products go to separate accumulators (Er_hh, Ei_hh, Er_c, Ei_c; one buffer),
-// so the accumulator that carries the large values takes two instructions per
-// 16-wide k step instead of six -- the tensor core's FP32 accumulation loses a
-// fraction of an ulp towards zero per instruction, and at a PSF peak those
-// losses add up coherently.  SPLIT4 also adds the lo*lo product, whose omission
-// biases coherent sums of conjugate pairs upwards by about 2^-16.
-enum AccMode { FAST = 0, SPLIT3 = 1, SPLIT4 = 2 };
+// Read CW consecutive complex values of one row of a plane-major operand
+// (the value each represents: hi + lo).
+template <int F>
+__device__ __forceinline__ void load_row(const void *base, size_t ps, size_t off, float (&re)[CW], float (&im)[CW],
+                                         int nvalid) {
+    if (nvalid == CW) {
+        if constexpr (F == FMT_BF16X4 || F == FMT_BF16X2) {
+            const __nv_bfloat16 *p = (const __nv_bfloat16 *)base + off;
+#pragma unroll
+            for (int q = 0; q < CW / 8; ++q) {
+                __align__(16) __nv_bfloat16 a[8], b[8], c[8], d[8];
+                *(uint4 *)a = __ldg((const uint4 *)(p + 8 * q));
+                if constexpr (F == FMT_BF16X4) {
+                    *(uint4 *)b = __ldg((const uint4 *)(p + ps + 8 * q));
+                    *(uint4 *)c = __ldg((const uint4 *)(p + 2 * ps + 8 * q));
+                    *(uint4 *)d = __ldg((const uint4 *)(p + 3 * ps + 8 * q));
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        re[8 * q + i] = __bfloat162float(a[i]) + __bfloat162float(b[i]);
+                        im[8 * q + i] = __bfloat162float(c[i]) + __bfloat162float(d[i]);
+                    }
+                } else {
+                    *(uint4 *)c = __ldg((const uint4 *)(p + ps + 8 * q));
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        re[8 * q + i] = __bfloat162float(a[i]);
+                        im[8 * q + i] = __bfloat162float(c[i]);
+                    }
+                }
+            }
+        } else {
+            const float *p = (const float *)base + off;
+#pragma unroll
+            for (int q = 0; q < CW / 4; ++q) {
+                const float4 h = __ldg((const float4 *)(p + 4 * q)), l = __ldg((const float4 *)(p + ps + 4 * q));
+                const float4 hi = __ldg((const float4 *)(p + 2 * ps + 4 * q)),
+                             li = __ldg((const float4 *)(p + 3 * ps + 4 * q));
+                re[4 * q + 0] = h.x + l.x;
+                re[4 * q + 1] = h.y + l.y;
+                re[4 * q + 2] = h.z + l.z;
+                re[4 * q + 3] = h.w + l.w;
+                im[4 * q + 0] = hi.x + li.x;
+                im[4 * q + 1] = hi.y + li.y;
+                im[4 * q + 2] = hi.z + li.z;
+                im[4 * q + 3] = hi.w + li.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < CW; ++i) {
+            float2 v = make_float2(0.f, 0.f);
+            if (i < nvalid) v = load_cplx<F>(base, ps, off + i);
+            re[i] = v.x;
+            im[i] = v.y;
+        }
+    }
+}
 
-template <int F, int MODE>
+// ------------------------------------------------------------------ the kernel
+template <int F, int MODE, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
     using C = Cfg<F>;
@@ -332,18 +419,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tmem_slot;
-    const int nk = (a.K + C::KB - 1) / C::KB;
 
     if (warp == PRODUCER_WARP) {
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
             for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-                int g, rse, tile;
-                const int nj = decode_unit_jobs(a, u, g, rse, tile);
+                int g = 0, rse = 0;
+                const int nj = decode_unit_jobs<KIND>(a, u, g, rse);
                 for (int j = 0; j < nj && ok; ++j) {
-                    const Job J = decode(a, u, j);
-                    for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const Job J = decode<KIND>(a, u, j);
+                    for (int kb = J.kb0; kb < J.kb1; ++kb, ++it) {
                         const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
                         if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort_flag, a.err, 1)) {
                             ok = false;
@@ -371,8 +457,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             bool ok = true;
             const uint32_t id_pos = idesc<F>(false), id_neg = idesc<F>(true);
             for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-                int g, rse, tile;
-                const int nj = decode_unit_jobs(a, u, g, rse, tile);
+                int g = 0, rse = 0;
+                const int nj = decode_unit_jobs<KIND>(a, u, g, rse);
                 for (int j = 0; j < nj && ok; ++j, ++jt) {
                     const uint32_t buf = jt % NBUF, tph = (jt / NBUF) & 1;
                     if (!mbar_wait(tempty0 + 8 * buf, tph ^ 1, abort_flag, a.err, 3)) {
@@ -381,7 +467,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t dr = tbase + buf * 256, di = dr + 128;
-                    for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const Job J = decode<KIND>(a, u, j);
+                    for (int kb = J.kb0; kb < J.kb1; ++kb, ++it) {
                         const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
                         if (!mbar_wait(full0 + 8 * s, ph, abort_flag, a.err, 4)) {
                             ok = false;
@@ -391,7 +478,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES), sb = sa + C::PL * PLANE_BYTES;
 #pragma unroll
                         for (int ks = 0; ks < C::NKSTEP; ++ks) {
-                            const uint32_t first = (kb == 0 && ks == 0) ? 0u : 1u;
+                            const uint32_t first = (kb == J.kb0 && ks == 0) ? 0u : 1u;
                             const uint32_t ko = ks * 32;
                             auto A = [&](int p) { return sdesc(sa + p * PLANE_BYTES + ko); };
                             auto Bd = [&](int p) { return sdesc(sb + p * PLANE_BYTES + ko); };
@@ -450,20 +537,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_wait(drain, 0, abort_flag, a.err, 5, true, 100000000ull);
         }
     } else {
-        // ---------------- epilogue warps 0..7
+        // ---------------- epilogue warps 0..7: lane quarter q, column half h
         const int q = warp & 3, h = warp >> 2;
         const int row = 32 * q + lane;
         uint32_t jt = 0;
         bool ok = true;
-        float acc[64];
+        float acc[64];  // spectral |E|^2 accumulation (stage 2 only)
+        if constexpr (KIND == KS2) {
 #pragma unroll
-        for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+            for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+        }
         for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-            int g = 0, rse = 0, tile = 0;
-            const int nj = decode_unit_jobs(a, u, g, rse, tile);
+            int g = 0, rse = 0;
+            const int nj = decode_unit_jobs<KIND>(a, u, g, rse);
             Job J{};
             for (int j = 0; j < nj; ++j, ++jt) {
-                J = decode(a, u, j);
+                J = decode<KIND>(a, u, j);
                 const uint32_t buf = jt % NBUF, tph = (jt / NBUF) & 1;
                 // every lane waits; the warp proceeds only if all lanes saw the phase,
                 // so the warp-collective tensor-memory loads never diverge
@@ -474,59 +563,84 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const int m = J.m0 + row;
+                // per-job constants of the epilogues
+                float w = 0.f, c = 0.f, k2 = 0.f;
+                const float *gi = nullptr;
+                if constexpr (KIND == KS2) w = a.wnorm[(size_t)J.r * a.nl + J.l];
+                if constexpr (KIND == KGE) {
+                    const int s = J.se / a.ne, e = J.se % a.ne;
+                    c = 2.f * a.wnorm[(size_t)J.r * a.nl + J.l] * slot_ptr(a.prm, PFLUX, J.r)[s];
+                    gi = a.GI + ((size_t)J.r * a.ne + e) * a.nd * a.nd + min(m, a.M - 1) / a.os;
+                }
+                if constexpr (KIND == KGP) k2 = (float)(6.283185307179586476925286766559 / a.lam[J.l]);
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int c0 = 64 * h + 32 * cc;
+                for (int cc = 0; cc < 64 / CW; ++cc) {
+                    const int c0 = 64 * h + CW * cc;
                     const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + c0;
-                    float er[32], ei[32];
-                    tmem_ld32(ta, er);
-                    tmem_ld32(ta + 128, ei);
+                    float er[CW], ei[CW];
+                    tmem_ld16(ta, er);
+                    tmem_ld16(ta + 128, ei);
                     if constexpr (MODE != FAST) {
-                        float t[32];
-                        tmem_ld32(ta + 256, t);
+                        float t[CW];
+                        tmem_ld16(ta + 256, t);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) er[i] += t[i];
-                        tmem_ld32(ta + 384, t);
+                        for (int i = 0; i < CW; ++i) er[i] += t[i];
+                        tmem_ld16(ta + 384, t);
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) ei[i] += t[i];
+                        for (int i = 0; i < CW; ++i) ei[i] += t[i];
                     }
                     const int n0 = J.n0 + c0;
-                    const int nvalid = min(32, a.N - n0);
-                    if (a.kind == KS2) {
-                        const float w = a.wnorm[(size_t)J.r * a.nl + J.l];
+                    const int nvalid = min(CW, a.N - n0);
+                    if constexpr (KIND == KS2) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) acc[32 * cc + i] = fmaf(w, er[i] * er[i] + ei[i] * ei[i], acc[32 * cc + i]);
-                    } else if (m < a.M && nvalid > 0) {
-                        if (a.kind == KGE) {
-                            // rows kx, columns ky: scale by 2 w_l F_s GI[e][bin(ky, kx)]
-                            const int s = J.se / a.ne, e = J.se % a.ne;
-                            const float c = 2.f * a.wnorm[(size_t)J.r * a.nl + J.l] * slot_ptr(a.prm, PFLUX, J.r)[s];
-                            const float *gi = a.GI + ((size_t)J.r * a.ne + e) * a.nd * a.nd + m / a.os;
+                        for (int i = 0; i < CW; ++i)
+                            acc[CW * cc + i] = fmaf(w, er[i] * er[i] + ei[i] * ei[i], acc[CW * cc + i]);
+                    } else {
+                        if (m < a.M && nvalid > 0) {
+                            if constexpr (KIND == KGE) {
+                                // rows kx, columns ky: scale by 2 w_l F_s GI[e][bin(ky, kx)]; the
+                                // detector row of column ky = n0 + i advances without divisions
+                                int brow = n0 / a.os, rem = n0 - brow * a.os;
+                                const int bmax = (a.N - 1) / a.os;
 #pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                const int ky = min(n0 + i, a.N - 1);
-                                const float f = c * gi[(ky / a.os) * a.nd];
-                                er[i] *= f;
-                                ei[i] *= f;
-                            }
-                        }
-                        if (a.kind == KGP) {
-                            // rows ny, columns nx: gphi = (2 pi / lambda) Im(G_P conj P)
-                            const float k2 = (float)(6.283185307179586476925286766559 / a.lam[J.l]);
-                            const size_t pps = (size_t)a.ni * a.ldi;
-                            const char *pb = (const char *)a.P + (size_t)J.b * C::PL * pps * C::ES;
-                            float *o = a.gphi + (size_t)J.b * a.ni * a.ni + (size_t)m * a.ni + n0;
-#pragma unroll
-                            for (int i = 0; i < 32; ++i) {
-                                if (i < nvalid) {
-                                    const float2 pv = load_cplx<F>(pb, pps, (size_t)m * a.ldi + n0 + i);
-                                    o[i] = k2 * (ei[i] * pv.x - er[i] * pv.y);
+                                for (int i = 0; i < CW; ++i) {
+                                    const float f = c * gi[min(brow, bmax) * a.nd];
+                                    er[i] *= f;
+                                    ei[i] *= f;
+                                    if (++rem == a.os) {
+                                        rem = 0;
+                                        ++brow;
+                                    }
                                 }
                             }
-                        } else {
-                            const int zb = (a.kind == KS1) ? J.b : J.z;
-                            char *ob = (char *)a.out + (size_t)zb * C::PL * a.out_ps * C::ES;
-                            store_row32<F>(ob, a.out_ps, (size_t)m * a.out_ld + n0, er, ei, nvalid);
+                            if constexpr (KIND == KGP) {
+                                // rows ny, columns nx: gphi = (2 pi / lambda) Im(G_P conj P)
+                                const size_t pps = (size_t)a.ni * a.ldi;
+                                const char *pb = (const char *)a.P + (size_t)J.b * C::PL * pps * C::ES;
+                                float *o = a.gphi + ((size_t)J.b * a.ksplit + J.split) * a.ni * a.ni + (size_t)m * a.ni +
+                                           n0;
+                                float pr[CW], pi[CW];
+                                load_row<F>(pb, pps, (size_t)m * a.ldi + n0, pr, pi, nvalid);
+                                if (nvalid == CW && (a.ni & 3) == 0) {
+#pragma unroll
+                                    for (int qq = 0; qq < CW / 4; ++qq) {
+                                        float4 v;
+                                        v.x = k2 * (ei[4 * qq + 0] * pr[4 * qq + 0] - er[4 * qq + 0] * pi[4 * qq + 0]);
+                                        v.y = k2 * (ei[4 * qq + 1] * pr[4 * qq + 1] - er[4 * qq + 1] * pi[4 * qq + 1]);
+                                        v.z = k2 * (ei[4 * qq + 2] * pr[4 * qq + 2] - er[4 * qq + 2] * pi[4 * qq + 2]);
+                                        v.w = k2 * (ei[4 * qq + 3] * pr[4 * qq + 3] - er[4 * qq + 3] * pi[4 * qq + 3]);
+                                        *(float4 *)(o + 4 * qq) = v;
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int i = 0; i < CW; ++i)
+                                        if (i < nvalid) o[i] = k2 * (ei[i] * pr[i] - er[i] * pi[i]);
+                                }
+                            } else {
+                                const int zb = (KIND == KS1) ? J.b : J.z;
+                                char *ob = (char *)a.out + (size_t)zb * C::PL * a.out_ps * C::ES;
+                                store_row<F>(ob, a.out_ps, (size_t)m * a.out_ld + n0, er, ei, nvalid);
+                            }
                         }
                     }
                 }
@@ -535,7 +649,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
             }
             if (!ok) break;
-            if (a.kind == KS2) {
+            if constexpr (KIND == KS2) {
                 const int m = J.m0 + row;
                 if (m < a.M) {
                     float *o = a.Is + ((size_t)g * a.Rnse + rse) * a.no * a.no + (size_t)m * a.no;
@@ -595,12 +709,12 @@ bool make_map(dlx_plan *p, Operand &o, std::string *why) {
     return true;
 }
 
-template <int F, int MODE = FAST>
+template <int F, int MODE, int KIND>
 cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, TcArgs &a, cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k_tc_gemm<F, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<F>::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F, MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Cfg<F>::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -620,11 +734,13 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, TcArgs &a, c
     a.lam = p->lam_d;
     a.tm = (a.M + BM - 1) / BM;
     a.tn = (a.N + BN - 1) / BN;
+    a.KB = Cfg<F>::KB;
+    if (a.ksplit < 1) a.ksplit = 1;
     if (a.units <= 0) return cudaSuccess;
     const int grid = std::min(a.units, p->sm_count);
     static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
-    KScope ks(p, cls_of[a.kind], 1, st);
-    k_tc_gemm<F, MODE><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, a);
+    KScope ks(p, cls_of[KIND], 1, st);
+    k_tc_gemm<F, MODE, KIND><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, a);
     return cudaGetLastError();
 }
 
@@ -632,7 +748,6 @@ template <int F, int MODE>
 cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     TcArgs a{};
     // stage 1: T1t[b] = A(l) . P[b]^T   (M = No rows kx, N = Ni cols ny, K = Ni)
-    a.kind = KS1;
     a.M = p->no;
     a.N = p->ni;
     a.K = p->ni;
@@ -640,18 +755,17 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     a.out_ld = p->ldi;
     a.out_ps = (size_t)p->no * p->ldi;
     a.units = R * p->B * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
-    cudaError_t e = launch<F, MODE>(p, p->amat, p->P, a, st);
+    cudaError_t e = launch<F, MODE, KS1>(p, p->amat, p->P, a, st);
     if (e != cudaSuccess) return e;
     // stage 2 + intensity: Is[g][rse] = sum_l w |A(l) . T1t[b]^T|^2  (M = N = No, K = Ni)
     TcArgs c{};
-    c.kind = KS2;
     c.M = p->no;
     c.N = p->no;
     c.K = p->ni;
     c.Is = p->Is;
     c.Rnse = R * p->nse;
     c.units = c.Rnse * p->G * ((p->no + BM - 1) / BM) * ((p->no + BN - 1) / BN);
-    return launch<F, MODE>(p, p->amat, p->T1t, c, st);
+    return launch<F, MODE, KS2>(p, p->amat, p->T1t, c, st);
 }
 
 template <int F>
@@ -659,7 +773,6 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     const int tmo = (p->no + BM - 1) / BM, tmi = (p->ni + BM - 1) / BM;
     TcArgs a{};
     // recomputed field and dL/dE: GEt[z][kx][ky] = 2 w F GI o (T1t[b] . A(l)^T)
-    a.kind = KGE;
     a.M = p->no;
     a.N = p->no;
     a.K = p->ni;
@@ -670,11 +783,10 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     a.out_ld = p->ldo;
     a.out_ps = (size_t)p->no * p->ldo;
     a.units = nb * tmo * tmo;
-    cudaError_t e = launch<F>(p, p->T1t, p->amat, a, st);
+    cudaError_t e = launch<F, FAST, KGE>(p, p->T1t, p->amat, a, st);
     if (e != cudaSuccess) return e;
     // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No)
     TcArgs b{};
-    b.kind = KGT1;
     b.M = p->ni;
     b.N = p->no;
     b.K = p->no;
@@ -683,19 +795,20 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     b.out_ld = p->ldo;
     b.out_ps = (size_t)p->ni * p->ldo;
     b.units = nb * tmi * tmo;
-    e = launch<F>(p, p->amatH, p->GEt, b, st);
+    e = launch<F, FAST, KGT1>(p, p->amatH, p->GEt, b, st);
     if (e != cudaSuccess) return e;
-    // adjoint stage 1^T + phase gradient: gphi[b] = (2 pi/lambda) Im((GT1[z] . AH(l)^T) conj P[b])
+    // adjoint stage 1^T + phase gradient: gphi[b][split] = (2 pi/lambda) Im((GT1[z] . AH(l)^T) conj P[b]),
+    // the K = No contraction split in gsplit parts (their gphi planes are summed by the reductions)
     TcArgs c{};
-    c.kind = KGP;
     c.M = p->ni;
     c.N = p->ni;
     c.K = p->no;
     c.b0 = b0;
     c.P = p->P.ptr;
     c.gphi = p->gphi;
-    c.units = nb * tmi * tmi;
-    return launch<F>(p, p->GT1, p->amatH, c, st);
+    c.ksplit = p->gsplit;
+    c.units = nb * tmi * tmi * p->gsplit;
+    return launch<F, FAST, KGP>(p, p->GT1, p->amatH, c, st);
 }
 
 }  // namespace
