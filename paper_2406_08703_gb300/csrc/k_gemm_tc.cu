@@ -57,7 +57,11 @@ struct Cfg {
     static constexpr int KSTEP = (F == FMT_TF32X4) ? 8 : 16;  // k per MMA instruction (32 bytes)
     static constexpr int NKSTEP = KB / KSTEP;
     static constexpr uint32_t AB_FMT = (F == FMT_TF32X4) ? 2u : 1u;  // TF32 : BF16
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    // bf16 forms stage the operand tiles they write in one swizzled TMA box
+    // (128 rows x 64 bytes x all planes) and store them with bulk tensor copies
+    static constexpr bool TMA_STORE = (F == FMT_BF16X4 || F == FMT_BF16X2);
+    static constexpr int STG_BYTES = TMA_STORE ? PL * PLANE_BYTES : 0;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + STG_BYTES + 1024 + 256;
 };
 
 // Arguments of one launch.  Per-job operand coordinates come from decode().
@@ -245,6 +249,30 @@ __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t
     }
 }
 
+// Bulk tensor store of a staged box, and the bulk-group bookkeeping around it.
+__device__ __forceinline__ void tma_store4(const CUtensorMap *map, uint32_t src, int c0, int c1, int c2, int c3) {
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+                     (uint64_t)map),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// Barrier of the 256 epilogue threads (warps 0-7).
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// The same barrier returning whether `v` holds for every epilogue thread.
+__device__ __forceinline__ bool epi_all(bool v) {
+    uint32_t out;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(out)
+        : "r"((uint32_t)v)
+        : "memory");
+    return out != 0;
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
@@ -322,6 +350,36 @@ __device__ __forceinline__ void store_row(void *base, size_t ps, size_t off, con
     }
 }
 
+// Write 16 consecutive complex values of row r (columns 16h .. 16h+15 of a
+// 32-column box) into the staged TMA box: planes of 128 rows x 64 bytes,
+// 64-byte swizzle (16-byte granule g of row r sits at g ^ ((r >> 1) & 3)).
+template <int F>
+__device__ __forceinline__ void stage_row16(uint8_t *stg, int r, int h, const float (&re)[CW], const float (&im)[CW]) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float x = re[8 * q + i], y = im[8 * q + i];
+            rh[i] = __float2bfloat16_rn(x);
+            ih[i] = __float2bfloat16_rn(y);
+            rl[i] = __float2bfloat16_rn(x - __bfloat162float(rh[i]));
+            il[i] = __float2bfloat16_rn(y - __bfloat162float(ih[i]));
+        }
+        const int g = (2 * h + q) ^ ((r >> 1) & 3);
+        uint8_t *p = stg + r * 64 + g * 16;
+        if constexpr (F == FMT_BF16X4) {
+            *(uint4 *)(p) = *(uint4 *)rh;
+            *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)rl;
+            *(uint4 *)(p + 2 * PLANE_BYTES) = *(uint4 *)ih;
+            *(uint4 *)(p + 3 * PLANE_BYTES) = *(uint4 *)il;
+        } else {
+            *(uint4 *)(p) = *(uint4 *)rh;
+            *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)ih;
+        }
+    }
+}
+
 // Read CW consecutive complex values of one row of a plane-major operand
 // (the value each represents: hi + lo).
 template <int F>
@@ -383,12 +441,16 @@ __device__ __forceinline__ void load_row(const void *base, size_t ps, size_t off
 // ------------------------------------------------------------------ the kernel
 template <int F, int MODE, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, TcArgs a) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const __grid_constant__ CUtensorMap mapC, TcArgs a) {
     using C = Cfg<F>;
     constexpr uint32_t NBUF = (MODE == FAST) ? 2 : 1;
+    // operand-writing contractions of the bf16 forms store through a staged TMA box
+    constexpr bool TMA_OUT = C::TMA_STORE && (KIND == KS1 || KIND == KGE || KIND == KGT1);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *bars = (uint64_t *)(smem + C::STAGES * C::STAGE_BYTES);
+    uint8_t *stg = smem + C::STAGES * C::STAGE_BYTES;  // staged output box (TMA_OUT)
+    uint64_t *bars = (uint64_t *)(stg + C::STG_BYTES);
     // bars: full[S], empty[S], tfull[2], tempty[2], drain
     const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::STAGES, tfull0 = empty0 + 8 * C::STAGES,
                    tempty0 = tfull0 + 16, drain = tempty0 + 16;
@@ -557,7 +619,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 // every lane waits; the warp proceeds only if all lanes saw the phase,
                 // so the warp-collective tensor-memory loads never diverge
                 const bool got = mbar_wait(tfull0 + 8 * buf, tph, abort_flag, a.err, 6);
-                if (!__all_sync(0xffffffffu, got)) {
+                bool all_got;
+                if constexpr (TMA_OUT) all_got = epi_all(got);  // epilogue-wide: staging uses named barriers
+                else all_got = __all_sync(0xffffffffu, got);
+                if (!all_got) {
                     ok = false;
                     break;
                 }
@@ -573,8 +638,54 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     gi = a.GI + ((size_t)J.r * a.ne + e) * a.nd * a.nd + min(m, a.M - 1) / a.os;
                 }
                 if constexpr (KIND == KGP) k2 = (float)(6.283185307179586476925286766559 / a.lam[J.l]);
+                if constexpr (TMA_OUT) {
+                    // four rounds of one 32-column box: warp (q, h) fills rows 32q.., columns 16h..,
+                    // one thread stores the box; rows and columns past the tensor are clipped by TMA
+                    const int zb = (KIND == KS1) ? J.b : J.z;
+                    for (int t = 0; t < 4; ++t) {
+                        if (J.n0 + 32 * t >= a.out_ld) break;  // uniform over the epilogue warps
+                        const int c0 = 32 * t + 16 * h;
+                        const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + c0;
+                        float er[CW], ei[CW];
+                        tmem_ld16(ta, er);
+                        tmem_ld16(ta + 128, ei);
+                        if constexpr (MODE != FAST) {
+                            float tt[CW];
+                            tmem_ld16(ta + 256, tt);
 #pragma unroll
-                for (int cc = 0; cc < 64 / CW; ++cc) {
+                            for (int i = 0; i < CW; ++i) er[i] += tt[i];
+                            tmem_ld16(ta + 384, tt);
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) ei[i] += tt[i];
+                        }
+                        if constexpr (KIND == KGE) {
+                            const int n0 = J.n0 + c0;
+                            int brow = n0 / a.os, rem = n0 - brow * a.os;
+                            const int bmax = (a.N - 1) / a.os;
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                const float f = c * gi[min(brow, bmax) * a.nd];
+                                er[i] *= f;
+                                ei[i] *= f;
+                                if (++rem == a.os) {
+                                    rem = 0;
+                                    ++brow;
+                                }
+                            }
+                        }
+                        stage_row16<F>(stg, row, h, er, ei);
+                        fence_async_smem();
+                        epi_bar();
+                        if (threadIdx.x == 0) {
+                            tma_store4(&mapC, smem_u32(stg), J.n0 + 32 * t, J.m0, 0, zb);
+                            bulk_commit();
+                            bulk_wait_read0();  // the box may be refilled once TMA has read it
+                        }
+                        epi_bar();
+                    }
+                }
+#pragma unroll
+                for (int cc = 0; cc < (TMA_OUT ? 0 : 64 / CW); ++cc) {
                     const int c0 = 64 * h + CW * cc;
                     const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + c0;
                     float er[CW], ei[CW];
@@ -663,6 +774,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int i = 0; i < 64; ++i) acc[i] = 0.f;
             }
         }
+        if constexpr (TMA_OUT) {
+            if (threadIdx.x == 0) bulk_wait0();  // the last boxes have reached global memory
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -710,7 +824,8 @@ bool make_map(dlx_plan *p, Operand &o, std::string *why) {
 }
 
 template <int F, int MODE, int KIND>
-cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, TcArgs &a, cudaStream_t st) {
+cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operand *Cout, TcArgs &a,
+                   cudaStream_t st) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F, MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -740,7 +855,7 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, TcArgs &a, c
     const int grid = std::min(a.units, p->sm_count);
     static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
     KScope ks(p, cls_of[KIND], 1, st);
-    k_tc_gemm<F, MODE, KIND><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, a);
+    k_tc_gemm<F, MODE, KIND><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, Cout ? Cout->tmap : A.tmap, a);
     return cudaGetLastError();
 }
 
@@ -755,7 +870,7 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     a.out_ld = p->ldi;
     a.out_ps = (size_t)p->no * p->ldi;
     a.units = R * p->B * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
-    cudaError_t e = launch<F, MODE, KS1>(p, p->amat, p->P, a, st);
+    cudaError_t e = launch<F, MODE, KS1>(p, p->amat, p->P, &p->T1t, a, st);
     if (e != cudaSuccess) return e;
     // stage 2 + intensity: Is[g][rse] = sum_l w |A(l) . T1t[b]^T|^2  (M = N = No, K = Ni)
     TcArgs c{};
@@ -765,7 +880,7 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     c.Is = p->Is;
     c.Rnse = R * p->nse;
     c.units = c.Rnse * p->G * ((p->no + BM - 1) / BM) * ((p->no + BN - 1) / BN);
-    return launch<F, MODE, KS2>(p, p->amat, p->T1t, c, st);
+    return launch<F, MODE, KS2>(p, p->amat, p->T1t, nullptr, c, st);
 }
 
 template <int F>
@@ -783,7 +898,7 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     a.out_ld = p->ldo;
     a.out_ps = (size_t)p->no * p->ldo;
     a.units = nb * tmo * tmo;
-    cudaError_t e = launch<F, FAST, KGE>(p, p->T1t, p->amat, a, st);
+    cudaError_t e = launch<F, FAST, KGE>(p, p->T1t, p->amat, &p->GEt, a, st);
     if (e != cudaSuccess) return e;
     // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No)
     TcArgs b{};
@@ -795,7 +910,7 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     b.out_ld = p->ldo;
     b.out_ps = (size_t)p->ni * p->ldo;
     b.units = nb * tmi * tmo;
-    e = launch<F, FAST, KGT1>(p, p->amatH, p->GEt, b, st);
+    e = launch<F, FAST, KGT1>(p, p->amatH, p->GEt, &p->GT1, b, st);
     if (e != cudaSuccess) return e;
     // adjoint stage 1^T + phase gradient: gphi[b][split] = (2 pi/lambda) Im((GT1[z] . AH(l)^T) conj P[b]),
     // the K = No contraction split in gsplit parts (their gphi planes are summed by the reductions)
@@ -808,7 +923,7 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     c.gphi = p->gphi;
     c.ksplit = p->gsplit;
     c.units = nb * tmi * tmi * p->gsplit;
-    return launch<F, FAST, KGP>(p, p->GT1, p->amatH, c, st);
+    return launch<F, FAST, KGP>(p, p->GT1, p->amatH, nullptr, c, st);
 }
 
 }  // namespace
