@@ -46,6 +46,10 @@ def parse():
                     help="use only this many of the workload's wavelengths (same per-PSF shapes; profiling captures)")
     ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side FP32 / other-form lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--serving", action="store_true",
+                    help="the serving workload instead: mixed-size fit requests through dlx_submit/dlx_poll")
+    ap.add_argument("--serving-requests", type=int, default=36)
+    ap.add_argument("--serving-shapes", type=int, default=6)
     return ap.parse_args()
 
 
@@ -246,6 +250,115 @@ def cpu_baseline(workload, budget_s=20.0):
                        f"{dt:.2f} s each; value scaled by {frac:.4f} of the PSFs")
 
 
+SERVING_METRIC = "serving: fit requests (K Adam fwd+grad steps each) evals/s and p50/p99 request latency"
+
+
+def serving_requests(n_req, n_shapes, seed=55):
+    """Seeded fit requests of mixed sizes: pupil {128, 256, 512}, detector {64..512}, oversample {2, 4},
+    wavelengths {1, 8, 32, 64}, 1-3 stars, drawn from a pool of `n_shapes` shapes; truths as in the tiny
+    workload (Noll Zernikes, smoothed pixel OPD, flat field); data are Poisson counts of an analytic image."""
+    import workloads as W
+
+    shapes = W.serving_request_shapes(n_shapes, seed)
+    base = {}
+    rng = np.random.default_rng(seed + 1)
+    out = []
+    for i in range(n_req):
+        k = int(rng.integers(len(shapes)))
+        if k not in base:
+            sh = shapes[k]
+            base[k] = W.make_problem("custom", seed=seed + 10 + k, n_pupil=sh["n_pupil"], n_det=sh["n_det"],
+                                     oversample=sh["oversample"], n_lambda=sh["n_lambda"], n_src=sh["n_src"],
+                                     n_zern_max=8, opd_pix_rms=5e-9)
+        truth = base[k]
+        start = W.perturbed_start(truth, seed + 1000 + i)
+        start.opd_pix = np.zeros_like(truth.opd_pix)
+        data = W.synthetic_counts((truth.n_exp, truth.n_det, truth.n_det), float(np.sum(truth.flux)) * truth.n_exp,
+                                  truth.pos / truth.pixscale, 4.0, seed + 2000 + i)
+        out.append((k, start, data))
+    return out
+
+
+def serving_run(P, reqs, form, n_steps, rate=None, seed=0):
+    """Submit every request (all at once, or at Poisson arrival times of `rate` per
+    second) to a fresh server; returns per-request latencies and the evals/s."""
+    import threading
+
+    from paper_2406_08703_gb300.server import result_shapes
+
+    lr = dict(zern=1e-9, opd_pix=1e-10, flat=1e-3, flux=1e3, pos=1e-8)
+    srv = P.dlx_server_create(0, 0, 16)
+    prec = P.PRECISIONS[form]
+    # warm-up: one request per shape builds each bucket's plan and captures its graphs
+    warm = {}
+    for k, p, d in reqs:
+        if k not in warm:
+            warm[k] = srv.submit(p, d, n_steps=n_steps, lr=lr, precision=prec)
+    for k, t in warm.items():
+        srv.poll(t, 600.0)
+    tickets = [None] * len(reqs)
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+
+    def submitter():
+        t_next = time.perf_counter()
+        for i, (k, p, d) in enumerate(reqs):
+            if rate:
+                t_next += rng.exponential(1.0 / rate)
+                dt = t_next - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            tickets[i] = srv.submit(p, d, n_steps=n_steps, lr=lr, precision=prec)
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    lat, done = [], set()
+    while len(done) < len(reqs):
+        for i, (k, p, d) in enumerate(reqs):
+            if i in done or tickets[i] is None:
+                continue
+            r = srv.poll(tickets[i], 0.0)
+            if r is not None:
+                lat.append(r["latency_s"])
+                done.add(i)
+        time.sleep(0.0005)
+    th.join()
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    evals = len(reqs) * max(1, n_steps)
+    return dict(evals_per_s=evals / wall, requests_per_s=len(reqs) / wall, wall_s=wall,
+                p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
+                grouped_launches=int(stats["grouped_launches"]), graph_launches=int(stats["graph_launches"]))
+
+
+def serving_bench(args):
+    import torch
+
+    import paper_2406_08703_gb300 as P
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    P.load()
+    n_steps = 10
+    reqs = serving_requests(args.serving_requests, args.serving_shapes)
+    sat = serving_run(P, reqs, args.form, n_steps)
+    rates = {}
+    for frac in (0.5, 0.9):
+        rates[str(frac)] = serving_run(P, reqs, args.form, n_steps, rate=frac * sat["requests_per_s"], seed=7)
+    small = reqs[: max(4, len(reqs) // 4)]
+    fp32 = serving_run(P, small, "fp32", n_steps)
+    split_small = serving_run(P, small, args.form, n_steps)
+    line = dict(metric=SERVING_METRIC, value=sat["evals_per_s"], unit="evals/s", n_gpus=1, steps=n_steps,
+                warmup=1, ms_per_step=1e3 / sat["evals_per_s"], higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype=f"{args.form} split (fp32 accumulate)", data="synthetic",
+                config=dict(workload=f"{len(reqs)} fit requests of {args.serving_shapes} mixed shapes (pupil 128-512, "
+                                     "detector 64-512, oversample 2-4, 1-64 wavelengths, 1-3 stars), K=10 Adam "
+                                     "steps each", form=args.form),
+                saturated=sat, poisson_rates=rates,
+                forms={"fp32": dict(fp32, requests=len(small)), args.form: dict(split_small, requests=len(small))})
+    print(json.dumps(line), flush=True)
+
+
 def reference_arm(args, rank, world):
     """--impl reference: the FP64 CPU oracle timed on this host, rank 0 only."""
     if rank != 0:
@@ -284,6 +397,10 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.serving:
+        if rank == 0:
+            serving_bench(args)
         return
     import torch
 

@@ -400,17 +400,23 @@ void worker_loop(dlx_server *s) {
             auto bi = s->buckets.find(key);
             if (bi != s->buckets.end()) b = bi->second.get();
             if (!b) {
-                // free idle buckets of other shapes before creating a new one
-                for (auto e = s->buckets.begin(); e != s->buckets.end();) {
-                    if (e->second->active == 0) {
-                        s->in_use -= e->second->bytes;
-                        destroy_bucket(e->second.get());
-                        e = s->buckets.erase(e);
-                    } else {
-                        ++e;
-                    }
-                }
+                // keep idle buckets (their plans and graphs) cached; free them only when
+                // the new bucket would not fit in the budget otherwise
                 int rc = create_bucket(s, *q, &b);
+                if (rc == DLX_ERR_NOMEM) {
+                    bool freed = false;
+                    for (auto e = s->buckets.begin(); e != s->buckets.end();) {
+                        if (e->second->active == 0) {
+                            s->in_use -= e->second->bytes;
+                            destroy_bucket(e->second.get());
+                            e = s->buckets.erase(e);
+                            freed = true;
+                        } else {
+                            ++e;
+                        }
+                    }
+                    if (freed) rc = create_bucket(s, *q, &b);
+                }
                 if (rc == DLX_ERR_NOMEM) {
                     ++it;  // wait for memory to free up
                     continue;
