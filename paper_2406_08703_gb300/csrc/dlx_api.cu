@@ -230,6 +230,11 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
     const size_t nslice = (npx + 2047) / 2048;  // slices of the sliced gradient reductions
     if (e == cudaSuccess) e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * p->gsplit * nslice);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->npart, sizeof(float2) * kNormParts * R_max);
+    if (e == cudaSuccess && p->prec != DLX_FP32_SIMT) {
+        const size_t tiles = (size_t)((p->ni + 127) / 128) * ((p->ni + 127) / 128);
+        e = plan_alloc(p, &p->mom, sizeof(float) * 2 * 8 * tiles * Bt * p->gsplit);
+    }
     if (e == cudaSuccess) e = plan_alloc(p, &p->zpart, sizeof(double) * R_max * std::max(1, p->nz) * nslice);
     if (e == cudaSuccess) e = plan_alloc(p, &p->err, sizeof(int32_t));
     if (e == cudaSuccess) e = plan_alloc(p, &p->clamped, sizeof(unsigned long long));

@@ -155,6 +155,8 @@ struct dlx_plan {
     int red_blocks = 0;
     double *pos_part = nullptr;// [R*B][slices][2] position-moment partials
     double *zpart = nullptr;   // [R][n_zern][slices] Zernike-gradient partials
+    float *mom = nullptr;      // tensor-core forms: [R*B][gsplit][tiles][8 warps][2] position moments
+    float2 *npart = nullptr;   // [R][kNormParts] block partials of sum T^2 (compensated pairs)
     int32_t *err = nullptr;    // device error flag
     unsigned long long *clamped = nullptr;
     size_t workspace = 0;
@@ -175,6 +177,7 @@ struct dlx_plan {
 namespace dlx {
 
 constexpr int kMaxSrc = 8;
+constexpr int kNormParts = 1024;  // maximum blocks of the OPD / pupil-power pass
 
 enum KClass { KC_MATRICES = 0, KC_PROLOGUE, KC_STAGE1, KC_STAGE2, KC_BIN, KC_LOSS, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1,
               KC_GRAD, KC_ADAM, KC_N };

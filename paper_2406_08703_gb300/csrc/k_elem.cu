@@ -106,49 +106,63 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// Per slot: pupil normalisation of BasisOptic(normalise=True), 1/sqrt(sum T^2),
-// and the normalised spectral weights w_l / sum w.  One block per slot.
-__global__ void k_norms(DevParams prm, int npx, int nl, float *pscale, float *wnorm) {
-    __shared__ df sh[32];
-    const int r = blockIdx.x;
-    const float *T = slot_ptr(prm, PT, r), *w = slot_ptr(prm, PW, r);
-    df v[1] = {{0.f, 0.f}};
-    int i = threadIdx.x;
-    for (; i + 7 * (int)blockDim.x < npx; i += 8 * blockDim.x) {
-        float t[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) t[q] = __ldg(T + i + q * blockDim.x);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) v[0] = df_add(v[0], t[q] * t[q]);
-    }
-    for (; i < npx; i += blockDim.x) v[0] = df_add(v[0], T[i] * T[i]);
-    block_sum<1>(v, sh);
-    __shared__ float s_scale;
-    if (threadIdx.x == 0) {
-        s_scale = (float)(1.0 / sqrt(df_to_double(v[0])));
-        pscale[r] = s_scale;
-    }
-    df ws{0.f, 0.f};
-    for (int l = 0; l < nl; ++l) ws = df_add(ws, w[l]);
-    const float wsum = ws.hi + ws.lo;
-    for (int l = threadIdx.x; l < nl; l += blockDim.x) wnorm[(size_t)r * nl + l] = w[l] / wsum;
-}
-
 // OPD = OPD_fixed + sum_j c_j Z_j + OPD_pix (Sec. 3: BasisOptic coefficients on a
-// Zernike basis, the fixed mask, and the free per-pixel map).  grid.y = slot.
-__global__ void k_opd(DevParams prm, int nz, int npx, float *__restrict__ opd) {
+// Zernike basis, the fixed mask, and the free per-pixel map), grid (blocks, R).
+// The same pass reduces this block's share of sum T^2 (for the pupil
+// normalisation of BasisOptic(normalise=True)) into npart[r][block], and block 0
+// of each slot writes the normalised spectral weights w_l / sum w.
+__global__ void k_opd_norm(DevParams prm, int nz, int npx, int nl, float *__restrict__ opd, float2 *npart,
+                           float *wnorm) {
     extern __shared__ float c_sh[];
+    __shared__ df sh[32];
     const int r = blockIdx.y;
     const float *fixed = slot_ptr(prm, POPDF, r), *basis = slot_ptr(prm, PBASIS, r);
-    const float *coeff = slot_ptr(prm, PCOEFF, r), *pix = slot_ptr(prm, POPDPIX, r);
+    const float *coeff = slot_ptr(prm, PCOEFF, r), *pix = slot_ptr(prm, POPDPIX, r), *T = slot_ptr(prm, PT, r);
     for (int j = threadIdx.x; j < nz; j += blockDim.x) c_sh[j] = coeff[j];
     __syncthreads();
+    df t2[1] = {{0.f, 0.f}};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npx; i += gridDim.x * blockDim.x) {
         float v = fixed ? fixed[i] : 0.f;
-        for (int j = 0; j < nz; ++j) v = fmaf(c_sh[j], __ldg(basis + (size_t)j * npx + i), v);
+        int j = 0;
+        for (; j + 4 <= nz; j += 4) {
+            const float b0 = __ldg(basis + (size_t)j * npx + i), b1 = __ldg(basis + (size_t)(j + 1) * npx + i);
+            const float b2 = __ldg(basis + (size_t)(j + 2) * npx + i), b3 = __ldg(basis + (size_t)(j + 3) * npx + i);
+            v = fmaf(c_sh[j], b0, v);
+            v = fmaf(c_sh[j + 1], b1, v);
+            v = fmaf(c_sh[j + 2], b2, v);
+            v = fmaf(c_sh[j + 3], b3, v);
+        }
+        for (; j < nz; ++j) v = fmaf(c_sh[j], __ldg(basis + (size_t)j * npx + i), v);
         if (pix) v += pix[i];
         opd[(size_t)r * npx + i] = v;
+        const float t = T[i];
+        t2[0] = df_add(t2[0], t * t);
     }
+    block_sum<1>(t2, sh);
+    if (threadIdx.x == 0) npart[(size_t)r * gridDim.x + blockIdx.x] = make_float2(t2[0].hi, t2[0].lo);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const float *w = slot_ptr(prm, PW, r);
+        df ws{0.f, 0.f};
+        for (int l = 0; l < nl; ++l) ws = df_add(ws, w[l]);
+        const float wsum = ws.hi + ws.lo;
+        for (int l = 0; l < nl; ++l) wnorm[(size_t)r * nl + l] = w[l] / wsum;
+    }
+}
+
+// 1/sqrt(sum T^2) of slot r from the OPD pass's block partials (fixed order).
+__device__ float pupil_scale(const float2 *npart, int nblk, int r) {
+    __shared__ float s_scale;
+    if (threadIdx.x < 32) {
+        df v{0.f, 0.f};
+        for (int b = threadIdx.x; b < nblk; b += 32) {
+            const float2 x = npart[(size_t)r * nblk + b];
+            v = df_add(v, df{x.x, x.y});
+        }
+        v = warp_sum(v);
+        if (threadIdx.x == 0) s_scale = (float)(1.0 / sqrt(df_to_double(v)));
+    }
+    __syncthreads();
+    return s_scale;
 }
 
 // Separable tilt factors exp(i 2 pi x_n theta / lambda) per PSF and axis, with
@@ -175,13 +189,13 @@ __global__ void k_tilt(DevParams prm, const double *lam, int nbt, int B, int nse
 // the aberrations of interest, so FP32 is exact enough there.
 template <int F>
 __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
-                         const float *__restrict__ invlam, const float *__restrict__ pscale, int nbt, int B, int nse,
-                         int ni, int ldi, void *P) {
+                         const float *__restrict__ invlam, const float2 *__restrict__ npart, int nblk, int nbt, int B,
+                         int nse, int ni, int ldi, void *P) {
     // grid: x over pupil pixels, y over PSFs (no 64-bit index arithmetic)
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F);
     const int bg = blockIdx.y, r = bg / B, l = (bg % B) / nse;
     const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
-    const float sc = pscale[r], il = invlam[l];
+    const float sc = pupil_scale(npart, nblk, r), il = invlam[l];
     const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
     char *base = (char *)P + (size_t)bg * Pl * ni * ldi * es;
     const size_t ps = (size_t)ni * ldi;
@@ -205,17 +219,17 @@ __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const flo
 
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
     const int npx = p->ni * p->ni, nbt = R * p->B;
-    KScope ks(p, KC_PROLOGUE, 4, st);
-    k_norms<<<R, 1024, 0, st>>>(prm, npx, p->nl, p->pscale, p->wnorm);
-    int blocks = std::max(1, std::min((npx + 255) / 256, p->sm_count * 8 / R));
-    k_opd<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(prm, p->nz, npx, p->opd);
+    KScope ks(p, KC_PROLOGUE, 3, st);
+    const int blocks = std::max(1, std::min({(npx + 255) / 256, p->sm_count * 8 / R, kNormParts}));
+    k_opd_norm<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(prm, p->nz, npx, p->nl, p->opd,
+                                                                                     p->npart, p->wnorm);
     size_t tt = (size_t)nbt * 2 * p->ni;
     int tb = (int)std::min<size_t>((tt + 255) / 256, (size_t)p->sm_count * 8);
     k_tilt<<<tb, 256, 0, st>>>(prm, p->lam_d, nbt, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt);
     const int px = std::max(1, std::min((npx + 255) / 256, (p->sm_count * 16 + nbt - 1) / nbt));
     DLX_FMT_DISPATCH(p->fmt, F,
-                     k_phasor<F><<<dim3(px, nbt), 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->pscale, nbt,
-                                                                p->B, p->nse, p->ni, p->ldi, p->P.ptr));
+                     k_phasor<F><<<dim3(px, nbt), 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->npart, blocks,
+                                                                nbt, p->B, p->nse, p->ni, p->ldi, p->P.ptr));
     return cudaGetLastError();
 }
 
@@ -435,6 +449,23 @@ __global__ void k_pos_final(const double *part, int nsplit, int B, int nl, int n
     if (lane == 0) g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + ax] = (float)v;
 }
 
+// Tensor-core forms: the adjoint 1^T epilogue already reduced sum g x_n and
+// sum g y_n per (PSF, K split, tile, warp); dL/dtheta_s sums those of source s
+// over wavelengths and exposures.  One block per (slot, source, axis), fixed order.
+__global__ void k_pos_final_mom(const float *mom, int per_psf, int B, int nl, int ns, int ne, DevGrads g) {
+    __shared__ df sh[32];
+    const int r = blockIdx.x, s = blockIdx.y, ax = blockIdx.z;
+    const int nt = nl * ne * per_psf;
+    df v[1] = {{0.f, 0.f}};
+    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+        const int le = t / per_psf, k = t % per_psf, l = le / ne, e = le % ne;
+        const size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
+        v[0] = df_add(v[0], mom[(b * per_psf + k) * 2 + ax]);
+    }
+    block_sum<1>(v, sh);
+    if (threadIdx.x == 0) g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + ax] = v[0].hi + v[0].lo;
+}
+
 // dL/dc_j = <Z_j, g_OPD> over one slice of the pupil.  grid (n_slices, n_zern, R);
 // partials in zpart[r][j][slice].
 __global__ void k_zern_partial(DevParams prm, const float2 *__restrict__ gopd, int npx, double *zpart) {
@@ -473,10 +504,14 @@ cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const D
     const int npx = p->ni * p->ni, nslice = (npx + RED_SLICE - 1) / RED_SLICE;
     DevGrads gg{};
     if (g) gg = *g;
-    KScope ks(p, KC_GRAD, 1 + (gg.p[GPOS] ? 2 : 0) + ((gg.p[GZERN] && p->nz > 0) ? 2 : 0), st);
+    KScope ks(p, KC_GRAD, 1 + (gg.p[GPOS] ? (p->mom ? 1 : 2) : 0) + ((gg.p[GZERN] && p->nz > 0) ? 2 : 0), st);
     // gphi holds gsplit partial planes per PSF; they are summed with the PSFs
     k_gopd<<<dim3((npx + 63) / 64, R), 256, 0, st>>>(p->gphi, R, p->B * p->gsplit, npx, p->gopd, gg);
-    if (gg.p[GPOS]) {
+    if (gg.p[GPOS] && p->mom) {
+        const int tiles = ((p->ni + 127) / 128) * ((p->ni + 127) / 128);
+        k_pos_final_mom<<<dim3(R, p->ns, 2), 256, 0, st>>>(p->mom, p->gsplit * tiles * 8, p->B, p->nl, p->ns, p->ne,
+                                                           gg);
+    } else if (gg.p[GPOS]) {
         k_pos_moments<<<R * p->B * p->gsplit, 256, 0, st>>>(p->gphi, p->ni, (float)p->dx, p->pos_part);
         k_pos_final<<<dim3(R, p->ns, 2), 32, 0, st>>>(p->pos_part, p->gsplit, p->B, p->nl, p->ns, p->ne, gg);
     }

@@ -82,6 +82,8 @@ struct TcArgs {
     const void *P;    // phasor operand (KGP)
     const double *lam;
     float *gphi;
+    float *mom;       // per-warp position moments (KGP)
+    float dxf, cNf;   // pupil spacing and centre index (KGP)
     int32_t *err;
 };
 
@@ -628,6 +630,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 }
                 tc_fence_after();
                 const int m = J.m0 + row;
+                float mom_x = 0.f, mom_g = 0.f;  // position moments of this row (adjoint 1^T)
                 // per-job constants of the epilogues
                 float w = 0.f, c = 0.f, k2 = 0.f;
                 const float *gi = nullptr;
@@ -730,22 +733,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 const char *pb = (const char *)a.P + (size_t)J.b * C::PL * pps * C::ES;
                                 float *o = a.gphi + ((size_t)J.b * a.ksplit + J.split) * a.ni * a.ni + (size_t)m * a.ni +
                                            n0;
-                                float pr[CW], pi[CW];
+                                float pr[CW], pi[CW], gv[CW];
                                 load_row<F>(pb, pps, (size_t)m * a.ldi + n0, pr, pi, nvalid);
+#pragma unroll
+                                for (int i = 0; i < CW; ++i) {
+                                    gv[i] = (i < nvalid) ? k2 * (ei[i] * pr[i] - er[i] * pi[i]) : 0.f;
+                                    // position moments of this row: sum g x_n and sum g
+                                    mom_x = fmaf(gv[i], ((float)(n0 + i) - a.cNf) * a.dxf, mom_x);
+                                    mom_g += gv[i];
+                                }
                                 if (nvalid == CW && (a.ni & 3) == 0) {
 #pragma unroll
-                                    for (int qq = 0; qq < CW / 4; ++qq) {
-                                        float4 v;
-                                        v.x = k2 * (ei[4 * qq + 0] * pr[4 * qq + 0] - er[4 * qq + 0] * pi[4 * qq + 0]);
-                                        v.y = k2 * (ei[4 * qq + 1] * pr[4 * qq + 1] - er[4 * qq + 1] * pi[4 * qq + 1]);
-                                        v.z = k2 * (ei[4 * qq + 2] * pr[4 * qq + 2] - er[4 * qq + 2] * pi[4 * qq + 2]);
-                                        v.w = k2 * (ei[4 * qq + 3] * pr[4 * qq + 3] - er[4 * qq + 3] * pi[4 * qq + 3]);
-                                        *(float4 *)(o + 4 * qq) = v;
-                                    }
+                                    for (int qq = 0; qq < CW / 4; ++qq)
+                                        *(float4 *)(o + 4 * qq) =
+                                            make_float4(gv[4 * qq], gv[4 * qq + 1], gv[4 * qq + 2], gv[4 * qq + 3]);
                                 } else {
 #pragma unroll
                                     for (int i = 0; i < CW; ++i)
-                                        if (i < nvalid) o[i] = k2 * (ei[i] * pr[i] - er[i] * pi[i]);
+                                        if (i < nvalid) o[i] = gv[i];
                                 }
                             } else {
                                 const int zb = (KIND == KS1) ? J.b : J.z;
@@ -758,6 +763,23 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+                if constexpr (KIND == KGP) {
+                    // per-warp position moments of this tile, reduced in a fixed order:
+                    // mom[entry][tile][warp] = (sum g x_n, sum g y_n), entry = PSF x K split
+                    float sy = (m < a.M) ? mom_g * (((float)m - a.cNf) * a.dxf) : 0.f;
+                    float sx = mom_x;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                    }
+                    if (lane == 0) {
+                        const int tile = (J.m0 / BM) * a.tn + J.n0 / BN;
+                        const size_t ent = (size_t)J.b * a.ksplit + J.split;
+                        float2 *dst = (float2 *)a.mom + ((ent * a.tm * a.tn + tile) * EPI_WARPS + warp);
+                        *dst = make_float2(sx, sy);
+                    }
+                }
             }
             if (!ok) break;
             if constexpr (KIND == KS2) {
@@ -921,6 +943,9 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     c.b0 = b0;
     c.P = p->P.ptr;
     c.gphi = p->gphi;
+    c.mom = p->mom;
+    c.dxf = (float)p->dx;
+    c.cNf = 0.5f * (float)(p->ni - 1);
     c.ksplit = p->gsplit;
     c.units = nb * tmi * tmi * p->gsplit;
     return launch<F, FAST, KGP>(p, p->GT1, p->amatH, nullptr, c, st);

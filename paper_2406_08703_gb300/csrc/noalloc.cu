@@ -146,6 +146,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     need.take<float>((size_t)p.nse * nq);
     need.take<double>((size_t)p.red_blocks * (1 + dlx::kMaxSrc));
     need.take<unsigned long long>(1);
+    need.take<float2>(dlx::kNormParts);
     if (need.off > kNoAllocScratchBytes) {
         dlx_set_error("dlx_forward_noalloc: this shape needs " + std::to_string(need.off) +
                       " bytes of working memory, above the fixed 16 MiB scratch; use dlx_make_mft + dlx_forward");
@@ -169,6 +170,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     p.Is = c.take<float>((size_t)p.nse * nq);
     p.red = c.take<double>((size_t)p.red_blocks * (1 + dlx::kMaxSrc));
     p.clamped = c.take<unsigned long long>(1);
+    p.npart = c.take<float2>(dlx::kNormParts);
 
     // The FP32 contractions read operands only inside their true extents and every
     // region above is written before it is read in this call, so nothing has to be
