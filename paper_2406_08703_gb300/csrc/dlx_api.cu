@@ -8,6 +8,7 @@
 #include <string>
 
 #include "dlx_common.cuh"
+#include "s2_schedule.h"
 
 static thread_local std::string g_last_error;
 
@@ -88,7 +89,7 @@ static cudaEvent_t pool_get(dlx_plan *p) {
 }
 
 KScope::KScope(dlx_plan *p_, int c, int n_, cudaStream_t s) : p(p_), cls(c), n(n_), st(s) {
-    if (p->timing) {
+    if ((p->timing >> cls) & 1u) {
         cudaEvent_t a = pool_get(p);
         b = pool_get(p);
         cudaEventRecord(a, st);
@@ -182,13 +183,39 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
         chunk = (int)std::max<size_t>(1, std::min<size_t>(Bt, d->workspace_limit_bytes / per_psf));
     p->chunk = chunk;
 
-    // wavelength groups of the intensity contraction: enough independent output
-    // tiles to cover every SM.
-    {
-        int tile = (p->prec == DLX_FP32_SIMT) ? 64 : 128;
-        long units = (long)((p->no + tile - 1) / tile) * ((p->no + tile - 1) / tile) * p->nse;
-        long want = (p->prec == DLX_FP32_SIMT) ? 2L * p->sm_count : (long)p->sm_count;
-        p->G = (int)std::min<long>(p->nl, std::max<long>(1, (want + units - 1) / units));
+    // partial-intensity planes.  CUDA-core form: wavelength groups, enough
+    // independent 64-tiles to cover every SM twice.  Tensor-core forms: the
+    // planes of the balanced split of (tile, wavelength) jobs, for every count of
+    // active slots.
+    std::vector<int> s2_host;
+    if (p->prec == DLX_FP32_SIMT) {
+        long units = (long)((p->no + 63) / 64) * ((p->no + 63) / 64) * p->nse;
+        p->G = (int)std::min<long>(p->nl, std::max<long>(1, (2L * p->sm_count + units - 1) / units));
+    } else {
+        const int tt = ((p->no + 127) / 128) * ((p->no + 127) / 128);
+        p->G = 1;
+        p->s2.resize(R_max);
+        for (int R = 1; R <= R_max; ++R) {
+            const int nseg = tt * R * p->nse;
+            int nct = 0;
+            std::vector<int> off;
+            std::vector<S2Piece> pcs;
+            const int planes = s2_schedule(nseg, p->nl, p->sm_count, nct, off, pcs);
+            std::string why;
+            if (!s2_check(nseg, p->nl, nct, off, pcs, planes, &why)) {
+                free_plan(p);
+                return fail(DLX_ERR_CUDA, why);
+            }
+            p->G = std::max(p->G, planes);
+            dlx_plan::S2Split &sp = p->s2[R - 1];
+            sp.off = (long)s2_host.size();
+            s2_host.insert(s2_host.end(), off.begin(), off.end());
+            while (s2_host.size() % 4) s2_host.push_back(0);
+            sp.pcs = (long)s2_host.size();
+            for (const S2Piece &q : pcs) s2_host.insert(s2_host.end(), {q.seg, q.l0, q.l1, q.pz});
+            sp.nct = nct;
+            sp.npieces = (int)pcs.size();
+        }
     }
 
     cudaError_t e = cudaSuccess;
@@ -229,13 +256,21 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(float2) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
     const size_t nslice = (npx + 2047) / 2048;  // slices of the sliced gradient reductions
-    if (e == cudaSuccess) e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * p->gsplit * nslice);
+    if (e == cudaSuccess && p->prec == DLX_FP32_SIMT)
+        e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * p->gsplit);
     if (e == cudaSuccess) e = plan_alloc(p, &p->npart, sizeof(float2) * kNormParts * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->ncount, sizeof(unsigned int) * R_max);
+    if (e == cudaSuccess) e = cudaMemset(p->ncount, 0, sizeof(unsigned int) * R_max);
     if (e == cudaSuccess && p->prec != DLX_FP32_SIMT) {
         const size_t tiles = (size_t)((p->ni + 127) / 128) * ((p->ni + 127) / 128);
         e = plan_alloc(p, &p->mom, sizeof(float) * 2 * 8 * tiles * Bt * p->gsplit);
     }
     if (e == cudaSuccess) e = plan_alloc(p, &p->zpart, sizeof(double) * R_max * std::max(1, p->nz) * nslice);
+    if (e == cudaSuccess && !s2_host.empty()) {
+        e = plan_alloc(p, &p->s2_table, sizeof(int) * s2_host.size());
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p->s2_table, s2_host.data(), sizeof(int) * s2_host.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = plan_alloc(p, &p->err, sizeof(int32_t));
     if (e == cudaSuccess) e = plan_alloc(p, &p->clamped, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(p->err, 0, sizeof(int32_t));
@@ -426,9 +461,9 @@ int dlx_plan_diagnostics(dlx_plan *p, int64_t *clamped, int32_t *device_error) {
     return DLX_OK;
 }
 
-int dlx_plan_set_timing(dlx_plan *p, int enable) {
+int dlx_plan_set_timing(dlx_plan *p, int class_mask) {
     if (!p) return fail(DLX_ERR_INVALID_ARG, "plan is NULL");
-    p->timing = enable != 0;
+    p->timing = (uint32_t)class_mask;
     return DLX_OK;
 }
 

@@ -5,11 +5,12 @@
 // contraction length rounded up to a multiple of 8 (16-byte rows for the
 // tensor-memory-access engine; padding columns stay zero).  The planes depend
 // on the arithmetic form:
-//   F32    : re, im                   (float)           -- CUDA-core FP32 form
-//   BF16X3 : re_hi, re_lo, im_hi, im_lo (bf16)           -- split, 3 products
-//   BF16   : re, im                   (bf16)            -- hi only
-//   TF32X3 : re_hi, re_lo, im_hi, im_lo (tf32 in fp32)   -- split, 3 products
-// hi = round(x), lo = round(x - hi); the lo*lo product is dropped.
+//   FMT_F32    : re, im                     (float)         -- CUDA-core FP32 form
+//   FMT_BF16X4 : re_hi, re_lo, im_hi, im_lo (bf16)          -- BF16x3 and BF16x4 forms
+//   FMT_BF16X2 : re, im                     (bf16)          -- plain BF16 form
+//   FMT_TF32X4 : re_hi, re_lo, im_hi, im_lo (tf32 in fp32)  -- TF32x3 form
+// hi = round(x), lo = round(x - hi).  Which split products a contraction forms
+// (three, or four with lo*lo) is chosen by the tensor-core kernel per form.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -69,6 +70,66 @@ __device__ __forceinline__ void store_cplx(void *base, size_t pstride, size_t id
         p[pstride + idx] = tf32_round(re - rh);
         p[2 * pstride + idx] = ih;
         p[3 * pstride + idx] = tf32_round(im - ih);
+    }
+}
+
+// Store eight consecutive complex values at element `idx` (a multiple of 8) of
+// a plane-major operand: one 16-byte (bf16) or two (fp32) stores per plane.
+template <int F>
+__device__ __forceinline__ void store_cplx8(void *base, size_t pstride, size_t idx, const float (&re)[8],
+                                            const float (&im)[8]) {
+    if constexpr (F == FMT_F32 || F == FMT_TF32X4) {
+        float *p = (float *)base + idx;
+        float hr[8], hi[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            hr[q] = (F == FMT_F32) ? re[q] : tf32_round(re[q]);
+            hi[q] = (F == FMT_F32) ? im[q] : tf32_round(im[q]);
+        }
+        auto put = [&](float *d, const float *v) {
+            ((float4 *)d)[0] = make_float4(v[0], v[1], v[2], v[3]);
+            ((float4 *)d)[1] = make_float4(v[4], v[5], v[6], v[7]);
+        };
+        if constexpr (F == FMT_F32) {
+            put(p, hr);
+            put(p + pstride, hi);
+        } else {
+            float lr[8], li[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                lr[q] = tf32_round(re[q] - hr[q]);
+                li[q] = tf32_round(im[q] - hi[q]);
+            }
+            put(p, hr);
+            put(p + pstride, lr);
+            put(p + 2 * pstride, hi);
+            put(p + 3 * pstride, li);
+        }
+    } else {
+        __nv_bfloat16 *p = (__nv_bfloat16 *)base + idx;
+        uint32_t wr[4], wi[4], vr[4], vi[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const __nv_bfloat162 a = __floats2bfloat162_rn(re[2 * q], re[2 * q + 1]);
+            const __nv_bfloat162 b = __floats2bfloat162_rn(im[2 * q], im[2 * q + 1]);
+            wr[q] = *(const uint32_t *)&a;
+            wi[q] = *(const uint32_t *)&b;
+            if constexpr (F == FMT_BF16X4) {
+                const __nv_bfloat162 c = __floats2bfloat162_rn(re[2 * q] - __low2float(a), re[2 * q + 1] - __high2float(a));
+                const __nv_bfloat162 d = __floats2bfloat162_rn(im[2 * q] - __low2float(b), im[2 * q + 1] - __high2float(b));
+                vr[q] = *(const uint32_t *)&c;
+                vi[q] = *(const uint32_t *)&d;
+            }
+        }
+        if constexpr (F == FMT_BF16X4) {
+            *(uint4 *)p = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+            *(uint4 *)(p + pstride) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
+            *(uint4 *)(p + 2 * pstride) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+            *(uint4 *)(p + 3 * pstride) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
+        } else {
+            *(uint4 *)p = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+            *(uint4 *)(p + pstride) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+        }
     }
 }
 
@@ -136,7 +197,15 @@ struct dlx_plan {
     int ni, nd, os, no, nl, ns, ne, nz, B, nse, ldi, ldo;
     int prec, fmt, planes, esz;
     double dx, du;
-    int G = 1;       // wavelength groups of the intensity contraction (partial planes)
+    int G = 1;       // partial-intensity planes of the intensity contraction
+    // tensor-core forms: the intensity contraction's work split for R active slots
+    // (s2[R-1]); offsets and pieces live in s2_table (see s2_schedule.h)
+    struct S2Split {
+        long off = 0, pcs = 0;  // int offsets of the CTA offsets and of the pieces
+        int nct = 0, npieces = 0;
+    };
+    std::vector<S2Split> s2;
+    int *s2_table = nullptr;
     int chunk = 1;   // PSFs per adjoint pass
     int gsplit = 1;  // K splits of the adjoint 1^T contraction: gphi holds [R*B][gsplit][ni*ni]
     dlx::Operand amat, amatH, P, T1t, GEt, GT1;
@@ -153,10 +222,11 @@ struct dlx_plan {
     float2 *gopd = nullptr;    // [R][ni*ni] g_OPD as a compensated (hi, lo) FP32 pair
     double *red = nullptr;     // [R][red_blocks][1 + 8] reduction partials
     int red_blocks = 0;
-    double *pos_part = nullptr;// [R*B][slices][2] position-moment partials
+    double *pos_part = nullptr;// CUDA-core form: [R*B][gsplit][2] position-moment partials
     double *zpart = nullptr;   // [R][n_zern][slices] Zernike-gradient partials
     float *mom = nullptr;      // tensor-core forms: [R*B][gsplit][tiles][8 warps][2] position moments
     float2 *npart = nullptr;   // [R][kNormParts] block partials of sum T^2 (compensated pairs)
+    unsigned int *ncount = nullptr;  // [R] blocks of the prologue pass done (reset by the last one)
     int32_t *err = nullptr;    // device error flag
     unsigned long long *clamped = nullptr;
     size_t workspace = 0;
@@ -166,7 +236,7 @@ struct dlx_plan {
         int cls;
         cudaEvent_t a, b;
     };
-    bool timing = false;
+    uint32_t timing = 0;  // bit c: time kernel class c
     std::vector<TimedRec> recs;
     std::vector<cudaEvent_t> pool;
     size_t pool_next = 0;
@@ -199,7 +269,7 @@ void free_plan(dlx_plan *p);
 
 // ---- launchers (k_elem.cu); R = number of active slots (<= R_max)
 cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st);
-cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st);  // norms, OPD, tilt, phasor
+cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st);  // OPD, norm, tilt, phasor
 // binning + flat field (+ Poisson NLL and its partials when data != NULL)
 cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride,
                            float *model, size_t model_stride, const DevGrads *g, cudaStream_t st);

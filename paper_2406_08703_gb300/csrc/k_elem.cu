@@ -106,22 +106,29 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// OPD = OPD_fixed + sum_j c_j Z_j + OPD_pix (Sec. 3: BasisOptic coefficients on a
-// Zernike basis, the fixed mask, and the free per-pixel map), grid (blocks, R).
-// The same pass reduces this block's share of sum T^2 (for the pupil
-// normalisation of BasisOptic(normalise=True)) into npart[r][block], and block 0
-// of each slot writes the normalised spectral weights w_l / sum w.
-__global__ void k_opd_norm(DevParams prm, int nz, int npx, int nl, float *__restrict__ opd, float2 *npart,
-                           float *wnorm) {
+// Prologue pass, grid (blocks, R), slot r = blockIdx.y:
+//  * OPD = OPD_fixed + sum_j c_j Z_j + OPD_pix (Sec. 3: BasisOptic coefficients
+//    on a Zernike basis, the fixed mask, and the free per-pixel map);
+//  * sum T^2 for the pupil normalisation of BasisOptic(normalise=True): block
+//    partials go to npart[r][block], and the last block of the slot to finish
+//    sums them in a fixed order into pscale[r] = 1 / sqrt(sum T^2);
+//  * the separable tilt factors exp(i 2 pi x_n theta / lambda) of every PSF and
+//    axis, theta = pos[s] + dither[e], with the argument reduced in FP64;
+//  * block 0 writes the normalised spectral weights w_l / sum w.
+__global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__restrict__ opd, float2 *npart,
+                           unsigned int *ncount, float *pscale, float *wnorm, const double *__restrict__ lam, int B,
+                           int nse, int ne, int ni, double dx, float2 *__restrict__ tilt) {
     extern __shared__ float c_sh[];
     __shared__ df sh[32];
+    __shared__ bool s_last;
     const int r = blockIdx.y;
     const float *fixed = slot_ptr(prm, POPDF, r), *basis = slot_ptr(prm, PBASIS, r);
     const float *coeff = slot_ptr(prm, PCOEFF, r), *pix = slot_ptr(prm, POPDPIX, r), *T = slot_ptr(prm, PT, r);
     for (int j = threadIdx.x; j < nz; j += blockDim.x) c_sh[j] = coeff[j];
     __syncthreads();
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
     df t2[1] = {{0.f, 0.f}};
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npx; i += gridDim.x * blockDim.x) {
+    for (int i = tid; i < npx; i += nthr) {
         float v = fixed ? fixed[i] : 0.f;
         int j = 0;
         for (; j + 4 <= nz; j += 4) {
@@ -138,8 +145,42 @@ __global__ void k_opd_norm(DevParams prm, int nz, int npx, int nl, float *__rest
         const float t = T[i];
         t2[0] = df_add(t2[0], t * t);
     }
+    // tilt factors of this slot's PSFs: tilt[r B + bl][axis][n]
+    {
+        const float *pos = slot_ptr(prm, PPOS, r), *dith = slot_ptr(prm, PDITHER, r);
+        const double cN = 0.5 * (ni - 1);
+        float2 *tl = tilt + (size_t)r * B * 2 * ni;
+        for (int i = tid; i < B * 2 * ni; i += nthr) {
+            const int bl = i / (2 * ni), ax = (i / ni) & 1, n = i - (i / ni) * ni;
+            const int l = bl / nse, se = bl - l * nse, s = se / ne, e = se - s * ne;
+            const double th = (double)pos[2 * s + ax] + (dith ? (double)dith[2 * e + ax] : 0.0);
+            const double t = ((double)n - cN) * dx * th / lam[l];
+            float sn, cs;
+            sincospif((float)(2.0 * (t - rint(t))), &sn, &cs);
+            tl[i] = make_float2(cs, sn);
+        }
+    }
     block_sum<1>(t2, sh);
-    if (threadIdx.x == 0) npart[(size_t)r * gridDim.x + blockIdx.x] = make_float2(t2[0].hi, t2[0].lo);
+    if (threadIdx.x == 0) {
+        npart[(size_t)r * gridDim.x + blockIdx.x] = make_float2(t2[0].hi, t2[0].lo);
+        __threadfence();
+        s_last = (atomicAdd(ncount + r, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        // every other block's partial is visible (fence before its count); fixed order
+        __threadfence();
+        df v{0.f, 0.f};
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+            const float2 x = __ldcg(npart + (size_t)r * gridDim.x + b);
+            v = df_add(v, df{x.x, x.y});
+        }
+        v = warp_sum(v);
+        if (threadIdx.x == 0) {
+            pscale[r] = (float)(1.0 / sqrt(df_to_double(v)));
+            ncount[r] = 0;  // ready for the next launch
+        }
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         const float *w = slot_ptr(prm, PW, r);
         df ws{0.f, 0.f};
@@ -149,87 +190,84 @@ __global__ void k_opd_norm(DevParams prm, int nz, int npx, int nl, float *__rest
     }
 }
 
-// 1/sqrt(sum T^2) of slot r from the OPD pass's block partials (fixed order).
-__device__ float pupil_scale(const float2 *npart, int nblk, int r) {
-    __shared__ float s_scale;
-    if (threadIdx.x < 32) {
-        df v{0.f, 0.f};
-        for (int b = threadIdx.x; b < nblk; b += 32) {
-            const float2 x = npart[(size_t)r * nblk + b];
-            v = df_add(v, df{x.x, x.y});
-        }
-        v = warp_sum(v);
-        if (threadIdx.x == 0) s_scale = (float)(1.0 / sqrt(df_to_double(v)));
-    }
-    __syncthreads();
-    return s_scale;
-}
-
-// Separable tilt factors exp(i 2 pi x_n theta / lambda) per PSF and axis, with
-// the argument reduced in FP64 (B * 2 * Ni values).  theta = pos[s] + dither[e].
-__global__ void k_tilt(DevParams prm, const double *lam, int nbt, int B, int nse, int ne, int ni, double dx,
-                       float2 *tilt) {
-    const double cN = 0.5 * (ni - 1);
-    const size_t total = (size_t)nbt * 2 * ni;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        int bg = (int)(i / (2 * ni)), ax = (int)((i / ni) % 2), n = (int)(i % ni);
-        int r = bg / B, bl = bg % B, l = bl / nse, se = bl % nse, s = se / ne, e = se % ne;
-        const float *pos = slot_ptr(prm, PPOS, r), *dith = slot_ptr(prm, PDITHER, r);
-        double th = (double)pos[2 * s + ax] + (dith ? (double)dith[2 * e + ax] : 0.0);
-        double t = ((double)n - cN) * dx * th / lam[l];
-        double rr = t - rint(t);
-        float sn, cs;
-        sincospif((float)(2.0 * rr), &sn, &cs);
-        tilt[i] = make_float2(cs, sn);
-    }
-}
-
 // Pupil phasor P = T_hat exp(i 2 pi OPD / lambda) ex[nx] ey[ny] (Sec. 3), written
 // in the operand form of the contractions.  OPD / lambda is below one cycle for
-// the aberrations of interest, so FP32 is exact enough there.
+// the aberrations of interest, so FP32 is exact enough there.  One thread writes
+// eight consecutive columns of a row (16- or 32-byte stores per plane); columns
+// from Ni up to the padded row length are written as zeros.  Grid: x over the
+// eight-column groups of one PSF, y over PSFs.
 template <int F>
 __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
-                         const float *__restrict__ invlam, const float2 *__restrict__ npart, int nblk, int nbt, int B,
-                         int nse, int ni, int ldi, void *P) {
-    // grid: x over pupil pixels, y over PSFs (no 64-bit index arithmetic)
-    const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F);
+                         const float *__restrict__ invlam, const float *__restrict__ pscale, int B, int nse, int ni,
+                         int ldi, void *P) {
+    const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F), gpr = ldi >> 3;
     const int bg = blockIdx.y, r = bg / B, l = (bg % B) / nse;
     const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
-    const float sc = pupil_scale(npart, nblk, r), il = invlam[l];
+    const float sc = pscale[r], il = invlam[l];
     const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
     char *base = (char *)P + (size_t)bg * Pl * ni * ldi * es;
     const size_t ps = (size_t)ni * ldi;
-    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < npx; n += gridDim.x * blockDim.x) {
-        const int ny = n / ni, nx = n - ny * ni;
-        const float t = T[n] * sc;
-        float re = 0.f, im = 0.f;
-        if (t != 0.f) {
-            float ph = op[n] * il;
-            ph -= rintf(ph);
-            float sn, cs;
-            sincospif(2.f * ph, &sn, &cs);
-            const float2 ex = tx[nx], ey = ty[ny];
-            const float xr = ex.x * ey.x - ex.y * ey.y, xi = ex.x * ey.y + ex.y * ey.x;
-            re = t * (cs * xr - sn * xi);
-            im = t * (cs * xi + sn * xr);
+    // vector loads need 8-wide rows and a 16-byte aligned caller transmission map
+    const bool vec = (ni & 7) == 0 && ((uintptr_t)T & 15) == 0;
+    for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ni * gpr; gi += gridDim.x * blockDim.x) {
+        const int ny = gi / gpr, nx0 = (gi - ny * gpr) * 8;
+        float t[8], o[8];
+        float2 ex[8];
+        if (vec) {
+            const float4 *T4 = (const float4 *)(T + (size_t)ny * ni + nx0), *O4 = (const float4 *)(op + (size_t)ny * ni + nx0);
+            const float4 ta = __ldg(T4), tb = __ldg(T4 + 1), oa = __ldg(O4), ob = __ldg(O4 + 1);
+            t[0] = ta.x; t[1] = ta.y; t[2] = ta.z; t[3] = ta.w; t[4] = tb.x; t[5] = tb.y; t[6] = tb.z; t[7] = tb.w;
+            o[0] = oa.x; o[1] = oa.y; o[2] = oa.z; o[3] = oa.w; o[4] = ob.x; o[5] = ob.y; o[6] = ob.z; o[7] = ob.w;
+            const float4 *X4 = (const float4 *)(tx + nx0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 x = __ldg(X4 + q);
+                ex[2 * q] = make_float2(x.x, x.y);
+                ex[2 * q + 1] = make_float2(x.z, x.w);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const bool in = nx0 + q < ni;
+                t[q] = in ? __ldg(T + (size_t)ny * ni + nx0 + q) : 0.f;
+                o[q] = in ? __ldg(op + (size_t)ny * ni + nx0 + q) : 0.f;
+                ex[q] = in ? __ldg(tx + nx0 + q) : make_float2(0.f, 0.f);
+            }
         }
-        store_cplx<F>(base, ps, (size_t)ny * ldi + nx, re, im);
+        const float2 ey = __ldg(ty + ny);
+        float re[8], im[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            re[q] = 0.f;
+            im[q] = 0.f;
+            const float tq = t[q] * sc;
+            if (tq != 0.f) {
+                float ph = o[q] * il;
+                ph -= rintf(ph);
+                float sn, cs;
+                sincospif(2.f * ph, &sn, &cs);
+                const float xr = ex[q].x * ey.x - ex[q].y * ey.y, xi = ex[q].x * ey.y + ex[q].y * ey.x;
+                re[q] = tq * (cs * xr - sn * xi);
+                im[q] = tq * (cs * xi + sn * xr);
+            }
+        }
+        store_cplx8<F>(base, ps, (size_t)ny * ldi + nx0, re, im);
     }
 }
 
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
     const int npx = p->ni * p->ni, nbt = R * p->B;
-    KScope ks(p, KC_PROLOGUE, 3, st);
-    const int blocks = std::max(1, std::min({(npx + 255) / 256, p->sm_count * 8 / R, kNormParts}));
-    k_opd_norm<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(prm, p->nz, npx, p->nl, p->opd,
-                                                                                     p->npart, p->wnorm);
-    size_t tt = (size_t)nbt * 2 * p->ni;
-    int tb = (int)std::min<size_t>((tt + 255) / 256, (size_t)p->sm_count * 8);
-    k_tilt<<<tb, 256, 0, st>>>(prm, p->lam_d, nbt, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt);
-    const int px = std::max(1, std::min((npx + 255) / 256, (p->sm_count * 16 + nbt - 1) / nbt));
+    KScope ks(p, KC_PROLOGUE, 2, st);
+    const int work = std::max(npx, p->B * 2 * p->ni);
+    const int blocks = std::max(1, std::min({(work + 255) / 256, p->sm_count * 8 / R, kNormParts}));
+    k_prologue<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(
+        prm, p->nz, npx, p->nl, p->opd, p->npart, p->ncount, p->pscale, p->wnorm, p->lam_d, p->B, p->nse, p->ne,
+        p->ni, p->dx, p->tilt);
+    const int groups = p->ni * (p->ldi / 8);
+    const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nbt - 1) / nbt));
     DLX_FMT_DISPATCH(p->fmt, F,
-                     k_phasor<F><<<dim3(px, nbt), 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->npart, blocks,
-                                                                nbt, p->B, p->nse, p->ni, p->ldi, p->P.ptr));
+                     k_phasor<F><<<dim3(px, nbt), 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->pscale, p->B,
+                                                                p->nse, p->ni, p->ldi, p->P.ptr));
     return cudaGetLastError();
 }
 
@@ -241,12 +279,15 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
 //   g_m = 1 - d / max(m, 1e-30);  GI = FF g_m;  dL/dFF[p] = sum_e g_m B_e;
 //   flux partials sum_p FF g_m B_{e,s}.
 // Per-block partials (converted to FP64 once) go to red[r][blk][1 + kMaxSrc].
-__global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os,
+// OS > 0 fixes the oversample at compile time (unrolled, vector loads of the
+// os-wide row segments); OS = 0 takes it from `os`.
+template <int OS>
+__global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os_rt,
                           int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped) {
     __shared__ df sh[32 * (1 + kMaxSrc)];
-    const int np = nd * nd, r = blockIdx.y;
+    const int np = nd * nd, r = blockIdx.y, os = OS > 0 ? OS : os_rt;
     const float *flux = slot_ptr(prm, PFLUX, r), *flat = slot_ptr(prm, PFLAT, r);
     const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
     float *mod = model + (size_t)r * mstride;
@@ -271,9 +312,23 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                     float v = 0.f;
                     for (int gg = 0; gg < G; ++gg) {
                         const float *src = Is + ((size_t)gg * Rnse + rse) * plane;
-                        for (int a = 0; a < os; ++a) {
-                            const float *row = src + (size_t)(py * os + a) * no + (size_t)px * os;
-                            for (int c = 0; c < os; ++c) v += row[c];
+                        if constexpr (OS == 4) {
+#pragma unroll
+                            for (int a = 0; a < 4; ++a) {
+                                const float4 q = __ldg((const float4 *)(src + (size_t)(py * 4 + a) * no + px * 4));
+                                v += (q.x + q.y) + (q.z + q.w);
+                            }
+                        } else if constexpr (OS == 2) {
+#pragma unroll
+                            for (int a = 0; a < 2; ++a) {
+                                const float2 q = __ldg((const float2 *)(src + (size_t)(py * 2 + a) * no + px * 2));
+                                v += q.x + q.y;
+                            }
+                        } else {
+                            for (int a = 0; a < os; ++a) {
+                                const float *row = src + (size_t)(py * os + a) * no + (size_t)px * os;
+                                for (int c = 0; c < os; ++c) v += __ldg(row + c);
+                            }
                         }
                     }
                     bs[s] = v;
@@ -313,9 +368,17 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     DevGrads gg{};
     if (g) gg = *g;
     KScope ks(p, KC_BIN, 1, st);
-    k_bin_nll<<<dim3(p->red_blocks, R), 256, 0, st>>>(p->Is, p->G, R * p->nse, p->nse, p->ns, p->ne, p->nd, p->os,
-                                                        p->no, prm, data, data_stride, model, model_stride, p->GI, gg,
-                                                        p->red, p->clamped);
+    auto go = [&](auto kern) {
+        kern<<<dim3(p->red_blocks, R), 256, 0, st>>>(p->Is, p->G, R * p->nse, p->nse, p->ns, p->ne, p->nd, p->os, p->no,
+                                                     prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
+                                                     p->clamped);
+    };
+    if (p->os == 4)
+        go(k_bin_nll<4>);
+    else if (p->os == 2)
+        go(k_bin_nll<2>);
+    else
+        go(k_bin_nll<0>);
     return cudaGetLastError();
 }
 

@@ -84,6 +84,9 @@ struct TcArgs {
     float *gphi;
     float *mom;       // per-warp position moments (KGP)
     float dxf, cNf;   // pupil spacing and centre index (KGP)
+    const int *s2off; // stage 2: CTA c runs pieces s2pc[s2off[c] .. s2off[c+1])
+    const int4 *s2pc; // stage 2 pieces (segment, l0, l1, plane | first plane to clear << 16)
+    int grid;         // CTAs (0: min(units, SMs))
     int32_t *err;
 };
 
@@ -97,29 +100,43 @@ struct Job {
     int split;
 };
 
+// Units of this CTA: stage 2 runs its pieces of the host-built split (see
+// s2_schedule.h); every other contraction takes units blockIdx.x + k gridDim.x.
 template <int KIND>
-__device__ __forceinline__ int decode_unit_jobs(const TcArgs &a, int u, int &g, int &rse) {
+__device__ __forceinline__ void unit_range(const TcArgs &a, int &u0, int &u1, int &du) {
+    if constexpr (KIND == KS2) {
+        u0 = __ldg(a.s2off + blockIdx.x);
+        u1 = __ldg(a.s2off + blockIdx.x + 1);
+        du = 1;
+    } else {
+        u0 = blockIdx.x;
+        u1 = a.units;
+        du = gridDim.x;
+    }
+}
+
+// Jobs of unit u (stage 2: the wavelengths of its piece `pc`).
+template <int KIND>
+__device__ __forceinline__ int decode_unit_jobs(const TcArgs &a, int u, int4 &pc) {
     if constexpr (KIND != KS2) {
         return 1;
     } else {
-        const int rest = u / (a.tm * a.tn);
-        g = rest % a.G;
-        rse = rest / a.G;
-        const int l0 = (int)((long)g * a.nl / a.G), l1 = (int)((long)(g + 1) * a.nl / a.G);
-        return l1 - l0;
+        pc = __ldg(a.s2pc + u);
+        return pc.z - pc.y;
     }
 }
 
 template <int KIND>
-__device__ __forceinline__ Job decode(const TcArgs &a, int u, int j) {
+__device__ __forceinline__ Job decode(const TcArgs &a, int u, int j, const int4 &pc) {
     Job J;
     const int tt = a.tm * a.tn;
     int tile = u % tt;
     J.split = 0;
     if constexpr (KIND == KS2) {
-        const int rest = u / tt, g = rest % a.G, rse = rest / a.G;
-        const int l0 = (int)((long)g * a.nl / a.G);
-        J.l = l0 + j;
+        // segment = (slot, source, exposure) x tile, tile fastest
+        tile = pc.x % tt;
+        const int rse = pc.x / tt;
+        J.l = pc.y + j;
         J.r = rse / a.nse;
         J.se = rse % a.nse;
         J.b = J.r * a.B + J.l * a.nse + J.se;
@@ -488,11 +505,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-                int g = 0, rse = 0;
-                const int nj = decode_unit_jobs<KIND>(a, u, g, rse);
+            int u0, u1, du;
+            unit_range<KIND>(a, u0, u1, du);
+            for (int u = u0; u < u1 && ok; u += du) {
+                int4 pc{};
+                const int nj = decode_unit_jobs<KIND>(a, u, pc);
                 for (int j = 0; j < nj && ok; ++j) {
-                    const Job J = decode<KIND>(a, u, j);
+                    const Job J = decode<KIND>(a, u, j, pc);
                     for (int kb = J.kb0; kb < J.kb1; ++kb, ++it) {
                         const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
                         if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort_flag, a.err, 1)) {
@@ -520,9 +539,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             uint32_t it = 0, jt = 0;
             bool ok = true;
             const uint32_t id_pos = idesc<F>(false), id_neg = idesc<F>(true);
-            for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-                int g = 0, rse = 0;
-                const int nj = decode_unit_jobs<KIND>(a, u, g, rse);
+            int u0, u1, du;
+            unit_range<KIND>(a, u0, u1, du);
+            for (int u = u0; u < u1 && ok; u += du) {
+                int4 pc{};
+                const int nj = decode_unit_jobs<KIND>(a, u, pc);
                 for (int j = 0; j < nj && ok; ++j, ++jt) {
                     const uint32_t buf = jt % NBUF, tph = (jt / NBUF) & 1;
                     if (!mbar_wait(tempty0 + 8 * buf, tph ^ 1, abort_flag, a.err, 3)) {
@@ -531,7 +552,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                     tc_fence_after();
                     const uint32_t dr = tbase + buf * 256, di = dr + 128;
-                    const Job J = decode<KIND>(a, u, j);
+                    const Job J = decode<KIND>(a, u, j, pc);
                     for (int kb = J.kb0; kb < J.kb1; ++kb, ++it) {
                         const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
                         if (!mbar_wait(full0 + 8 * s, ph, abort_flag, a.err, 4)) {
@@ -611,12 +632,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
             for (int i = 0; i < 64; ++i) acc[i] = 0.f;
         }
-        for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
-            int g = 0, rse = 0;
-            const int nj = decode_unit_jobs<KIND>(a, u, g, rse);
+        int u0, u1, du;
+        unit_range<KIND>(a, u0, u1, du);
+        for (int u = u0; u < u1 && ok; u += du) {
+            int4 pc{};
+            const int nj = decode_unit_jobs<KIND>(a, u, pc);
             Job J{};
             for (int j = 0; j < nj; ++j, ++jt) {
-                J = decode<KIND>(a, u, j);
+                J = decode<KIND>(a, u, j, pc);
                 const uint32_t buf = jt % NBUF, tph = (jt / NBUF) & 1;
                 // every lane waits; the warp proceeds only if all lanes saw the phase,
                 // so the warp-collective tensor-memory loads never diverge
@@ -783,13 +806,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
             if (!ok) break;
             if constexpr (KIND == KS2) {
-                const int m = J.m0 + row;
+                // the piece's partial sum goes to its plane; the last piece of a segment
+                // also clears the planes the split left unwritten for this tile
+                const int m = J.m0 + row, rse = pc.x / (a.tm * a.tn);
+                const int plane = pc.w & 0xffff, zf = pc.w >> 16;
                 if (m < a.M) {
-                    float *o = a.Is + ((size_t)g * a.Rnse + rse) * a.no * a.no + (size_t)m * a.no;
+                    const size_t pl = (size_t)a.no * a.no;
+                    float *o = a.Is + ((size_t)plane * a.Rnse + rse) * pl + (size_t)m * a.no + J.n0 + 64 * h;
+                    const int nv = a.N - (J.n0 + 64 * h);
+                    if (nv >= 64 && (a.no & 3) == 0) {
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) {
-                        const int n = J.n0 + 64 * h + i;
-                        if (n < a.N) o[n] = acc[i];
+                        for (int i = 0; i < 64; i += 4)
+                            *(float4 *)(o + i) = make_float4(acc[i], acc[i + 1], acc[i + 2], acc[i + 3]);
+                        for (int q = zf; q < a.G; ++q) {
+                            float *z = o + (size_t)(q - plane) * a.Rnse * pl;
+#pragma unroll
+                            for (int i = 0; i < 64; i += 4) *(float4 *)(z + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 64; ++i)
+                            if (i < nv) o[i] = acc[i];
+                        for (int q = zf; q < a.G; ++q) {
+                            float *z = o + (size_t)(q - plane) * a.Rnse * pl;
+                            for (int i = 0; i < 64 && i < nv; ++i) z[i] = 0.f;
+                        }
                     }
                 }
 #pragma unroll
@@ -874,7 +915,7 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
     a.KB = Cfg<F>::KB;
     if (a.ksplit < 1) a.ksplit = 1;
     if (a.units <= 0) return cudaSuccess;
-    const int grid = std::min(a.units, p->sm_count);
+    const int grid = a.grid > 0 ? a.grid : std::min(a.units, p->sm_count);
     static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
     KScope ks(p, cls_of[KIND], 1, st);
     k_tc_gemm<F, MODE, KIND><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, Cout ? Cout->tmap : A.tmap, a);
@@ -901,7 +942,11 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     c.K = p->ni;
     c.Is = p->Is;
     c.Rnse = R * p->nse;
-    c.units = c.Rnse * p->G * ((p->no + BM - 1) / BM) * ((p->no + BN - 1) / BN);
+    const dlx_plan::S2Split &sp = p->s2[R - 1];
+    c.s2off = p->s2_table + sp.off;
+    c.s2pc = (const int4 *)(p->s2_table + sp.pcs);
+    c.grid = sp.nct;
+    c.units = sp.npieces;
     return launch<F, MODE, KS2>(p, p->amat, p->T1t, nullptr, c, st);
 }
 

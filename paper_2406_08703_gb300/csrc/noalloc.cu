@@ -147,6 +147,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     need.take<double>((size_t)p.red_blocks * (1 + dlx::kMaxSrc));
     need.take<unsigned long long>(1);
     need.take<float2>(dlx::kNormParts);
+    need.take<unsigned int>(1);
     if (need.off > kNoAllocScratchBytes) {
         dlx_set_error("dlx_forward_noalloc: this shape needs " + std::to_string(need.off) +
                       " bytes of working memory, above the fixed 16 MiB scratch; use dlx_make_mft + dlx_forward");
@@ -171,6 +172,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     p.red = c.take<double>((size_t)p.red_blocks * (1 + dlx::kMaxSrc));
     p.clamped = c.take<unsigned long long>(1);
     p.npart = c.take<float2>(dlx::kNormParts);
+    p.ncount = c.take<unsigned int>(1);
 
     // The FP32 contractions read operands only inside their true extents and every
     // region above is written before it is read in this call, so nothing has to be
@@ -184,6 +186,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
         inv[l] = (float)(1.0 / d->lambda_m[l]);
     }
     cudaError_t e = cudaMemcpyAsync(p.lam_d, lam, sizeof(double) * p.nl, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.ncount, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(p.invlam, inv, sizeof(float) * p.nl, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = dlx::launch_mft_matrices(&p, st);
     if (e != cudaSuccess) {
