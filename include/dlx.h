@@ -59,8 +59,12 @@ typedef enum {
                           contractions accumulate hi*hi apart from the corrections) */
     DLX_BF16X3 = 2,    /* tcgen05 kind::f16 (BF16), operands split hi + lo, 3 products */
     DLX_BF16 = 3,      /* tcgen05 kind::f16 (BF16), hi only */
-    DLX_BF16X4 = 4     /* as BF16X3, plus the lo*lo product, and in the forward contractions the
+    DLX_BF16X4 = 4,    /* as BF16X3, plus the lo*lo product, and in the forward contractions the
                           hi*hi products accumulate apart from the correction products */
+    DLX_F16X3 = 5      /* tcgen05 kind::f16 (FP16), operands split hi + lo (22 significant bits),
+                          3 products (forward contractions accumulate hi*hi apart); every
+                          operand is stored times an exact power of two chosen from a bound on
+                          its magnitude, so it stays inside FP16's exponent range */
 } dlx_prec;
 
 typedef struct dlx_plan dlx_plan;
@@ -172,9 +176,13 @@ int dlx_plan_diagnostics(dlx_plan *plan, int64_t *clamped, int32_t *device_error
 
 /* Per-kernel-class device time of the evaluations issued on this plan while
  * timing is enabled: CUDA events are recorded on the launching stream around
- * each class of launch (so the times include no host gaps), and every kernel
- * launch is counted whether timing is on or not.  dlx_plan_get_timing is
- * synchronous and resets the accumulators and counters. */
+ * each timed class of launch (so the times include no host gaps), and every
+ * kernel launch is counted whether timing is on or not.  `class_mask` selects
+ * the timed classes: bit c times class c (the order of dlx_kernel_times.name),
+ * -1 times all of them and 0 turns timing off; each timed launch group costs
+ * two event records on the stream, so timing one class disturbs an evaluation
+ * far less than timing all.  dlx_plan_get_timing is synchronous and resets the
+ * accumulators and counters. */
 typedef struct {
     int n_classes;
     const char *name[16];   /* e.g. "stage2_intensity", "adjoint_field" */
@@ -183,7 +191,7 @@ typedef struct {
     int64_t launches[16];   /* kernel launches */
     int64_t total_launches;
 } dlx_kernel_times;
-int dlx_plan_set_timing(dlx_plan *plan, int enable);
+int dlx_plan_set_timing(dlx_plan *plan, int class_mask);
 int dlx_plan_get_timing(dlx_plan *plan, dlx_kernel_times *out);
 
 /* Adam update (Kingma & Ba; the optimiser of Sec. 4) of n parameters in place:

@@ -16,7 +16,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _native as N
-from ._native import DLX_BF16, DLX_BF16X3, DLX_BF16X4, DLX_FP32_SIMT, DLX_TF32X3, PRECISIONS, DlxError  # noqa: F401
+from ._native import DLX_BF16, DLX_BF16X3, DLX_BF16X4, DLX_F16X3, DLX_FP32_SIMT, DLX_TF32X3, PRECISIONS, DlxError  # noqa: F401
 
 PARAM_KEYS = ("transmission", "opd_fixed", "zern_basis", "zern_coeff", "opd_pix", "weights", "flux", "pos", "dither",
               "flat")
@@ -243,8 +243,26 @@ def dlx_plan_diagnostics(plan: Plan):
     return dict(clamped=c.value, device_error=e.value)
 
 
-def dlx_plan_set_timing(plan: Plan, enable: bool = True) -> None:
-    N.check(load().dlx_plan_set_timing(plan.handle, 1 if enable else 0), "dlx_plan_set_timing")
+def dlx_plan_set_timing(plan: Plan, enable: bool = True, classes=None) -> None:
+    """Times every kernel class (enable=True), none (False), or only the named ones."""
+    if not enable:
+        mask = 0
+    elif classes is None:
+        mask = -1
+    else:
+        names = list(dlx_plan_get_timing_names())
+        mask = 0
+        for c in classes:
+            mask |= 1 << names.index(c)
+    N.check(load().dlx_plan_set_timing(plan.handle, mask), "dlx_plan_set_timing")
+
+
+KERNEL_CLASSES = ("mft_matrices", "prologue", "stage1", "stage2_intensity", "bin_nll", "loss", "adjoint_field",
+                  "adjoint_stage2T", "adjoint_stage1T", "grad_reduce", "adam")
+
+
+def dlx_plan_get_timing_names():
+    return KERNEL_CLASSES
 
 
 def dlx_plan_get_timing(plan: Plan) -> dict:

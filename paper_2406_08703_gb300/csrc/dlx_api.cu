@@ -124,7 +124,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     for (int l = 0; l < d->n_lambda; ++l)
         if (!(d->lambda_m[l] > 0) || !std::isfinite(d->lambda_m[l]))
             return fail(DLX_ERR_INVALID_ARG, "wavelengths must be finite and > 0");
-    if (d->precision < DLX_FP32_SIMT || d->precision > DLX_BF16X4) return fail(DLX_ERR_INVALID_ARG, "bad precision");
+    if (d->precision < DLX_FP32_SIMT || d->precision > DLX_F16X3) return fail(DLX_ERR_INVALID_ARG, "bad precision");
     if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 8 sources per plan");
     const long long no_ll = (long long)d->n_det * d->oversample;
     if (d->n_pupil > 8192 || no_ll > 16384) return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and n_det*oversample <= 16384");
@@ -237,7 +237,17 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->red_blocks = std::max(1, std::min((int)((np + 255) / 256), std::max(1, p->sm_count * 2 / R_max)));
     if (e == cudaSuccess) e = plan_alloc(p, &p->lam_d, sizeof(double) * p->nl);
     if (e == cudaSuccess) e = plan_alloc(p, &p->wnorm, sizeof(float) * p->nl * R_max);
-    if (e == cudaSuccess) e = plan_alloc(p, &p->pscale, sizeof(float) * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->pscale, sizeof(float) * 2 * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->tpart, sizeof(float) * kNormParts * R_max);
+    if (p->fmt == FMT_F16X4) {
+        // FP16 operand scales: alpha_l = 2^-ceil(log2 sqrt(dx du / lambda_l)); adjoint maxima
+        std::vector<float> al(p->nl);
+        for (int l = 0; l < p->nl; ++l) al[l] = inv_pow2_ceil((float)std::sqrt(p->dx * p->du / p->lambdas[l]));
+        if (e == cudaSuccess) e = plan_alloc(p, &p->ascale, sizeof(float) * p->nl);
+        if (e == cudaSuccess) e = cudaMemcpy(p->ascale, al.data(), sizeof(float) * p->nl, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->qmax, sizeof(unsigned int) * R_max * p->nse);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->gmax, sizeof(unsigned int) * Bt);
+    }
     if (e == cudaSuccess) e = plan_alloc(p, &p->invlam, sizeof(float) * p->nl);
     if (e == cudaSuccess) e = plan_alloc(p, &p->tilt, sizeof(float2) * Bt * 2 * p->ni);
     if (e == cudaSuccess) e = plan_alloc(p, &p->opd, sizeof(float) * npx * R_max);
@@ -245,11 +255,13 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->GI, sizeof(float) * p->ne * np * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->model_tmp, sizeof(float) * p->ne * np * R_max);
     if (p->prec != DLX_FP32_SIMT) {
-        // split the long-K adjoint 1^T contraction until its 128-tiles fill the SMs a few times over
+        // split the long-K adjoint 1^T contraction only while its 128-tiles do not fill
+        // the SMs once: every split adds a gphi plane and a re-read of the phasor tile
+        // in the epilogue, which costs more than a partial last wave
         const long units = (long)p->chunk * ((p->ni + 127) / 128) * ((p->ni + 127) / 128);
         const int kblocks = (p->no + 31) / 32;
         int s = 1;
-        while (s < 8 && units * s < 4L * p->sm_count && kblocks / (2 * s) >= 4) s *= 2;
+        while (s < 8 && units * s < (long)p->sm_count && kblocks / (2 * s) >= 4) s *= 2;
         p->gsplit = s;
     }
     if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx * p->gsplit);

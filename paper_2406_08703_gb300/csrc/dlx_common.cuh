@@ -9,11 +9,15 @@
 //   FMT_BF16X4 : re_hi, re_lo, im_hi, im_lo (bf16)          -- BF16x3 and BF16x4 forms
 //   FMT_BF16X2 : re, im                     (bf16)          -- plain BF16 form
 //   FMT_TF32X4 : re_hi, re_lo, im_hi, im_lo (tf32 in fp32)  -- TF32x3 form
+//   FMT_F16X4  : re_hi, re_lo, im_hi, im_lo (fp16)          -- FP16x3 form
 // hi = round(x), lo = round(x - hi).  Which split products a contraction forms
 // (three, or four with lo*lo) is chosen by the tensor-core kernel per form.
+// FP16 operands hold x times a power of two that keeps |x| <= 1 (see the
+// scale helpers below), so hi and lo stay inside FP16's exponent range.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda.h>
 #include <stdint.h>
 #include <string>
@@ -23,10 +27,28 @@
 
 namespace dlx {
 
-enum Fmt { FMT_F32 = 0, FMT_BF16X4 = 1, FMT_BF16X2 = 2, FMT_TF32X4 = 3 };
+enum Fmt { FMT_F32 = 0, FMT_BF16X4 = 1, FMT_BF16X2 = 2, FMT_TF32X4 = 3, FMT_F16X4 = 4 };
 
-__host__ __device__ constexpr int fmt_planes(int f) { return (f == FMT_BF16X4 || f == FMT_TF32X4) ? 4 : 2; }
-__host__ __device__ constexpr int fmt_esize(int f) { return (f == FMT_BF16X4 || f == FMT_BF16X2) ? 2 : 4; }
+__host__ __device__ constexpr int fmt_planes(int f) {
+    return (f == FMT_BF16X4 || f == FMT_TF32X4 || f == FMT_F16X4) ? 4 : 2;
+}
+__host__ __device__ constexpr int fmt_esize(int f) {
+    return (f == FMT_BF16X4 || f == FMT_BF16X2 || f == FMT_F16X4) ? 2 : 4;
+}
+
+// 16-bit element type of a 16-bit form and its round-to-nearest conversions.
+template <int F>
+struct H16 {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
+    static __device__ __forceinline__ float to(T x) { return __bfloat162float(x); }
+};
+template <>
+struct H16<FMT_F16X4> {
+    using T = __half;
+    static __device__ __forceinline__ T from(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ float to(T x) { return __half2float(x); }
+};
 
 inline int fmt_of_prec(int prec) {
     switch (prec) {
@@ -34,6 +56,7 @@ inline int fmt_of_prec(int prec) {
         case DLX_TF32X3: return FMT_TF32X4;
         case DLX_BF16X3: return FMT_BF16X4;
         case DLX_BF16X4: return FMT_BF16X4;
+        case DLX_F16X3: return FMT_F16X4;
         default: return FMT_BF16X2;
     }
 }
@@ -52,13 +75,14 @@ __device__ __forceinline__ void store_cplx(void *base, size_t pstride, size_t id
         float *p = (float *)base;
         p[idx] = re;
         p[pstride + idx] = im;
-    } else if constexpr (F == FMT_BF16X4) {
-        __nv_bfloat16 *p = (__nv_bfloat16 *)base;
-        __nv_bfloat16 rh = __float2bfloat16_rn(re), ih = __float2bfloat16_rn(im);
+    } else if constexpr (F == FMT_BF16X4 || F == FMT_F16X4) {
+        using H = H16<F>;
+        typename H::T *p = (typename H::T *)base;
+        const typename H::T rh = H::from(re), ih = H::from(im);
         p[idx] = rh;
-        p[pstride + idx] = __float2bfloat16_rn(re - __bfloat162float(rh));
+        p[pstride + idx] = H::from(re - H::to(rh));
         p[2 * pstride + idx] = ih;
-        p[3 * pstride + idx] = __float2bfloat16_rn(im - __bfloat162float(ih));
+        p[3 * pstride + idx] = H::from(im - H::to(ih));
     } else if constexpr (F == FMT_BF16X2) {
         __nv_bfloat16 *p = (__nv_bfloat16 *)base;
         p[idx] = __float2bfloat16_rn(re);
@@ -106,29 +130,24 @@ __device__ __forceinline__ void store_cplx8(void *base, size_t pstride, size_t i
             put(p + 3 * pstride, li);
         }
     } else {
-        __nv_bfloat16 *p = (__nv_bfloat16 *)base + idx;
-        uint32_t wr[4], wi[4], vr[4], vi[4];
+        using H = H16<F>;
+        typename H::T *p = (typename H::T *)base + idx;
+        __align__(16) typename H::T rh[8], ih[8], rl[8], il[8];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const __nv_bfloat162 a = __floats2bfloat162_rn(re[2 * q], re[2 * q + 1]);
-            const __nv_bfloat162 b = __floats2bfloat162_rn(im[2 * q], im[2 * q + 1]);
-            wr[q] = *(const uint32_t *)&a;
-            wi[q] = *(const uint32_t *)&b;
-            if constexpr (F == FMT_BF16X4) {
-                const __nv_bfloat162 c = __floats2bfloat162_rn(re[2 * q] - __low2float(a), re[2 * q + 1] - __high2float(a));
-                const __nv_bfloat162 d = __floats2bfloat162_rn(im[2 * q] - __low2float(b), im[2 * q + 1] - __high2float(b));
-                vr[q] = *(const uint32_t *)&c;
-                vi[q] = *(const uint32_t *)&d;
-            }
+        for (int q = 0; q < 8; ++q) {
+            rh[q] = H::from(re[q]);
+            ih[q] = H::from(im[q]);
+            rl[q] = H::from(re[q] - H::to(rh[q]));
+            il[q] = H::from(im[q] - H::to(ih[q]));
         }
-        if constexpr (F == FMT_BF16X4) {
-            *(uint4 *)p = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-            *(uint4 *)(p + pstride) = make_uint4(vr[0], vr[1], vr[2], vr[3]);
-            *(uint4 *)(p + 2 * pstride) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
-            *(uint4 *)(p + 3 * pstride) = make_uint4(vi[0], vi[1], vi[2], vi[3]);
+        if constexpr (F == FMT_BF16X2) {
+            *(uint4 *)p = *(const uint4 *)rh;
+            *(uint4 *)(p + pstride) = *(const uint4 *)ih;
         } else {
-            *(uint4 *)p = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-            *(uint4 *)(p + pstride) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+            *(uint4 *)p = *(const uint4 *)rh;
+            *(uint4 *)(p + pstride) = *(const uint4 *)rl;
+            *(uint4 *)(p + 2 * pstride) = *(const uint4 *)ih;
+            *(uint4 *)(p + 3 * pstride) = *(const uint4 *)il;
         }
     }
 }
@@ -139,10 +158,10 @@ __device__ __forceinline__ float2 load_cplx(const void *base, size_t pstride, si
     if constexpr (F == FMT_F32) {
         const float *p = (const float *)base;
         return make_float2(p[idx], p[pstride + idx]);
-    } else if constexpr (F == FMT_BF16X4) {
-        const __nv_bfloat16 *p = (const __nv_bfloat16 *)base;
-        return make_float2(__bfloat162float(p[idx]) + __bfloat162float(p[pstride + idx]),
-                           __bfloat162float(p[2 * pstride + idx]) + __bfloat162float(p[3 * pstride + idx]));
+    } else if constexpr (F == FMT_BF16X4 || F == FMT_F16X4) {
+        using H = H16<F>;
+        const typename H::T *p = (const typename H::T *)base;
+        return make_float2(H::to(p[idx]) + H::to(p[pstride + idx]), H::to(p[2 * pstride + idx]) + H::to(p[3 * pstride + idx]));
     } else if constexpr (F == FMT_BF16X2) {
         const __nv_bfloat16 *p = (const __nv_bfloat16 *)base;
         return make_float2(__bfloat162float(p[idx]), __bfloat162float(p[pstride + idx]));
@@ -157,8 +176,18 @@ __device__ __forceinline__ float2 load_cplx(const void *base, size_t pstride, si
         case FMT_F32: { constexpr int F = FMT_F32; __VA_ARGS__; } break;     \
         case FMT_BF16X4: { constexpr int F = FMT_BF16X4; __VA_ARGS__; } break; \
         case FMT_BF16X2: { constexpr int F = FMT_BF16X2; __VA_ARGS__; } break; \
+        case FMT_F16X4: { constexpr int F = FMT_F16X4; __VA_ARGS__; } break;   \
         default: { constexpr int F = FMT_TF32X4; __VA_ARGS__; } break;         \
     }
+
+// 2^-ceil(log2 x) for finite x > 0 (so that x times it lies in (1/2, 1]), else 1:
+// the power-of-two operand scales of the FP16 form.
+__host__ __device__ inline float inv_pow2_ceil(float x) {
+    if (!(x > 0.f) || !(x < 3.0e38f)) return 1.f;
+    int e = 0;
+    const float m = frexpf(x, &e);  // x = m 2^e, m in [1/2, 1)
+    return ldexpf(1.f, m == 0.5f ? 1 - e : -e);
+}
 
 // One operand tensor (plane-major [batch][planes][rows][ld]) and its TMA map.
 struct Operand {
@@ -211,7 +240,11 @@ struct dlx_plan {
     dlx::Operand amat, amatH, P, T1t, GEt, GT1;
     double *lam_d = nullptr;   // [nl]
     float *wnorm = nullptr;    // [R][nl] weights / sum(weights)
-    float *pscale = nullptr;   // [R] 1/sqrt(sum T^2)
+    float *pscale = nullptr;   // [R][2] 1/sqrt(sum T^2), FP16 phasor scale pi_r
+    float *tpart = nullptr;    // [R][kNormParts] block maxima of |T|
+    float *ascale = nullptr;   // [nl] FP16 MFT-matrix scales alpha_l (FP16 form)
+    unsigned int *qmax = nullptr;  // [R][nse] FP16 form: max_q |GI| sqrt(I_se(q)) (float bits)
+    unsigned int *gmax = nullptr;  // [R*B] FP16 form: max |GEt'| per PSF (float bits)
     float *invlam = nullptr;   // [nl] 1/lambda (FP32)
     float2 *tilt = nullptr;    // [R*B][2][ni]
     float *opd = nullptr;      // [R][ni*ni]

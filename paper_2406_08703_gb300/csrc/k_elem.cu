@@ -71,10 +71,10 @@ __device__ void block_sum(df (&v)[NV], df *sh /* [32][NV] */) {
 // t = (n - (Ni-1)/2)(k - (No-1)/2) c, c = dx du / lambda_l.  The argument is
 // formed and reduced to r = t - rint(t) in FP64 before sin/cos, so the phase
 // error does not grow with |t|.  AH[l][n][k] = conj(A[l][k][n]).  Built once
-// per plan.
+// per plan.  FP16 operands hold A times alpha_l = ascale[l] (|A alpha_l| <= 1).
 template <int F>
-__global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, int nl, int ni, int no, int ldi, int ldo,
-                               double dx, double du) {
+__global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const float *ascale, int nl, int ni,
+                               int no, int ldi, int ldo, double dx, double du) {
     const int P = fmt_planes(F), es = fmt_esize(F);
     const size_t per = (size_t)no * ni, total = per * nl;
     const double cN = 0.5 * (ni - 1), cO = 0.5 * (no - 1);
@@ -86,7 +86,7 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, int n
         double r = t - rint(t);
         double s, co;
         sincospi(2.0 * r, &s, &co);
-        double sc = sqrt(c);
+        const double sc = sqrt(c) * (F == FMT_F16X4 ? (double)ascale[l] : 1.0);
         float re = (float)(sc * co), im = (float)(-sc * s);
         char *a = (char *)amat + (size_t)l * P * no * ldi * es;
         store_cplx<F>(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im);
@@ -100,8 +100,8 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
     KScope ks(p, KC_MATRICES, 1, st);
     DLX_FMT_DISPATCH(p->fmt, F,
-                     k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->nl, p->ni,
-                                                               p->no, p->ldi, p->ldo, p->dx, p->du));
+                     k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->ascale, p->nl,
+                                                               p->ni, p->no, p->ldi, p->ldo, p->dx, p->du));
     return cudaGetLastError();
 }
 
@@ -110,14 +110,18 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
 //  * OPD = OPD_fixed + sum_j c_j Z_j + OPD_pix (Sec. 3: BasisOptic coefficients
 //    on a Zernike basis, the fixed mask, and the free per-pixel map);
 //  * sum T^2 for the pupil normalisation of BasisOptic(normalise=True): block
-//    partials go to npart[r][block], and the last block of the slot to finish
-//    sums them in a fixed order into pscale[r] = 1 / sqrt(sum T^2);
+//    partials go to npart[r][block] (and max |T| to tpart), and the last block
+//    of the slot to finish combines them in a fixed order into
+//    pscale[r] = (1 / sqrt(sum T^2), pi_r), pi_r the FP16 operand scale of the
+//    phasor (2^-ceil(log2 max |T_hat|));
+//  * clears the slot's FP16 scale maxima (qmax, gmax) of the adjoint;
 //  * the separable tilt factors exp(i 2 pi x_n theta / lambda) of every PSF and
 //    axis, theta = pos[s] + dither[e], with the argument reduced in FP64;
 //  * block 0 writes the normalised spectral weights w_l / sum w.
 __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__restrict__ opd, float2 *npart,
-                           unsigned int *ncount, float *pscale, float *wnorm, const double *__restrict__ lam, int B,
-                           int nse, int ne, int ni, double dx, float2 *__restrict__ tilt) {
+                           float *tpart, unsigned int *ncount, float *pscale, float *wnorm,
+                           const double *__restrict__ lam, int B, int nse, int ne, int ni, double dx,
+                           float2 *__restrict__ tilt, unsigned int *qmax, unsigned int *gmax) {
     extern __shared__ float c_sh[];
     __shared__ df sh[32];
     __shared__ bool s_last;
@@ -127,7 +131,12 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
     for (int j = threadIdx.x; j < nz; j += blockDim.x) c_sh[j] = coeff[j];
     __syncthreads();
     const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+    if (qmax)
+        for (int i = tid; i < nse; i += nthr) qmax[(size_t)r * nse + i] = 0u;
+    if (gmax)
+        for (int i = tid; i < B; i += nthr) gmax[(size_t)r * B + i] = 0u;
     df t2[1] = {{0.f, 0.f}};
+    float tmax = 0.f;
     for (int i = tid; i < npx; i += nthr) {
         float v = fixed ? fixed[i] : 0.f;
         int j = 0;
@@ -144,6 +153,7 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
         opd[(size_t)r * npx + i] = v;
         const float t = T[i];
         t2[0] = df_add(t2[0], t * t);
+        tmax = fmaxf(tmax, fabsf(t));
     }
     // tilt factors of this slot's PSFs: tilt[r B + bl][axis][n]
     {
@@ -160,24 +170,36 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
             tl[i] = make_float2(cs, sn);
         }
     }
-    block_sum<1>(t2, sh);
+    __shared__ float s_tmax[32];
+    for (int o = 16; o > 0; o >>= 1) tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+    if ((threadIdx.x & 31) == 0) s_tmax[threadIdx.x >> 5] = tmax;
+    block_sum<1>(t2, sh);  // its barriers also publish s_tmax
     if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tmax = fmaxf(tmax, s_tmax[w]);
         npart[(size_t)r * gridDim.x + blockIdx.x] = make_float2(t2[0].hi, t2[0].lo);
+        tpart[(size_t)r * gridDim.x + blockIdx.x] = tmax;
         __threadfence();
         s_last = (atomicAdd(ncount + r, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (s_last && threadIdx.x < 32) {
+    if (s_last) {
         // every other block's partial is visible (fence before its count); fixed order
         __threadfence();
-        df v{0.f, 0.f};
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) {
+        df v[1] = {{0.f, 0.f}};
+        float m = 0.f;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
             const float2 x = __ldcg(npart + (size_t)r * gridDim.x + b);
-            v = df_add(v, df{x.x, x.y});
+            v[0] = df_add(v[0], df{x.x, x.y});
+            m = fmaxf(m, __ldcg(tpart + (size_t)r * gridDim.x + b));
         }
-        v = warp_sum(v);
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((threadIdx.x & 31) == 0) s_tmax[threadIdx.x >> 5] = m;
+        block_sum<1>(v, sh);  // its barriers also publish s_tmax
         if (threadIdx.x == 0) {
-            pscale[r] = (float)(1.0 / sqrt(df_to_double(v)));
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, s_tmax[w]);
+            const float sc = (float)(1.0 / sqrt(df_to_double(v[0])));
+            pscale[2 * r] = sc;
+            pscale[2 * r + 1] = inv_pow2_ceil(m * sc);
             ncount[r] = 0;  // ready for the next launch
         }
     }
@@ -203,7 +225,8 @@ __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const flo
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F), gpr = ldi >> 3;
     const int bg = blockIdx.y, r = bg / B, l = (bg % B) / nse;
     const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
-    const float sc = pscale[r], il = invlam[l];
+    // FP16 operands hold pi_r P
+    const float sc = pscale[2 * r] * (F == FMT_F16X4 ? pscale[2 * r + 1] : 1.f), il = invlam[l];
     const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
     char *base = (char *)P + (size_t)bg * Pl * ni * ldi * es;
     const size_t ps = (size_t)ni * ldi;
@@ -261,8 +284,8 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     const int work = std::max(npx, p->B * 2 * p->ni);
     const int blocks = std::max(1, std::min({(work + 255) / 256, p->sm_count * 8 / R, kNormParts}));
     k_prologue<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(
-        prm, p->nz, npx, p->nl, p->opd, p->npart, p->ncount, p->pscale, p->wnorm, p->lam_d, p->B, p->nse, p->ne,
-        p->ni, p->dx, p->tilt);
+        prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm, p->lam_d, p->B, p->nse,
+        p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax);
     const int groups = p->ni * (p->ldi / 8);
     const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nbt - 1) / nbt));
     DLX_FMT_DISPATCH(p->fmt, F,
@@ -274,92 +297,160 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
 // ---------------------------------------------------------------------------
 // Binning, flat field and Poisson NLL (Sec. 3 pixel response, Sec. 4 likelihood).
 // One thread per detector pixel p of slot r = blockIdx.y:
-//   B_{e,s}[p] = sum over the os x os block and the wavelength-group planes,
+//   B_{e,s}[p] = sum over the os x os block and the partial-intensity planes,
 //   m = FF sum_s F_s B_{e,s};  L += m - d ln max(m, 1e-30);
 //   g_m = 1 - d / max(m, 1e-30);  GI = FF g_m;  dL/dFF[p] = sum_e g_m B_e;
 //   flux partials sum_p FF g_m B_{e,s}.
 // Per-block partials (converted to FP64 once) go to red[r][blk][1 + kMaxSrc].
+// With qmax (FP16 form, loss and gradient) the same pass finds
+// Q_{s,e} = max over oversampled pixels q of |GI_e(bin q)| sqrt(I_{s,e}(q)), the
+// bound behind the scale of the adjoint field operand; maxima of non-negative
+// floats compare as their bit patterns, so the atomic maxima are exact and
+// order-independent.
 // OS > 0 fixes the oversample at compile time (unrolled, vector loads of the
-// os-wide row segments); OS = 0 takes it from `os`.
+// os-wide row segments); OS = 0 takes it from `os_rt`.
+constexpr int kQShared = 64;  // (source, exposure) maxima kept in shared memory
+
 template <int OS>
 __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os_rt,
                           int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
-                          unsigned long long *clamped) {
+                          unsigned long long *clamped, unsigned int *qmax) {
     __shared__ df sh[32 * (1 + kMaxSrc)];
+    __shared__ unsigned int s_q[kQShared];
     const int np = nd * nd, r = blockIdx.y, os = OS > 0 ? OS : os_rt;
     const float *flux = slot_ptr(prm, PFLUX, r), *flat = slot_ptr(prm, PFLAT, r);
     const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
     float *mod = model + (size_t)r * mstride;
     float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
+    const bool wantq = qmax && dat;
+    if (wantq)
+        for (int i = threadIdx.x; i < kQShared; i += blockDim.x) s_q[i] = 0u;
+    __syncthreads();
     df acc[1 + kMaxSrc];
 #pragma unroll
     for (int i = 0; i < 1 + kMaxSrc; ++i) acc[i] = {0.f, 0.f};
     unsigned long long nclamp = 0;
     const size_t plane = (size_t)no * no;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
-        const int py = p / nd, px = p % nd;
-        const float ff = flat[p];
+    // block-uniform trip count, so the warp-wide maxima below see every lane
+    for (int p0 = blockIdx.x * blockDim.x; p0 < np; p0 += gridDim.x * blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        const bool valid = p < np;
+        const int py = valid ? p / nd : 0, px = valid ? p % nd : 0;
+        const float ff = valid ? flat[p] : 0.f;
         float dff = 0.f;
         for (int e = 0; e < ne; ++e) {
-            float bs[kMaxSrc];
+            float bs[kMaxSrc], bmax[kMaxSrc];
             float btot = 0.f;
 #pragma unroll
             for (int s = 0; s < kMaxSrc; ++s) {
                 bs[s] = 0.f;
-                if (s < ns) {
-                    const int rse = r * nse + s * ne + e;
-                    float v = 0.f;
-                    for (int gg = 0; gg < G; ++gg) {
-                        const float *src = Is + ((size_t)gg * Rnse + rse) * plane;
-                        if constexpr (OS == 4) {
+                bmax[s] = 0.f;
+                if (s < ns && valid) {
+                    const size_t rse = (size_t)r * nse + s * ne + e;
+                    float v = 0.f, vm = 0.f;
+                    if constexpr (OS == 4 || OS == 2) {
+                        // per-subpixel sums over the planes; each plane's OS row loads are in flight together
+                        float q[OS][OS];
 #pragma unroll
-                            for (int a = 0; a < 4; ++a) {
-                                const float4 q = __ldg((const float4 *)(src + (size_t)(py * 4 + a) * no + px * 4));
-                                v += (q.x + q.y) + (q.z + q.w);
-                            }
-                        } else if constexpr (OS == 2) {
+                        for (int a = 0; a < OS; ++a)
 #pragma unroll
-                            for (int a = 0; a < 2; ++a) {
-                                const float2 q = __ldg((const float2 *)(src + (size_t)(py * 2 + a) * no + px * 2));
-                                v += q.x + q.y;
-                            }
-                        } else {
-                            for (int a = 0; a < os; ++a) {
-                                const float *row = src + (size_t)(py * os + a) * no + (size_t)px * os;
-                                for (int c = 0; c < os; ++c) v += __ldg(row + c);
+                            for (int c = 0; c < OS; ++c) q[a][c] = 0.f;
+                        for (int gg = 0; gg < G; ++gg) {
+                            const float *src = Is + ((size_t)gg * Rnse + rse) * plane + (size_t)(py * OS) * no + px * OS;
+                            if constexpr (OS == 4) {
+                                float4 t[4];
+#pragma unroll
+                                for (int a = 0; a < 4; ++a) t[a] = __ldg((const float4 *)(src + (size_t)a * no));
+#pragma unroll
+                                for (int a = 0; a < 4; ++a) {
+                                    q[a][0] += t[a].x;
+                                    q[a][1] += t[a].y;
+                                    q[a][2] += t[a].z;
+                                    q[a][3] += t[a].w;
+                                }
+                            } else {
+                                const float2 t0 = __ldg((const float2 *)src), t1 = __ldg((const float2 *)(src + no));
+                                q[0][0] += t0.x;
+                                q[0][1] += t0.y;
+                                q[1][0] += t1.x;
+                                q[1][1] += t1.y;
                             }
                         }
+#pragma unroll
+                        for (int a = 0; a < OS; ++a) {
+                            float rsum = 0.f;
+#pragma unroll
+                            for (int c = 0; c < OS; ++c) {
+                                rsum += q[a][c];
+                                vm = fmaxf(vm, q[a][c]);
+                            }
+                            v += rsum;
+                        }
+                    } else {
+                        for (int a = 0; a < os; ++a)
+                            for (int c = 0; c < os; ++c) {
+                                float q = 0.f;
+                                for (int gg = 0; gg < G; ++gg)
+                                    q += __ldg(Is + ((size_t)gg * Rnse + rse) * plane + (size_t)(py * os + a) * no +
+                                               (size_t)px * os + c);
+                                v += q;
+                                vm = fmaxf(vm, q);
+                            }
                     }
                     bs[s] = v;
+                    bmax[s] = vm;
                     btot = fmaf(flux[s], v, btot);
                 }
             }
             const float m = ff * btot;
-            mod[(size_t)e * np + p] = m;
-            if (dat) {
-                const float d = (float)dat[(size_t)e * np + p];
-                float mc = m;
-                if (!(mc >= 1e-30f)) {
-                    mc = 1e-30f;
-                    ++nclamp;
-                }
-                acc[0] = df_add(acc[0], m);
-                acc[0] = df_add(acc[0], -d * logf(mc));
-                const float gm = 1.f - d / mc;
-                GI[((size_t)r * ne + e) * np + p] = ff * gm;
-                dff = fmaf(gm, btot, dff);
+            float gi = 0.f;
+            if (valid) {
+                mod[(size_t)e * np + p] = m;
+                if (dat) {
+                    const float d = (float)dat[(size_t)e * np + p];
+                    float mc = m;
+                    if (!(mc >= 1e-30f)) {
+                        mc = 1e-30f;
+                        ++nclamp;
+                    }
+                    acc[0] = df_add(acc[0], m);
+                    acc[0] = df_add(acc[0], -d * logf(mc));
+                    const float gm = 1.f - d / mc;
+                    gi = ff * gm;
+                    GI[((size_t)r * ne + e) * np + p] = gi;
+                    dff = fmaf(gm, btot, dff);
 #pragma unroll
-                for (int s = 0; s < kMaxSrc; ++s)
-                    if (s < ns) acc[1 + s] = df_add(acc[1 + s], (ff * gm) * bs[s]);
+                    for (int s = 0; s < kMaxSrc; ++s)
+                        if (s < ns) acc[1 + s] = df_add(acc[1 + s], gi * bs[s]);
+                }
+            }
+            if (wantq) {
+#pragma unroll
+                for (int s = 0; s < kMaxSrc; ++s) {
+                    if (s >= ns) break;
+                    float qv = fabsf(gi) * sqrtf(bmax[s]);
+                    if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
+                    for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
+                    if ((threadIdx.x & 31) == 0) {
+                        const int k = s * ne + e;
+                        if (k < kQShared)
+                            atomicMax(s_q + k, __float_as_uint(qv));
+                        else
+                            atomicMax(qmax + (size_t)r * nse + k, __float_as_uint(qv));
+                    }
+                }
             }
         }
-        if (dat && dflat) dflat[p] = dff;
+        if (valid && dat && dflat) dflat[p] = dff;
     }
     block_sum<1 + kMaxSrc>(acc, sh);
     if (threadIdx.x == 0)
         for (int i = 0; i < 1 + kMaxSrc; ++i)
             red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = df_to_double(acc[i]);
+    if (wantq)
+        for (int k = threadIdx.x; k < nse && k < kQShared; k += blockDim.x)
+            atomicMax(qmax + (size_t)r * nse + k, s_q[k]);
     if (dat && nclamp) atomicAdd(clamped, nclamp);  // integer count: order-independent
 }
 
@@ -371,7 +462,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     auto go = [&](auto kern) {
         kern<<<dim3(p->red_blocks, R), 256, 0, st>>>(p->Is, p->G, R * p->nse, p->nse, p->ns, p->ne, p->nd, p->os, p->no,
                                                      prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
-                                                     p->clamped);
+                                                     p->clamped, p->qmax);
     };
     if (p->os == 4)
         go(k_bin_nll<4>);
@@ -514,19 +605,37 @@ __global__ void k_pos_final(const double *part, int nsplit, int B, int nl, int n
 
 // Tensor-core forms: the adjoint 1^T epilogue already reduced sum g x_n and
 // sum g y_n per (PSF, K split, tile, warp); dL/dtheta_s sums those of source s
-// over wavelengths and exposures.  One block per (slot, source, axis), fixed order.
-__global__ void k_pos_final_mom(const float *mom, int per_psf, int B, int nl, int ns, int ne, DevGrads g) {
-    __shared__ df sh[32];
-    const int r = blockIdx.x, s = blockIdx.y, ax = blockIdx.z;
+// over wavelengths and exposures.  One 1024-thread block per (slot, source)
+// covers both axes, four loads in flight per thread; fixed order.
+__global__ void __launch_bounds__(1024) k_pos_final_mom(const float *mom, int per_psf, int B, int nl, int ns, int ne,
+                                                         DevGrads g) {
+    __shared__ df sh[32 * 2];
+    const int r = blockIdx.x, s = blockIdx.y;
     const int nt = nl * ne * per_psf;
-    df v[1] = {{0.f, 0.f}};
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-        const int le = t / per_psf, k = t % per_psf, l = le / ne, e = le % ne;
-        const size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
-        v[0] = df_add(v[0], mom[(b * per_psf + k) * 2 + ax]);
+    df v[2] = {{0.f, 0.f}, {0.f, 0.f}};
+    for (int t0 = 0; t0 < nt; t0 += 4 * blockDim.x) {
+        float2 x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = t0 + q * blockDim.x + threadIdx.x;
+            x[q] = make_float2(0.f, 0.f);
+            if (t < nt) {
+                const int le = t / per_psf, k = t - le * per_psf, l = le / ne, e = le - l * ne;
+                const size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
+                x[q] = __ldg((const float2 *)mom + b * per_psf + k);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[0] = df_add(v[0], x[q].x);
+            v[1] = df_add(v[1], x[q].y);
+        }
     }
-    block_sum<1>(v, sh);
-    if (threadIdx.x == 0) g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + ax] = v[0].hi + v[0].lo;
+    block_sum<2>(v, sh);
+    if (threadIdx.x == 0) {
+        g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s] = v[0].hi + v[0].lo;
+        g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + 1] = v[1].hi + v[1].lo;
+    }
 }
 
 // dL/dc_j = <Z_j, g_OPD> over one slice of the pupil.  grid (n_slices, n_zern, R);
@@ -572,8 +681,7 @@ cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const D
     k_gopd<<<dim3((npx + 63) / 64, R), 256, 0, st>>>(p->gphi, R, p->B * p->gsplit, npx, p->gopd, gg);
     if (gg.p[GPOS] && p->mom) {
         const int tiles = ((p->ni + 127) / 128) * ((p->ni + 127) / 128);
-        k_pos_final_mom<<<dim3(R, p->ns, 2), 256, 0, st>>>(p->mom, p->gsplit * tiles * 8, p->B, p->nl, p->ns, p->ne,
-                                                           gg);
+        k_pos_final_mom<<<dim3(R, p->ns), 1024, 0, st>>>(p->mom, p->gsplit * tiles * 8, p->B, p->nl, p->ns, p->ne, gg);
     } else if (gg.p[GPOS]) {
         k_pos_moments<<<R * p->B * p->gsplit, 256, 0, st>>>(p->gphi, p->ni, (float)p->dx, p->pos_part);
         k_pos_final<<<dim3(R, p->ns, 2), 32, 0, st>>>(p->pos_part, p->gsplit, p->B, p->nl, p->ns, p->ne, gg);

@@ -56,10 +56,10 @@ struct Cfg {
     static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
     static constexpr int KSTEP = (F == FMT_TF32X4) ? 8 : 16;  // k per MMA instruction (32 bytes)
     static constexpr int NKSTEP = KB / KSTEP;
-    static constexpr uint32_t AB_FMT = (F == FMT_TF32X4) ? 2u : 1u;  // TF32 : BF16
-    // bf16 forms stage the operand tiles they write in one swizzled TMA box
+    static constexpr uint32_t AB_FMT = (F == FMT_TF32X4) ? 2u : (F == FMT_F16X4) ? 0u : 1u;  // TF32 : F16 : BF16
+    // 16-bit forms stage the operand tiles they write in one swizzled TMA box
     // (128 rows x 64 bytes x all planes) and store them with bulk tensor copies
-    static constexpr bool TMA_STORE = (F == FMT_BF16X4 || F == FMT_BF16X2);
+    static constexpr bool TMA_STORE = (F == FMT_BF16X4 || F == FMT_BF16X2 || F == FMT_F16X4);
     static constexpr int STG_BYTES = TMA_STORE ? PL * PLANE_BYTES : 0;
     static constexpr int SMEM = STAGES * STAGE_BYTES + STG_BYTES + 1024 + 256;
 };
@@ -84,6 +84,12 @@ struct TcArgs {
     float *gphi;
     float *mom;       // per-warp position moments (KGP)
     float dxf, cNf;   // pupil spacing and centre index (KGP)
+    // FP16 form: operand scales (all powers of two) -- alpha_l, (1/sqrt(sum T^2), pi_r)
+    // per slot, sigma1 of T1t, the adjoint-field bound maxima and per-PSF max |GEt'|
+    const float *ascale, *pscale;
+    float sig1;
+    const unsigned int *qmax;
+    unsigned int *gmax;
     const int *s2off; // stage 2: CTA c runs pieces s2pc[s2off[c] .. s2off[c+1])
     const int4 *s2pc; // stage 2 pieces (segment, l0, l1, plane | first plane to clear << 16)
     int grid;         // CTAs (0: min(units, SMs))
@@ -183,6 +189,22 @@ __device__ __forceinline__ Job decode(const TcArgs &a, int u, int j, const int4 
         J.kb1 = nkb;
     }
     return J;
+}
+
+// FP16 form: scale of the adjoint field operand of PSF b = (r, l, s, e).
+// |G_E(q)| = 2 w_l F_s |GI(q)| |E(q)| <= 2 F_s sqrt(w_l) |GI(q)| sqrt(I_se(q)),
+// since w_l |E_l(q)|^2 <= I_se(q) = sum_l w_l |E_l(q)|^2; gamma_b brings the bound
+// to <= 1.
+__device__ __forceinline__ float f16_gamma(const TcArgs &a, const Job &J) {
+    const int s = J.se / a.ne;
+    const float F = fabsf(slot_ptr(a.prm, PFLUX, J.r)[s]);
+    const float w = fabsf(a.wnorm[(size_t)J.r * a.nl + J.l]);
+    const float Q = __uint_as_float(a.qmax[(size_t)J.r * a.nse + J.se]);
+    return inv_pow2_ceil(2.f * F * sqrtf(w) * Q);
+}
+// FP16 form: scale of the adjoint 2^T output GT1 of PSF b: |GT1 alpha gamma| <= No max |GEt'|.
+__device__ __forceinline__ float f16_sigma2(const TcArgs &a, const Job &J) {
+    return inv_pow2_ceil((float)a.no * __uint_as_float(a.gmax[J.b]));
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -319,20 +341,21 @@ template <int F>
 __device__ __forceinline__ void store_row(void *base, size_t ps, size_t off, const float (&re)[CW],
                                           const float (&im)[CW], int nvalid) {
     if (nvalid == CW) {
-        if constexpr (F == FMT_BF16X4 || F == FMT_BF16X2) {
-            __nv_bfloat16 *p = (__nv_bfloat16 *)base + off;
+        if constexpr (F == FMT_BF16X4 || F == FMT_BF16X2 || F == FMT_F16X4) {
+            using H = H16<F>;
+            typename H::T *p = (typename H::T *)base + off;
 #pragma unroll
             for (int q = 0; q < CW / 8; ++q) {
-                __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
+                __align__(16) typename H::T rh[8], ih[8], rl[8], il[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const float x = re[8 * q + i], y = im[8 * q + i];
-                    rh[i] = __float2bfloat16_rn(x);
-                    ih[i] = __float2bfloat16_rn(y);
-                    rl[i] = __float2bfloat16_rn(x - __bfloat162float(rh[i]));
-                    il[i] = __float2bfloat16_rn(y - __bfloat162float(ih[i]));
+                    rh[i] = H::from(x);
+                    ih[i] = H::from(y);
+                    rl[i] = H::from(x - H::to(rh[i]));
+                    il[i] = H::from(y - H::to(ih[i]));
                 }
-                if constexpr (F == FMT_BF16X4) {
+                if constexpr (F != FMT_BF16X2) {
                     *(uint4 *)(p + 8 * q) = *(uint4 *)rh;
                     *(uint4 *)(p + ps + 8 * q) = *(uint4 *)rl;
                     *(uint4 *)(p + 2 * ps + 8 * q) = *(uint4 *)ih;
@@ -374,20 +397,21 @@ __device__ __forceinline__ void store_row(void *base, size_t ps, size_t off, con
 // 64-byte swizzle (16-byte granule g of row r sits at g ^ ((r >> 1) & 3)).
 template <int F>
 __device__ __forceinline__ void stage_row16(uint8_t *stg, int r, int h, const float (&re)[CW], const float (&im)[CW]) {
+    using H = H16<F>;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
+        __align__(16) typename H::T rh[8], ih[8], rl[8], il[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const float x = re[8 * q + i], y = im[8 * q + i];
-            rh[i] = __float2bfloat16_rn(x);
-            ih[i] = __float2bfloat16_rn(y);
-            rl[i] = __float2bfloat16_rn(x - __bfloat162float(rh[i]));
-            il[i] = __float2bfloat16_rn(y - __bfloat162float(ih[i]));
+            rh[i] = H::from(x);
+            ih[i] = H::from(y);
+            rl[i] = H::from(x - H::to(rh[i]));
+            il[i] = H::from(y - H::to(ih[i]));
         }
         const int g = (2 * h + q) ^ ((r >> 1) & 3);
         uint8_t *p = stg + r * 64 + g * 16;
-        if constexpr (F == FMT_BF16X4) {
+        if constexpr (F != FMT_BF16X2) {
             *(uint4 *)(p) = *(uint4 *)rh;
             *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)rl;
             *(uint4 *)(p + 2 * PLANE_BYTES) = *(uint4 *)ih;
@@ -405,27 +429,28 @@ template <int F>
 __device__ __forceinline__ void load_row(const void *base, size_t ps, size_t off, float (&re)[CW], float (&im)[CW],
                                          int nvalid) {
     if (nvalid == CW) {
-        if constexpr (F == FMT_BF16X4 || F == FMT_BF16X2) {
-            const __nv_bfloat16 *p = (const __nv_bfloat16 *)base + off;
+        if constexpr (F == FMT_BF16X4 || F == FMT_BF16X2 || F == FMT_F16X4) {
+            using H = H16<F>;
+            const typename H::T *p = (const typename H::T *)base + off;
 #pragma unroll
             for (int q = 0; q < CW / 8; ++q) {
-                __align__(16) __nv_bfloat16 a[8], b[8], c[8], d[8];
+                __align__(16) typename H::T a[8], b[8], c[8], d[8];
                 *(uint4 *)a = __ldg((const uint4 *)(p + 8 * q));
-                if constexpr (F == FMT_BF16X4) {
+                if constexpr (F != FMT_BF16X2) {
                     *(uint4 *)b = __ldg((const uint4 *)(p + ps + 8 * q));
                     *(uint4 *)c = __ldg((const uint4 *)(p + 2 * ps + 8 * q));
                     *(uint4 *)d = __ldg((const uint4 *)(p + 3 * ps + 8 * q));
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        re[8 * q + i] = __bfloat162float(a[i]) + __bfloat162float(b[i]);
-                        im[8 * q + i] = __bfloat162float(c[i]) + __bfloat162float(d[i]);
+                        re[8 * q + i] = H::to(a[i]) + H::to(b[i]);
+                        im[8 * q + i] = H::to(c[i]) + H::to(d[i]);
                     }
                 } else {
                     *(uint4 *)c = __ldg((const uint4 *)(p + ps + 8 * q));
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        re[8 * q + i] = __bfloat162float(a[i]);
-                        im[8 * q + i] = __bfloat162float(c[i]);
+                        re[8 * q + i] = H::to(a[i]);
+                        im[8 * q + i] = H::to(c[i]);
                     }
                 }
             }
@@ -655,7 +680,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 const int m = J.m0 + row;
                 float mom_x = 0.f, mom_g = 0.f;  // position moments of this row (adjoint 1^T)
                 // per-job constants of the epilogues
-                float w = 0.f, c = 0.f, k2 = 0.f;
+                float w = 0.f, c = 0.f, k2 = 0.f, osc = 1.f, gmx = 0.f;
                 const float *gi = nullptr;
                 if constexpr (KIND == KS2) w = a.wnorm[(size_t)J.r * a.nl + J.l];
                 if constexpr (KIND == KGE) {
@@ -664,6 +689,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     gi = a.GI + ((size_t)J.r * a.ne + e) * a.nd * a.nd + min(m, a.M - 1) / a.os;
                 }
                 if constexpr (KIND == KGP) k2 = (float)(6.283185307179586476925286766559 / a.lam[J.l]);
+                if constexpr (F == FMT_F16X4) {
+                    // undo / apply the power-of-two operand scales (exact):
+                    // T1t' = alpha pi sigma1 T1t, so the recomputed field carries u^-1
+                    const float al = a.ascale[J.l], pi = a.pscale[2 * J.r + 1];
+                    const float u = 1.f / (al * al * pi * a.sig1);
+                    if constexpr (KIND == KS1) osc = a.sig1;
+                    if constexpr (KIND == KS2) w *= u * u;
+                    if constexpr (KIND == KGE) c *= f16_gamma(a, J) * u;
+                    if constexpr (KIND == KGT1) osc = f16_sigma2(a, J);
+                    if constexpr (KIND == KGP) k2 /= al * al * f16_gamma(a, J) * f16_sigma2(a, J) * pi;
+                }
                 if constexpr (TMA_OUT) {
                     // four rounds of one 32-column box: warp (q, h) fills rows 32q.., columns 16h..,
                     // one thread stores the box; rows and columns past the tensor are clipped by TMA
@@ -697,6 +733,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                     rem = 0;
                                     ++brow;
                                 }
+                            }
+                            if constexpr (F == FMT_F16X4) {
+#pragma unroll
+                                for (int i = 0; i < CW; ++i) gmx = fmaxf(gmx, fmaxf(fabsf(er[i]), fabsf(ei[i])));
+                            }
+                        } else if constexpr (F == FMT_F16X4) {
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                er[i] *= osc;
+                                ei[i] *= osc;
                             }
                         }
                         stage_row16<F>(stg, row, h, er, ei);
@@ -786,6 +832,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+                if constexpr (F == FMT_F16X4 && KIND == KGE) {
+                    // max |GEt'| of this PSF (non-negative floats order as their bits)
+                    if (!(gmx < 3.0e38f)) gmx = 3.0e38f;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) gmx = fmaxf(gmx, __shfl_xor_sync(0xffffffffu, gmx, o));
+                    if (lane == 0) atomicMax(a.gmax + J.b, __float_as_uint(gmx));
+                }
                 if constexpr (KIND == KGP) {
                     // per-warp position moments of this tile, reduced in a fixed order:
                     // mom[entry][tile][warp] = (sum g x_n, sum g y_n), entry = PSF x K split
@@ -875,8 +928,9 @@ bool make_map(dlx_plan *p, Operand &o, std::string *why) {
                              (cuuint64_t)PL * o.rows * o.ld * es};
     cuuint32_t box[4] = {(cuuint32_t)(64 / es), 128u, (cuuint32_t)PL, 1u};
     cuuint32_t estr[4] = {1, 1, 1, 1};
-    CUtensorMapDataType dt =
-        (p->fmt == FMT_TF32X4) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    CUtensorMapDataType dt = (p->fmt == FMT_TF32X4)  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : (p->fmt == FMT_F16X4) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     CUresult r = enc(&o.tmap, dt, 4, o.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -910,6 +964,11 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
     a.G = p->G;
     a.wnorm = p->wnorm;
     a.lam = p->lam_d;
+    a.ascale = p->ascale;
+    a.pscale = p->pscale;
+    a.sig1 = inv_pow2_ceil((float)p->ni);
+    a.qmax = p->qmax;
+    a.gmax = p->gmax;
     a.tm = (a.M + BM - 1) / BM;
     a.tn = (a.N + BN - 1) / BN;
     a.KB = Cfg<F>::KB;
@@ -973,6 +1032,7 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     b.N = p->no;
     b.K = p->no;
     b.b0 = b0;
+    b.prm = prm;
     b.out = p->GT1.ptr;
     b.out_ld = p->ldo;
     b.out_ps = (size_t)p->ni * p->ldo;
@@ -986,6 +1046,7 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     c.N = p->ni;
     c.K = p->no;
     c.b0 = b0;
+    c.prm = prm;
     c.P = p->P.ptr;
     c.gphi = p->gphi;
     c.mom = p->mom;
@@ -1018,6 +1079,7 @@ cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st) {
                                          : forward_impl<FMT_BF16X4, FAST>(p, R, st);
         case FMT_BF16X2: return forward_impl<FMT_BF16X2, FAST>(p, R, st);
         case FMT_TF32X4: return forward_impl<FMT_TF32X4, SPLIT3>(p, R, st);
+        case FMT_F16X4: return forward_impl<FMT_F16X4, SPLIT3>(p, R, st);
         default: return cudaErrorNotSupported;
     }
 }
@@ -1027,6 +1089,7 @@ cudaError_t tc_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb, 
         case FMT_BF16X4: return adjoint_impl<FMT_BF16X4>(p, prm, b0, nb, st);
         case FMT_BF16X2: return adjoint_impl<FMT_BF16X2>(p, prm, b0, nb, st);
         case FMT_TF32X4: return adjoint_impl<FMT_TF32X4>(p, prm, b0, nb, st);
+        case FMT_F16X4: return adjoint_impl<FMT_F16X4>(p, prm, b0, nb, st);
         default: return cudaErrorNotSupported;
     }
 }

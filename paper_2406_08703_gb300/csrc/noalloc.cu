@@ -136,7 +136,8 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     need.take<double>(p.nl);
     need.take<float>(p.nl);
     need.take<float>(p.nl);
-    need.take<float>(1);
+    need.take<float>(2);
+    need.take<float>(dlx::kNormParts);
     need.take<float2>((size_t)p.B * 2 * p.ni);
     need.take<float>(npx);
     need.take<float>((size_t)p.nl * 2 * p.no * p.ldi);
@@ -161,7 +162,8 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     p.lam_d = c.take<double>(p.nl);
     p.invlam = c.take<float>(p.nl);
     p.wnorm = c.take<float>(p.nl);
-    p.pscale = c.take<float>(1);
+    p.pscale = c.take<float>(2);
+    p.tpart = c.take<float>(dlx::kNormParts);
     p.tilt = c.take<float2>((size_t)p.B * 2 * p.ni);
     p.opd = c.take<float>(npx);
     p.amat.ptr = c.take<float>((size_t)p.nl * 2 * p.no * p.ldi);
