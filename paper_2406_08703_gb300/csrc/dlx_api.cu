@@ -267,7 +267,6 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx * p->gsplit);
     if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(float2) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
-    const size_t nslice = (npx + 2047) / 2048;  // slices of the sliced gradient reductions
     if (e == cudaSuccess && p->prec == DLX_FP32_SIMT)
         e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * p->gsplit);
     if (e == cudaSuccess) e = plan_alloc(p, &p->npart, sizeof(float2) * kNormParts * R_max);
@@ -277,7 +276,10 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
         const size_t tiles = (size_t)((p->ni + 127) / 128) * ((p->ni + 127) / 128);
         e = plan_alloc(p, &p->mom, sizeof(float) * 2 * 8 * tiles * Bt * p->gsplit);
     }
-    if (e == cudaSuccess) e = plan_alloc(p, &p->zpart, sizeof(double) * R_max * std::max(1, p->nz) * nslice);
+    if (e == cudaSuccess)
+        e = plan_alloc(p, &p->zpart, sizeof(float2) * R_max * std::max(1, p->nz) * ((npx + 63) / 64));
+    if (e == cudaSuccess) e = plan_alloc(p, &p->bcount, sizeof(unsigned int) * R_max);
+    if (e == cudaSuccess) e = cudaMemset(p->bcount, 0, sizeof(unsigned int) * R_max);
     if (e == cudaSuccess && !s2_host.empty()) {
         e = plan_alloc(p, &p->s2_table, sizeof(int) * s2_host.size());
         if (e == cudaSuccess)
@@ -331,8 +333,7 @@ int eval_loss_grad(dlx_plan *p, const DevParams &prm, int R, const int32_t *data
         model = p->model_tmp;
         model_stride = (size_t)p->ne * p->nd * p->nd;
     }
-    DLX_CU(launch_bin_nll(p, prm, R, data, data_stride, model, model_stride, g, st), "bin+nll");
-    DLX_CU(launch_finalize_loss(p, R, loss, g, st), "loss");
+    DLX_CU(launch_bin_nll(p, prm, R, data, data_stride, model, model_stride, g, loss, st), "bin+nll+loss");
     const bool pupil = g && (g->p[GZERN] || g->p[GPIX] || g->p[GPOS]);
     if (pupil) {
         const int Bt = R * p->B;
@@ -430,7 +431,7 @@ int dlx_forward(dlx_plan *p, const dlx_params *prm, float *model, void *stream) 
     cudaStream_t st = (cudaStream_t)stream;
     const dlx::DevParams d = dev_params(prm);
     if ((rc = dlx::eval_forward(p, d, 1, st))) return rc;
-    DLX_CU(dlx::launch_bin_nll(p, d, 1, nullptr, 0, model, 0, nullptr, st), "bin");
+    DLX_CU(dlx::launch_bin_nll(p, d, 1, nullptr, 0, model, 0, nullptr, nullptr, st), "bin");
     return DLX_OK;
 }
 

@@ -256,7 +256,8 @@ struct dlx_plan {
     double *red = nullptr;     // [R][red_blocks][1 + 8] reduction partials
     int red_blocks = 0;
     double *pos_part = nullptr;// CUDA-core form: [R*B][gsplit][2] position-moment partials
-    double *zpart = nullptr;   // [R][n_zern][slices] Zernike-gradient partials
+    float2 *zpart = nullptr;   // [R][n_zern][ceil(Ni^2 / 64)] Zernike-gradient partials (compensated pairs)
+    unsigned int *bcount = nullptr;  // [R] blocks of the binning pass done (reset by the last one)
     float *mom = nullptr;      // tensor-core forms: [R*B][gsplit][tiles][8 warps][2] position moments
     float2 *npart = nullptr;   // [R][kNormParts] block partials of sum T^2 (compensated pairs)
     unsigned int *ncount = nullptr;  // [R] blocks of the prologue pass done (reset by the last one)
@@ -304,10 +305,10 @@ void free_plan(dlx_plan *p);
 cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st);
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st);  // OPD, norm, tilt, phasor
 // binning + flat field (+ Poisson NLL and its partials when data != NULL)
+// with data, the last block also writes loss[r] (may be NULL) and dL/dF_s
 cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride,
-                           float *model, size_t model_stride, const DevGrads *g, cudaStream_t st);
+                           float *model, size_t model_stride, const DevGrads *g, double *loss, cudaStream_t st);
 cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaStream_t st);
-cudaError_t launch_finalize_loss(dlx_plan *p, int R, double *loss, const DevGrads *g, cudaStream_t st);
 cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st);
 cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, size_t n, float lr, float b1, float b2,
                         float eps, int t, cudaStream_t st);

@@ -301,7 +301,9 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
 //   m = FF sum_s F_s B_{e,s};  L += m - d ln max(m, 1e-30);
 //   g_m = 1 - d / max(m, 1e-30);  GI = FF g_m;  dL/dFF[p] = sum_e g_m B_e;
 //   flux partials sum_p FF g_m B_{e,s}.
-// Per-block partials (converted to FP64 once) go to red[r][blk][1 + kMaxSrc].
+// Per-block partials (converted to FP64 once) go to red[r][blk][1 + kMaxSrc];
+// with data, the last block of the slot to finish sums them in a fixed order into
+// loss[r] and dL/dF_s (bcount counts the finished blocks and is reset by it).
 // With qmax (FP16 form, loss and gradient) the same pass finds
 // Q_{s,e} = max over oversampled pixels q of |GI_e(bin q)| sqrt(I_{s,e}(q)), the
 // bound behind the scale of the adjoint field operand; maxima of non-negative
@@ -315,9 +317,10 @@ template <int OS>
 __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os_rt,
                           int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
-                          unsigned long long *clamped, unsigned int *qmax) {
+                          unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount) {
     __shared__ df sh[32 * (1 + kMaxSrc)];
     __shared__ unsigned int s_q[kQShared];
+    __shared__ bool s_last;
     const int np = nd * nd, r = blockIdx.y, os = OS > 0 ? OS : os_rt;
     const float *flux = slot_ptr(prm, PFLUX, r), *flat = slot_ptr(prm, PFLAT, r);
     const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
@@ -445,24 +448,50 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
         if (valid && dat && dflat) dflat[p] = dff;
     }
     block_sum<1 + kMaxSrc>(acc, sh);
-    if (threadIdx.x == 0)
-        for (int i = 0; i < 1 + kMaxSrc; ++i)
-            red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = df_to_double(acc[i]);
     if (wantq)
         for (int k = threadIdx.x; k < nse && k < kQShared; k += blockDim.x)
             atomicMax(qmax + (size_t)r * nse + k, s_q[k]);
     if (dat && nclamp) atomicAdd(clamped, nclamp);  // integer count: order-independent
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 1 + kMaxSrc; ++i)
+            red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = df_to_double(acc[i]);
+        s_last = false;
+        if (dat && bcount) {
+            __threadfence();
+            s_last = atomicAdd(bcount + r, 1u) == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (s_last) {
+        // loss and dL/dF_s of the slot: one warp per quantity, FP64 over the block partials
+        __threadfence();
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int i = w; i <= ns; i += blockDim.x >> 5) {
+            double v = 0.0;
+            for (int b = lane; b < (int)gridDim.x; b += 32)
+                v += __ldcg(red + ((size_t)r * gridDim.x + b) * (1 + kMaxSrc) + i);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) {
+                if (i == 0) {
+                    if (loss) loss[r] = v;
+                } else if (g.p[GFLUX]) {
+                    g.p[GFLUX][(size_t)r * g.s[GFLUX] + (i - 1)] = (float)v;
+                }
+            }
+        }
+        if (threadIdx.x == 0) bcount[r] = 0;  // ready for the next launch
+    }
 }
 
 cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride,
-                           float *model, size_t model_stride, const DevGrads *g, cudaStream_t st) {
+                           float *model, size_t model_stride, const DevGrads *g, double *loss, cudaStream_t st) {
     DevGrads gg{};
     if (g) gg = *g;
     KScope ks(p, KC_BIN, 1, st);
     auto go = [&](auto kern) {
         kern<<<dim3(p->red_blocks, R), 256, 0, st>>>(p->Is, p->G, R * p->nse, p->nse, p->ns, p->ne, p->nd, p->os, p->no,
                                                      prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
-                                                     p->clamped, p->qmax);
+                                                     p->clamped, p->qmax, loss, p->bcount);
     };
     if (p->os == 4)
         go(k_bin_nll<4>);
@@ -497,43 +526,23 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
     return cudaGetLastError();
 }
 
-// Fixed-order sum of the per-block partials of slot r = blockIdx.x: loss[r] and
-// dL/dF_s.  One warp per quantity; FP64 over a few hundred partials.
-__global__ void k_finalize_loss(const double *red, int nblk, int ns, double *loss, DevGrads g) {
-    const int r = blockIdx.x, i = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (i > ns) return;
-    double v = 0.0;
-    for (int b = lane; b < nblk; b += 32) v += red[((size_t)r * nblk + b) * (1 + kMaxSrc) + i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane != 0) return;
-    if (i == 0) {
-        if (loss) loss[r] = v;
-    } else if (g.p[GFLUX]) {
-        g.p[GFLUX][(size_t)r * g.s[GFLUX] + (i - 1)] = (float)v;
-    }
-}
-
-cudaError_t launch_finalize_loss(dlx_plan *p, int R, double *loss, const DevGrads *g, cudaStream_t st) {
-    DevGrads gg{};
-    if (g) gg = *g;
-    KScope ks(p, KC_LOSS, 1, st);
-    k_finalize_loss<<<R, 32 * (1 + p->ns), 0, st>>>(p->red, p->red_blocks, p->ns, loss, gg);
-    return cudaGetLastError();
-}
-
 // ---------------------------------------------------------------------------
 // Gradient reductions.  gphi[bg][n] already carries 2 pi / lambda_l.  Loads are
-// issued eight at a time ahead of the compensated additions, and long sums are
-// split over many blocks (slices of RED_SLICE pupil pixels), so no kernel waits
-// on one memory latency per element.
-constexpr int RED_SLICE = 2048;  // pupil pixels per block in the sliced reductions (256 threads x 8)
+// issued four or eight at a time ahead of the compensated additions, and long
+// sums are split over many blocks, so no kernel waits on one memory latency per
+// element.
 
-// g_OPD[r][n] = sum_{b in slot r} gphi[b][n] (compensated);  dL/dOPD_pix = g_OPD.
-// A block covers 64 pupil pixels with 4 threads per pixel, each summing every
-// 4th entry (8 loads in flight); the 4 partial sums are combined in a fixed order.
-__global__ void k_gopd(const float *__restrict__ gphi, int R, int B, int npx, float2 *__restrict__ gopd, DevGrads g) {
+// g_OPD[r][n] = sum_{b in slot r} gphi[b][n] (compensated);  dL/dOPD_pix = g_OPD;
+// and the Zernike partials <Z_j, g_OPD> over the block's 64 pupil pixels
+// (zpart[r][j][block], compensated pairs).  A block covers 64 pupil pixels with 4
+// threads per pixel, each summing every 4th entry (8 loads in flight); the 4
+// partial sums are combined in a fixed order.  For the Zernike partials the 64
+// threads of group k take the terms j = k, k + 4, ...
+__global__ void k_gopd_zern(const float *__restrict__ gphi, int B, int npx, float2 *__restrict__ gopd, DevGrads g,
+                            DevParams prm, int nz, float2 *__restrict__ zpart) {
     __shared__ df sh[4][64];
-    const int r = blockIdx.y, px = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    __shared__ df shz[8];
+    const int r = blockIdx.y, px = threadIdx.x & 63, grp = threadIdx.x >> 6, lane = threadIdx.x & 31;
     const int n = blockIdx.x * 64 + px;
     df acc{0.f, 0.f};
     if (n < npx) {
@@ -550,10 +559,28 @@ __global__ void k_gopd(const float *__restrict__ gphi, int R, int B, int npx, fl
     }
     sh[grp][px] = acc;
     __syncthreads();
+    const df t = df_add(df_add(sh[0][px], sh[1][px]), df_add(sh[2][px], sh[3][px]));
     if (grp == 0 && n < npx) {
-        df t = df_add(df_add(sh[0][px], sh[1][px]), df_add(sh[2][px], sh[3][px]));
         gopd[(size_t)r * npx + n] = make_float2(t.hi, t.lo);
         if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = t.hi + t.lo;
+    }
+    if (!zpart) return;
+    const float *basis = slot_ptr(prm, PBASIS, r);
+    for (int j0 = 0; j0 < nz; j0 += 4) {
+        const int j = j0 + grp;
+        df v{0.f, 0.f};
+        if (j < nz && n < npx) {
+            const float z = __ldg(basis + (size_t)j * npx + n);
+            v = df_add(df_add(v, z * t.hi), z * t.lo);
+        }
+        v = warp_sum(v);
+        if (lane == 0) shz[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (px == 0 && j < nz) {
+            const df w = df_add(shz[2 * grp], shz[2 * grp + 1]);
+            zpart[((size_t)r * nz + j) * gridDim.x + blockIdx.x] = make_float2(w.hi, w.lo);
+        }
+        __syncthreads();
     }
 }
 
@@ -603,92 +630,77 @@ __global__ void k_pos_final(const double *part, int nsplit, int B, int nl, int n
     if (lane == 0) g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + ax] = (float)v;
 }
 
-// Tensor-core forms: the adjoint 1^T epilogue already reduced sum g x_n and
-// sum g y_n per (PSF, K split, tile, warp); dL/dtheta_s sums those of source s
-// over wavelengths and exposures.  One 1024-thread block per (slot, source)
-// covers both axes, four loads in flight per thread; fixed order.
-__global__ void __launch_bounds__(1024) k_pos_final_mom(const float *mom, int per_psf, int B, int nl, int ns, int ne,
-                                                         DevGrads g) {
+// Final sums of the gradient reductions, grid (n_zern + n_src, R), fixed order:
+// block j < n_zern: dL/dc_j = sum of the Zernike partials of slot r;
+// block n_zern + s (tensor-core forms): dL/dtheta_s from the position moments the
+// adjoint 1^T epilogue reduced per (PSF, K split, tile, warp), over wavelengths and
+// exposures of source s.
+__global__ void k_grad_final(const float2 *__restrict__ zpart, int nz, int nzb, const float *__restrict__ mom,
+                             int per_psf, int B, int nl, int ns, int ne, DevGrads g) {
     __shared__ df sh[32 * 2];
-    const int r = blockIdx.x, s = blockIdx.y;
-    const int nt = nl * ne * per_psf;
+    const int r = blockIdx.y, k = blockIdx.x;
     df v[2] = {{0.f, 0.f}, {0.f, 0.f}};
-    for (int t0 = 0; t0 < nt; t0 += 4 * blockDim.x) {
-        float2 x[4];
+    if (k < nz) {
+        const float2 *src = zpart + ((size_t)r * nz + k) * nzb;
+        for (int t0 = 0; t0 < nzb; t0 += 4 * blockDim.x) {
+            float2 x[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int t = t0 + q * blockDim.x + threadIdx.x;
-            x[q] = make_float2(0.f, 0.f);
-            if (t < nt) {
-                const int le = t / per_psf, k = t - le * per_psf, l = le / ne, e = le - l * ne;
-                const size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
-                x[q] = __ldg((const float2 *)mom + b * per_psf + k);
+            for (int q = 0; q < 4; ++q) {
+                const int t = t0 + q * blockDim.x + threadIdx.x;
+                x[q] = t < nzb ? __ldg(src + t) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[0] = df_add(v[0], df{x[q].x, x[q].y});
+        }
+        block_sum<2>(v, sh);
+        if (threadIdx.x == 0) g.p[GZERN][(size_t)r * g.s[GZERN] + k] = v[0].hi + v[0].lo;
+    } else {
+        const int s = k - nz, nt = nl * ne * per_psf;
+        for (int t0 = 0; t0 < nt; t0 += 4 * blockDim.x) {
+            float2 x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int t = t0 + q * blockDim.x + threadIdx.x;
+                x[q] = make_float2(0.f, 0.f);
+                if (t < nt) {
+                    const int le = t / per_psf, kk = t - le * per_psf, l = le / ne, e = le - l * ne;
+                    const size_t b = (size_t)r * B + (size_t)l * ns * ne + s * ne + e;
+                    x[q] = __ldg((const float2 *)mom + b * per_psf + kk);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                v[0] = df_add(v[0], x[q].x);
+                v[1] = df_add(v[1], x[q].y);
             }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            v[0] = df_add(v[0], x[q].x);
-            v[1] = df_add(v[1], x[q].y);
+        block_sum<2>(v, sh);
+        if (threadIdx.x == 0) {
+            g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s] = v[0].hi + v[0].lo;
+            g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + 1] = v[1].hi + v[1].lo;
         }
     }
-    block_sum<2>(v, sh);
-    if (threadIdx.x == 0) {
-        g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s] = v[0].hi + v[0].lo;
-        g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + 1] = v[1].hi + v[1].lo;
-    }
-}
-
-// dL/dc_j = <Z_j, g_OPD> over one slice of the pupil.  grid (n_slices, n_zern, R);
-// partials in zpart[r][j][slice].
-__global__ void k_zern_partial(DevParams prm, const float2 *__restrict__ gopd, int npx, double *zpart) {
-    __shared__ df sh[32];
-    const int slice = blockIdx.x, j = blockIdx.y, r = blockIdx.z;
-    const float *basis = slot_ptr(prm, PBASIS, r) + (size_t)j * npx;
-    const float2 *go = gopd + (size_t)r * npx;
-    const int n0 = slice * RED_SLICE;
-    float z[8];
-    float2 gv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int n = n0 + q * 256 + threadIdx.x;
-        z[q] = n < npx ? __ldg(basis + n) : 0.f;
-        gv[q] = n < npx ? go[n] : make_float2(0.f, 0.f);
-    }
-    df v[1] = {{0.f, 0.f}};
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        v[0] = df_add(v[0], z[q] * gv[q].x);
-        v[0] = df_add(v[0], z[q] * gv[q].y);
-    }
-    block_sum<1>(v, sh);
-    if (threadIdx.x == 0) zpart[((size_t)r * gridDim.y + j) * gridDim.x + slice] = df_to_double(v[0]);
-}
-
-__global__ void k_zern_final(const double *zpart, int nslice, int nz, DevGrads g) {
-    const int j = blockIdx.x, r = blockIdx.y, lane = threadIdx.x;
-    double v = 0.0;
-    for (int t = lane; t < nslice; t += 32) v += zpart[((size_t)r * nz + j) * nslice + t];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) g.p[GZERN][(size_t)r * g.s[GZERN] + j] = (float)v;
 }
 
 cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st) {
-    const int npx = p->ni * p->ni, nslice = (npx + RED_SLICE - 1) / RED_SLICE;
+    const int npx = p->ni * p->ni, nzb = (npx + 63) / 64;
     DevGrads gg{};
     if (g) gg = *g;
-    KScope ks(p, KC_GRAD, 1 + (gg.p[GPOS] ? (p->mom ? 1 : 2) : 0) + ((gg.p[GZERN] && p->nz > 0) ? 2 : 0), st);
+    const bool zern = gg.p[GZERN] && p->nz > 0, pos_tc = gg.p[GPOS] && p->mom, pos_simt = gg.p[GPOS] && !p->mom;
+    const int nfinal = (zern ? p->nz : 0) + (pos_tc ? p->ns : 0);
+    KScope ks(p, KC_GRAD, 1 + (nfinal > 0 ? 1 : 0) + (pos_simt ? 2 : 0), st);
     // gphi holds gsplit partial planes per PSF; they are summed with the PSFs
-    k_gopd<<<dim3((npx + 63) / 64, R), 256, 0, st>>>(p->gphi, R, p->B * p->gsplit, npx, p->gopd, gg);
-    if (gg.p[GPOS] && p->mom) {
-        const int tiles = ((p->ni + 127) / 128) * ((p->ni + 127) / 128);
-        k_pos_final_mom<<<dim3(R, p->ns), 1024, 0, st>>>(p->mom, p->gsplit * tiles * 8, p->B, p->nl, p->ns, p->ne, gg);
-    } else if (gg.p[GPOS]) {
+    k_gopd_zern<<<dim3(nzb, R), 256, 0, st>>>(p->gphi, p->B * p->gsplit, npx, p->gopd, gg, prm, zern ? p->nz : 0,
+                                              zern ? p->zpart : nullptr);
+    if (pos_simt) {
         k_pos_moments<<<R * p->B * p->gsplit, 256, 0, st>>>(p->gphi, p->ni, (float)p->dx, p->pos_part);
         k_pos_final<<<dim3(R, p->ns, 2), 32, 0, st>>>(p->pos_part, p->gsplit, p->B, p->nl, p->ns, p->ne, gg);
     }
-    if (gg.p[GZERN] && p->nz > 0) {
-        k_zern_partial<<<dim3(nslice, p->nz, R), 256, 0, st>>>(prm, p->gopd, npx, p->zpart);
-        k_zern_final<<<dim3(p->nz, R), 32, 0, st>>>(p->zpart, nslice, p->nz, gg);
+    if (nfinal > 0) {
+        const int tiles = ((p->ni + 127) / 128) * ((p->ni + 127) / 128);
+        // source blocks follow the Zernike blocks; with no Zernike gradient they start at 0
+        k_grad_final<<<dim3(nfinal, R), 256, 0, st>>>(p->zpart, zern ? p->nz : 0, nzb, p->mom,
+                                                      p->gsplit * tiles * 8, p->B, p->nl, p->ns, p->ne, gg);
     }
     return cudaGetLastError();
 }

@@ -208,7 +208,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     dp.p[dlx::PFLAT] = prm->flat;
     rc = dlx::eval_forward(&p, dp, 1, st);
     if (rc) return rc;
-    e = dlx::launch_bin_nll(&p, dp, 1, nullptr, 0, model, 0, nullptr, st);
+    e = dlx::launch_bin_nll(&p, dp, 1, nullptr, 0, model, 0, nullptr, nullptr, st);
     if (e != cudaSuccess) {
         dlx_set_error(std::string("dlx_forward_noalloc: ") + cudaGetErrorString(e));
         return DLX_ERR_CUDA;
