@@ -464,6 +464,11 @@ def main():
              "bf16": 1.0,
              "fp32": 1.0}[args.form]
     nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
+    # DRAM bytes of the stage-2 contraction (BF16x4) from one ncu capture of this build on the
+    # 8-wavelength case (16 PSFs: 52.15 MB read + written), scaled by the PSF count, in which
+    # the traffic grows; any other kernel or form has no capture of the current code
+    traffic = 52.15e6 / 16 * B if (args.form == "bf16x4" and dom == "stage2_intensity" and
+                                   args.workload == "binary") else None
     roof = None
     if dom in alg and classes[dom]["events"] > 0:
         per_launch_ms = classes[dom]["ms"] / max(classes[dom]["events"], 1)
@@ -476,7 +481,7 @@ def main():
             base = peaks.get("bf16_tflops_sustained", 1707.9)
             peak = base * nom_ratio[args.form]
             roof = dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                        traffic=None, kernel=dom,
+                        traffic=traffic, traffic_unit="bytes per launch", kernel=dom,
                         executed_tflops=achieved * split, executed_frac=achieved * split / peak,
                         peak_source="MEASURED_PEAKS.json bf16_tflops_sustained" +
                                     (" x nominal tf32/bf16 ratio 1.1/2.25" if args.form == "tf32x3" else "") +
