@@ -180,6 +180,30 @@ __device__ __forceinline__ float2 load_cplx(const void *base, size_t pstride, si
         default: { constexpr int F = FMT_TF32X4; __VA_ARGS__; } break;         \
     }
 
+// Programmatic dependent launch.  The kernels of one evaluation run back to back
+// on one stream; each signals at its start that the next may be launched
+// (pdl_trigger) and waits for the previous grid to finish and its writes to be
+// visible (pdl_wait) before it touches global memory, so the next kernel's launch
+// and set-up overlap the tail of the previous one.  Without a programmatic
+// dependency both are no-ops.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, ((KArgs)args)...);
+}
+
 // 2^-ceil(log2 x) for finite x > 0 (so that x times it lies in (1/2, 1]), else 1:
 // the power-of-two operand scales of the FP16 form.
 __host__ __device__ inline float inv_pow2_ceil(float x) {

@@ -122,6 +122,8 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
                            float *tpart, unsigned int *ncount, float *pscale, float *wnorm,
                            const double *__restrict__ lam, int B, int nse, int ne, int ni, double dx,
                            float2 *__restrict__ tilt, unsigned int *qmax, unsigned int *gmax) {
+    pdl_trigger();
+    pdl_wait();
     extern __shared__ float c_sh[];
     __shared__ df sh[32];
     __shared__ bool s_last;
@@ -222,6 +224,8 @@ template <int F>
 __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
                          const float *__restrict__ invlam, const float *__restrict__ pscale, int B, int nse, int ni,
                          int ldi, void *P) {
+    pdl_trigger();
+    pdl_wait();
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F), gpr = ldi >> 3;
     const int bg = blockIdx.y, r = bg / B, l = (bg % B) / nse;
     const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
@@ -283,15 +287,16 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     KScope ks(p, KC_PROLOGUE, 2, st);
     const int work = std::max(npx, p->B * 2 * p->ni);
     const int blocks = std::max(1, std::min({(work + 255) / 256, p->sm_count * 8 / R, kNormParts}));
-    k_prologue<<<dim3(blocks, R), 256, sizeof(float) * (p->nz > 0 ? p->nz : 1), st>>>(
-        prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm, p->lam_d, p->B, p->nse,
-        p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax);
+    cudaError_t e = launch_pdl(k_prologue, dim3(blocks, R), dim3(256), sizeof(float) * (p->nz > 0 ? p->nz : 1), st,
+                               prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm,
+                               p->lam_d, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax);
+    if (e != cudaSuccess) return e;
     const int groups = p->ni * (p->ldi / 8);
     const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nbt - 1) / nbt));
     DLX_FMT_DISPATCH(p->fmt, F,
-                     k_phasor<F><<<dim3(px, nbt), 256, 0, st>>>(prm, p->opd, p->tilt, p->invlam, p->pscale, p->B,
-                                                                p->nse, p->ni, p->ldi, p->P.ptr));
-    return cudaGetLastError();
+                     e = launch_pdl(k_phasor<F>, dim3(px, nbt), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam,
+                                    p->pscale, p->B, p->nse, p->ni, p->ldi, p->P.ptr));
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -318,6 +323,8 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                           int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ df sh[32 * (1 + kMaxSrc)];
     __shared__ unsigned int s_q[kQShared];
     __shared__ bool s_last;
@@ -489,17 +496,13 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     if (g) gg = *g;
     KScope ks(p, KC_BIN, 1, st);
     auto go = [&](auto kern) {
-        kern<<<dim3(p->red_blocks, R), 256, 0, st>>>(p->Is, p->G, R * p->nse, p->nse, p->ns, p->ne, p->nd, p->os, p->no,
-                                                     prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
-                                                     p->clamped, p->qmax, loss, p->bcount);
+        return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse, p->ns,
+                          p->ne, p->nd, p->os, p->no, prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
+                          p->clamped, p->qmax, loss, p->bcount);
     };
-    if (p->os == 4)
-        go(k_bin_nll<4>);
-    else if (p->os == 2)
-        go(k_bin_nll<2>);
-    else
-        go(k_bin_nll<0>);
-    return cudaGetLastError();
+    if (p->os == 4) return go(k_bin_nll<4>);
+    if (p->os == 2) return go(k_bin_nll<2>);
+    return go(k_bin_nll<0>);
 }
 
 __global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, int ne, size_t plane,
@@ -540,6 +543,8 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
 // threads of group k take the terms j = k, k + 4, ...
 __global__ void k_gopd_zern(const float *__restrict__ gphi, int B, int npx, float2 *__restrict__ gopd, DevGrads g,
                             DevParams prm, int nz, float2 *__restrict__ zpart) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ df sh[4][64];
     __shared__ df shz[8];
     const int r = blockIdx.y, px = threadIdx.x & 63, grp = threadIdx.x >> 6, lane = threadIdx.x & 31;
@@ -637,6 +642,8 @@ __global__ void k_pos_final(const double *part, int nsplit, int B, int nl, int n
 // exposures of source s.
 __global__ void k_grad_final(const float2 *__restrict__ zpart, int nz, int nzb, const float *__restrict__ mom,
                              int per_psf, int B, int nl, int ns, int ne, DevGrads g) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ df sh[32 * 2];
     const int r = blockIdx.y, k = blockIdx.x;
     df v[2] = {{0.f, 0.f}, {0.f, 0.f}};
@@ -690,8 +697,9 @@ cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const D
     const int nfinal = (zern ? p->nz : 0) + (pos_tc ? p->ns : 0);
     KScope ks(p, KC_GRAD, 1 + (nfinal > 0 ? 1 : 0) + (pos_simt ? 2 : 0), st);
     // gphi holds gsplit partial planes per PSF; they are summed with the PSFs
-    k_gopd_zern<<<dim3(nzb, R), 256, 0, st>>>(p->gphi, p->B * p->gsplit, npx, p->gopd, gg, prm, zern ? p->nz : 0,
-                                              zern ? p->zpart : nullptr);
+    cudaError_t e = launch_pdl(k_gopd_zern, dim3(nzb, R), dim3(256), 0, st, p->gphi, p->B * p->gsplit, npx, p->gopd,
+                               gg, prm, zern ? p->nz : 0, zern ? p->zpart : nullptr);
+    if (e != cudaSuccess) return e;
     if (pos_simt) {
         k_pos_moments<<<R * p->B * p->gsplit, 256, 0, st>>>(p->gphi, p->ni, (float)p->dx, p->pos_part);
         k_pos_final<<<dim3(R, p->ns, 2), 32, 0, st>>>(p->pos_part, p->gsplit, p->B, p->nl, p->ns, p->ne, gg);
@@ -699,8 +707,9 @@ cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const D
     if (nfinal > 0) {
         const int tiles = ((p->ni + 127) / 128) * ((p->ni + 127) / 128);
         // source blocks follow the Zernike blocks; with no Zernike gradient they start at 0
-        k_grad_final<<<dim3(nfinal, R), 256, 0, st>>>(p->zpart, zern ? p->nz : 0, nzb, p->mom,
-                                                      p->gsplit * tiles * 8, p->B, p->nl, p->ns, p->ne, gg);
+        e = launch_pdl(k_grad_final, dim3(nfinal, R), dim3(256), 0, st, p->zpart, zern ? p->nz : 0, nzb, p->mom,
+                       p->gsplit * tiles * 8, p->B, p->nl, p->ns, p->ne, gg);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

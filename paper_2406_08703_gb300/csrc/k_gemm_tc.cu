@@ -501,6 +501,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     volatile int *abort_flag = (volatile int *)(bars + 2 * C::STAGES + 5);
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * C::STAGES + 6);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    pdl_trigger();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -525,6 +526,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tbase = *tmem_slot;
+    pdl_wait();  // the previous kernel's outputs (operands, scales, GI) are complete from here on
 
     if (warp == PRODUCER_WARP) {
         if (lane == 0) {
@@ -977,8 +979,8 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
     const int grid = a.grid > 0 ? a.grid : std::min(a.units, p->sm_count);
     static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
     KScope ks(p, cls_of[KIND], 1, st);
-    k_tc_gemm<F, MODE, KIND><<<grid, NTHREADS, Cfg<F>::SMEM, st>>>(A.tmap, B.tmap, Cout ? Cout->tmap : A.tmap, a);
-    return cudaGetLastError();
+    return launch_pdl(k_tc_gemm<F, MODE, KIND>, dim3(grid), dim3(NTHREADS), Cfg<F>::SMEM, st, A.tmap, B.tmap,
+                      Cout ? Cout->tmap : A.tmap, a);
 }
 
 template <int F, int MODE>
