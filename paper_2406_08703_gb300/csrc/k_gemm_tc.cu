@@ -747,15 +747,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 ei[i] *= osc;
                             }
                         }
+                        // the previous round's box may be refilled once the TMA has read it; that
+                        // read overlapped this round's tensor-memory loads and scaling
+                        if (threadIdx.x == 0) bulk_wait_read0();
+                        epi_bar();
                         stage_row16<F>(stg, row, h, er, ei);
                         fence_async_smem();
                         epi_bar();
                         if (threadIdx.x == 0) {
                             tma_store4(&mapC, smem_u32(stg), J.n0 + 32 * t, J.m0, 0, zb);
                             bulk_commit();
-                            bulk_wait_read0();  // the box may be refilled once TMA has read it
                         }
-                        epi_bar();
                     }
                 }
 #pragma unroll
