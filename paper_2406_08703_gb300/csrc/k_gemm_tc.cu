@@ -706,10 +706,30 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     // four rounds of one 32-column box: warp (q, h) fills rows 32q.., columns 16h..,
                     // one thread stores the box; rows and columns past the tensor are clipped by TMA
                     const int zb = (KIND == KS1) ? J.b : J.z;
+                    // adjoint field: the 16 GI factors of a round's columns ky (detector row ky / os),
+                    // loaded one round ahead so their latency overlaps the previous round
+                    float gcur[CW], gnxt[CW];
+                    auto gi_round = [&](int t, float (&g)[CW]) {
+                        const int n0 = J.n0 + 32 * t + 16 * h;
+                        int brow = n0 / a.os, rem = n0 - brow * a.os;
+                        const int bmax = (a.N - 1) / a.os;
+#pragma unroll
+                        for (int i = 0; i < CW; ++i) {
+                            g[i] = __ldg(gi + (size_t)min(brow, bmax) * a.nd);
+                            if (++rem == a.os) {
+                                rem = 0;
+                                ++brow;
+                            }
+                        }
+                    };
+                    if constexpr (KIND == KGE) gi_round(0, gcur);
                     for (int t = 0; t < 4; ++t) {
                         if (J.n0 + 32 * t >= a.out_ld) break;  // uniform over the epilogue warps
                         const int c0 = 32 * t + 16 * h;
                         const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + c0;
+                        if constexpr (KIND == KGE) {
+                            if (t < 3) gi_round(t + 1, gnxt);
+                        }
                         float er[CW], ei[CW];
                         tmem_ld16(ta, er);
                         tmem_ld16(ta + 128, ei);
@@ -723,18 +743,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             for (int i = 0; i < CW; ++i) ei[i] += tt[i];
                         }
                         if constexpr (KIND == KGE) {
-                            const int n0 = J.n0 + c0;
-                            int brow = n0 / a.os, rem = n0 - brow * a.os;
-                            const int bmax = (a.N - 1) / a.os;
 #pragma unroll
                             for (int i = 0; i < CW; ++i) {
-                                const float f = c * gi[min(brow, bmax) * a.nd];
+                                const float f = c * gcur[i];
                                 er[i] *= f;
                                 ei[i] *= f;
-                                if (++rem == a.os) {
-                                    rem = 0;
-                                    ++brow;
-                                }
+                                gcur[i] = gnxt[i];
                             }
                             if constexpr (F == FMT_F16X4) {
 #pragma unroll
