@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--form", default="bf16x4", choices=["f16x3", "bf16x4", "bf16x3", "tf32x3", "bf16", "fp32"])
+    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "bf16x4", "f16x3", "tf32x3", "bf16", "fp32"])
     ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
     ap.add_argument("--workload", default="binary")
     ap.add_argument("--lambdas", type=int, default=0,

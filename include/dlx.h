@@ -57,7 +57,11 @@ typedef enum {
     DLX_FP32_SIMT = 0, /* FP32 FMA on CUDA cores */
     DLX_TF32X3 = 1,    /* tcgen05 kind::tf32, operands split hi + lo, 3 products (forward
                           contractions accumulate hi*hi apart from the corrections) */
-    DLX_BF16X3 = 2,    /* tcgen05 kind::f16 (BF16), operands split hi + lo, 3 products */
+    DLX_BF16X3 = 2,    /* tcgen05 kind::f16 (BF16), operands split hi + lo, 3 products; the forward
+                          operands are split by stochastic rounding (hash-seeded, reproducible)
+                          so that the dropped lo*lo term and the rounding errors are zero-mean,
+                          and stage 2 (stage 1 too above 256-long contractions) accumulates the
+                          hi*hi products apart */
     DLX_BF16 = 3,      /* tcgen05 kind::f16 (BF16), hi only */
     DLX_BF16X4 = 4,    /* as BF16X3, plus the lo*lo product, and in the forward contractions the
                           hi*hi products accumulate apart from the correction products */

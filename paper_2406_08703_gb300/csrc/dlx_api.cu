@@ -156,6 +156,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->ldo = round8(p->no);
     p->prec = d->precision;
     p->fmt = fmt_of_prec(p->prec);
+    p->sr = (p->prec == DLX_BF16X3) ? 0x6d2b79f5u : 0u;  // stochastic split of the forward operands
     p->planes = fmt_planes(p->fmt);
     p->esz = fmt_esize(p->fmt);
     p->dx = d->diameter_m / p->ni;

@@ -72,9 +72,10 @@ __device__ void block_sum(df (&v)[NV], df *sh /* [32][NV] */) {
 // formed and reduced to r = t - rint(t) in FP64 before sin/cos, so the phase
 // error does not grow with |t|.  AH[l][n][k] = conj(A[l][k][n]).  Built once
 // per plan.  FP16 operands hold A times alpha_l = ascale[l] (|A alpha_l| <= 1).
+// With sr != 0 (BF16x3 form) A is split stochastically; AH (adjoint) is not.
 template <int F>
 __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const float *ascale, int nl, int ni,
-                               int no, int ldi, int ldo, double dx, double du) {
+                               int no, int ldi, int ldo, double dx, double du, uint32_t sr) {
     const int P = fmt_planes(F), es = fmt_esize(F);
     const size_t per = (size_t)no * ni, total = per * nl;
     const double cN = 0.5 * (ni - 1), cO = 0.5 * (no - 1);
@@ -89,7 +90,16 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const
         const double sc = sqrt(c) * (F == FMT_F16X4 ? (double)ascale[l] : 1.0);
         float re = (float)(sc * co), im = (float)(-sc * s);
         char *a = (char *)amat + (size_t)l * P * no * ldi * es;
-        store_cplx<F>(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im);
+        if constexpr (F == FMT_BF16X4) {
+            if (sr) {
+                store_cplx_sr(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im, ((size_t)l * no + k) * ldi + n,
+                              sr ^ 0x2545f491u);
+            } else {
+                store_cplx<F>(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im);
+            }
+        } else {
+            store_cplx<F>(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im);
+        }
         char *ah = (char *)amatH + (size_t)l * P * ni * ldo * es;
         store_cplx<F>(ah, (size_t)ni * ldo, (size_t)n * ldo + k, re, -im);
     }
@@ -101,7 +111,7 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
     KScope ks(p, KC_MATRICES, 1, st);
     DLX_FMT_DISPATCH(p->fmt, F,
                      k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->ascale, p->nl,
-                                                               p->ni, p->no, p->ldi, p->ldo, p->dx, p->du));
+                                                               p->ni, p->no, p->ldi, p->ldo, p->dx, p->du, p->sr));
     return cudaGetLastError();
 }
 
@@ -127,6 +137,7 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
     extern __shared__ float c_sh[];
     __shared__ df sh[32];
     __shared__ bool s_last;
+    __shared__ float s_part[4][64];
     const int r = blockIdx.y;
     const float *fixed = slot_ptr(prm, POPDF, r), *basis = slot_ptr(prm, PBASIS, r);
     const float *coeff = slot_ptr(prm, PCOEFF, r), *pix = slot_ptr(prm, POPDPIX, r), *T = slot_ptr(prm, PT, r);
@@ -139,23 +150,29 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
         for (int i = tid; i < B; i += nthr) gmax[(size_t)r * B + i] = 0u;
     df t2[1] = {{0.f, 0.f}};
     float tmax = 0.f;
-    for (int i = tid; i < npx; i += nthr) {
-        float v = fixed ? fixed[i] : 0.f;
-        int j = 0;
-        for (; j + 4 <= nz; j += 4) {
-            const float b0 = __ldg(basis + (size_t)j * npx + i), b1 = __ldg(basis + (size_t)(j + 1) * npx + i);
-            const float b2 = __ldg(basis + (size_t)(j + 2) * npx + i), b3 = __ldg(basis + (size_t)(j + 3) * npx + i);
-            v = fmaf(c_sh[j], b0, v);
-            v = fmaf(c_sh[j + 1], b1, v);
-            v = fmaf(c_sh[j + 2], b2, v);
-            v = fmaf(c_sh[j + 3], b3, v);
+    // 64 pupil pixels per block and pass, 4 threads per pixel: thread group k sums the
+    // Zernike terms j = k, k + 4, ... (all its loads in flight), group 0 adds the four
+    // partial sums in a fixed order
+    const int lpx = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    for (int i0 = blockIdx.x * 64; i0 < npx; i0 += gridDim.x * 64) {  // block-uniform trip count
+        const int i = i0 + lpx;
+        float v = 0.f;
+        if (i < npx) {
+#pragma unroll 4
+            for (int j = grp; j < nz; j += 4) v = fmaf(c_sh[j], __ldg(basis + (size_t)j * npx + i), v);
         }
-        for (; j < nz; ++j) v = fmaf(c_sh[j], __ldg(basis + (size_t)j * npx + i), v);
-        if (pix) v += pix[i];
-        opd[(size_t)r * npx + i] = v;
-        const float t = T[i];
-        t2[0] = df_add(t2[0], t * t);
-        tmax = fmaxf(tmax, fabsf(t));
+        s_part[grp][lpx] = v;
+        __syncthreads();
+        if (grp == 0 && i < npx) {
+            float o = fixed ? fixed[i] : 0.f;
+            o += (s_part[0][lpx] + s_part[1][lpx]) + (s_part[2][lpx] + s_part[3][lpx]);
+            if (pix) o += pix[i];
+            opd[(size_t)r * npx + i] = o;
+            const float t = T[i];
+            t2[0] = df_add(t2[0], t * t);
+            tmax = fmaxf(tmax, fabsf(t));
+        }
+        __syncthreads();
     }
     // tilt factors of this slot's PSFs: tilt[r B + bl][axis][n]
     {
@@ -216,86 +233,109 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
 
 // Pupil phasor P = T_hat exp(i 2 pi OPD / lambda) ex[nx] ey[ny] (Sec. 3), written
 // in the operand form of the contractions.  OPD / lambda is below one cycle for
-// the aberrations of interest, so FP32 is exact enough there.  One thread writes
-// eight consecutive columns of a row (16- or 32-byte stores per plane); columns
-// from Ni up to the padded row length are written as zeros.  Grid: x over the
-// eight-column groups of one PSF, y over PSFs.
+// the aberrations of interest, so FP32 is exact enough there.  One thread takes
+// eight consecutive columns of a row for one wavelength: the common factor
+// T_hat exp(i 2 pi OPD / lambda) is formed once and multiplied by the tilt of
+// each source and exposure of that wavelength (16- or 32-byte stores per
+// plane); columns from Ni up to the padded row length are written as zeros.
+// Grid: x over the eight-column groups, y over (slot, wavelength).
 template <int F>
 __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
-                         const float *__restrict__ invlam, const float *__restrict__ pscale, int B, int nse, int ni,
-                         int ldi, void *P) {
+                         const float *__restrict__ invlam, const float *__restrict__ pscale, int B, int nl, int nse,
+                         int ni, int ldi, void *P, uint32_t sr) {
     pdl_trigger();
     pdl_wait();
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F), gpr = ldi >> 3;
-    const int bg = blockIdx.y, r = bg / B, l = (bg % B) / nse;
+    const int r = blockIdx.y / nl, l = blockIdx.y - r * nl;
     const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
     // FP16 operands hold pi_r P
     const float sc = pscale[2 * r] * (F == FMT_F16X4 ? pscale[2 * r + 1] : 1.f), il = invlam[l];
-    const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
-    char *base = (char *)P + (size_t)bg * Pl * ni * ldi * es;
     const size_t ps = (size_t)ni * ldi;
     // vector loads need 8-wide rows and a 16-byte aligned caller transmission map
     const bool vec = (ni & 7) == 0 && ((uintptr_t)T & 15) == 0;
     for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < ni * gpr; gi += gridDim.x * blockDim.x) {
         const int ny = gi / gpr, nx0 = (gi - ny * gpr) * 8;
         float t[8], o[8];
-        float2 ex[8];
         if (vec) {
             const float4 *T4 = (const float4 *)(T + (size_t)ny * ni + nx0), *O4 = (const float4 *)(op + (size_t)ny * ni + nx0);
             const float4 ta = __ldg(T4), tb = __ldg(T4 + 1), oa = __ldg(O4), ob = __ldg(O4 + 1);
             t[0] = ta.x; t[1] = ta.y; t[2] = ta.z; t[3] = ta.w; t[4] = tb.x; t[5] = tb.y; t[6] = tb.z; t[7] = tb.w;
             o[0] = oa.x; o[1] = oa.y; o[2] = oa.z; o[3] = oa.w; o[4] = ob.x; o[5] = ob.y; o[6] = ob.z; o[7] = ob.w;
-            const float4 *X4 = (const float4 *)(tx + nx0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 x = __ldg(X4 + q);
-                ex[2 * q] = make_float2(x.x, x.y);
-                ex[2 * q + 1] = make_float2(x.z, x.w);
-            }
         } else {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 const bool in = nx0 + q < ni;
                 t[q] = in ? __ldg(T + (size_t)ny * ni + nx0 + q) : 0.f;
                 o[q] = in ? __ldg(op + (size_t)ny * ni + nx0 + q) : 0.f;
-                ex[q] = in ? __ldg(tx + nx0 + q) : make_float2(0.f, 0.f);
             }
         }
-        const float2 ey = __ldg(ty + ny);
-        float re[8], im[8];
+        // T_hat exp(i 2 pi OPD / lambda), common to every source and exposure
+        float br[8], bi[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            re[q] = 0.f;
-            im[q] = 0.f;
+            br[q] = 0.f;
+            bi[q] = 0.f;
             const float tq = t[q] * sc;
             if (tq != 0.f) {
                 float ph = o[q] * il;
                 ph -= rintf(ph);
                 float sn, cs;
                 sincospif(2.f * ph, &sn, &cs);
-                const float xr = ex[q].x * ey.x - ex[q].y * ey.y, xi = ex[q].x * ey.y + ex[q].y * ey.x;
-                re[q] = tq * (cs * xr - sn * xi);
-                im[q] = tq * (cs * xi + sn * xr);
+                br[q] = tq * cs;
+                bi[q] = tq * sn;
             }
         }
-        store_cplx8<F>(base, ps, (size_t)ny * ldi + nx0, re, im);
+        for (int se = 0; se < nse; ++se) {
+            const int bg = r * B + l * nse + se;
+            const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
+            float2 ex[8];
+            if (vec) {
+                const float4 *X4 = (const float4 *)(tx + nx0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 x = __ldg(X4 + q);
+                    ex[2 * q] = make_float2(x.x, x.y);
+                    ex[2 * q + 1] = make_float2(x.z, x.w);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) ex[q] = nx0 + q < ni ? __ldg(tx + nx0 + q) : make_float2(0.f, 0.f);
+            }
+            const float2 ey = __ldg(ty + ny);
+            float re[8], im[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float xr = ex[q].x * ey.x - ex[q].y * ey.y, xi = ex[q].x * ey.y + ex[q].y * ey.x;
+                re[q] = br[q] * xr - bi[q] * xi;
+                im[q] = br[q] * xi + bi[q] * xr;
+            }
+            char *pb = (char *)P + (size_t)bg * Pl * ps * es;
+            if constexpr (F == FMT_BF16X4) {
+                if (sr) {  // BF16x3 form: stochastic split
+                    store_cplx8_sr(pb, ps, (size_t)ny * ldi + nx0, re, im, ((size_t)bg * ni + ny) * ldi + nx0,
+                                   sr ^ 0x1b873593u);
+                    continue;
+                }
+            }
+            store_cplx8<F>(pb, ps, (size_t)ny * ldi + nx0, re, im);
+        }
     }
 }
 
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
-    const int npx = p->ni * p->ni, nbt = R * p->B;
+    const int npx = p->ni * p->ni;
     KScope ks(p, KC_PROLOGUE, 2, st);
-    const int work = std::max(npx, p->B * 2 * p->ni);
-    const int blocks = std::max(1, std::min({(work + 255) / 256, p->sm_count * 8 / R, kNormParts}));
+    const int work = std::max((npx + 63) / 64, (p->B * 2 * p->ni + 255) / 256);
+    const int blocks = std::max(1, std::min({work, p->sm_count * 8 / R, kNormParts}));
     cudaError_t e = launch_pdl(k_prologue, dim3(blocks, R), dim3(256), sizeof(float) * (p->nz > 0 ? p->nz : 1), st,
                                prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm,
                                p->lam_d, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax);
     if (e != cudaSuccess) return e;
-    const int groups = p->ni * (p->ldi / 8);
-    const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nbt - 1) / nbt));
+    const int groups = p->ni * (p->ldi / 8), nyl = R * p->nl;
+    const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nyl - 1) / nyl));
     DLX_FMT_DISPATCH(p->fmt, F,
-                     e = launch_pdl(k_phasor<F>, dim3(px, nbt), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam,
-                                    p->pscale, p->B, p->nse, p->ni, p->ldi, p->P.ptr));
+                     e = launch_pdl(k_phasor<F>, dim3(px, nyl), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam,
+                                    p->pscale, p->B, p->nl, p->nse, p->ni, p->ldi, p->P.ptr, p->sr));
     return e;
 }
 
@@ -475,8 +515,17 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
         const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int i = w; i <= ns; i += blockDim.x >> 5) {
             double v = 0.0;
-            for (int b = lane; b < (int)gridDim.x; b += 32)
-                v += __ldcg(red + ((size_t)r * gridDim.x + b) * (1 + kMaxSrc) + i);
+            const double *src = red + (size_t)r * gridDim.x * (1 + kMaxSrc) + i;
+            int b = lane;
+            for (; b + 96 < (int)gridDim.x; b += 128) {  // four loads in flight
+                const double x0 = __ldcg(src + (size_t)b * (1 + kMaxSrc)), x1 = __ldcg(src + (size_t)(b + 32) * (1 + kMaxSrc));
+                const double x2 = __ldcg(src + (size_t)(b + 64) * (1 + kMaxSrc)), x3 = __ldcg(src + (size_t)(b + 96) * (1 + kMaxSrc));
+                v += x0;
+                v += x1;
+                v += x2;
+                v += x3;
+            }
+            for (; b < (int)gridDim.x; b += 32) v += __ldcg(src + (size_t)b * (1 + kMaxSrc));
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) {
                 if (i == 0) {
@@ -571,13 +620,17 @@ __global__ void k_gopd_zern(const float *__restrict__ gphi, int B, int npx, floa
     }
     if (!zpart) return;
     const float *basis = slot_ptr(prm, PBASIS, r);
-    for (int j0 = 0; j0 < nz; j0 += 4) {
-        const int j = j0 + grp;
+    // the basis values of this thread's terms (up to 16 per group) are loaded up front
+    constexpr int ZQ = 16;
+    float zb[ZQ];
+#pragma unroll
+    for (int q = 0; q < ZQ; ++q) {
+        const int j = 4 * q + grp;
+        zb[q] = (j < nz && n < npx) ? __ldg(basis + (size_t)j * npx + n) : 0.f;
+    }
+    auto partial = [&](int j, float z) {
         df v{0.f, 0.f};
-        if (j < nz && n < npx) {
-            const float z = __ldg(basis + (size_t)j * npx + n);
-            v = df_add(df_add(v, z * t.hi), z * t.lo);
-        }
+        if (j < nz && n < npx) v = df_add(df_add(v, z * t.hi), z * t.lo);
         v = warp_sum(v);
         if (lane == 0) shz[threadIdx.x >> 5] = v;
         __syncthreads();
@@ -586,6 +639,15 @@ __global__ void k_gopd_zern(const float *__restrict__ gphi, int B, int npx, floa
             zpart[((size_t)r * nz + j) * gridDim.x + blockIdx.x] = make_float2(w.hi, w.lo);
         }
         __syncthreads();
+    };
+#pragma unroll
+    for (int q = 0; q < ZQ; ++q) {
+        if (4 * q >= nz) break;  // uniform
+        partial(4 * q + grp, zb[q]);
+    }
+    for (int j0 = 4 * ZQ; j0 < nz; j0 += 4) {
+        const int j = j0 + grp;
+        partial(j, (j < nz && n < npx) ? __ldg(basis + (size_t)j * npx + n) : 0.f);
     }
 }
 

@@ -93,6 +93,7 @@ struct TcArgs {
     const int *s2off; // stage 2: CTA c runs pieces s2pc[s2off[c] .. s2off[c+1])
     const int4 *s2pc; // stage 2 pieces (segment, l0, l1, plane | first plane to clear << 16)
     int grid;         // CTAs (0: min(units, SMs))
+    uint32_t sr;      // stage 1 of the BF16x3 form: stochastic split of T1t (seed), else 0
     int32_t *err;
 };
 
@@ -420,6 +421,28 @@ __device__ __forceinline__ void stage_row16(uint8_t *stg, int r, int h, const fl
             *(uint4 *)(p) = *(uint4 *)rh;
             *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)ih;
         }
+    }
+}
+
+// stage_row16 with the stochastic split of the BF16x3 form; element i of the
+// row has global index gidx + i.
+__device__ __forceinline__ void stage_row16_sr(uint8_t *stg, int r, int h, const float (&re)[CW], const float (&im)[CW],
+                                               uint64_t gidx, uint32_t seed) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint2 rb = sr_bits(gidx + 8 * q + i, seed);
+            split_sr(re[8 * q + i], rb.x, rh[i], rl[i]);
+            split_sr(im[8 * q + i], rb.y, ih[i], il[i]);
+        }
+        const int g = (2 * h + q) ^ ((r >> 1) & 3);
+        uint8_t *p = stg + r * 64 + g * 16;
+        *(uint4 *)(p) = *(uint4 *)rh;
+        *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)rl;
+        *(uint4 *)(p + 2 * PLANE_BYTES) = *(uint4 *)ih;
+        *(uint4 *)(p + 3 * PLANE_BYTES) = *(uint4 *)il;
     }
 }
 
@@ -765,7 +788,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         // read overlapped this round's tensor-memory loads and scaling
                         if (threadIdx.x == 0) bulk_wait_read0();
                         epi_bar();
-                        stage_row16<F>(stg, row, h, er, ei);
+                        bool staged = false;
+                        if constexpr (KIND == KS1 && F == FMT_BF16X4) {
+                            if (a.sr) {
+                                const int n = J.n0 + c0;
+                                stage_row16_sr(stg, row, h, er, ei, ((size_t)J.b * a.M + m) * a.out_ld + n,
+                                               a.sr ^ 0xcc9e2d51u);
+                                staged = true;
+                            }
+                        }
+                        if (!staged) stage_row16<F>(stg, row, h, er, ei);
                         fence_async_smem();
                         epi_bar();
                         if (threadIdx.x == 0) {
@@ -987,6 +1019,7 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
     a.sig1 = inv_pow2_ceil((float)p->ni);
     a.qmax = p->qmax;
     a.gmax = p->gmax;
+    a.sr = (KIND == KS1) ? p->sr : 0u;
     a.tm = (a.M + BM - 1) / BM;
     a.tn = (a.N + BN - 1) / BN;
     a.KB = Cfg<F>::KB;
@@ -999,7 +1032,8 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
                       Cout ? Cout->tmap : A.tmap, a);
 }
 
-template <int F, int MODE>
+// MODE1 / MODE2: accumulation modes of stage 1 and stage 2
+template <int F, int MODE1, int MODE2>
 cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     TcArgs a{};
     // stage 1: T1t[b] = A(l) . P[b]^T   (M = No rows kx, N = Ni cols ny, K = Ni)
@@ -1010,7 +1044,7 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     a.out_ld = p->ldi;
     a.out_ps = (size_t)p->no * p->ldi;
     a.units = R * p->B * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
-    cudaError_t e = launch<F, MODE, KS1>(p, p->amat, p->P, &p->T1t, a, st);
+    cudaError_t e = launch<F, MODE1, KS1>(p, p->amat, p->P, &p->T1t, a, st);
     if (e != cudaSuccess) return e;
     // stage 2 + intensity: Is[g][rse] = sum_l w |A(l) . T1t[b]^T|^2  (M = N = No, K = Ni)
     TcArgs c{};
@@ -1024,7 +1058,7 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     c.s2pc = (const int4 *)(p->s2_table + sp.pcs);
     c.grid = sp.nct;
     c.units = sp.npieces;
-    return launch<F, MODE, KS2>(p, p->amat, p->T1t, nullptr, c, st);
+    return launch<F, MODE2, KS2>(p, p->amat, p->T1t, nullptr, c, st);
 }
 
 template <int F>
@@ -1093,11 +1127,14 @@ int tc_make_maps(dlx_plan *p, std::string *why) {
 cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st) {
     switch (p->fmt) {
         case FMT_BF16X4:
-            return p->prec == DLX_BF16X4 ? forward_impl<FMT_BF16X4, SPLIT4>(p, R, st)
-                                         : forward_impl<FMT_BF16X4, FAST>(p, R, st);
-        case FMT_BF16X2: return forward_impl<FMT_BF16X2, FAST>(p, R, st);
-        case FMT_TF32X4: return forward_impl<FMT_TF32X4, SPLIT3>(p, R, st);
-        case FMT_F16X4: return forward_impl<FMT_F16X4, SPLIT3>(p, R, st);
+            if (p->prec == DLX_BF16X4) return forward_impl<FMT_BF16X4, SPLIT4, SPLIT4>(p, R, st);
+            // BF16x3 (stochastic split): stage 1 double-buffers its accumulators up to a 256-long
+            // contraction; beyond, hi*hi accumulates apart there too (its truncation grows with K)
+            return p->ni <= 256 ? forward_impl<FMT_BF16X4, FAST, SPLIT3>(p, R, st)
+                                : forward_impl<FMT_BF16X4, SPLIT3, SPLIT3>(p, R, st);
+        case FMT_BF16X2: return forward_impl<FMT_BF16X2, FAST, FAST>(p, R, st);
+        case FMT_TF32X4: return forward_impl<FMT_TF32X4, SPLIT3, SPLIT3>(p, R, st);
+        case FMT_F16X4: return forward_impl<FMT_F16X4, SPLIT3, SPLIT3>(p, R, st);
         default: return cudaErrorNotSupported;
     }
 }

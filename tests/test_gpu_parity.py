@@ -131,6 +131,7 @@ def test_calib_full_size_sampled(calib_full, form):
     q_idx.append(int(q0))
     ref = oracle.model_at(p, e_idx, q_idx)
     got = m.reshape(p.n_exp, -1)[e_idx, q_idx]
+    print(form, "calib sampled model error / peak", float(np.max(np.abs(got - ref)) / ref[-1]))
     assert np.max(np.abs(got - ref)) <= TOL[form]["psf"] * ref[-1]
     g = out["grads"]
     s_m = float(np.sum(m - data))
