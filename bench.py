@@ -481,11 +481,14 @@ def main():
              "bf16": 1.0,
              "fp32": 1.0}[args.form]
     nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
-    # DRAM bytes of the stage-2 contraction (BF16x4) from one ncu capture of this build on the
-    # 8-wavelength case (16 PSFs: 52.15 MB read + written), scaled by the PSF count, in which
-    # the traffic grows; any other kernel or form has no capture of the current code
-    traffic = 52.15e6 / 16 * B if (args.form == "bf16x4" and dom == "stage2_intensity" and
-                                   args.workload == "binary") else None
+    # DRAM bytes (read + written) of the contractions of the BF16x3 form from one ncu capture of
+    # this build on the 8-wavelength case (16 PSFs), scaled by the PSF count, in which their
+    # traffic grows (the adjoint 1^T splits K differently at that size and is left out); any
+    # other kernel or form has no capture of the current code
+    traffic_16 = {"stage1": 25.59e6, "stage2_intensity": 51.81e6, "adjoint_field": 129.95e6,
+                  "adjoint_stage2T": 172.03e6}
+    traffic = (traffic_16[dom] / 16 * B if (args.form == "bf16x3" and dom in traffic_16 and
+                                            args.workload == "binary") else None)
     roof = None
     if dom in alg and classes[dom]["events"] > 0:
         per_launch_ms = classes[dom]["ms"] / max(classes[dom]["events"], 1)
