@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "bf16x4", "f16x3", "tf32x3", "bf16", "fp32"])
+    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "bf16x3sa", "bf16x4", "f16x3", "tf32x3", "bf16", "fp32"])
     ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
     ap.add_argument("--workload", default="binary")
     ap.add_argument("--lambdas", type=int, default=0,
@@ -477,10 +477,11 @@ def main():
         "adjoint_stage1T": 8.0 * B * ni * ni * no,
     }
     # tensor instructions per algorithmic product: forward contractions of BF16x4 take 4, its adjoint 3
-    split = {"bf16x4": 3.0 if (dom or "").startswith("adjoint") else 4.0, "f16x3": 3.0, "bf16x3": 3.0, "tf32x3": 3.0,
+    adj = (dom or "").startswith("adjoint")
+    split = {"bf16x4": 3.0 if adj else 4.0, "bf16x3sa": 1.0 if adj else 3.0, "f16x3": 3.0, "bf16x3": 3.0, "tf32x3": 3.0,
              "bf16": 1.0,
              "fp32": 1.0}[args.form]
-    nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
+    nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16x3sa": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
     # DRAM bytes (read + written) of the contractions of the BF16x3 form from one ncu capture of
     # this build on the 8-wavelength case (16 PSFs), scaled by the PSF count, in which their
     # traffic grows (the adjoint 1^T splits K differently at that size and is left out); any
@@ -509,7 +510,8 @@ def main():
 
     line = dict(metric=METRIC, value=evals_per_s, unit="evals/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype={"f16x3": "f16x3 split (fp32 accumulate)", "bf16x4": "bf16x4 split (fp32 accumulate)", "bf16x3": "bf16x3 split (fp32 accumulate)",
+                dtype={"f16x3": "f16x3 split (fp32 accumulate)", "bf16x4": "bf16x4 split (fp32 accumulate)",
+                       "bf16x3sa": "bf16x3 stochastic split, bf16 stochastic adjoint (fp32 accumulate)", "bf16x3": "bf16x3 split (fp32 accumulate)",
                        "tf32x3": "tf32x3 split (fp32 accumulate)",
                        "bf16": "bf16 (fp32 accumulate)", "fp32": "f32"}[args.form],
                 data="synthetic",
@@ -533,7 +535,7 @@ def main():
 
     if not args.no_forms and rank == 0:
         forms = {}
-        for f in ("fp32", "f16x3", "bf16x4", "bf16x3", "tf32x3", "bf16"):
+        for f in ("fp32", "f16x3", "bf16x4", "bf16x3", "bf16x3sa", "tf32x3", "bf16"):
             if f == args.form:
                 continue
             try:

@@ -65,10 +65,15 @@ typedef enum {
     DLX_BF16 = 3,      /* tcgen05 kind::f16 (BF16), hi only */
     DLX_BF16X4 = 4,    /* as BF16X3, plus the lo*lo product, and in the forward contractions the
                           hi*hi products accumulate apart from the correction products */
-    DLX_F16X3 = 5      /* tcgen05 kind::f16 (FP16), operands split hi + lo (22 significant bits),
+    DLX_F16X3 = 5,     /* tcgen05 kind::f16 (FP16), operands split hi + lo (22 significant bits),
                           3 products (forward contractions accumulate hi*hi apart); every
                           operand is stored times an exact power of two chosen from a bound on
                           its magnitude, so it stays inside FP16's exponent range */
+    DLX_BF16X3SA = 6   /* forward as DLX_BF16X3; the adjoint contractions use the stochastically
+                          rounded hi parts alone (one BF16 product per real product): each hi is
+                          an unbiased estimate of its value, so the gradient carries zero-mean
+                          noise of about 2^-8 / sqrt(K) of each contraction's terms instead of
+                          the split's bias-free 2^-16; the PSF and loss are those of DLX_BF16X3 */
 } dlx_prec;
 
 typedef struct dlx_plan dlx_plan;

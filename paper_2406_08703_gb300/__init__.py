@@ -16,7 +16,8 @@ from typing import Optional, Sequence
 import numpy as np
 
 from . import _native as N
-from ._native import DLX_BF16, DLX_BF16X3, DLX_BF16X4, DLX_F16X3, DLX_FP32_SIMT, DLX_TF32X3, PRECISIONS, DlxError  # noqa: F401
+from ._native import (DLX_BF16, DLX_BF16X3, DLX_BF16X3SA, DLX_BF16X4, DLX_F16X3, DLX_FP32_SIMT, DLX_TF32X3,  # noqa: F401
+                      PRECISIONS, DlxError)
 
 PARAM_KEYS = ("transmission", "opd_fixed", "zern_basis", "zern_coeff", "opd_pix", "weights", "flux", "pos", "dither",
               "flat")

@@ -16,9 +16,9 @@ from . import build as _build
 DLX_OK, DLX_PENDING = 0, 1
 DLX_ERR = {-1: "INVALID_ARG", -2: "NOMEM", -3: "CUDA", -4: "NONFINITE", -5: "TIMEOUT", -6: "RANGE",
            -7: "UNSUPPORTED"}
-DLX_FP32_SIMT, DLX_TF32X3, DLX_BF16X3, DLX_BF16, DLX_BF16X4, DLX_F16X3 = 0, 1, 2, 3, 4, 5
+DLX_FP32_SIMT, DLX_TF32X3, DLX_BF16X3, DLX_BF16, DLX_BF16X4, DLX_F16X3, DLX_BF16X3SA = 0, 1, 2, 3, 4, 5, 6
 PRECISIONS = {"fp32": DLX_FP32_SIMT, "tf32x3": DLX_TF32X3, "bf16x3": DLX_BF16X3, "bf16": DLX_BF16, "bf16x4": DLX_BF16X4,
-              "f16x3": DLX_F16X3}
+              "f16x3": DLX_F16X3, "bf16x3sa": DLX_BF16X3SA}
 
 _fp = C.POINTER(C.c_float)
 

@@ -124,7 +124,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     for (int l = 0; l < d->n_lambda; ++l)
         if (!(d->lambda_m[l] > 0) || !std::isfinite(d->lambda_m[l]))
             return fail(DLX_ERR_INVALID_ARG, "wavelengths must be finite and > 0");
-    if (d->precision < DLX_FP32_SIMT || d->precision > DLX_F16X3) return fail(DLX_ERR_INVALID_ARG, "bad precision");
+    if (d->precision < DLX_FP32_SIMT || d->precision > DLX_BF16X3SA) return fail(DLX_ERR_INVALID_ARG, "bad precision");
     if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 8 sources per plan");
     const long long no_ll = (long long)d->n_det * d->oversample;
     if (d->n_pupil > 8192 || no_ll > 16384) return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and n_det*oversample <= 16384");
@@ -156,7 +156,8 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->ldo = round8(p->no);
     p->prec = d->precision;
     p->fmt = fmt_of_prec(p->prec);
-    p->sr = (p->prec == DLX_BF16X3) ? 0x6d2b79f5u : 0u;  // stochastic split of the forward operands
+    p->sr = (p->prec == DLX_BF16X3 || p->prec == DLX_BF16X3SA) ? 0x6d2b79f5u : 0u;  // stochastic split
+    p->adj1 = (p->prec == DLX_BF16X3SA);
     p->planes = fmt_planes(p->fmt);
     p->esz = fmt_esize(p->fmt);
     p->dx = d->diameter_m / p->ni;
@@ -176,7 +177,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
 
     const int Bt = p->B * R_max;
     // adjoint chunk: the per-wavelength recomputation batch
-    const size_t per_psf = (size_t)p->planes * p->esz * ((size_t)p->no * p->ldo + (size_t)p->ni * p->ldo);
+    const size_t per_psf = (size_t)(p->adj1 ? 2 : p->planes) * p->esz * ((size_t)p->no * p->ldo + (size_t)p->ni * p->ldo);
     int chunk = Bt;
     if (d->psf_chunk > 0)
         chunk = std::min(d->psf_chunk, Bt);
@@ -220,20 +221,23 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     }
 
     cudaError_t e = cudaSuccess;
-    auto op_alloc = [&](Operand &o, int batch, int rows, int ld) {
+    auto op_alloc = [&](Operand &o, int batch, int rows, int ld, int planes) {
         o.batch = batch;
         o.rows = rows;
         o.ld = ld;
-        o.bytes = (size_t)batch * p->planes * rows * ld * p->esz;
+        o.planes = planes;
+        o.bytes = (size_t)batch * planes * rows * ld * p->esz;
         if (e == cudaSuccess) e = plan_alloc(p, &o.ptr, o.bytes);
         if (e == cudaSuccess) e = cudaMemset(o.ptr, 0, o.bytes);
     };
-    op_alloc(p->amat, p->nl, p->no, p->ldi);
-    op_alloc(p->amatH, p->nl, p->ni, p->ldo);
-    op_alloc(p->P, Bt, p->ni, p->ldi);
-    op_alloc(p->T1t, Bt, p->no, p->ldi);
-    op_alloc(p->GEt, p->chunk, p->no, p->ldo);
-    op_alloc(p->GT1, p->chunk, p->ni, p->ldo);
+    // BF16x3sa: the adjoint-only operands (AH, GEt, GT1) hold the stochastic hi parts alone
+    const int adj_planes = p->adj1 ? 2 : p->planes;
+    op_alloc(p->amat, p->nl, p->no, p->ldi, p->planes);
+    op_alloc(p->amatH, p->nl, p->ni, p->ldo, adj_planes);
+    op_alloc(p->P, Bt, p->ni, p->ldi, p->planes);
+    op_alloc(p->T1t, Bt, p->no, p->ldi, p->planes);
+    op_alloc(p->GEt, p->chunk, p->no, p->ldo, adj_planes);
+    op_alloc(p->GT1, p->chunk, p->ni, p->ldo, adj_planes);
     const size_t npx = (size_t)p->ni * p->ni, np = (size_t)p->nd * p->nd, nq = (size_t)p->no * p->no;
     p->red_blocks = std::max(1, std::min((int)((np + 255) / 256), std::max(1, p->sm_count * 2 / R_max)));
     if (e == cudaSuccess) e = plan_alloc(p, &p->lam_d, sizeof(double) * p->nl);

@@ -57,6 +57,7 @@ inline int fmt_of_prec(int prec) {
         case DLX_BF16X3: return FMT_BF16X4;
         case DLX_BF16X4: return FMT_BF16X4;
         case DLX_F16X3: return FMT_F16X4;
+        case DLX_BF16X3SA: return FMT_BF16X4;
         default: return FMT_BF16X2;
     }
 }
@@ -283,8 +284,10 @@ __host__ __device__ inline float inv_pow2_ceil(float x) {
 struct Operand {
     void *ptr = nullptr;
     int batch = 0, rows = 0, ld = 0;  // ld = padded contraction length
+    int planes = 0;                   // planes of this operand (the plan's form, or 2 for hi-only ones)
     size_t bytes = 0;
     CUtensorMap tmap;                 // valid when the plan uses a tensor-core form
+    CUtensorMap tmap_hi;              // split operands of the BF16x3sa form: the hi planes (re_hi, im_hi) only
 };
 
 // Parameters of R independent same-shape models ("slots"): array k of slot r
@@ -349,7 +352,8 @@ struct dlx_plan {
     float2 *zpart = nullptr;   // [R][n_zern][ceil(Ni^2 / 64)] Zernike-gradient partials (compensated pairs)
     unsigned int *bcount = nullptr;  // [R] blocks of the binning pass done (reset by the last one)
     float *mom = nullptr;      // tensor-core forms: [R*B][gsplit][tiles][8 warps][2] position moments
-    uint32_t sr = 0;           // BF16x3 form: stochastic splitting of the forward operands (seed base), else 0
+    uint32_t sr = 0;           // BF16x3 forms: stochastic splitting of the forward operands (seed base), else 0
+    bool adj1 = false;         // BF16x3sa: the adjoint contracts the stochastic hi parts only (2-plane bf16)
     float2 *npart = nullptr;   // [R][kNormParts] block partials of sum T^2 (compensated pairs)
     unsigned int *ncount = nullptr;  // [R] blocks of the prologue pass done (reset by the last one)
     int32_t *err = nullptr;    // device error flag

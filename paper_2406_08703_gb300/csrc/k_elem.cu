@@ -72,10 +72,12 @@ __device__ void block_sum(df (&v)[NV], df *sh /* [32][NV] */) {
 // formed and reduced to r = t - rint(t) in FP64 before sin/cos, so the phase
 // error does not grow with |t|.  AH[l][n][k] = conj(A[l][k][n]).  Built once
 // per plan.  FP16 operands hold A times alpha_l = ascale[l] (|A alpha_l| <= 1).
-// With sr != 0 (BF16x3 form) A is split stochastically; AH (adjoint) is not.
+// With sr != 0 (BF16x3 forms) A is split stochastically; AH (adjoint) is split by
+// rounding to nearest, or (ah_hi, BF16x3sa form) holds only the stochastically
+// rounded hi parts in two planes (re, im).
 template <int F>
 __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const float *ascale, int nl, int ni,
-                               int no, int ldi, int ldo, double dx, double du, uint32_t sr) {
+                               int no, int ldi, int ldo, double dx, double du, uint32_t sr, int ah_hi) {
     const int P = fmt_planes(F), es = fmt_esize(F);
     const size_t per = (size_t)no * ni, total = per * nl;
     const double cN = 0.5 * (ni - 1), cO = 0.5 * (no - 1);
@@ -100,6 +102,16 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const
         } else {
             store_cplx<F>(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im);
         }
+        if constexpr (F == FMT_BF16X4) {
+            if (ah_hi) {
+                __nv_bfloat16 *ah = (__nv_bfloat16 *)amatH + (size_t)l * 2 * ni * ldo;
+                const uint2 rb = sr_bits(((size_t)l * ni + n) * ldo + k, sr ^ 0x68e31da4u);
+                const size_t o = (size_t)n * ldo + k;
+                ah[o] = bf16_sr(re, rb.x & 0xffffu);
+                ah[(size_t)ni * ldo + o] = bf16_sr(-im, rb.y & 0xffffu);
+                continue;
+            }
+        }
         char *ah = (char *)amatH + (size_t)l * P * ni * ldo * es;
         store_cplx<F>(ah, (size_t)ni * ldo, (size_t)n * ldo + k, re, -im);
     }
@@ -111,7 +123,8 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
     KScope ks(p, KC_MATRICES, 1, st);
     DLX_FMT_DISPATCH(p->fmt, F,
                      k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->ascale, p->nl,
-                                                               p->ni, p->no, p->ldi, p->ldo, p->dx, p->du, p->sr));
+                                                               p->ni, p->no, p->ldi, p->ldo, p->dx, p->du, p->sr,
+                                                               p->adj1 ? 1 : 0));
     return cudaGetLastError();
 }
 

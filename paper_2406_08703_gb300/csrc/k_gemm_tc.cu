@@ -93,7 +93,8 @@ struct TcArgs {
     const int *s2off; // stage 2: CTA c runs pieces s2pc[s2off[c] .. s2off[c+1])
     const int4 *s2pc; // stage 2 pieces (segment, l0, l1, plane | first plane to clear << 16)
     int grid;         // CTAs (0: min(units, SMs))
-    uint32_t sr;      // stage 1 of the BF16x3 form: stochastic split of T1t (seed), else 0
+    uint32_t sr;      // BF16x3 forms: stochastic split (seed) of the operand this launch writes, else 0
+    int p4;           // BF16x3sa adjoint 1^T: the phasor is a four-plane split
     int32_t *err;
 };
 
@@ -443,6 +444,26 @@ __device__ __forceinline__ void stage_row16_sr(uint8_t *stg, int r, int h, const
         *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)rl;
         *(uint4 *)(p + 2 * PLANE_BYTES) = *(uint4 *)ih;
         *(uint4 *)(p + 3 * PLANE_BYTES) = *(uint4 *)il;
+    }
+}
+
+// stage_row16 of a two-plane (re, im) bf16 operand with stochastic rounding (the
+// BF16x3sa adjoint); element i of the row has global index gidx + i.
+__device__ __forceinline__ void stage_row16_hi_sr(uint8_t *stg, int r, int h, const float (&re)[CW],
+                                                  const float (&im)[CW], uint64_t gidx, uint32_t seed) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        __align__(16) __nv_bfloat16 rh[8], ih[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const uint32_t rb = fmix32((uint32_t)(gidx + 8 * q + i) ^ seed ^ ((uint32_t)(gidx >> 32) * 0x9e3779b9u));
+            rh[i] = bf16_sr(re[8 * q + i], rb & 0xffffu);
+            ih[i] = bf16_sr(im[8 * q + i], rb >> 16);
+        }
+        const int g = (2 * h + q) ^ ((r >> 1) & 3);
+        uint8_t *p = stg + r * 64 + g * 16;
+        *(uint4 *)(p) = *(uint4 *)rh;
+        *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)ih;
     }
 }
 
@@ -797,6 +818,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 staged = true;
                             }
                         }
+                        if constexpr ((KIND == KGE || KIND == KGT1) && F == FMT_BF16X2) {
+                            if (a.sr) {  // BF16x3sa adjoint: stochastically rounded hi parts only
+                                const int n = J.n0 + c0;
+                                stage_row16_hi_sr(stg, row, h, er, ei, ((size_t)J.b * a.M + m) * a.out_ld + n,
+                                                  a.sr);
+                                staged = true;
+                            }
+                        }
                         if (!staged) stage_row16<F>(stg, row, h, er, ei);
                         fence_async_smem();
                         epi_bar();
@@ -849,11 +878,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             if constexpr (KIND == KGP) {
                                 // rows ny, columns nx: gphi = (2 pi / lambda) Im(G_P conj P)
                                 const size_t pps = (size_t)a.ni * a.ldi;
-                                const char *pb = (const char *)a.P + (size_t)J.b * C::PL * pps * C::ES;
                                 float *o = a.gphi + ((size_t)J.b * a.ksplit + J.split) * a.ni * a.ni + (size_t)m * a.ni +
                                            n0;
                                 float pr[CW], pi[CW], gv[CW];
-                                load_row<F>(pb, pps, (size_t)m * a.ldi + n0, pr, pi, nvalid);
+                                if constexpr (F == FMT_BF16X2) {
+                                    if (a.p4) {  // BF16x3sa: the phasor is a four-plane split, read hi + lo
+                                        const char *pb = (const char *)a.P + (size_t)J.b * 4 * pps * 2;
+                                        load_row<FMT_BF16X4>(pb, pps, (size_t)m * a.ldi + n0, pr, pi, nvalid);
+                                    } else {
+                                        const char *pb = (const char *)a.P + (size_t)J.b * C::PL * pps * C::ES;
+                                        load_row<F>(pb, pps, (size_t)m * a.ldi + n0, pr, pi, nvalid);
+                                    }
+                                } else {
+                                    const char *pb = (const char *)a.P + (size_t)J.b * C::PL * pps * C::ES;
+                                    load_row<F>(pb, pps, (size_t)m * a.ldi + n0, pr, pi, nvalid);
+                                }
 #pragma unroll
                                 for (int i = 0; i < CW; ++i) {
                                     gv[i] = (i < nvalid) ? k2 * (ei[i] * pr[i] - er[i] * pi[i]) : 0.f;
@@ -966,23 +1005,27 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
     return fn;
 }
 
-bool make_map(dlx_plan *p, Operand &o, std::string *why) {
+// Tensor map of an operand: 4-D {k, row, plane, batch}, box 128 rows x 64 bytes x all
+// planes.  hi_view: the planes re_hi and im_hi (0 and 2) of a four-plane split operand,
+// as a two-plane tensor (plane stride doubled).
+bool make_map(dlx_plan *p, Operand &o, std::string *why, bool hi_view = false) {
     auto enc = get_encoder();
     if (!enc) {
         *why = "cuTensorMapEncodeTiled unavailable";
         return false;
     }
-    const int es = p->esz, PL = p->planes;
+    const int es = p->esz, PL = hi_view ? 2 : o.planes;
+    const cuuint64_t plane = (cuuint64_t)o.rows * o.ld * es;
     cuuint64_t dims[4] = {(cuuint64_t)o.ld, (cuuint64_t)o.rows, (cuuint64_t)PL, (cuuint64_t)o.batch};
-    cuuint64_t strides[3] = {(cuuint64_t)o.ld * es, (cuuint64_t)o.rows * o.ld * es,
-                             (cuuint64_t)PL * o.rows * o.ld * es};
+    cuuint64_t strides[3] = {(cuuint64_t)o.ld * es, (hi_view ? 2 : 1) * plane, (cuuint64_t)o.planes * plane};
     cuuint32_t box[4] = {(cuuint32_t)(64 / es), 128u, (cuuint32_t)PL, 1u};
     cuuint32_t estr[4] = {1, 1, 1, 1};
     CUtensorMapDataType dt = (p->fmt == FMT_TF32X4)  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : (p->fmt == FMT_F16X4) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    CUresult r = enc(&o.tmap, dt, 4, o.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(hi_view ? &o.tmap_hi : &o.tmap, dt, 4, o.ptr, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *why = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
         return false;
@@ -1019,7 +1062,11 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
     a.sig1 = inv_pow2_ceil((float)p->ni);
     a.qmax = p->qmax;
     a.gmax = p->gmax;
-    a.sr = (KIND == KS1) ? p->sr : 0u;
+    a.sr = (KIND == KS1) ? p->sr
+           : (p->adj1 && KIND == KGE) ? p->sr ^ 0x85ebca77u
+           : (p->adj1 && KIND == KGT1) ? p->sr ^ 0xc2b2ae3du
+                                       : 0u;
+    a.p4 = (p->adj1 && KIND == KGP) ? 1 : 0;
     a.tm = (a.M + BM - 1) / BM;
     a.tn = (a.N + BN - 1) / BN;
     a.KB = Cfg<F>::KB;
@@ -1076,7 +1123,13 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     a.out_ld = p->ldo;
     a.out_ps = (size_t)p->no * p->ldo;
     a.units = nb * tmo * tmo;
-    cudaError_t e = launch<F, FAST, KGE>(p, p->T1t, p->amat, &p->GEt, a, st);
+    // BF16x3sa: the recomputed field contracts the stochastic hi planes of T1t and A only
+    Operand T1 = p->T1t, Am = p->amat;
+    if (p->adj1) {
+        T1.tmap = p->T1t.tmap_hi;
+        Am.tmap = p->amat.tmap_hi;
+    }
+    cudaError_t e = launch<F, FAST, KGE>(p, T1, Am, &p->GEt, a, st);
     if (e != cudaSuccess) return e;
     // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No)
     TcArgs b{};
@@ -1120,8 +1173,10 @@ int tc_supported(const dlx_plan *p, std::string *why) {
 }
 
 int tc_make_maps(dlx_plan *p, std::string *why) {
-    return make_map(p, p->amat, why) && make_map(p, p->amatH, why) && make_map(p, p->P, why) &&
-           make_map(p, p->T1t, why) && make_map(p, p->GEt, why) && make_map(p, p->GT1, why);
+    bool ok = make_map(p, p->amat, why) && make_map(p, p->amatH, why) && make_map(p, p->P, why) &&
+              make_map(p, p->T1t, why) && make_map(p, p->GEt, why) && make_map(p, p->GT1, why);
+    if (ok && p->adj1) ok = make_map(p, p->amat, why, true) && make_map(p, p->T1t, why, true);
+    return ok;
 }
 
 cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st) {
@@ -1141,7 +1196,9 @@ cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st) {
 
 cudaError_t tc_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st) {
     switch (p->fmt) {
-        case FMT_BF16X4: return adjoint_impl<FMT_BF16X4>(p, prm, b0, nb, st);
+        case FMT_BF16X4:
+            // BF16x3sa: one product per real product on the stochastic hi parts (two-plane kernels)
+            return p->adj1 ? adjoint_impl<FMT_BF16X2>(p, prm, b0, nb, st) : adjoint_impl<FMT_BF16X4>(p, prm, b0, nb, st);
         case FMT_BF16X2: return adjoint_impl<FMT_BF16X2>(p, prm, b0, nb, st);
         case FMT_TF32X4: return adjoint_impl<FMT_TF32X4>(p, prm, b0, nb, st);
         case FMT_F16X4: return adjoint_impl<FMT_F16X4>(p, prm, b0, nb, st);

@@ -581,7 +581,7 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
     if (!s || !rq || !ticket) return fail(DLX_ERR_INVALID_ARG, "NULL argument");
     const dlx_mft_desc &d = rq->desc;
     if (d.n_pupil < 2 || d.n_det < 1 || d.oversample < 1 || d.n_lambda < 1 || d.n_src < 1 || d.n_exp < 1 ||
-        d.n_zern < 0 || !d.lambda_m || d.precision < DLX_FP32_SIMT || d.precision > DLX_F16X3)
+        d.n_zern < 0 || !d.lambda_m || d.precision < DLX_FP32_SIMT || d.precision > DLX_BF16X3SA)
         return fail(DLX_ERR_INVALID_ARG, "bad request shape");
     if (d.n_src > dlx::kMaxSrc) return fail(DLX_ERR_RANGE, "at most 8 sources");
     if (!rq->transmission || !rq->weights || !rq->flux || !rq->pos || !rq->flat || !rq->data ||

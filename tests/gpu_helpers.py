@@ -19,6 +19,10 @@ import workloads as W
 # aligns them to a growing FP32 accumulator, so coherent sums lose low bits:
 # measured 1.6e-6 of peak at a 64 pupil, 4.2e-6 at 256 and 1.5e-5 at 512; the
 # PSF is bounded at 2e-5 and the gradients at the FP32 bound.
+# BF16x3sa shares BF16x3's forward; its adjoint contracts the stochastically
+# rounded hi parts alone, so its gradients carry zero-mean noise of about
+# 2^-8 / sqrt(K) per contraction: measured 3e-4 (binary-star workload) to 1.5e-3
+# (64 pupil) relative L2, bounded at 3e-3.
 # Plain BF16 is reported as measured and only bounded loosely here.
 TOL = {
     "f16x3": dict(psf=2e-5, loss=1e-6, grad=1e-4),
@@ -26,6 +30,7 @@ TOL = {
     "tf32x3": dict(psf=2e-5, loss=1e-6, grad=1e-4),
     "bf16x4": dict(psf=1e-5, loss=1e-6, grad=1e-3),
     "bf16x3": dict(psf=1e-5, loss=1e-6, grad=1e-3),
+    "bf16x3sa": dict(psf=1e-5, loss=1e-6, grad=3e-3),
     "bf16": dict(psf=5e-3, loss=1e-3, grad=5e-2),
 }
 

@@ -12,7 +12,7 @@ from gpu_helpers import TOL, compare, fit_problem, gpu_eval, oracle_eval, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-FORMS = ["fp32", "f16x3", "bf16x4", "bf16x3", "tf32x3", "bf16"]
+FORMS = ["fp32", "f16x3", "bf16x4", "bf16x3", "bf16x3sa", "tf32x3", "bf16"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -77,7 +77,7 @@ def binary_full():
     return start, data, oracle_eval(start, data)
 
 
-@pytest.mark.parametrize("form", ["fp32", "f16x3", "bf16x4", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("form", ["fp32", "f16x3", "bf16x4", "bf16x3", "bf16x3sa", "tf32x3"])
 def test_binary_full_size(binary_full, form):
     """The full binary-star workload: 32 wavelengths x 2 stars = 64 PSFs of 1024^2."""
     start, data, ref = binary_full
@@ -116,7 +116,7 @@ def calib_full():
     return p, data
 
 
-@pytest.mark.parametrize("form", ["fp32", "f16x3", "bf16x4", "bf16x3", "tf32x3"])
+@pytest.mark.parametrize("form", ["fp32", "f16x3", "bf16x4", "bf16x3", "bf16x3sa", "tf32x3"])
 def test_calib_full_size_sampled(calib_full, form):
     """512^2 pupil, 16 wavelengths x 8 exposures, 2048^2 grid: sampled model pixels
     against direct sums, and identities that hold at any size."""
