@@ -339,9 +339,7 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     const int npx = p->ni * p->ni;
     KScope ks(p, KC_PROLOGUE, 2, st);
     const int work = std::max((npx + 63) / 64, (p->B * 2 * p->ni + 255) / 256);
-    // about two blocks per SM: every block also adds its partial sums and one arrival on the
-    // slot's counter, which serialises
-    const int blocks = std::max(1, std::min({work, p->sm_count * 2 / R, kNormParts}));
+    const int blocks = std::max(1, std::min({work, p->sm_count * 8 / R, kNormParts}));
     cudaError_t e = launch_pdl(k_prologue, dim3(blocks, R), dim3(256), sizeof(float) * (p->nz > 0 ? p->nz : 1), st,
                                prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm,
                                p->lam_d, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax);
