@@ -17,6 +17,8 @@
  *   I_e   = sum_s F_s sum_l w_l |E_{l,s,e}|^2, w normalised to sum 1
  *   B_e   = os x os block sums of I_e;  m = FF * B_e         (pixel response, Sec. 3)
  *   L     = sum_e sum_p (m - d ln m)                         (Poisson likelihood, Sec. 4)
+ *           + sum_p (FF_p - 1)^2 / (2 sigma^2)                 (chi^2 log prior on the pixel
+ *                                                              response, Sec. 4; sigma = 0: none)
  * and the analytic adjoint of L with respect to the Zernike coefficients, the
  * pixel OPD map, the flat field, the source fluxes and the source positions
  * (Sec. 4 takes gradients of this loss with respect to exactly these groups).
@@ -61,6 +63,7 @@ typedef struct {
     const double *opd_fixed;    /* [n][n] */
     const double *opd_pix;      /* [n][n] or NULL */
     const double *flat;         /* [n_det][n_det] */
+    double prf_sigma;           /* s.d. of the chi^2 prior on the flat field about 1; 0 = no prior */
 } orc_problem;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -334,6 +337,21 @@ static long poisson_nll(size_t n, const double *model, const int *data, double *
     return clamped;
 }
 
+/* chi^2 log prior on the pixel response (Sec. 4: mean 1, s.d. sigma):
+ * sum_p (FF_p - 1)^2 / (2 sigma^2); adds its gradient (FF_p - 1) / sigma^2 to
+ * g_flat when g_flat is not NULL.  Zero when sigma = 0. */
+static double prf_prior(const orc_problem *q, double *g_flat) {
+    if (!(q->prf_sigma > 0)) return 0.0;
+    size_t np = (size_t)q->n_det * q->n_det;
+    double acc = 0, s2 = q->prf_sigma * q->prf_sigma;
+    for (size_t p = 0; p < np; ++p) {
+        double dev = q->flat[p] - 1.0;
+        acc += dev * dev / (2.0 * s2);
+        if (g_flat) g_flat[p] += dev / s2;
+    }
+    return acc;
+}
+
 /* Loss only (used by the finite-difference pins). */
 double orc_loss(const orc_problem *q, const int *data) {
     size_t np = (size_t)q->n_det * q->n_det * q->n_exp;
@@ -341,7 +359,7 @@ double orc_loss(const orc_problem *q, const int *data) {
     orc_forward(q, model, NULL);
     poisson_nll(np, model, data, &L, NULL);
     free(model);
-    return L;
+    return L + prf_prior(q, NULL);
 }
 
 /* Loss and its gradient by the analytic adjoint (reverse-mode chain rule of Sec. 4's loss).
@@ -380,6 +398,7 @@ long orc_loss_grad(const orc_problem *q, const int *data, double *loss, double *
             }
             g_flat[p] = acc;
         }
+    *loss += prf_prior(q, g_flat);
     if (g_flux)
         for (int s = 0; s < q->n_src; ++s) {
             double acc = 0;

@@ -376,3 +376,49 @@ def test_sampled_model_equals_full_forward(oracle_lib, fit_case):
     q = rng.integers(0, p.n_det * p.n_det, 12)
     got = oracle_lib.model_at(p, e, q)
     assert np.allclose(got, m.reshape(p.n_exp, -1)[e, q], rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------- chi^2 prior on the pixel response
+
+def test_prf_prior_posterior_mode(oracle_lib, fit_case):
+    """With the chi^2 prior (Sec. 4: pixel response about 1, s.d. sigma) and one exposure, the
+    flat-field gradient of one pixel is b - d/FF + (FF - 1)/sigma^2 with b the unflattened model,
+    so it vanishes at the positive root of FF^2/sigma^2 + (b - 1/sigma^2) FF - d = 0: the
+    per-pixel posterior mode, found here by the quadratic formula, not by the oracle."""
+    p, _ = fit_case
+    q = p.copy()
+    q.dither = q.dither[:1]
+    q.flat = np.ones_like(q.flat)
+    b = oracle_lib.forward(q)[0]  # FF = 1: the model is the binned flux-weighted intensity
+    d = W.poisson_counts(b[None], 31)
+    sigma = 0.1
+    a2 = 1.0 / sigma**2
+    c1 = b - a2
+    ff = (-c1 + np.sqrt(c1 * c1 + 4 * a2 * d[0])) / (2 * a2)
+    q.flat = ff
+    q.prf_sigma = sigma
+    g = oracle_lib.loss_grad(q, d)["flat"]
+    scale = b + d[0] / ff + np.abs(ff - 1) * a2  # size of the three terms
+    assert np.max(np.abs(g) / scale) < 1e-12
+    # without the prior the same point is not stationary
+    q.prf_sigma = 0.0
+    assert np.max(np.abs(oracle_lib.loss_grad(q, d)["flat"]) / scale) > 1e-3
+
+
+def test_prf_prior_gradient_central_differences(oracle_lib, fit_case):
+    p, d = fit_case
+    q = p.copy()
+    q.prf_sigma = 0.1
+    g = oracle_lib.loss_grad(q, d)
+    rng = np.random.default_rng(9)
+    for _ in range(6):
+        iy, ix = rng.integers(0, 8, 2)
+
+        def s(r, h, iy=iy, ix=ix):
+            r.flat = r.flat.copy()
+            r.flat[iy, ix] += h
+        assert g["flat"][iy, ix] == pytest.approx(_fd(oracle_lib, q, d, s, 1e-6), rel=2e-6)
+    # the prior changes no other group
+    g0 = oracle_lib.loss_grad(p, d)
+    for k in ("coeff", "opd_pix", "flux", "pos"):
+        assert np.array_equal(g[k], g0[k])

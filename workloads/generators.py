@@ -214,6 +214,7 @@ class Problem:
     opd_fixed: np.ndarray  # (n, n) m
     opd_pix: Optional[np.ndarray]  # (n, n) m, or None when the pixel OPD map is not a parameter
     flat: np.ndarray  # (n_det, n_det)
+    prf_sigma: float = 0.0  # s.d. of the chi^2 prior on the flat field about 1 (0: no prior)
 
     @property
     def n_lambda(self) -> int:
