@@ -89,13 +89,16 @@ typedef struct {
     int oversample;          /* os >= 1; MFT output No = Nd * os */
     int n_lambda;            /* number of wavelengths, >= 1 */
     const double *lambda_m;  /* HOST array [n_lambda], metres; copied */
-    int n_src;               /* point sources, >= 1 */
+    int n_src;               /* point sources, 1 .. 32 */
     int n_exp;               /* exposures (known dithers), >= 1 */
     int n_zern;              /* Zernike basis terms, >= 0 */
     int precision;           /* dlx_prec */
     int psf_chunk;           /* PSFs per adjoint pass (per-wavelength recomputation batch);
                                 0 = automatic from workspace_limit_bytes */
     size_t workspace_limit_bytes; /* 0 = no limit; bounds the adjoint workspace */
+    double prf_prior_sigma;  /* > 0: the loss adds the chi^2 log prior on the pixel response
+                                (Sec. 4) sum_p (FF_p - 1)^2 / (2 sigma^2), and dL/dFF its
+                                gradient (FF_p - 1) / sigma^2; 0 = none */
 } dlx_mft_desc;
 
 /* Parameters and fixed inputs of one evaluation.  Device pointers. */
@@ -155,7 +158,7 @@ int dlx_forward(dlx_plan *plan, const dlx_params *params, float *model, void *cu
  * file-scope device array of 16 MiB that every GPU loading the library holds
  * until the process exits.  Arguments are dlx_forward's, with `desc` in place
  * of a plan (desc->lambda_m is host memory, read during the call).
- * Limits: at most 8 sources and 256 wavelengths, and the working memory of
+ * Limits: at most 32 sources and 256 wavelengths, and the working memory of
  *   8*nl + 8*nl + 8*B*Ni + 4*Ni^2 + 8*nl*No*Ni8 + 8*nl*Ni*No8 + 8*B*Ni*Ni8
  *   + 8*B*No*Ni8 + 4*nS*nE*No^2 + reduction partials   (bytes, Ni8/No8 = sizes rounded up to 8)
  * must fit in 16 MiB; larger shapes return DLX_ERR_RANGE with the byte count.

@@ -49,12 +49,13 @@ class MftDesc:
     precision: int = DLX_BF16X3
     psf_chunk: int = 0
     workspace_limit_bytes: int = 0
+    prf_prior_sigma: float = 0.0
 
     def to_c(self):
         lam = (C.c_double * len(self.lambdas))(*[float(x) for x in self.lambdas])
         d = N.MftDesc(self.n_pupil, self.diameter_m, self.n_det, self.pixscale_rad, self.oversample,
                       len(self.lambdas), C.cast(lam, C.POINTER(C.c_double)), self.n_src, self.n_exp, self.n_zern,
-                      int(self.precision), self.psf_chunk, self.workspace_limit_bytes)
+                      int(self.precision), self.psf_chunk, self.workspace_limit_bytes, float(self.prf_prior_sigma))
         return d, lam
 
 
@@ -81,6 +82,7 @@ class Plan:
 
 def desc_from_problem(p, precision=DLX_BF16X3, **kw) -> MftDesc:
     """MftDesc of a workloads.Problem-like object (duck-typed)."""
+    kw.setdefault("prf_prior_sigma", float(getattr(p, "prf_sigma", 0.0) or 0.0))
     return MftDesc(n_pupil=p.n_pupil, diameter_m=p.diameter, n_det=p.n_det, pixscale_rad=p.pixscale,
                    oversample=p.oversample, lambdas=list(p.lambdas), n_src=len(p.flux), n_exp=len(p.dither),
                    n_zern=len(p.coeff), precision=precision, **kw)

@@ -27,7 +27,7 @@ class MftDesc(C.Structure):
     _fields_ = [("n_pupil", C.c_int), ("diameter_m", C.c_double), ("n_det", C.c_int), ("pixscale_rad", C.c_double),
                 ("oversample", C.c_int), ("n_lambda", C.c_int), ("lambda_m", C.POINTER(C.c_double)),
                 ("n_src", C.c_int), ("n_exp", C.c_int), ("n_zern", C.c_int), ("precision", C.c_int),
-                ("psf_chunk", C.c_int), ("workspace_limit_bytes", C.c_size_t)]
+                ("psf_chunk", C.c_int), ("workspace_limit_bytes", C.c_size_t), ("prf_prior_sigma", C.c_double)]
 
 
 class Params(C.Structure):

@@ -125,7 +125,9 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
         if (!(d->lambda_m[l] > 0) || !std::isfinite(d->lambda_m[l]))
             return fail(DLX_ERR_INVALID_ARG, "wavelengths must be finite and > 0");
     if (d->precision < DLX_FP32_SIMT || d->precision > DLX_BF16X3SA) return fail(DLX_ERR_INVALID_ARG, "bad precision");
-    if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 8 sources per plan");
+    if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 32 sources per plan");
+    if (!(d->prf_prior_sigma >= 0) || !std::isfinite(d->prf_prior_sigma))
+        return fail(DLX_ERR_INVALID_ARG, "prf_prior_sigma must be finite and >= 0");
     const long long no_ll = (long long)d->n_det * d->oversample;
     if (d->n_pupil > 8192 || no_ll > 16384) return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and n_det*oversample <= 16384");
 
@@ -158,6 +160,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->fmt = fmt_of_prec(p->prec);
     p->sr = (p->prec == DLX_BF16X3 || p->prec == DLX_BF16X3SA) ? 0x6d2b79f5u : 0u;  // stochastic split
     p->adj1 = (p->prec == DLX_BF16X3SA);
+    p->prf_inv = d->prf_prior_sigma > 0 ? (float)(1.0 / (d->prf_prior_sigma * d->prf_prior_sigma)) : 0.f;
     p->planes = fmt_planes(p->fmt);
     p->esz = fmt_esize(p->fmt);
     p->dx = d->diameter_m / p->ni;

@@ -354,6 +354,7 @@ struct dlx_plan {
     float *mom = nullptr;      // tensor-core forms: [R*B][gsplit][tiles][8 warps][2] position moments
     uint32_t sr = 0;           // BF16x3 forms: stochastic splitting of the forward operands (seed base), else 0
     bool adj1 = false;         // BF16x3sa: the adjoint contracts the stochastic hi parts only (2-plane bf16)
+    float prf_inv = 0.f;       // 1 / sigma^2 of the chi^2 prior on the flat field, 0 = none
     float2 *npart = nullptr;   // [R][kNormParts] block partials of sum T^2 (compensated pairs)
     unsigned int *ncount = nullptr;  // [R] blocks of the prologue pass done (reset by the last one)
     int32_t *err = nullptr;    // device error flag
@@ -375,7 +376,7 @@ struct dlx_plan {
 
 namespace dlx {
 
-constexpr int kMaxSrc = 8;
+constexpr int kMaxSrc = 32;  // sources per plan
 constexpr int kNormParts = 1024;  // maximum blocks of the OPD / pupil-power pass
 
 enum KClass { KC_MATRICES = 0, KC_PROLOGUE, KC_STAGE1, KC_STAGE2, KC_BIN, KC_LOSS, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1,

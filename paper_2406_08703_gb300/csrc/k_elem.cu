@@ -371,14 +371,15 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
 // os-wide row segments); OS = 0 takes it from `os_rt`.
 constexpr int kQShared = 64;  // (source, exposure) maxima kept in shared memory
 
-template <int OS>
+template <int OS, int MAXS>
 __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os_rt,
                           int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
-                          unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount) {
+                          unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount,
+                          float prf_inv) {
     pdl_trigger();
     pdl_wait();
-    __shared__ df sh[32 * (1 + kMaxSrc)];
+    __shared__ df sh[32 * (1 + MAXS)];
     __shared__ unsigned int s_q[kQShared];
     __shared__ bool s_last;
     const int np = nd * nd, r = blockIdx.y, os = OS > 0 ? OS : os_rt;
@@ -390,9 +391,9 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
     if (wantq)
         for (int i = threadIdx.x; i < kQShared; i += blockDim.x) s_q[i] = 0u;
     __syncthreads();
-    df acc[1 + kMaxSrc];
+    df acc[1 + MAXS];
 #pragma unroll
-    for (int i = 0; i < 1 + kMaxSrc; ++i) acc[i] = {0.f, 0.f};
+    for (int i = 0; i < 1 + MAXS; ++i) acc[i] = {0.f, 0.f};
     unsigned long long nclamp = 0;
     const size_t plane = (size_t)no * no;
     // block-uniform trip count, so the warp-wide maxima below see every lane
@@ -403,10 +404,10 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
         const float ff = valid ? flat[p] : 0.f;
         float dff = 0.f;
         for (int e = 0; e < ne; ++e) {
-            float bs[kMaxSrc], bmax[kMaxSrc];
+            float bs[MAXS], bmax[MAXS];
             float btot = 0.f;
 #pragma unroll
-            for (int s = 0; s < kMaxSrc; ++s) {
+            for (int s = 0; s < MAXS; ++s) {
                 bs[s] = 0.f;
                 bmax[s] = 0.f;
                 if (s < ns && valid) {
@@ -484,13 +485,13 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                     GI[((size_t)r * ne + e) * np + p] = gi;
                     dff = fmaf(gm, btot, dff);
 #pragma unroll
-                    for (int s = 0; s < kMaxSrc; ++s)
+                    for (int s = 0; s < MAXS; ++s)
                         if (s < ns) acc[1 + s] = df_add(acc[1 + s], gi * bs[s]);
                 }
             }
             if (wantq) {
 #pragma unroll
-                for (int s = 0; s < kMaxSrc; ++s) {
+                for (int s = 0; s < MAXS; ++s) {
                     if (s >= ns) break;
                     float qv = fabsf(gi) * sqrtf(bmax[s]);
                     if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
@@ -505,15 +506,21 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                 }
             }
         }
+        if (valid && dat && prf_inv > 0.f) {
+            // chi^2 log prior on the pixel response (Sec. 4): (FF - 1)^2 / (2 sigma^2)
+            const float dev = ff - 1.f;
+            acc[0] = df_add(acc[0], 0.5f * prf_inv * dev * dev);
+            dff = fmaf(prf_inv, dev, dff);
+        }
         if (valid && dat && dflat) dflat[p] = dff;
     }
-    block_sum<1 + kMaxSrc>(acc, sh);
+    block_sum<1 + MAXS>(acc, sh);
     if (wantq)
         for (int k = threadIdx.x; k < nse && k < kQShared; k += blockDim.x)
             atomicMax(qmax + (size_t)r * nse + k, s_q[k]);
     if (dat && nclamp) atomicAdd(clamped, nclamp);  // integer count: order-independent
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 1 + kMaxSrc; ++i)
+        for (int i = 0; i < 1 + MAXS; ++i)
             red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = df_to_double(acc[i]);
         s_last = false;
         if (dat && bcount) {
@@ -560,11 +567,17 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     auto go = [&](auto kern) {
         return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse, p->ns,
                           p->ne, p->nd, p->os, p->no, prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
-                          p->clamped, p->qmax, loss, p->bcount);
+                          p->clamped, p->qmax, loss, p->bcount, p->prf_inv);
     };
-    if (p->os == 4) return go(k_bin_nll<4>);
-    if (p->os == 2) return go(k_bin_nll<2>);
-    return go(k_bin_nll<0>);
+    // per-source registers for up to 8 sources, or up to kMaxSrc
+    if (p->ns <= 8) {
+        if (p->os == 4) return go(k_bin_nll<4, 8>);
+        if (p->os == 2) return go(k_bin_nll<2, 8>);
+        return go(k_bin_nll<0, 8>);
+    }
+    if (p->os == 4) return go(k_bin_nll<4, kMaxSrc>);
+    if (p->os == 2) return go(k_bin_nll<2, kMaxSrc>);
+    return go(k_bin_nll<0, kMaxSrc>);
 }
 
 __global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, int ne, size_t plane,

@@ -89,7 +89,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
             return DLX_ERR_INVALID_ARG;
         }
     if (d->n_src > dlx::kMaxSrc || d->n_lambda > kMaxLambdas) {
-        dlx_set_error("dlx_forward_noalloc: at most 8 sources and 256 wavelengths");
+        dlx_set_error("dlx_forward_noalloc: at most 32 sources and 256 wavelengths");
         return DLX_ERR_RANGE;
     }
 

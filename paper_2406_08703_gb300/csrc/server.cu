@@ -169,6 +169,7 @@ std::string bucket_key(const Req &r) {
     put(&d.precision, sizeof(int));
     int hp = r.has_pix;
     put(&hp, sizeof(int));
+    put(&d.prf_prior_sigma, sizeof(double));  // the plan's loss
     put(r.lambdas.data(), r.lambdas.size() * sizeof(double));
     return k;
 }
@@ -583,7 +584,7 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
     if (d.n_pupil < 2 || d.n_det < 1 || d.oversample < 1 || d.n_lambda < 1 || d.n_src < 1 || d.n_exp < 1 ||
         d.n_zern < 0 || !d.lambda_m || d.precision < DLX_FP32_SIMT || d.precision > DLX_BF16X3SA)
         return fail(DLX_ERR_INVALID_ARG, "bad request shape");
-    if (d.n_src > dlx::kMaxSrc) return fail(DLX_ERR_RANGE, "at most 8 sources");
+    if (d.n_src > dlx::kMaxSrc) return fail(DLX_ERR_RANGE, "at most 32 sources");
     if (!rq->transmission || !rq->weights || !rq->flux || !rq->pos || !rq->flat || !rq->data ||
         (d.n_zern > 0 && (!rq->zern_basis || !rq->zern_coeff)) || rq->n_steps < 0)
         return fail(DLX_ERR_INVALID_ARG, "missing request input");

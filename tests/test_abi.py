@@ -47,7 +47,7 @@ def test_invalid_shapes_rejected_without_a_device(native):
     h = C.c_void_p()
     bad = [
         dict(n_pupil=1), dict(n_det=0), dict(oversample=0), dict(n_src=0), dict(n_exp=0), dict(precision=9),
-        dict(diameter_m=0.0), dict(pixscale_rad=-1.0),
+        dict(diameter_m=0.0), dict(pixscale_rad=-1.0), dict(prf_prior_sigma=-0.1),
     ]
     for over in bad:
         kw = dict(n_pupil=16, diameter_m=0.1, n_det=8, pixscale_rad=1e-6, oversample=2, n_lambda=1,
@@ -58,8 +58,9 @@ def test_invalid_shapes_rejected_without_a_device(native):
         rc = lib.dlx_make_mft(C.byref(d), 0, C.byref(h))
         assert rc == -1, (over, rc)
         assert lib.dlx_last_error()
-    kw["n_src"] = 9
+    kw["n_src"] = 33
     kw["precision"] = 0
+    kw["prf_prior_sigma"] = 0.0
     kw["diameter_m"] = 0.1
     kw["pixscale_rad"] = 1e-6
     d = native.MftDesc(**kw)

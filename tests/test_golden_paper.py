@@ -33,7 +33,9 @@ def test_paper_problem_matches_listing():
     assert p.diameter == g["diameter_m"] and p.n_det == g["det_npix"]
     assert math.isclose(p.pixscale / W.ARCSEC, g["det_pixsize_arcsec"])
     assert p.noll[0] == g["noll_first"] and len(p.noll) == g["noll_count"]
-    assert p.n_src == g["n_stars"] and p.n_psf == g["n_psf"]
+    # 60 PSFs per image (stars x wavelengths), in each of the 5 images
+    assert p.n_src == g["n_stars"] and p.n_src * p.n_lambda == g["n_psf"]
+    assert p.n_exp == g["n_images"] and p.n_psf == g["n_psf"] * g["n_images"]
     assert p.n_pupil == g["wavefront_npix_text"]
 
 
@@ -54,5 +56,8 @@ def test_paper_dither_and_sampling():
     p = W.make_problem("paper")
     lam_over_d = p.lambdas[1] / p.diameter
     assert abs(g["dither_px"] * p.pixscale / lam_over_d - g["dither_lambda_over_d"]) < 0.03
+    # the dithers are whole pixels of g["dither_px"] along each axis (the first image is undithered)
+    steps = p.dither / p.pixscale
+    assert np.allclose(steps[0], 0) and np.allclose(np.abs(steps[1:]), g["dither_px"])
     nyq = lam_over_d / 2
     assert abs(nyq / p.pixscale / g["nyquist_factor"] - 1) < 0.03

@@ -183,3 +183,49 @@ def test_adam_matches_numpy():
         th = th - lr * (m / (1 - b1**t)) / (np.sqrt(v / (1 - b2**t)) + eps)
     torch.cuda.synchronize()
     assert rel_l2(T["th"].cpu().numpy(), th) < 1e-6
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "bf16x4"])
+def test_many_sources_with_prf_prior(form):
+    """12 sources (past the 8-source register path), 2 dithered exposures, and the chi^2 prior
+    on the pixel response (Sec. 4), element by element against the oracle."""
+    _, data, start = fit_problem("custom", seed=14, n_pupil=48, n_det=24, oversample=2, n_lambda=2, n_src=12,
+                                 n_exp=2, dither_px=0.5, obscuration=0.2, grating=True, n_zern_max=6)
+    start.prf_sigma = 0.1
+    start.flat = W.flat_field(start.n_det, 0.1, 15)
+    err = compare(gpu_eval(start, data, form, want_psf=False), oracle_eval(start, data), form)
+    print(form, err)
+
+
+@pytest.fixture(scope="module")
+def paper_full():
+    """The paper's example at full size (Sec. 3-4): 20 stars x 3 wavelengths x 5 dithered images,
+    512^2 pupil -> 1024^2 detector, chi^2 prior on the pixel response; data from an analytic image."""
+    p = W.perturbed_start(W.make_problem("paper"), 61)
+    data = W.synthetic_counts((p.n_exp, p.n_det, p.n_det), 1e8, p.pos / p.pixscale, 3.0, 62)
+    return p, data
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_paper_full_size_sampled(paper_full, form):
+    """300 PSFs at 512^2 -> 1024^2: sampled model pixels against direct sums, and the Euler
+    identities of the flux and flat-field gradients (the prior's own part taken out)."""
+    p, data = paper_full
+    out = gpu_eval(p, data, form, want_psf=False)
+    m = out["model"]
+    rng = np.random.default_rng(1)
+    e_idx = list(rng.integers(0, p.n_exp, 12))
+    q_idx = list(rng.integers(0, p.n_det**2, 12))
+    e0, q0 = np.unravel_index(np.argmax(m.reshape(p.n_exp, -1)), (p.n_exp, p.n_det**2))
+    e_idx.append(int(e0))
+    q_idx.append(int(q0))
+    ref = oracle.model_at(p, e_idx, q_idx)
+    got = m.reshape(p.n_exp, -1)[e_idx, q_idx]
+    print(form, "paper sampled model error / peak", float(np.max(np.abs(got - ref)) / ref[-1]))
+    assert np.max(np.abs(got - ref)) <= TOL[form]["psf"] * ref[-1]
+    g = out["grads"]
+    s_m = float(np.sum(m - data))
+    prior_part = (p.flat - 1.0) / p.prf_sigma**2
+    assert np.dot(p.flux, g["d_flux"]) == pytest.approx(s_m, rel=1e-4)
+    assert np.sum(p.flat * (g["d_flat"] - prior_part)) == pytest.approx(s_m, rel=1e-4)
+    assert out["diag"]["device_error"] == 0

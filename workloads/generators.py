@@ -294,10 +294,12 @@ def make_problem(name: str, seed: Optional[int] = None, **over) -> Problem:
                    grating=False, n_src=1, flux_total=1e9, sep_arcsec=0.0, ratio=1.0, n_exp=8,
                    dither_px=0.5, flat_sd=0.02, dead_frac=0.01, opd_pix_rms=5e-9)
     elif name == "paper":
+        # Sec. 3's example: 20 stars x 3 wavelengths, 512^2 wavefront -> 1024^2 detector, the
+        # undithered image and four integer-pixel dithers of +-20 pixels (5 images)
         cfg = dict(n_pupil=512, diameter=0.5, n_det=1024, pix_arcsec=0.012, oversample=1, n_lambda=3,
                    lam_single=None, noll=list(range(4, 11)), zern_rms=20e-9, obscuration=0.2,
-                   grating=True, n_src=20, flux_total=1e8, sep_arcsec=None, ratio=1.0, n_exp=1,
-                   dither_px=0.0, flat_sd=0.1, dead_frac=0.0, opd_pix_rms=None)
+                   grating=True, n_src=20, flux_total=1e8, sep_arcsec=None, ratio=1.0, n_exp=5,
+                   dither_px=20.0, flat_sd=0.1, dead_frac=0.0, opd_pix_rms=None)
     elif name == "custom":
         cfg = dict(n_pupil=64, diameter=0.125, n_det=64, pix_arcsec=0.375, oversample=4, n_lambda=1,
                    lam_single=595e-9, noll=list(range(4, 12)), zern_rms=20e-9, obscuration=0.0,
@@ -346,7 +348,11 @@ def make_problem(name: str, seed: Optional[int] = None, **over) -> Problem:
         flux = np.full(ns, cfg["flux_total"] / ns)
     ne = cfg["n_exp"]
     flux = flux / ne  # total flux spread evenly over the exposures (Sec. 3)
-    if ne > 1 and cfg["dither_px"]:
+    if name == "paper":
+        # (0, 0) and the four (+-20, +-20) pixel offsets, cut to n_exp
+        steps = np.array([[0, 0], [1, 1], [1, -1], [-1, 1], [-1, -1]], np.float64)
+        dither = cfg["dither_px"] * pix * steps[:ne] if ne <= 5 else np.zeros((ne, 2))
+    elif ne > 1 and cfg["dither_px"]:
         dither = rng.uniform(-cfg["dither_px"], cfg["dither_px"], size=(ne, 2)) * pix
     else:
         dither = np.zeros((ne, 2))
@@ -354,10 +360,12 @@ def make_problem(name: str, seed: Optional[int] = None, **over) -> Problem:
     if cfg["opd_pix_rms"] is not None:
         opd_pix = smooth_gaussian_noise(ni, cfg["opd_pix_rms"], 3.0, seed + 200)
     flat = flat_field(nd, cfg["flat_sd"], seed + 300, cfg["dead_frac"])
+    # Sec. 4 fits the paper's example with a chi^2 prior matching the pixel-response spread
+    prf_sigma = cfg["flat_sd"] if name == "paper" else 0.0
     return Problem(name=name, n_pupil=ni, diameter=D, n_det=nd, pixscale=pix, oversample=osf,
                    lambdas=lambdas, weights=weights, flux=flux, pos=pos, dither=dither, noll=noll,
                    basis=basis, coeff=coeff, transmission=trans, opd_fixed=opd_fixed, opd_pix=opd_pix,
-                   flat=flat)
+                   flat=flat, prf_sigma=prf_sigma)
 
 
 def perturbed_start(truth: Problem, seed: int) -> Problem:
