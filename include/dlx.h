@@ -147,6 +147,68 @@ int dlx_plan_get_info(const dlx_plan *plan, dlx_plan_info *out);
  * `model` is device [n_exp][Nd][Nd]. */
 int dlx_forward(dlx_plan *plan, const dlx_params *params, float *model, void *cuda_stream);
 
+/* Directional derivative of the model (forward mode), for the Laplace
+ * approximation of the parameter errors (Sec. 4): jvp = dm/dalpha at alpha = 0
+ * for the phasors of the sources whose bit is set in `src_mask` (bit s = source
+ * s, every exposure) multiplied by exp(i alpha (2 pi / lambda) t[n]), i.e. the
+ * derivative along a change of optical path t (metres, device float [Ni][Ni]).
+ * t = a Zernike basis map with every bit set gives dm/dc_j; t = the pupil x or y
+ * coordinate (n - (Ni-1)/2) Ni/D for one source gives dm/dtheta_x or theta_y of
+ * that source.  The model is a quadratic form of the phasor, so the central
+ * difference (m(P (1 + i a)) - m(P (1 - i a))) / (2 alpha), a = alpha (2 pi /
+ * lambda) t, is the derivative itself for any alpha > 0; alpha only sets the
+ * size of the two models against their rounding (alpha max |a| near 1 is a good
+ * choice).  `jvp` and `work` are device float [n_exp][Nd][Nd]; `work` is
+ * overwritten.  Asynchronous on the stream; t_map must stay valid until the
+ * work has run.  Errors: INVALID_ARG (NULL pointers, alpha not > 0), those of
+ * dlx_forward. */
+int dlx_model_jvp(dlx_plan *plan, const dlx_params *params, const float *t_map, uint32_t src_mask, double alpha,
+                  float *jvp, float *work, void *cuda_stream);
+
+/* Vector-Jacobian product (reverse mode): grads = J^T cot, the gradient of
+ * sum_p cot[p] m[p] with respect to every parameter, where `cot` is a device
+ * float [n_exp][Nd][Nd] weight on the model pixels.  With cot = 1 - d/m it is
+ * the likelihood gradient of dlx_loss_grad without the prior term.  Arrays of
+ * `grads` left NULL are not computed.  Asynchronous on the stream. */
+int dlx_model_vjp(dlx_plan *plan, const dlx_params *params, const float *cot, const dlx_grads *grads,
+                  void *cuda_stream);
+
+/* Derivative of J^T cot along the phasor tangent of dlx_model_jvp, with cot
+ * held fixed: grads[i] = sum_p cot[p] d^2 m[p] / (d theta_i d alpha).  This is
+ * the term of the likelihood Hessian that the Fisher matrix J^T diag(d/m^2) J
+ * leaves out (Laplace approximation, Sec. 4): with cot = 1 - d/m it gives, for a
+ * tangent t = dOPD/dtheta_j, column j of sum_p (1 - d_p/m_p) d^2 m_p.  J^T cot
+ * is a quadratic form of the phasor, so the central difference over 2 alpha is
+ * exact, as in dlx_model_jvp.  `work` needs every array that `grads` has (same
+ * sizes; overwritten).  Errors: INVALID_ARG, those of dlx_model_vjp. */
+int dlx_model_vjp_jvp(dlx_plan *plan, const dlx_params *params, const float *cot, const float *t_map,
+                      uint32_t src_mask, double alpha, const dlx_grads *grads, const dlx_grads *work,
+                      void *cuda_stream);
+
+/* The weights dL/dm of the Poisson negative log-likelihood sum (m - d ln m)
+ * (Sec. 4): cot[i] = 1 - data[i] / max(model[i], 1e-30), all device arrays of
+ * n elements (model float, data int32, cot float).  The cotangent that turns
+ * dlx_model_vjp into the likelihood gradient and dlx_model_vjp_jvp into the
+ * second-order part of its Hessian.  Asynchronous on the stream. */
+int dlx_nll_cotangent(const float *model, const int32_t *data, size_t n, float *cot, void *cuda_stream);
+
+/* Weighted Gram matrix of Jacobian rows, the information matrix of the Poisson
+ * likelihood (Laplace approximation, Sec. 4):
+ *   F[i][j] = sum_p J[i][p] J[j][p] w_p,
+ *   w_p = 1 / max(m_p, 1e-30)               (data == NULL: expected Fisher information)
+ *   w_p = d_p / max(m_p, 1e-30)^2           (observed Gauss-Newton term of the Hessian).
+ * J: device float [n_par][n_pix] row-major; model: device float [n_pix];
+ * data: device int32 [n_pix] or NULL; F: device double [n_par][n_par] (both
+ * triangles written); work: device double scratch of at least
+ * DLX_GRAM_BLOCKS * n_par (n_par + 1) / 2 elements.  Products are summed in
+ * FP32 over 32-pixel chunks and in FP64 beyond; the result is the same on every
+ * run.  Errors: INVALID_ARG (NULL, n_pix = 0), RANGE (n_par outside
+ * 1..DLX_GRAM_MAX_PAR). */
+#define DLX_GRAM_MAX_PAR 128
+#define DLX_GRAM_BLOCKS 256
+int dlx_fisher_gram(const float *J, int n_par, size_t n_pix, const float *model, const int32_t *data, double *F,
+                    double *work, void *cuda_stream);
+
 /* The paper has no counterpart of this entry point; it exists for callers that
  * cannot allocate device memory -- host applications that reserve all of the
  * GPU's memory through their own allocator at start-up and forbid further

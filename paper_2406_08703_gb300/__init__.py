@@ -172,6 +172,27 @@ def dlx_forward(plan: Plan, params: dict, model=None, stream=None):
     return model
 
 
+def dlx_model_jvp(plan: Plan, params: dict, t_map, src_mask: int, alpha: float, jvp=None, work=None,
+                  stream=None):
+    """dm/dalpha of the model along the optical-path change t_map (metres,
+    [Ni][Ni] float32 device tensor) of the sources in src_mask (bit s = source s)."""
+    torch = _torch()
+    i = plan.info
+    shp = (i.n_exp, i.n_det, i.n_det)
+    dev = f"cuda:{plan.device}"
+    if jvp is None:
+        jvp = torch.empty(shp, dtype=torch.float32, device=dev)
+    if work is None:
+        work = torch.empty(shp, dtype=torch.float32, device=dev)
+    _check_tensor("t_map", t_map, (i.n_pupil, i.n_pupil), torch.float32, plan.device)
+    _check_tensor("jvp", jvp, shp, torch.float32, plan.device)
+    _check_tensor("work", work, shp, torch.float32, plan.device)
+    prm = _params_c(plan, params)
+    N.check(load().dlx_model_jvp(plan.handle, C.byref(prm), _ptr(t_map), C.c_uint32(src_mask & 0xffffffff),
+                                 float(alpha), _ptr(jvp), _ptr(work), _stream(plan, stream)), "dlx_model_jvp")
+    return jvp
+
+
 def dlx_forward_noalloc(desc: MftDesc, params: dict, model, device: int = 0, stream=None):
     """dlx_forward in the FP32 form without a plan and without any device
     allocation (working memory from the library's fixed 16 MiB device array);
@@ -237,6 +258,100 @@ def dlx_loss_grad(plan: Plan, params: dict, data, loss=None, grads: Optional[dic
     N.check(load().dlx_loss_grad(plan.handle, C.byref(prm), _ptr(data), _ptr(loss), C.byref(g), _ptr(model),
                                  _stream(plan, stream)), "dlx_loss_grad")
     return loss, grads, model
+
+
+def _grads_c(plan: Plan, grads: dict):
+    torch = _torch()
+    i = plan.info
+    gshapes = dict(d_zern=(i.n_zern,), d_opd_pix=(i.n_pupil, i.n_pupil), d_flat=(i.n_det, i.n_det),
+                   d_flux=(i.n_src,), d_pos=(i.n_src, 2))
+    for k in GRAD_KEYS:
+        _check_tensor(k, grads.get(k), gshapes[k], torch.float32, plan.device)
+    return N.Grads(*[_ptr(grads.get(k)) for k in GRAD_KEYS])
+
+
+def dlx_model_vjp(plan: Plan, params: dict, cot, grads: Optional[dict] = None, stream=None) -> dict:
+    """grads = J^T cot: the gradient of sum_p cot[p] m[p] (cot float32 [n_exp][Nd][Nd])."""
+    torch = _torch()
+    i = plan.info
+    _check_tensor("cot", cot, (i.n_exp, i.n_det, i.n_det), torch.float32, plan.device)
+    if grads is None:
+        grads = empty_grads(plan)
+    g = _grads_c(plan, grads)
+    prm = _params_c(plan, params)
+    N.check(load().dlx_model_vjp(plan.handle, C.byref(prm), _ptr(cot), C.byref(g), _stream(plan, stream)),
+            "dlx_model_vjp")
+    return grads
+
+
+def dlx_model_vjp_jvp(plan: Plan, params: dict, cot, t_map, src_mask: int, alpha: float,
+                      grads: Optional[dict] = None, work: Optional[dict] = None, stream=None) -> dict:
+    """d/dalpha of J^T cot along the phasor tangent t_map of the sources in src_mask, cot fixed."""
+    torch = _torch()
+    i = plan.info
+    _check_tensor("cot", cot, (i.n_exp, i.n_det, i.n_det), torch.float32, plan.device)
+    _check_tensor("t_map", t_map, (i.n_pupil, i.n_pupil), torch.float32, plan.device)
+    if grads is None:
+        grads = empty_grads(plan)
+    if work is None:
+        work = empty_grads(plan, [k for k in GRAD_KEYS if grads.get(k) is not None])
+    g, w = _grads_c(plan, grads), _grads_c(plan, work)
+    prm = _params_c(plan, params)
+    N.check(load().dlx_model_vjp_jvp(plan.handle, C.byref(prm), _ptr(cot), _ptr(t_map),
+                                     C.c_uint32(src_mask & 0xffffffff), float(alpha), C.byref(g), C.byref(w),
+                                     _stream(plan, stream)), "dlx_model_vjp_jvp")
+    return grads
+
+
+def dlx_nll_cotangent(model, data, cot=None, stream=None):
+    """cot = 1 - d / max(m, 1e-30): the Poisson NLL's dL/dm (model float32, data int32, same size)."""
+    torch = _torch()
+    if model.numel() != data.numel():
+        raise ValueError("model and data differ in size")
+    dev = model.device.index
+    _check_tensor("model", model, tuple(model.shape), torch.float32, dev)
+    _check_tensor("data", data, tuple(model.shape), torch.int32, dev)
+    if cot is None:
+        cot = torch.empty_like(model)
+    _check_tensor("cot", cot, tuple(model.shape), torch.float32, dev)
+    st = torch.cuda.current_stream(dev) if stream is None else stream
+    N.check(load().dlx_nll_cotangent(_ptr(model), _ptr(data), int(model.numel()), _ptr(cot),
+                                     C.c_void_p(st.cuda_stream if hasattr(st, "cuda_stream") else int(st))),
+            "dlx_nll_cotangent")
+    return cot
+
+
+GRAM_MAX_PAR = 128
+GRAM_BLOCKS = 256
+
+
+def dlx_fisher_gram(J, model, data=None, F=None, work=None, stream=None):
+    """F = J diag(w) J^T with w = 1/m (data None) or d/m^2; J float32 [n_par][n_pix] on the device,
+    model float32 and data int32 of n_pix elements.  Returns F (float64 [n_par][n_par])."""
+    torch = _torch()
+    if J.dim() != 2 or not J.is_cuda or J.dtype != torch.float32 or not J.is_contiguous():
+        raise TypeError("J: expected a contiguous 2-D float32 CUDA tensor")
+    n, npix = J.shape
+    dev = J.device.index
+    if model.numel() != npix:
+        raise ValueError(f"model has {model.numel()} elements, J rows have {npix}")
+    _check_tensor("model", model, tuple(model.shape), torch.float32, dev)
+    if data is not None:
+        if data.numel() != npix:
+            raise ValueError(f"data has {data.numel()} elements, J rows have {npix}")
+        _check_tensor("data", data, tuple(data.shape), torch.int32, dev)
+    if F is None:
+        F = torch.empty((n, n), dtype=torch.float64, device=J.device)
+    if work is None:
+        work = torch.empty(GRAM_BLOCKS * n * (n + 1) // 2, dtype=torch.float64, device=J.device)
+    _check_tensor("F", F, (n, n), torch.float64, dev)
+    if work.dtype != torch.float64 or work.numel() < GRAM_BLOCKS * n * (n + 1) // 2:
+        raise ValueError("work: float64 tensor of at least GRAM_BLOCKS * n (n + 1) / 2 elements")
+    st = torch.cuda.current_stream(dev) if stream is None else stream
+    N.check(load().dlx_fisher_gram(_ptr(J), int(n), int(npix), _ptr(model), _ptr(data), _ptr(F), _ptr(work),
+                                   C.c_void_p(st.cuda_stream if hasattr(st, "cuda_stream") else int(st))),
+            "dlx_fisher_gram")
+    return F
 
 
 def dlx_plan_diagnostics(plan: Plan):

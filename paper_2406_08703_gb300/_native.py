@@ -76,6 +76,14 @@ SIGNATURES = {
     "dlx_destroy_plan": (C.c_int, [C.c_void_p]),
     "dlx_plan_get_info": (C.c_int, [C.c_void_p, C.POINTER(PlanInfo)]),
     "dlx_forward": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p]),
+    "dlx_model_jvp": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_uint32, C.c_double, C.c_void_p,
+                                C.c_void_p, C.c_void_p]),
+    "dlx_model_vjp": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.POINTER(Grads), C.c_void_p]),
+    "dlx_model_vjp_jvp": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p, C.c_uint32, C.c_double,
+                                    C.POINTER(Grads), C.POINTER(Grads), C.c_void_p]),
+    "dlx_nll_cotangent": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]),
+    "dlx_fisher_gram": (C.c_int, [C.c_void_p, C.c_int, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p]),
     "dlx_psf": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p]),
     "dlx_forward_noalloc": (C.c_int, [C.POINTER(MftDesc), C.POINTER(Params), C.c_void_p, C.c_void_p]),
     "dlx_loss_grad": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p, C.POINTER(Grads),

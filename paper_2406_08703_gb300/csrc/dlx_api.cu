@@ -443,6 +443,105 @@ int dlx_forward(dlx_plan *p, const dlx_params *prm, float *model, void *stream) 
     return DLX_OK;
 }
 
+int dlx_model_jvp(dlx_plan *p, const dlx_params *prm, const float *t_map, uint32_t src_mask, double alpha, float *jvp,
+                  float *work, void *stream) {
+    if (!p || !t_map || !jvp || !work) return fail(DLX_ERR_INVALID_ARG, "plan/t_map/jvp/work is NULL");
+    if (!(alpha > 0) || !std::isfinite(alpha)) return fail(DLX_ERR_INVALID_ARG, "alpha must be finite and > 0");
+    int rc = validate_params(p, prm);
+    if (rc) return rc;
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const dlx::DevParams d = dev_params(prm);
+    // m(+alpha) into jvp, m(-alpha) into work; the model is quadratic in the phasor, so the
+    // central difference over 2 alpha is the derivative itself
+    p->tan_map = t_map;
+    p->tan_mask = src_mask;
+    for (int k = 0; k < 2 && rc == 0; ++k) {
+        p->tan_coef = (float)(k == 0 ? alpha : -alpha);
+        rc = dlx::eval_forward(p, d, 1, st);
+        if (rc == 0) {
+            cudaError_t e = dlx::launch_bin_nll(p, d, 1, nullptr, 0, k == 0 ? jvp : work, 0, nullptr, nullptr, st);
+            if (e != cudaSuccess) rc = cuda_fail(e, "bin");
+        }
+    }
+    p->tan_map = nullptr;
+    p->tan_coef = 0.f;
+    p->tan_mask = 0;
+    if (rc) return rc;
+    DLX_CU(dlx::launch_scaled_diff(jvp, work, (size_t)p->ne * p->nd * p->nd, (float)(0.5 / alpha), st), "jvp");
+    return DLX_OK;
+}
+
+int dlx_model_vjp(dlx_plan *p, const dlx_params *prm, const float *cot, const dlx_grads *g, void *stream) {
+    if (!p || !cot || !g) return fail(DLX_ERR_INVALID_ARG, "plan/cot/grads is NULL");
+    int rc = validate_params(p, prm);
+    if (rc) return rc;
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevGrads dg = dev_grads(g);
+    p->cot = cot;
+    rc = dlx::eval_loss_grad(p, d, 1, nullptr, 0, nullptr, &dg, nullptr, 0, st);
+    p->cot = nullptr;
+    return rc;
+}
+
+int dlx_model_vjp_jvp(dlx_plan *p, const dlx_params *prm, const float *cot, const float *t_map, uint32_t src_mask,
+                      double alpha, const dlx_grads *g, const dlx_grads *work, void *stream) {
+    if (!p || !cot || !t_map || !g || !work) return fail(DLX_ERR_INVALID_ARG, "plan/cot/t_map/grads/work is NULL");
+    if (!(alpha > 0) || !std::isfinite(alpha)) return fail(DLX_ERR_INVALID_ARG, "alpha must be finite and > 0");
+    const float *gp[5] = {g->d_zern, g->d_opd_pix, g->d_flat, g->d_flux, g->d_pos};
+    const float *wp[5] = {work->d_zern, work->d_opd_pix, work->d_flat, work->d_flux, work->d_pos};
+    for (int k = 0; k < 5; ++k)
+        if (gp[k] && !wp[k]) return fail(DLX_ERR_INVALID_ARG, "work lacks an array that grads has");
+    int rc = validate_params(p, prm);
+    if (rc) return rc;
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const dlx::DevParams d = dev_params(prm);
+    // J^T cot at the phasors P (1 + i a) into g and P (1 - i a) into work; it is a quadratic
+    // form of the phasor, so the central difference over 2 alpha is its derivative
+    dlx_grads wk = *g;
+    wk.d_zern = g->d_zern ? work->d_zern : nullptr;
+    wk.d_opd_pix = g->d_opd_pix ? work->d_opd_pix : nullptr;
+    wk.d_flat = g->d_flat ? work->d_flat : nullptr;
+    wk.d_flux = g->d_flux ? work->d_flux : nullptr;
+    wk.d_pos = g->d_pos ? work->d_pos : nullptr;
+    p->cot = cot;
+    p->tan_map = t_map;
+    p->tan_mask = src_mask;
+    for (int k = 0; k < 2 && rc == 0; ++k) {
+        p->tan_coef = (float)(k == 0 ? alpha : -alpha);
+        const dlx::DevGrads dg = dev_grads(k == 0 ? g : &wk);
+        rc = dlx::eval_loss_grad(p, d, 1, nullptr, 0, nullptr, &dg, nullptr, 0, st);
+    }
+    p->cot = nullptr;
+    p->tan_map = nullptr;
+    p->tan_coef = 0.f;
+    p->tan_mask = 0;
+    if (rc) return rc;
+    const size_t n[5] = {(size_t)p->nz, (size_t)p->ni * p->ni, (size_t)p->nd * p->nd, (size_t)p->ns,
+                         (size_t)2 * p->ns};
+    for (int k = 0; k < 5; ++k)
+        if (gp[k]) DLX_CU(dlx::launch_scaled_diff((float *)gp[k], wp[k], n[k], (float)(0.5 / alpha), st), "vjp_jvp");
+    return DLX_OK;
+}
+
+int dlx_nll_cotangent(const float *model, const int32_t *data, size_t n, float *cot, void *stream) {
+    if (!model || !data || !cot) return fail(DLX_ERR_INVALID_ARG, "model/data/cot is NULL");
+    DLX_CU(dlx::launch_nll_cotangent(model, data, n, cot, (cudaStream_t)stream), "nll_cotangent");
+    return DLX_OK;
+}
+
+int dlx_fisher_gram(const float *J, int n_par, size_t n_pix, const float *model, const int32_t *data, double *F,
+                    double *work, void *stream) {
+    if (!J || !model || !F || !work) return fail(DLX_ERR_INVALID_ARG, "J/model/F/work is NULL");
+    if (n_par < 1 || n_par > DLX_GRAM_MAX_PAR) return fail(DLX_ERR_RANGE, "n_par must be 1..DLX_GRAM_MAX_PAR");
+    if (n_pix == 0) return fail(DLX_ERR_INVALID_ARG, "n_pix is 0");
+    DLX_CU(dlx::launch_fisher_gram(J, n_par, n_pix, model, data, F, work, (cudaStream_t)stream), "fisher_gram");
+    return DLX_OK;
+}
+
 int dlx_psf(dlx_plan *p, const dlx_params *prm, float *psf_os, void *stream) {
     if (!p || !psf_os) return fail(DLX_ERR_INVALID_ARG, "plan/psf is NULL");
     int rc = validate_params(p, prm);

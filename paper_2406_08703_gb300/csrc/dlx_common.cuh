@@ -355,6 +355,14 @@ struct dlx_plan {
     uint32_t sr = 0;           // BF16x3 forms: stochastic splitting of the forward operands (seed base), else 0
     bool adj1 = false;         // BF16x3sa: the adjoint contracts the stochastic hi parts only (2-plane bf16)
     float prf_inv = 0.f;       // 1 / sigma^2 of the chi^2 prior on the flat field, 0 = none
+    // forward-mode derivative (dlx_model_jvp): while tan_map is set, the phasors of the sources
+    // in tan_mask are multiplied by (1 + i tan_coef (2 pi / lambda) tan_map[n])
+    const float *tan_map = nullptr;
+    float tan_coef = 0.f;
+    uint32_t tan_mask = 0;
+    // vector-Jacobian product (dlx_model_vjp): while set, the adjoint weights dL/dm are this
+    // cotangent [n_exp][Nd][Nd] instead of 1 - d/m
+    const float *cot = nullptr;
     float2 *npart = nullptr;   // [R][kNormParts] block partials of sum T^2 (compensated pairs)
     unsigned int *ncount = nullptr;  // [R] blocks of the prologue pass done (reset by the last one)
     int32_t *err = nullptr;    // device error flag
@@ -408,6 +416,13 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
 cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st);
 cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, size_t n, float lr, float b1, float b2,
                         float eps, int t, cudaStream_t st);
+// F = J diag(w) J^T (dlx_fisher_gram); work holds DLX_GRAM_BLOCKS x n(n+1)/2 doubles
+cudaError_t launch_fisher_gram(const float *J, int n, size_t npix, const float *model, const int32_t *data, double *F,
+                               double *work, cudaStream_t st);
+// cot = 1 - d / max(m, 1e-30) elementwise (dlx_nll_cotangent)
+cudaError_t launch_nll_cotangent(const float *m, const int32_t *d, size_t n, float *cot, cudaStream_t st);
+// a = (a - b) * c elementwise (the central difference of dlx_model_jvp)
+cudaError_t launch_scaled_diff(float *a, const float *b, size_t n, float c, cudaStream_t st);
 // Adam over R packed slots of n parameters each; group k of a slot is
 // [off[k], off[k+1]) with learning rate lr[r][k]; step[r] is 1-based.
 cudaError_t launch_adam_slots(float *theta, const float *grad, float *m, float *v, size_t n, int R, const int *off,

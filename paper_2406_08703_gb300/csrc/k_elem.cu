@@ -255,7 +255,8 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
 template <int F>
 __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
                          const float *__restrict__ invlam, const float *__restrict__ pscale, int B, int nl, int nse,
-                         int ni, int ldi, void *P, uint32_t sr) {
+                         int ne, int ni, int ldi, void *P, uint32_t sr, const float *__restrict__ tmap, float tcoef,
+                         uint32_t tmask) {
     pdl_trigger();
     pdl_wait();
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F), gpr = ldi >> 3;
@@ -282,6 +283,11 @@ __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const flo
                 o[q] = in ? __ldg(op + (size_t)ny * ni + nx0 + q) : 0.f;
             }
         }
+        // tangent direction of dlx_model_jvp: a = tcoef (2 pi / lambda) t[n] for the masked sources
+        float ta[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            ta[q] = (tmap && nx0 + q < ni) ? tcoef * 6.283185307f * il * __ldg(tmap + (size_t)ny * ni + nx0 + q) : 0.f;
         // T_hat exp(i 2 pi OPD / lambda), common to every source and exposure
         float br[8], bi[8];
 #pragma unroll
@@ -315,12 +321,19 @@ __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const flo
                 for (int q = 0; q < 8; ++q) ex[q] = nx0 + q < ni ? __ldg(tx + nx0 + q) : make_float2(0.f, 0.f);
             }
             const float2 ey = __ldg(ty + ny);
+            const bool tan = tmap && ((tmask >> (se / ne)) & 1u);
             float re[8], im[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
+                float cr = br[q], ci = bi[q];
+                if (tan) {  // times (1 + i a)
+                    const float a = ta[q], nr = cr - a * ci;
+                    ci = ci + a * cr;
+                    cr = nr;
+                }
                 const float xr = ex[q].x * ey.x - ex[q].y * ey.y, xi = ex[q].x * ey.y + ex[q].y * ey.x;
-                re[q] = br[q] * xr - bi[q] * xi;
-                im[q] = br[q] * xi + bi[q] * xr;
+                re[q] = cr * xr - ci * xi;
+                im[q] = cr * xi + ci * xr;
             }
             char *pb = (char *)P + (size_t)bg * Pl * ps * es;
             if constexpr (F == FMT_BF16X4) {
@@ -348,7 +361,8 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nyl - 1) / nyl));
     DLX_FMT_DISPATCH(p->fmt, F,
                      e = launch_pdl(k_phasor<F>, dim3(px, nyl), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam,
-                                    p->pscale, p->B, p->nl, p->nse, p->ni, p->ldi, p->P.ptr, p->sr));
+                                    p->pscale, p->B, p->nl, p->nse, p->ne, p->ni, p->ldi, p->P.ptr, p->sr,
+                                    p->tan_map, p->tan_coef, p->tan_mask));
     return e;
 }
 
@@ -376,7 +390,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                           int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount,
-                          float prf_inv) {
+                          float prf_inv, const float *__restrict__ cot) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[32 * (1 + MAXS)];
@@ -387,7 +401,10 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
     const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
     float *mod = model + (size_t)r * mstride;
     float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
-    const bool wantq = qmax && dat;
+    // with a cotangent the weights dL/dm are cot itself (vector-Jacobian product, no loss)
+    const float *ct = cot ? cot + (size_t)r * ne * np : nullptr;
+    const bool grad = dat || ct;
+    const bool wantq = qmax && grad;
     if (wantq)
         for (int i = threadIdx.x; i < kQShared; i += blockDim.x) s_q[i] = 0u;
     __syncthreads();
@@ -471,16 +488,21 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
             float gi = 0.f;
             if (valid) {
                 mod[(size_t)e * np + p] = m;
-                if (dat) {
-                    const float d = (float)dat[(size_t)e * np + p];
-                    float mc = m;
-                    if (!(mc >= 1e-30f)) {
-                        mc = 1e-30f;
-                        ++nclamp;
+                if (grad) {
+                    float gm;
+                    if (ct) {
+                        gm = __ldg(ct + (size_t)e * np + p);
+                    } else {
+                        const float d = (float)dat[(size_t)e * np + p];
+                        float mc = m;
+                        if (!(mc >= 1e-30f)) {
+                            mc = 1e-30f;
+                            ++nclamp;
+                        }
+                        acc[0] = df_add(acc[0], m);
+                        acc[0] = df_add(acc[0], -d * logf(mc));
+                        gm = 1.f - d / mc;
                     }
-                    acc[0] = df_add(acc[0], m);
-                    acc[0] = df_add(acc[0], -d * logf(mc));
-                    const float gm = 1.f - d / mc;
                     gi = ff * gm;
                     GI[((size_t)r * ne + e) * np + p] = gi;
                     dff = fmaf(gm, btot, dff);
@@ -506,13 +528,13 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                 }
             }
         }
-        if (valid && dat && prf_inv > 0.f) {
+        if (valid && dat && !ct && prf_inv > 0.f) {
             // chi^2 log prior on the pixel response (Sec. 4): (FF - 1)^2 / (2 sigma^2)
             const float dev = ff - 1.f;
             acc[0] = df_add(acc[0], 0.5f * prf_inv * dev * dev);
             dff = fmaf(prf_inv, dev, dff);
         }
-        if (valid && dat && dflat) dflat[p] = dff;
+        if (valid && grad && dflat) dflat[p] = dff;
     }
     block_sum<1 + MAXS>(acc, sh);
     if (wantq)
@@ -523,7 +545,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
         for (int i = 0; i < 1 + MAXS; ++i)
             red[((size_t)r * gridDim.x + blockIdx.x) * (1 + kMaxSrc) + i] = df_to_double(acc[i]);
         s_last = false;
-        if (dat && bcount) {
+        if (grad && bcount) {
             __threadfence();
             s_last = atomicAdd(bcount + r, 1u) == gridDim.x - 1;
         }
@@ -567,7 +589,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     auto go = [&](auto kern) {
         return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse, p->ns,
                           p->ne, p->nd, p->os, p->no, prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
-                          p->clamped, p->qmax, loss, p->bcount, p->prf_inv);
+                          p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot);
     };
     // per-source registers for up to 8 sources, or up to kMaxSrc
     if (p->ns <= 8) {
@@ -822,6 +844,133 @@ cudaError_t launch_adam(float *theta, const float *grad, float *m, float *v, siz
     float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
     int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
     k_adam<<<blocks, 256, 0, st>>>(theta, grad, m, v, n, lr, b1, b2, eps, c1, c2);
+    return cudaGetLastError();
+}
+
+// cot = dL/dm of the Poisson NLL sum (m - d ln m): 1 - d / max(m, 1e-30)
+__global__ void k_nll_cotangent(const float *__restrict__ m, const int32_t *__restrict__ d, size_t n,
+                                float *__restrict__ cot) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        cot[i] = 1.f - (float)d[i] / fmaxf(m[i], 1e-30f);
+}
+
+cudaError_t launch_nll_cotangent(const float *m, const int32_t *d, size_t n, float *cot, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_nll_cotangent<<<blocks, 256, 0, st>>>(m, d, n, cot);
+    return cudaGetLastError();
+}
+
+// jvp = (m(+alpha) - m(-alpha)) * c, in place over the first operand
+__global__ void k_scaled_diff(float *__restrict__ a, const float *__restrict__ b, size_t n, float c) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a[i] = (a[i] - b[i]) * c;
+}
+
+cudaError_t launch_scaled_diff(float *a, const float *b, size_t n, float c, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    int blocks = (int)std::min<size_t>((n + 255) / 256, 4096);
+    k_scaled_diff<<<blocks, 256, 0, st>>>(a, b, n, c);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Weighted Gram matrix of the Jacobian rows (Fisher information of the Poisson
+// likelihood, Sec. 4): F[i][j] = sum_p J[i][p] J[j][p] w_p over the upper
+// triangle.  Each block takes 32-pixel chunks (rows padded to 33 floats so the
+// threads of a warp, which share i and run over consecutive j, hit distinct
+// banks), sums a chunk in FP32 and adds it to its FP64 partials; a second kernel
+// adds the block partials in block order, so the result does not depend on timing.
+constexpr int kGramChunk = 32, kGramPad = 33, kGramPairsPerThread = (DLX_GRAM_MAX_PAR * (DLX_GRAM_MAX_PAR + 1) / 2 + 255) / 256;
+
+__global__ void __launch_bounds__(256) k_fisher_gram(const float *__restrict__ J, int n, size_t npix,
+                                                     const float *__restrict__ model,
+                                                     const int32_t *__restrict__ data, double *__restrict__ part) {
+    extern __shared__ float sm[];
+    float *Js = sm, *Jw = sm + (size_t)n * kGramPad, *w = Jw + (size_t)n * kGramPad;
+    const int npair = n * (n + 1) / 2;
+    // this thread's pairs k = tid + 256 m, row-major over the upper triangle
+    int pij[kGramPairsPerThread];  // i << 8 | j
+    double acc[kGramPairsPerThread];
+#pragma unroll
+    for (int m = 0; m < kGramPairsPerThread; ++m) {
+        int k = threadIdx.x + 256 * m, i = 0;
+        acc[m] = 0.0;
+        if (k < npair) {
+            while (k >= n - i) {
+                k -= n - i;
+                ++i;
+            }
+        } else {
+            k = 0;
+        }
+        pij[m] = i << 8 | (i + k);
+    }
+    const size_t nchunk = (npix + kGramChunk - 1) / kGramChunk;
+    for (size_t c = blockIdx.x; c < nchunk; c += gridDim.x) {
+        const size_t p0 = c * kGramChunk;
+        __syncthreads();
+        if (threadIdx.x < kGramChunk) {
+            const size_t q = p0 + threadIdx.x;
+            float wq = 0.f;
+            if (q < npix) {
+                const float m = fmaxf(model[q], 1e-30f);
+                wq = data ? (float)data[q] / (m * m) : 1.f / m;
+            }
+            w[threadIdx.x] = wq;
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < n * kGramChunk; idx += blockDim.x) {
+            const int i = idx / kGramChunk, q = idx % kGramChunk;
+            const float v = p0 + q < npix ? __ldg(J + (size_t)i * npix + p0 + q) : 0.f;
+            Js[i * kGramPad + q] = v;
+            Jw[i * kGramPad + q] = v * w[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < kGramPairsPerThread; ++m) {
+            if (threadIdx.x + 256 * m >= npair) break;
+            const float *a = Jw + (pij[m] >> 8) * kGramPad, *b = Js + (pij[m] & 255) * kGramPad;
+            float s = 0.f;
+#pragma unroll 8
+            for (int q = 0; q < kGramChunk; ++q) s = fmaf(a[q], b[q], s);
+            acc[m] += (double)s;
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < kGramPairsPerThread; ++m) {
+        const int k = threadIdx.x + 256 * m;
+        if (k < npair) part[(size_t)blockIdx.x * npair + k] = acc[m];
+    }
+}
+
+__global__ void k_fisher_final(const double *__restrict__ part, int nb, int n, double *__restrict__ F) {
+    const int npair = n * (n + 1) / 2;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < npair; k += gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int b = 0; b < nb; ++b) v += part[(size_t)b * npair + k];
+        int i = 0, kk = k;
+        while (kk >= n - i) {
+            kk -= n - i;
+            ++i;
+        }
+        const int j = i + kk;
+        F[(size_t)i * n + j] = v;
+        F[(size_t)j * n + i] = v;
+    }
+}
+
+cudaError_t launch_fisher_gram(const float *J, int n, size_t npix, const float *model, const int32_t *data, double *F,
+                               double *work, cudaStream_t st) {
+    const size_t nchunk = (npix + kGramChunk - 1) / kGramChunk;
+    const int nb = (int)std::min<size_t>(nchunk, DLX_GRAM_BLOCKS);
+    const size_t smem = ((size_t)2 * n * kGramPad + kGramChunk) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(k_fisher_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fisher_gram<<<nb, 256, smem, st>>>(J, n, npix, model, data, work);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int npair = n * (n + 1) / 2;
+    k_fisher_final<<<(npair + 255) / 256, 256, 0, st>>>(work, nb, n, F);
     return cudaGetLastError();
 }
 

@@ -69,5 +69,18 @@ def test_invalid_shapes_rejected_without_a_device(native):
     assert lib.dlx_adam(None, None, None, None, 5, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
 
 
+def test_laplace_entries_validate_without_a_device(native):
+    lib = native.load()
+    fake = C.c_void_p(16)  # never dereferenced: every call below fails its argument checks first
+    assert lib.dlx_model_jvp(None, None, fake, 1, 1.0, fake, fake, None) == -1
+    assert lib.dlx_model_vjp(None, None, fake, None, None) == -1
+    assert lib.dlx_model_vjp_jvp(None, None, fake, fake, 1, 1.0, None, None, None) == -1
+    assert lib.dlx_nll_cotangent(None, fake, 4, fake, None) == -1
+    for n_par in (0, 129):
+        assert lib.dlx_fisher_gram(fake, n_par, 10, fake, None, fake, fake, None) == -6  # RANGE
+    assert lib.dlx_fisher_gram(fake, 4, 0, fake, None, fake, fake, None) == -1
+    assert lib.dlx_fisher_gram(None, 4, 10, fake, None, fake, fake, None) == -1
+
+
 def test_version_string(native):
     assert b"sm_103a" in native.load().dlx_version()
