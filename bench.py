@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--fit", action="store_true",
                     help="time the paper's staged fit instead (Sec. 4: 100 epochs with the pixel response frozen, "
                          "then 50 of the pixel response alone) on --workload (default paper)")
+    ap.add_argument("--laplace", action="store_true",
+                    help="time the Laplace-approximation errors instead (Sec. 4: the likelihood Hessian over "
+                         "positions, fluxes and Zernikes, inverted) on --workload (default paper)")
     ap.add_argument("--serving-requests", type=int, default=36)
     ap.add_argument("--serving-shapes", type=int, default=6)
     return ap.parse_args()
@@ -459,6 +462,87 @@ def fit_bench(args):
     print(json.dumps(line), flush=True)
 
 
+LAPLACE_METRIC = ("Laplace errors (Sec. 4): wall-clock seconds for the likelihood Hessian over positions, fluxes "
+                  "and Zernikes and its inverse")
+
+
+def laplace_bench(args):
+    """The paper's error estimate at the paper's scale: the Hessian of the Poisson likelihood over
+    the 20 stars' positions and fluxes and the Zernike coefficients (pixel response fixed), and
+    the marginal errors from its inverse; also the Fisher and Gauss-Newton matrices.  Each timed
+    step is one full Laplace.errors() call, host inversion included.  Data: Poisson counts of the
+    model at the truth (made on the device by the forward model, then drawn on the host), so the
+    fit point is the truth."""
+    import torch
+
+    import paper_2406_08703_gb300 as P
+    from paper_2406_08703_gb300.laplace import Laplace
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    P.load()
+    import workloads as W
+
+    wl = args.workload if args.workload != "binary" else "paper"
+    truth = W.make_problem(wl)
+    plan = P.dlx_make_mft(P.desc_from_problem(truth, P.PRECISIONS[args.form]))
+    prm = P.params_from_problem(truth)
+    m = P.dlx_forward(plan, prm).cpu().numpy()
+    data = W.poisson_counts(m, 91)
+    dt = torch.as_tensor(data, device="cuda")
+    lp = Laplace(plan)
+    out = {}
+    for kind in ("fisher", "gauss_newton", "hessian"):
+        for _ in range(max(args.warmup, 3) if kind == "hessian" else 1):
+            lp.errors(prm, dt, kind)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n = max(1, args.steps if kind == "hessian" else 1)
+        for _ in range(n):
+            res = lp.errors(prm, dt, kind)
+        torch.cuda.synchronize()
+        out[kind] = ((time.perf_counter() - t0) / n, res)
+    clocks = Clocks(0)
+    clocks.start()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    J = lp.jacobian(prm)
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_jac = a.elapsed_time(b) / 1e3
+    secs, res = out["hessian"]
+    i = plan.info
+    ns = i.n_src
+    # each star's expected counts over all images: F_s times the sum of its unit-flux model
+    n_s = np.array([float(J[lp.labels.index(("flux", s))].double().sum()) for s in range(ns)]) * truth.flux
+    del J
+    # Sec. 5's photon-noise relations and its mean ratio of recovered to expected error:
+    # sigma_F / F = 1 / sqrt(N), sigma_theta = (1/pi) sqrt(2 / N) lambda / D, sigma_zern = 1 / sqrt(N) rad RMS
+    lam_c = float(np.sum(truth.weights * truth.lambdas) / np.sum(truth.weights))
+    rel_flux = (res["sigma_flux"] / truth.flux) * np.sqrt(n_s)
+    rel_pos = res["sigma_pos"] / ((1 / np.pi) * np.sqrt(2 / n_s)[:, None] * lam_c / truth.diameter)
+    rel_zern = res["sigma_zern"] * (2 * np.pi / lam_c) * np.sqrt(n_s.sum())
+    line = dict(metric=LAPLACE_METRIC, value=secs, unit="s", n_gpus=1, steps=max(1, args.steps),
+                warmup=max(args.warmup, 3), ms_per_step=1e3 * secs, higher_is_better=False, scaling="weak",
+                vs_baseline=None, dtype={"bf16x3": "bf16x3 split (fp32 accumulate)"}.get(args.form, args.form),
+                data="synthetic", gpu_launches=None,
+                config=dict(workload=workload_name(wl), form=args.form, psfs_per_eval=i.n_psf, pupil=i.n_pupil,
+                            mft_out=i.n_out, n_par=len(lp.labels), n_src=ns, n_zern=i.n_zern),
+                seconds=dict(hessian=secs, gauss_newton=out["gauss_newton"][0], fisher=out["fisher"][0],
+                             jacobian_only=t_jac),
+                sigma=dict(pos_mas_median=float(np.median(res["sigma_pos"]) * 206264.806e3),
+                           flux_rel_median=float(np.median(res["sigma_flux"] / truth.flux)),
+                           zern_nm=[float(x) * 1e9 for x in res["sigma_zern"]],
+                           total_counts=float(n_s.sum())),
+                sigma_relative=dict(flux=float(np.mean(rel_flux)), position=float(np.mean(rel_pos)),
+                                    zernike=float(np.mean(rel_zern))),
+                clocks=clk,
+                context="the paper computes these errors (Hessian marginalised over positions, fluxes and "
+                        "aberrations) without reporting a time")
+    plan.close()
+    print(json.dumps(line), flush=True)
+
+
 def reference_arm(args, rank, world):
     """--impl reference: the FP64 CPU oracle timed on this host, rank 0 only."""
     if rank != 0:
@@ -505,6 +589,10 @@ def main():
     if args.fit:
         if rank == 0:
             fit_bench(args)
+        return
+    if args.laplace:
+        if rank == 0:
+            laplace_bench(args)
         return
     import torch
 

@@ -182,3 +182,44 @@ def test_jvp_rejects_bad_alpha():
     for a in (0.0, -1.0, float("nan"), float("inf")):
         with pytest.raises(P.DlxError):
             P.dlx_model_jvp(plan, prm, t, 1, a)
+
+
+@pytest.mark.parametrize("form", ["bf16x3"])
+def test_paper_full_size_sampled(form):
+    """The paper's example (20 stars x 3 wavelengths x 5 images, 512^2 -> 1024^2, Noll 4-10): Jacobian
+    entries at sampled pixels against the oracle's differences of direct sums, and properties of the
+    Hessian that hold at any size (symmetric, positive definite at the truth, marginal errors no
+    smaller than the conditional ones 1/sqrt(H_ii))."""
+    import torch
+
+    import oracle
+    import paper_2406_08703_gb300 as P
+    import workloads as W
+    from oracle import laplace as OL
+    from paper_2406_08703_gb300.laplace import Laplace
+
+    p = W.make_problem("paper")
+    plan = P.dlx_make_mft(P.desc_from_problem(p, P.PRECISIONS[form]))
+    prm = P.params_from_problem(p)
+    lp = Laplace(plan)
+    J = lp.jacobian(prm)
+    rows = [lp.labels.index(lab) for lab in (("pos", 0, 0), ("pos", 7, 1), ("flux", 3), ("zern", 2))]
+    rng = np.random.default_rng(5)
+    for k in rows:
+        lab = lp.labels[k]
+        row = J[k].double().cpu().numpy()
+        top = np.argsort(np.abs(row))[-4:]
+        idx = np.concatenate([top, rng.integers(0, row.size, 4)])
+        e_idx, q_idx = np.unravel_index(idx, (p.n_exp, p.n_det**2))
+        ref = OL._richardson(lambda q: oracle.model_at(q, list(e_idx), list(q_idx)), p, lab)
+        err = float(np.max(np.abs(row[idx] - ref)) / np.max(np.abs(ref)))
+        print(form, lab, "sampled J error / row max", err)
+        assert err < TOL[form]["J"]
+    del J
+    m = P.dlx_forward(plan, prm).cpu().numpy()
+    dt = torch.as_tensor(W.poisson_counts(m, 17), device="cuda")
+    H = lp.information(prm, dt, "hessian").cpu().numpy()
+    assert np.max(np.abs(H - H.T)) <= 1e-12 * np.max(np.abs(H))
+    res = OL.sigma(H)  # raises if H is singular
+    assert np.all(np.linalg.eigvalsh(H / np.sqrt(np.outer(np.diag(H), np.diag(H)))) > 0)
+    assert np.all(res >= (1 - 1e-9) / np.sqrt(np.diag(H)))
