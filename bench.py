@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--laplace", action="store_true",
                     help="time the Laplace-approximation errors instead (Sec. 4: the likelihood Hessian over "
                          "positions, fluxes and Zernikes, inverted) on --workload (default paper)")
+    ap.add_argument("--no-crop", action="store_true",
+                    help="--fit / --laplace: compute every image's PSFs, not windows of one larger detector per "
+                         "source, even where the dithers are whole pixels")
     ap.add_argument("--serving-requests", type=int, default=36)
     ap.add_argument("--serving-shapes", type=int, default=6)
     return ap.parse_args()
@@ -404,6 +407,19 @@ def serving_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def use_crop(P, problem, args) -> bool:
+    """Integer-pixel dithers become windows of one larger detector per source (Sec. 3) unless
+    --no-crop is given."""
+    return (not args.no_crop) and problem.n_exp > 1 and P.integer_dithers(problem) is not None
+
+
+def dither_mode(crop, problem) -> str:
+    if crop:
+        return (f"{problem.n_exp} integer dithers as windows of one PSF per source and wavelength on a larger "
+                "detector (Sec. 3)")
+    return f"{problem.n_exp} exposures, each with its own PSFs"
+
+
 FIT_METRIC = "staged fit (Sec. 4): wall-clock seconds for 150 epochs of loss + gradient + Adam"
 
 
@@ -428,7 +444,8 @@ def fit_bench(args):
     start = W.perturbed_start(truth, 81)
     data = W.synthetic_counts((start.n_exp, start.n_det, start.n_det), float(np.sum(truth.flux)) * start.n_exp,
                               truth.pos / truth.pixscale, 3.0, 82)
-    plan = P.dlx_make_mft(P.desc_from_problem(start, P.PRECISIONS[args.form]))
+    crop = use_crop(P, start, args)
+    plan = P.dlx_make_mft(P.desc_from_problem(start, P.PRECISIONS[args.form], crop=crop))
     prm = P.params_from_problem(start)
     dt = torch.as_tensor(data, device="cuda")
     lr = dict(zern=1e-9, flux=2e-3 * float(np.mean(truth.flux)), pos=0.05 * truth.pixscale, flat=2e-3)
@@ -452,7 +469,8 @@ def fit_bench(args):
                 ms_per_step=1e3 * secs / n, higher_is_better=False, scaling="weak", vs_baseline=None,
                 dtype={"bf16x3": "bf16x3 split (fp32 accumulate)"}.get(args.form, args.form), data="synthetic",
                 config=dict(workload=workload_name(wl), form=args.form, psfs_per_eval=i.n_psf, pupil=i.n_pupil,
-                            mft_out=i.n_out, epochs=[s[0] for s in stages], lr=lr,
+                            mft_out=i.n_mft_out, dithers=dither_mode(crop, start), epochs=[s[0] for s in stages],
+                            lr=lr,
                             l2="no flush: per-step working set > 129 MB L2"),
                 evals_per_s=n / secs, loss_first=float(L[0]), loss_last_stage1=float(L[stages[0][0] - 1]),
                 loss_last=float(L[-1]), clocks=clk,
@@ -484,7 +502,8 @@ def laplace_bench(args):
 
     wl = args.workload if args.workload != "binary" else "paper"
     truth = W.make_problem(wl)
-    plan = P.dlx_make_mft(P.desc_from_problem(truth, P.PRECISIONS[args.form]))
+    crop = use_crop(P, truth, args)
+    plan = P.dlx_make_mft(P.desc_from_problem(truth, P.PRECISIONS[args.form], crop=crop))
     prm = P.params_from_problem(truth)
     m = P.dlx_forward(plan, prm).cpu().numpy()
     data = W.poisson_counts(m, 91)
@@ -527,7 +546,8 @@ def laplace_bench(args):
                 vs_baseline=None, dtype={"bf16x3": "bf16x3 split (fp32 accumulate)"}.get(args.form, args.form),
                 data="synthetic", gpu_launches=None,
                 config=dict(workload=workload_name(wl), form=args.form, psfs_per_eval=i.n_psf, pupil=i.n_pupil,
-                            mft_out=i.n_out, n_par=len(lp.labels), n_src=ns, n_zern=i.n_zern),
+                            mft_out=i.n_mft_out, dithers=dither_mode(crop, truth), n_par=len(lp.labels),
+                            n_src=ns, n_zern=i.n_zern),
                 seconds=dict(hessian=secs, gauss_newton=out["gauss_newton"][0], fisher=out["fisher"][0],
                              jacobian_only=t_jac),
                 sigma=dict(pos_mas_median=float(np.median(res["sigma_pos"]) * 206264.806e3),

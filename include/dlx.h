@@ -99,6 +99,14 @@ typedef struct {
     double prf_prior_sigma;  /* > 0: the loss adds the chi^2 log prior on the pixel response
                                 (Sec. 4) sum_p (FF_p - 1)^2 / (2 sigma^2), and dL/dFF its
                                 gradient (FF_p - 1) / sigma^2; 0 = none */
+    const int32_t *dither_px;/* NULL: the exposures' dithers are params->dither (any angle).
+                                Else HOST [n_exp][2] integer-pixel dithers (x, y), copied, each
+                                |dither| <= 4096: every source's PSF is computed once on a
+                                (Nd + 2 max|dither_px|)^2 detector and image e is the Nd x Nd
+                                window of it shifted by dither_px[e] (Sec. 3's integer dithers),
+                                which equals the model with params->dither = dither_px * pixscale
+                                at 1/n_exp of the MFT work; params->dither is then not read.
+                                Not accepted by the server (dlx_submit). */
 } dlx_mft_desc;
 
 /* Parameters and fixed inputs of one evaluation.  Device pointers. */
@@ -132,6 +140,7 @@ typedef struct {
     double flop_forward;       /* algorithmic MFT FLOP of one forward (8 per complex MAC) */
     double flop_loss_grad;     /* algorithmic MFT FLOP of one loss+gradient incl. recomputation */
     int gemm_tiles_stage2;     /* output tiles of the dominant contraction */
+    int n_mft_out;             /* the MFT's output grid per side: n_out, or (Nd + 2 max|dither_px|) * os */
 } dlx_plan_info;
 
 /* Build a plan: validates the shape, allocates the MFT matrices A(lambda) and

@@ -50,13 +50,23 @@ class MftDesc:
     psf_chunk: int = 0
     workspace_limit_bytes: int = 0
     prf_prior_sigma: float = 0.0
+    # integer-pixel dithers [n_exp][2] (x, y): one MFT per source on a larger detector, images
+    # as windows of it (Sec. 3); None = dithers are the params' angles
+    dither_px: Optional[Sequence] = None
 
     def to_c(self):
         lam = (C.c_double * len(self.lambdas))(*[float(x) for x in self.lambdas])
+        dpx = None
+        if self.dither_px is not None:
+            flat = [int(v) for row in self.dither_px for v in row]
+            if len(flat) != 2 * self.n_exp:
+                raise ValueError("dither_px needs n_exp (x, y) pairs")
+            dpx = (C.c_int32 * len(flat))(*flat)
         d = N.MftDesc(self.n_pupil, self.diameter_m, self.n_det, self.pixscale_rad, self.oversample,
                       len(self.lambdas), C.cast(lam, C.POINTER(C.c_double)), self.n_src, self.n_exp, self.n_zern,
-                      int(self.precision), self.psf_chunk, self.workspace_limit_bytes, float(self.prf_prior_sigma))
-        return d, lam
+                      int(self.precision), self.psf_chunk, self.workspace_limit_bytes, float(self.prf_prior_sigma),
+                      C.cast(dpx, C.POINTER(C.c_int32)) if dpx is not None else None)
+        return d, (lam, dpx)
 
 
 class Plan:
@@ -80,9 +90,23 @@ class Plan:
             pass
 
 
-def desc_from_problem(p, precision=DLX_BF16X3, **kw) -> MftDesc:
-    """MftDesc of a workloads.Problem-like object (duck-typed)."""
+def integer_dithers(p) -> Optional[list]:
+    """The problem's dithers in whole pixels [(x, y), ...] when every one is an integer number of
+    pixels (to 1e-6 of a pixel), else None."""
+    k = np.asarray(p.dither, dtype=np.float64) / p.pixscale
+    r = np.rint(k)
+    return r.astype(int).tolist() if np.all(np.abs(k - r) <= 1e-6) else None
+
+
+def desc_from_problem(p, precision=DLX_BF16X3, crop: bool = False, **kw) -> MftDesc:
+    """MftDesc of a workloads.Problem-like object (duck-typed).  crop=True computes integer-pixel
+    dithers as windows of one larger detector (raises if a dither is not a whole pixel)."""
     kw.setdefault("prf_prior_sigma", float(getattr(p, "prf_sigma", 0.0) or 0.0))
+    if crop:
+        dpx = integer_dithers(p)
+        if dpx is None:
+            raise ValueError("crop=True needs dithers of whole pixels")
+        kw.setdefault("dither_px", dpx)
     return MftDesc(n_pupil=p.n_pupil, diameter_m=p.diameter, n_det=p.n_det, pixscale_rad=p.pixscale,
                    oversample=p.oversample, lambdas=list(p.lambdas), n_src=len(p.flux), n_exp=len(p.dither),
                    n_zern=len(p.coeff), precision=precision, **kw)

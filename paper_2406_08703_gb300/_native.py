@@ -27,7 +27,8 @@ class MftDesc(C.Structure):
     _fields_ = [("n_pupil", C.c_int), ("diameter_m", C.c_double), ("n_det", C.c_int), ("pixscale_rad", C.c_double),
                 ("oversample", C.c_int), ("n_lambda", C.c_int), ("lambda_m", C.POINTER(C.c_double)),
                 ("n_src", C.c_int), ("n_exp", C.c_int), ("n_zern", C.c_int), ("precision", C.c_int),
-                ("psf_chunk", C.c_int), ("workspace_limit_bytes", C.c_size_t), ("prf_prior_sigma", C.c_double)]
+                ("psf_chunk", C.c_int), ("workspace_limit_bytes", C.c_size_t), ("prf_prior_sigma", C.c_double),
+                ("dither_px", C.POINTER(C.c_int32))]
 
 
 class Params(C.Structure):
@@ -43,7 +44,7 @@ class PlanInfo(C.Structure):
     _fields_ = [(k, C.c_int) for k in ("n_pupil", "n_det", "oversample", "n_out", "n_lambda", "n_src", "n_exp",
                                        "n_zern", "n_psf", "precision", "psf_chunk")] + [
         ("workspace_bytes", C.c_size_t), ("flop_forward", C.c_double), ("flop_loss_grad", C.c_double),
-        ("gemm_tiles_stage2", C.c_int)]
+        ("gemm_tiles_stage2", C.c_int), ("n_mft_out", C.c_int)]
 
 
 class KernelTimes(C.Structure):

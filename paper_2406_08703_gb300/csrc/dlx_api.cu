@@ -128,8 +128,19 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 32 sources per plan");
     if (!(d->prf_prior_sigma >= 0) || !std::isfinite(d->prf_prior_sigma))
         return fail(DLX_ERR_INVALID_ARG, "prf_prior_sigma must be finite and >= 0");
-    const long long no_ll = (long long)d->n_det * d->oversample;
-    if (d->n_pupil > 8192 || no_ll > 16384) return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and n_det*oversample <= 16384");
+    // integer-pixel dithers: one MFT per source on a detector wide enough for every window
+    int delta = 0;
+    if (d->dither_px) {
+        for (int k = 0; k < 2 * d->n_exp; ++k) {
+            const int v = d->dither_px[k];
+            if (v < -4096 || v > 4096) return fail(DLX_ERR_RANGE, "|dither_px| <= 4096");
+            delta = std::max(delta, v < 0 ? -v : v);
+        }
+    }
+    const long long nd_mft = (long long)d->n_det + 2LL * delta;
+    const long long no_ll = nd_mft * d->oversample;
+    if (d->n_pupil > 8192 || no_ll > 16384)
+        return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and (n_det + 2 max|dither_px|) * oversample <= 16384");
 
     DeviceGuard guard(device);
     cudaDeviceProp prop;
@@ -139,18 +150,22 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->desc = *d;
     p->lambdas.assign(d->lambda_m, d->lambda_m + d->n_lambda);
     p->desc.lambda_m = p->lambdas.data();
+    if (d->dither_px) p->dither_px.assign(d->dither_px, d->dither_px + 2 * d->n_exp);
+    p->desc.dither_px = d->dither_px ? p->dither_px.data() : nullptr;
     p->device = device;
     p->R_max = R_max;
     p->sm_count = prop.multiProcessorCount;
     p->cc_major = prop.major;
     p->cc_minor = prop.minor;
     p->ni = d->n_pupil;
-    p->nd = d->n_det;
+    p->ndi = d->n_det;
+    p->nei = d->n_exp;
+    p->nd = (int)nd_mft;
     p->os = d->oversample;
     p->no = (int)no_ll;
     p->nl = d->n_lambda;
     p->ns = d->n_src;
-    p->ne = d->n_exp;
+    p->ne = d->dither_px ? 1 : d->n_exp;
     p->nz = d->n_zern;
     p->nse = p->ns * p->ne;
     p->B = p->nl * p->nse;
@@ -242,7 +257,8 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     op_alloc(p->GEt, p->chunk, p->no, p->ldo, adj_planes);
     op_alloc(p->GT1, p->chunk, p->ni, p->ldo, adj_planes);
     const size_t npx = (size_t)p->ni * p->ni, np = (size_t)p->nd * p->nd, nq = (size_t)p->no * p->no;
-    p->red_blocks = std::max(1, std::min((int)((np + 255) / 256), std::max(1, p->sm_count * 2 / R_max)));
+    const size_t npi = (size_t)p->ndi * p->ndi;
+    p->red_blocks = std::max(1, std::min((int)((npi + 255) / 256), std::max(1, p->sm_count * 2 / R_max)));
     if (e == cudaSuccess) e = plan_alloc(p, &p->lam_d, sizeof(double) * p->nl);
     if (e == cudaSuccess) e = plan_alloc(p, &p->wnorm, sizeof(float) * p->nl * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->pscale, sizeof(float) * 2 * R_max);
@@ -261,7 +277,18 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->opd, sizeof(float) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->Is, sizeof(float) * (size_t)p->G * p->nse * R_max * nq);
     if (e == cudaSuccess) e = plan_alloc(p, &p->GI, sizeof(float) * p->ne * np * R_max);
-    if (e == cudaSuccess) e = plan_alloc(p, &p->model_tmp, sizeof(float) * p->ne * np * R_max);
+    if (e == cudaSuccess) e = plan_alloc(p, &p->model_tmp, sizeof(float) * p->nei * npi * R_max);
+    if (d->dither_px) {
+        // window of image e: big-detector pixel (x, y) = image pixel + (delta - dither_x, delta - dither_y)
+        std::vector<int> off(2 * p->nei);
+        for (int k = 0; k < p->nei; ++k) {
+            off[2 * k] = delta - d->dither_px[2 * k];
+            off[2 * k + 1] = delta - d->dither_px[2 * k + 1];
+        }
+        if (e == cudaSuccess) e = plan_alloc(p, &p->GIimg, sizeof(float) * p->nei * npi * R_max);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->crop, sizeof(int) * 2 * p->nei);
+        if (e == cudaSuccess) e = cudaMemcpy(p->crop, off.data(), sizeof(int) * 2 * p->nei, cudaMemcpyHostToDevice);
+    }
     if (p->prec != DLX_FP32_SIMT) {
         // split the long-K adjoint 1^T contraction only while its 128-tiles do not fill
         // the SMs once: every split adds a gphi plane and a re-read of the phasor tile
@@ -339,7 +366,7 @@ int eval_loss_grad(dlx_plan *p, const DevParams &prm, int R, const int32_t *data
     if (rc) return rc;
     if (!model) {
         model = p->model_tmp;
-        model_stride = (size_t)p->ne * p->nd * p->nd;
+        model_stride = (size_t)p->nei * p->ndi * p->ndi;
     }
     DLX_CU(launch_bin_nll(p, prm, R, data, data_stride, model, model_stride, g, loss, st), "bin+nll+loss");
     const bool pupil = g && (g->p[GZERN] || g->p[GPIX] || g->p[GPOS]);
@@ -362,7 +389,7 @@ int eval_loss_grad(dlx_plan *p, const DevParams &prm, int R, const int32_t *data
 
 namespace {
 
-dlx::DevParams dev_params(const dlx_params *q) {
+dlx::DevParams dev_params(const dlx_plan *p, const dlx_params *q) {
     dlx::DevParams d{};
     d.p[dlx::PT] = q->transmission;
     d.p[dlx::POPDF] = q->opd_fixed;
@@ -372,7 +399,7 @@ dlx::DevParams dev_params(const dlx_params *q) {
     d.p[dlx::PW] = q->weights;
     d.p[dlx::PFLUX] = q->flux;
     d.p[dlx::PPOS] = q->pos;
-    d.p[dlx::PDITHER] = q->dither;
+    d.p[dlx::PDITHER] = p->crop ? nullptr : q->dither;  // integer dithers are windows, not tilts
     d.p[dlx::PFLAT] = q->flat;
     return d;
 }
@@ -410,12 +437,13 @@ int dlx_plan_get_info(const dlx_plan *p, dlx_plan_info *o) {
     if (!p || !o) return fail(DLX_ERR_INVALID_ARG, "NULL argument");
     memset(o, 0, sizeof(*o));
     o->n_pupil = p->ni;
-    o->n_det = p->nd;
+    o->n_det = p->ndi;
     o->oversample = p->os;
-    o->n_out = p->no;
+    o->n_out = p->ndi * p->os;
+    o->n_mft_out = p->no;
     o->n_lambda = p->nl;
     o->n_src = p->ns;
-    o->n_exp = p->ne;
+    o->n_exp = p->nei;
     o->n_zern = p->nz;
     o->n_psf = p->B;
     o->precision = p->prec;
@@ -437,7 +465,7 @@ int dlx_forward(dlx_plan *p, const dlx_params *prm, float *model, void *stream) 
     if (rc) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevParams d = dev_params(p, prm);
     if ((rc = dlx::eval_forward(p, d, 1, st))) return rc;
     DLX_CU(dlx::launch_bin_nll(p, d, 1, nullptr, 0, model, 0, nullptr, nullptr, st), "bin");
     return DLX_OK;
@@ -451,7 +479,7 @@ int dlx_model_jvp(dlx_plan *p, const dlx_params *prm, const float *t_map, uint32
     if (rc) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevParams d = dev_params(p, prm);
     // m(+alpha) into jvp, m(-alpha) into work; the model is quadratic in the phasor, so the
     // central difference over 2 alpha is the derivative itself
     p->tan_map = t_map;
@@ -468,7 +496,7 @@ int dlx_model_jvp(dlx_plan *p, const dlx_params *prm, const float *t_map, uint32
     p->tan_coef = 0.f;
     p->tan_mask = 0;
     if (rc) return rc;
-    DLX_CU(dlx::launch_scaled_diff(jvp, work, (size_t)p->ne * p->nd * p->nd, (float)(0.5 / alpha), st), "jvp");
+    DLX_CU(dlx::launch_scaled_diff(jvp, work, (size_t)p->nei * p->ndi * p->ndi, (float)(0.5 / alpha), st), "jvp");
     return DLX_OK;
 }
 
@@ -478,7 +506,7 @@ int dlx_model_vjp(dlx_plan *p, const dlx_params *prm, const float *cot, const dl
     if (rc) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevParams d = dev_params(p, prm);
     const dlx::DevGrads dg = dev_grads(g);
     p->cot = cot;
     rc = dlx::eval_loss_grad(p, d, 1, nullptr, 0, nullptr, &dg, nullptr, 0, st);
@@ -498,7 +526,7 @@ int dlx_model_vjp_jvp(dlx_plan *p, const dlx_params *prm, const float *cot, cons
     if (rc) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevParams d = dev_params(p, prm);
     // J^T cot at the phasors P (1 + i a) into g and P (1 - i a) into work; it is a quadratic
     // form of the phasor, so the central difference over 2 alpha is its derivative
     dlx_grads wk = *g;
@@ -520,7 +548,7 @@ int dlx_model_vjp_jvp(dlx_plan *p, const dlx_params *prm, const float *cot, cons
     p->tan_coef = 0.f;
     p->tan_mask = 0;
     if (rc) return rc;
-    const size_t n[5] = {(size_t)p->nz, (size_t)p->ni * p->ni, (size_t)p->nd * p->nd, (size_t)p->ns,
+    const size_t n[5] = {(size_t)p->nz, (size_t)p->ni * p->ni, (size_t)p->ndi * p->ndi, (size_t)p->ns,
                          (size_t)2 * p->ns};
     for (int k = 0; k < 5; ++k)
         if (gp[k]) DLX_CU(dlx::launch_scaled_diff((float *)gp[k], wp[k], n[k], (float)(0.5 / alpha), st), "vjp_jvp");
@@ -548,7 +576,7 @@ int dlx_psf(dlx_plan *p, const dlx_params *prm, float *psf_os, void *stream) {
     if (rc) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
-    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevParams d = dev_params(p, prm);
     if ((rc = dlx::eval_forward(p, d, 1, st))) return rc;
     DLX_CU(dlx::launch_psf_out(p, d, psf_os, st), "psf");
     return DLX_OK;
@@ -562,7 +590,7 @@ int dlx_loss_grad(dlx_plan *p, const dlx_params *prm, const int32_t *data, doubl
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     DLX_CU(cudaMemsetAsync(p->clamped, 0, sizeof(unsigned long long), st), "memset");
-    const dlx::DevParams d = dev_params(prm);
+    const dlx::DevParams d = dev_params(p, prm);
     const dlx::DevGrads dg = dev_grads(g);
     return dlx::eval_loss_grad(p, d, 1, data, 0, loss, g ? &dg : nullptr, model_opt, 0, st);
 }

@@ -316,7 +316,13 @@ struct dlx_plan {
     std::vector<double> lambdas;
     int device = 0, sm_count = 0, cc_major = 0, cc_minor = 0;
     int R_max = 1;
-    int ni, nd, os, no, nl, ns, ne, nz, B, nse, ldi, ldo;
+    int ni, nd, os, no, nl, ns, ne, nz, B, nse, ldi, ldo;  // nd, ne, no: the MFT's detector
+    // the images: ndi x ndi pixels, nei of them.  Equal to nd, ne unless the dithers are integer
+    // pixels (desc.dither_px): then the MFT runs once per source on nd = ndi + 2 max|dither| with
+    // ne = 1, and image e is the window of it at crop[e] (device int2 (x, y) offsets, pixels)
+    int ndi, nei;
+    int *crop = nullptr;
+    std::vector<int32_t> dither_px;  // host copy of desc.dither_px ([nei][2]) or empty
     int prec, fmt, planes, esz;
     double dx, du;
     int G = 1;       // partial-intensity planes of the intensity contraction
@@ -342,8 +348,9 @@ struct dlx_plan {
     float2 *tilt = nullptr;    // [R*B][2][ni]
     float *opd = nullptr;      // [R][ni*ni]
     float *Is = nullptr;       // [G][R*nse][no][no] per-source intensity partials
-    float *GI = nullptr;       // [R][ne][nd*nd] FF * dL/dm
-    float *model_tmp = nullptr;// [R][ne][nd*nd]
+    float *GI = nullptr;       // [R][ne][nd*nd] FF * dL/dm on the MFT's detector
+    float *GIimg = nullptr;    // integer dithers: [R][nei][ndi*ndi] the images' FF * dL/dm
+    float *model_tmp = nullptr;// [R][nei][ndi*ndi]
     float *gphi = nullptr;     // [R*B][ni*ni] (2 pi / lambda) dL/dphase
     float2 *gopd = nullptr;    // [R][ni*ni] g_OPD as a compensated (hi, lo) FP32 pair
     double *red = nullptr;     // [R][red_blocks][1 + 8] reduction partials

@@ -387,7 +387,7 @@ constexpr int kQShared = 64;  // (source, exposure) maxima kept in shared memory
 
 template <int OS, int MAXS>
 __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os_rt,
-                          int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
+                          int no, int nem, const int2 *__restrict__ crop, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount,
                           float prf_inv, const float *__restrict__ cot) {
@@ -423,12 +423,17 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
         for (int e = 0; e < ne; ++e) {
             float bs[MAXS], bmax[MAXS];
             float btot = 0.f;
+            // image e is the window at crop[e] of the one MFT plane per source (integer dithers),
+            // or the source's own plane of exposure e
+            const int2 oc = crop ? __ldg(crop + e) : make_int2(0, 0);
+            const int em = crop ? 0 : e;
+            const int ry = (py + oc.y) * os, rx = (px + oc.x) * os;
 #pragma unroll
             for (int s = 0; s < MAXS; ++s) {
                 bs[s] = 0.f;
                 bmax[s] = 0.f;
                 if (s < ns && valid) {
-                    const size_t rse = (size_t)r * nse + s * ne + e;
+                    const size_t rse = (size_t)r * nse + s * nem + em;
                     float v = 0.f, vm = 0.f;
                     if constexpr (OS == 4 || OS == 2) {
                         // per-subpixel sums over the planes; each plane's OS row loads are in flight together
@@ -438,7 +443,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
 #pragma unroll
                             for (int c = 0; c < OS; ++c) q[a][c] = 0.f;
                         for (int gg = 0; gg < G; ++gg) {
-                            const float *src = Is + ((size_t)gg * Rnse + rse) * plane + (size_t)(py * OS) * no + px * OS;
+                            const float *src = Is + ((size_t)gg * Rnse + rse) * plane + (size_t)ry * no + rx;
                             if constexpr (OS == 4) {
                                 float4 t[4];
 #pragma unroll
@@ -473,8 +478,8 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                             for (int c = 0; c < os; ++c) {
                                 float q = 0.f;
                                 for (int gg = 0; gg < G; ++gg)
-                                    q += __ldg(Is + ((size_t)gg * Rnse + rse) * plane + (size_t)(py * os + a) * no +
-                                               (size_t)px * os + c);
+                                    q += __ldg(Is + ((size_t)gg * Rnse + rse) * plane + (size_t)(ry + a) * no +
+                                               (size_t)rx + c);
                                 v += q;
                                 vm = fmaxf(vm, q);
                             }
@@ -519,7 +524,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                     if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
                     for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
                     if ((threadIdx.x & 31) == 0) {
-                        const int k = s * ne + e;
+                        const int k = s * nem + em;
                         if (k < kQShared)
                             atomicMax(s_q + k, __float_as_uint(qv));
                         else
@@ -581,37 +586,67 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
     }
 }
 
+// GI[r][P] = sum_e GIimg[r][e][P - crop[e]] over the images whose window holds big-detector pixel P
+// (fixed order over e)
+__global__ void k_crop_fold(const float *__restrict__ gimg, const int2 *__restrict__ crop, int ne, int nd,
+                            float *__restrict__ gi, int nb) {
+    pdl_trigger();
+    pdl_wait();
+    const int r = blockIdx.y;
+    const size_t npb = (size_t)nb * nb, np = (size_t)nd * nd;
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < npb; q += (size_t)gridDim.x * blockDim.x) {
+        const int y = (int)(q / nb), x = (int)(q % nb);
+        float v = 0.f;
+        for (int e = 0; e < ne; ++e) {
+            const int2 o = __ldg(crop + e);
+            const int iy = y - o.y, ix = x - o.x;
+            if (iy >= 0 && iy < nd && ix >= 0 && ix < nd) v += __ldg(gimg + ((size_t)r * ne + e) * np + (size_t)iy * nd + ix);
+        }
+        gi[(size_t)r * npb + q] = v;
+    }
+}
+
 cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride,
                            float *model, size_t model_stride, const DevGrads *g, double *loss, cudaStream_t st) {
     DevGrads gg{};
     if (g) gg = *g;
     KScope ks(p, KC_BIN, 1, st);
+    float *gi = p->crop ? p->GIimg : p->GI;
     auto go = [&](auto kern) {
         return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse, p->ns,
-                          p->ne, p->nd, p->os, p->no, prm, data, data_stride, model, model_stride, p->GI, gg, p->red,
-                          p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot);
+                          p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data, data_stride, model,
+                          model_stride, gi, gg, p->red, p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot);
     };
     // per-source registers for up to 8 sources, or up to kMaxSrc
-    if (p->ns <= 8) {
-        if (p->os == 4) return go(k_bin_nll<4, 8>);
-        if (p->os == 2) return go(k_bin_nll<2, 8>);
-        return go(k_bin_nll<0, 8>);
-    }
-    if (p->os == 4) return go(k_bin_nll<4, kMaxSrc>);
-    if (p->os == 2) return go(k_bin_nll<2, kMaxSrc>);
-    return go(k_bin_nll<0, kMaxSrc>);
+    cudaError_t e;
+    if (p->ns <= 8)
+        e = p->os == 4 ? go(k_bin_nll<4, 8>) : p->os == 2 ? go(k_bin_nll<2, 8>) : go(k_bin_nll<0, 8>);
+    else
+        e = p->os == 4 ? go(k_bin_nll<4, kMaxSrc>) : p->os == 2 ? go(k_bin_nll<2, kMaxSrc>) : go(k_bin_nll<0, kMaxSrc>);
+    if (e != cudaSuccess || !p->crop || !(data || p->cot)) return e;
+    // integer dithers: the adjoint weights of the big detector are the images' weights placed back
+    // at their windows and summed
+    const size_t nb = (size_t)p->nd * p->nd;
+    const int blocks = (int)std::min<size_t>((nb + 255) / 256, (size_t)p->sm_count * 8);
+    return launch_pdl(k_crop_fold, dim3(blocks, R), dim3(256), 0, st, (const float *)p->GIimg,
+                      (const int2 *)p->crop, p->nei, p->ndi, p->GI, p->nd);
 }
 
-__global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, int ne, size_t plane,
-                          const float *__restrict__ flux, float *__restrict__ psf) {
-    size_t total = (size_t)ne * plane;
+// psf[e][y][x] = sum_s F_s sum_g Is[g][s nem + em][y + oy][x + ox]: the image-sized oversampled
+// intensity of image e (the window at crop[e] of the source's one plane with integer dithers)
+__global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, int nem, int no, int ne, int noi,
+                          const int2 *__restrict__ crop, int os, const float *__restrict__ flux, float *__restrict__ psf) {
+    const size_t plane = (size_t)no * no, iplane = (size_t)noi * noi, total = (size_t)ne * iplane;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-        int e = (int)(i / plane);
-        size_t q = i % plane;
+        const int e = (int)(i / iplane);
+        const int y = (int)(i % iplane / noi), x = (int)(i % noi);
+        const int2 o = crop ? __ldg(crop + e) : make_int2(0, 0);
+        const int em = crop ? 0 : e;
+        const size_t q = (size_t)(y + o.y * os) * no + x + o.x * os;
         float v = 0.f;
         for (int s = 0; s < ns; ++s) {
             float vs = 0.f;
-            for (int gg = 0; gg < G; ++gg) vs += Is[((size_t)gg * nse + s * ne + e) * plane + q];
+            for (int gg = 0; gg < G; ++gg) vs += Is[((size_t)gg * nse + s * nem + em) * plane + q];
             v = fmaf(flux[s], vs, v);
         }
         psf[i] = v;
@@ -619,10 +654,12 @@ __global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, 
 }
 
 cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaStream_t st) {
-    size_t plane = (size_t)p->no * p->no, total = plane * p->ne;
+    const int noi = p->ndi * p->os;
+    const size_t total = (size_t)noi * noi * p->nei;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
     KScope ks(p, KC_BIN, 1, st);
-    k_psf_out<<<blocks, 256, 0, st>>>(p->Is, p->G, p->nse, p->ns, p->ne, plane, prm.p[PFLUX], psf);
+    k_psf_out<<<blocks, 256, 0, st>>>(p->Is, p->G, p->nse, p->ns, p->ne, p->no, p->nei, noi, (const int2 *)p->crop,
+                                      p->os, prm.p[PFLUX], psf);
     return cudaGetLastError();
 }
 

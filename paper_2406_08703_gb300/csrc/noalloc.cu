@@ -88,6 +88,10 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
             dlx_set_error("wavelengths must be finite and > 0");
             return DLX_ERR_INVALID_ARG;
         }
+    if (d->dither_px) {
+        dlx_set_error("dlx_forward_noalloc: integer-pixel dither windows (dither_px) need a plan");
+        return DLX_ERR_UNSUPPORTED;
+    }
     if (d->n_src > dlx::kMaxSrc || d->n_lambda > kMaxLambdas) {
         dlx_set_error("dlx_forward_noalloc: at most 32 sources and 256 wavelengths");
         return DLX_ERR_RANGE;
@@ -105,6 +109,8 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     p.ns = d->n_src;
     p.ne = d->n_exp;
     p.nz = d->n_zern;
+    p.ndi = p.nd;
+    p.nei = p.ne;
     p.nse = p.ns * p.ne;
     p.B = p.nl * p.nse;
     p.ldi = (p.ni + 7) / 8 * 8;

@@ -585,6 +585,7 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
         d.n_zern < 0 || !d.lambda_m || d.precision < DLX_FP32_SIMT || d.precision > DLX_BF16X3SA)
         return fail(DLX_ERR_INVALID_ARG, "bad request shape");
     if (d.n_src > dlx::kMaxSrc) return fail(DLX_ERR_RANGE, "at most 32 sources");
+    if (d.dither_px) return fail(DLX_ERR_UNSUPPORTED, "integer-pixel dither windows (dither_px) are not served");
     if (!rq->transmission || !rq->weights || !rq->flux || !rq->pos || !rq->flat || !rq->data ||
         (d.n_zern > 0 && (!rq->zern_basis || !rq->zern_coeff)) || rq->n_steps < 0)
         return fail(DLX_ERR_INVALID_ARG, "missing request input");

@@ -52,12 +52,12 @@ def fit_problem(name, seed=3, **over):
     return truth, data, start
 
 
-def gpu_eval(problem, data, precision, psf_chunk=0, want_psf=True):
+def gpu_eval(problem, data, precision, psf_chunk=0, want_psf=True, crop=False):
     import torch
 
     import paper_2406_08703_gb300 as P
 
-    plan = P.dlx_make_mft(P.desc_from_problem(problem, P.PRECISIONS[precision], psf_chunk=psf_chunk))
+    plan = P.dlx_make_mft(P.desc_from_problem(problem, P.PRECISIONS[precision], psf_chunk=psf_chunk, crop=crop))
     prm = P.params_from_problem(problem)
     psf = P.dlx_psf(plan, prm) if want_psf else None
     model = P.dlx_forward(plan, prm)

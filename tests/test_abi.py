@@ -66,6 +66,16 @@ def test_invalid_shapes_rejected_without_a_device(native):
     d = native.MftDesc(**kw)
     assert lib.dlx_make_mft(C.byref(d), 0, C.byref(h)) == -6  # RANGE
     assert lib.dlx_make_mft(None, 0, C.byref(h)) == -1
+    kw["n_src"] = 1
+    kw["n_exp"] = 2
+    for bad_px, code in (((0, 0, 4097, 0), -6), ((0, 0, 0, -5000), -6)):
+        dpx = (C.c_int32 * 4)(*bad_px)
+        d = native.MftDesc(**kw, dither_px=C.cast(dpx, C.POINTER(C.c_int32)))
+        assert lib.dlx_make_mft(C.byref(d), 0, C.byref(h)) == code
+    kw["n_det"] = 4000
+    dpx = (C.c_int32 * 4)(0, 0, 4096, 0)  # (4000 + 8192) * 2 > 16384
+    d = native.MftDesc(**kw, dither_px=C.cast(dpx, C.POINTER(C.c_int32)))
+    assert lib.dlx_make_mft(C.byref(d), 0, C.byref(h)) == -6
     assert lib.dlx_adam(None, None, None, None, 5, 1e-3, 0.9, 0.999, 1e-8, 1, None) == -1
 
 

@@ -206,12 +206,15 @@ def paper_full():
     return p, data
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
-def test_paper_full_size_sampled(paper_full, form):
-    """300 PSFs at 512^2 -> 1024^2: sampled model pixels against direct sums, and the Euler
-    identities of the flux and flat-field gradients (the prior's own part taken out)."""
+@pytest.mark.parametrize("form,crop", [("fp32", False), ("bf16x3", False), ("bf16x3", True)])
+def test_paper_full_size_sampled(paper_full, form, crop):
+    """300 PSFs at 512^2 -> 1024^2 (or, with crop, 60 on a 1064^2 detector and five windows of
+    each, as Sec. 3 does): sampled model pixels against direct sums, and the Euler identities of
+    the flux and flat-field gradients (the prior's own part taken out)."""
     p, data = paper_full
-    out = gpu_eval(p, data, form, want_psf=False)
+    out = gpu_eval(p, data, form, want_psf=False, crop=crop)
+    if crop:
+        assert out["info"].n_psf == 60 and out["info"].n_mft_out == 1064
     m = out["model"]
     rng = np.random.default_rng(1)
     e_idx = list(rng.integers(0, p.n_exp, 12))
@@ -229,3 +232,51 @@ def test_paper_full_size_sampled(paper_full, form):
     assert np.dot(p.flux, g["d_flux"]) == pytest.approx(s_m, rel=1e-4)
     assert np.sum(p.flat * (g["d_flat"] - prior_part)) == pytest.approx(s_m, rel=1e-4)
     assert out["diag"]["device_error"] == 0
+
+
+CROP = [
+    # the paper's pattern (centre and four diagonal steps), small: 3 stars, 2 wavelengths, os 2
+    dict(n_pupil=40, n_det=24, oversample=2, n_lambda=2, n_src=3, n_exp=5, obscuration=0.2, grating=True,
+         n_zern_max=6, dither=[(0, 0), (3, 3), (3, -3), (-3, 3), (-3, -3)]),
+    # asymmetric steps, odd detector, os 4 (the float4 window loads), one image at the edge of the window
+    dict(n_pupil=33, n_det=15, oversample=4, n_lambda=1, n_src=2, n_exp=3, n_zern_max=4,
+         dither=[(0, 0), (5, -1), (-2, 4)]),
+    # os 3 (the generic binning path), a single undithered image
+    dict(n_pupil=24, n_det=10, oversample=3, n_lambda=2, n_src=1, n_exp=1, n_zern_max=3, dither=[(0, 0)]),
+]
+
+
+def _crop_problem(case, seed):
+    kw = dict(CROP[case])
+    dpx = np.array(kw.pop("dither"), dtype=np.float64)
+    truth, data, start = fit_problem("custom", seed=seed, **kw)
+    start.dither = dpx * start.pixscale
+    truth.dither = start.dither.copy()
+    data = W.poisson_counts(oracle.forward(truth), seed)
+    return start, data
+
+
+@pytest.mark.parametrize("case", range(len(CROP)))
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "bf16x4", "f16x3"])
+def test_integer_dither_windows(case, form):
+    """Integer-pixel dithers as windows of one larger detector (Sec. 3): model, PSF, loss and every
+    gradient against the oracle's plain per-exposure model with the same dithers as angles."""
+    start, data = _crop_problem(case, 20 + case)
+    out = gpu_eval(start, data, form, crop=True)
+    assert out["info"].n_mft_out == (start.n_det + 2 * int(round(np.max(np.abs(start.dither)) / start.pixscale))) \
+        * start.oversample
+    err = compare(out, oracle_eval(start, data), form)
+    print(form, case, err)
+
+
+def test_integer_dither_windows_match_angles_on_the_gpu():
+    """The window model and the per-exposure model agree on the GPU itself (FP32 form)."""
+    start, data = _crop_problem(0, 30)
+    a = gpu_eval(start, data, "fp32", crop=True)
+    b = gpu_eval(start, data, "fp32", crop=False)
+    peak = np.max(np.abs(b["model"]))
+    assert np.max(np.abs(a["model"] - b["model"])) <= 2e-6 * peak
+    assert a["loss"] == pytest.approx(b["loss"], rel=1e-6)
+    for k in a["grads"]:
+        if b["grads"][k] is not None:
+            assert rel_l2(a["grads"][k], b["grads"][k]) < 1e-5, k
