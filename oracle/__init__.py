@@ -28,7 +28,7 @@ class _Problem(C.Structure):
         ("oversample", C.c_int), ("n_lambda", C.c_int), ("lambdas", _d), ("weights", _d), ("n_src", C.c_int),
         ("flux", _d), ("pos", _d), ("n_exp", C.c_int), ("dither", _d), ("n_zern", C.c_int), ("basis", _d),
         ("coeff", _d), ("transmission", _d), ("opd_fixed", _d), ("opd_pix", _d), ("flat", _d),
-        ("prf_sigma", C.c_double),
+        ("prf_sigma", C.c_double), ("focal_length", C.c_double), ("focal_shift", C.c_double),
     ]
 
 
@@ -82,6 +82,8 @@ class _Marshalled:
         s.pixscale, s.oversample = p.pixscale, p.oversample
         s.n_lambda, s.n_src, s.n_exp, s.n_zern = len(p.lambdas), len(p.flux), len(p.dither), len(p.coeff)
         s.prf_sigma = float(getattr(p, "prf_sigma", 0.0) or 0.0)
+        s.focal_length = float(getattr(p, "focal_length", 0.0) or 0.0)
+        s.focal_shift = float(getattr(p, "focal_shift", 0.0) or 0.0)
         for k, a in self.arrs.items():
             setattr(s, k, C.cast(a.ctypes.data, _d) if a is not None else None)
         self.s = s

@@ -19,6 +19,13 @@
  *   L     = sum_e sum_p (m - d ln m)                         (Poisson likelihood, Sec. 4)
  *           + sum_p (FF_p - 1)^2 / (2 sigma^2)                 (chi^2 log prior on the pixel
  *                                                              response, Sec. 4; sigma = 0: none)
+ * In the Fresnel regime (Sec. 1: a detector slightly out of focus adds
+ * quadratic phase factors before and after the transform), with a lens of
+ * focal length f and the detector at z = f + dz, the field at detector
+ * position r (pitch pixscale * f) is
+ *   E(r) = exp(i pi |r|^2 / (lambda z)) * MFT[ exp(i pi |x|^2 (1/z - 1/f) / lambda) P ](r / z),
+ * the transform taken at angles r / z, i.e. with du = (pixscale / os) f / z;
+ * focal_length = 0 is the Fraunhofer model above.
  * and the analytic adjoint of L with respect to the Zernike coefficients, the
  * pixel OPD map, the flat field, the source fluxes and the source positions
  * (Sec. 4 takes gradients of this loss with respect to exactly these groups).
@@ -64,6 +71,8 @@ typedef struct {
     const double *opd_pix;      /* [n][n] or NULL */
     const double *flat;         /* [n_det][n_det] */
     double prf_sigma;           /* s.d. of the chi^2 prior on the flat field about 1; 0 = no prior */
+    double focal_length;        /* f > 0: Fresnel regime with the detector at f + focal_shift; 0: Fraunhofer */
+    double focal_shift;
 } orc_problem;
 
 static const double TWO_PI = 6.283185307179586476925286766559;
@@ -73,6 +82,40 @@ static double coord(int i, int n, double spacing) { return ((double)i - 0.5 * (d
 
 void orc_coords(int n, double spacing, double *out) {
     for (int i = 0; i < n; ++i) out[i] = coord(i, n, spacing);
+}
+
+/* Angle step of the transform's output samples: pixscale / os, times f / z in the Fresnel regime. */
+static double mft_du(const orc_problem *q) {
+    double du = q->pixscale / q->oversample;
+    if (q->focal_length > 0) du *= q->focal_length / (q->focal_length + q->focal_shift);
+    return du;
+}
+
+/* Fresnel factor before the transform: P *= exp(sgn i pi |x|^2 (1/z - 1/f) / lambda). */
+static void fresnel_pre(const orc_problem *q, double lam, int sgn, cplx *P) {
+    if (!(q->focal_length > 0)) return;
+    int n = q->n_pupil;
+    double dx = q->diameter / n, f = q->focal_length, z = f + q->focal_shift;
+    for (int ny = 0; ny < n; ++ny)
+        for (int nx = 0; nx < n; ++nx) {
+            double x = coord(nx, n, dx), y = coord(ny, n, dx);
+            double ph = sgn * (0.5 * TWO_PI) * (x * x + y * y) * (1.0 / z - 1.0 / f) / lam;
+            P[(size_t)ny * n + nx] *= cos(ph) + I * sin(ph);
+        }
+}
+
+/* Fresnel factor after the transform: E *= exp(sgn i pi |r|^2 / (lambda z)), r the detector
+ * position of each output sample (pitch pixscale * f / os). */
+static void fresnel_post(const orc_problem *q, double lam, int sgn, cplx *E) {
+    if (!(q->focal_length > 0)) return;
+    int no = q->n_det * q->oversample;
+    double f = q->focal_length, z = f + q->focal_shift, dr = q->pixscale * f / q->oversample;
+    for (int ky = 0; ky < no; ++ky)
+        for (int kx = 0; kx < no; ++kx) {
+            double rx = coord(kx, no, dr), ry = coord(ky, no, dr);
+            double ph = sgn * (0.5 * TWO_PI) * (rx * rx + ry * ry) / (lam * z);
+            E[(size_t)ky * no + kx] *= cos(ph) + I * sin(ph);
+        }
 }
 
 /* Two-sided MFT matrix (Sec. 3, Soummer et al. 2007):
@@ -226,7 +269,9 @@ void orc_psf_field(const orc_problem *q, int l, int s, int e, cplx *E) {
     cplx *P = (cplx *)malloc((size_t)n * n * sizeof(cplx));
     orc_opd(q, opd);
     orc_phasor(q, opd, l, s, e, P);
-    orc_mft(n, q->diameter / n, no, q->pixscale / q->oversample, q->lambdas[l], P, E);
+    fresnel_pre(q, q->lambdas[l], 1, P);
+    orc_mft(n, q->diameter / n, no, mft_du(q), q->lambdas[l], P, E);
+    fresnel_post(q, q->lambdas[l], 1, E);
     free(opd);
     free(P);
 }
@@ -248,7 +293,9 @@ static void intensity_src(const orc_problem *q, cplx **mats, double *I_src) {
             double *Ie = I_src + ((size_t)e * q->n_src + s) * nq;
             for (int l = 0; l < q->n_lambda; ++l) {
                 orc_phasor(q, opd, l, s, e, P);
+                fresnel_pre(q, q->lambdas[l], 1, P);
                 mft_with(mats[l], n, no, P, E);
+                fresnel_post(q, q->lambdas[l], 1, E);
                 double w = q->weights[l] / wn;
                 for (size_t k = 0; k < nq; ++k) Ie[k] += w * (creal(E[k]) * creal(E[k]) + cimag(E[k]) * cimag(E[k]));
             }
@@ -263,7 +310,7 @@ static cplx **make_mats(const orc_problem *q) {
     cplx **mats = (cplx **)malloc((size_t)q->n_lambda * sizeof(cplx *));
     for (int l = 0; l < q->n_lambda; ++l) {
         mats[l] = (cplx *)malloc((size_t)no * n * sizeof(cplx));
-        orc_mft_matrix(no, n, q->diameter / n, q->pixscale / q->oversample, q->lambdas[l], mats[l]);
+        orc_mft_matrix(no, n, q->diameter / n, mft_du(q), q->lambdas[l], mats[l]);
     }
     return mats;
 }
@@ -413,6 +460,7 @@ long orc_loss_grad(const orc_problem *q, const int *data, double *loss, double *
     cplx *P = (cplx *)malloc(npx * sizeof(cplx));
     cplx *E = (cplx *)malloc(nq * sizeof(cplx));
     cplx *GP = (cplx *)malloc(npx * sizeof(cplx));
+    cplx *PF = (cplx *)malloc(npx * sizeof(cplx));
     orc_opd(q, opd);
     if (g_pos) memset(g_pos, 0, (size_t)2 * q->n_src * sizeof(double));
     for (int e = 0; e < q->n_exp; ++e)
@@ -420,13 +468,19 @@ long orc_loss_grad(const orc_problem *q, const int *data, double *loss, double *
             for (int l = 0; l < q->n_lambda; ++l) {
                 double lam = q->lambdas[l], c = 2.0 * (q->weights[l] / wn) * q->flux[s];
                 orc_phasor(q, opd, l, s, e, P);
-                mft_with(mats[l], n, no, P, E);
+                memcpy(PF, P, npx * sizeof(cplx));
+                fresnel_pre(q, lam, 1, PF);
+                mft_with(mats[l], n, no, PF, E);
+                fresnel_post(q, lam, 1, E);
                 for (int ky = 0; ky < no; ++ky)
                     for (int kx = 0; kx < no; ++kx) {
                         size_t p = (size_t)(ky / os) * nd + (kx / os);
                         E[(size_t)ky * no + kx] *= c * q->flat[p] * g_m[(size_t)e * np + p];
                     }
+                /* adjoints of the three linear steps, in reverse order */
+                fresnel_post(q, lam, -1, E);
                 mft_adjoint_with(mats[l], n, no, E, GP);
+                fresnel_pre(q, lam, -1, GP);
                 double k = TWO_PI / lam, sx = 0, sy = 0;
                 for (int ny = 0; ny < n; ++ny)
                     for (int nx = 0; nx < n; ++nx) {
@@ -453,6 +507,7 @@ long orc_loss_grad(const orc_problem *q, const int *data, double *loss, double *
     free(P);
     free(E);
     free(GP);
+    free(PF);
     free(I_src);
     free(B_src);
     free(model);
@@ -468,7 +523,7 @@ long orc_loss_grad(const orc_problem *q, const int *data, double *loss, double *
 void orc_model_at(const orc_problem *q, int n_pix, const int *e_idx, const int *p_idx, double *out) {
     int n = q->n_pupil, nd = q->n_det, os = q->oversample, no = nd * os;
     size_t npx = (size_t)n * n;
-    double dx = q->diameter / n, du = q->pixscale / os, wn = weight_norm(q);
+    double dx = q->diameter / n, du = mft_du(q), wn = weight_norm(q);
     double *opd = (double *)malloc(npx * sizeof(double));
     cplx *P = (cplx *)malloc(npx * sizeof(cplx));
     cplx *ax = (cplx *)malloc((size_t)n * sizeof(cplx)), *ay = (cplx *)malloc((size_t)n * sizeof(cplx));
@@ -482,6 +537,7 @@ void orc_model_at(const orc_problem *q, int n_pix, const int *e_idx, const int *
                 if (!any) continue;
                 double lam = q->lambdas[l], sc = sqrt(dx * du / lam), w = q->weights[l] / wn;
                 orc_phasor(q, opd, l, s, e, P);
+                fresnel_pre(q, lam, 1, P);
                 for (int i = 0; i < n_pix; ++i) {
                     if (e_idx[i] != e) continue;
                     int py = p_idx[i] / nd, px = p_idx[i] % nd;
@@ -500,6 +556,12 @@ void orc_model_at(const orc_problem *q, int n_pix, const int *e_idx, const int *
                                 cplx row = 0;
                                 for (int nx = 0; nx < n; ++nx) row += P[(size_t)ny * n + nx] * ax[nx];
                                 E += ay[ny] * row;
+                            }
+                            if (q->focal_length > 0) { /* the factor after the transform */
+                                double f = q->focal_length, z = f + q->focal_shift, dr = q->pixscale * f / os;
+                                double rx = coord(kx, no, dr), ry = coord(ky, no, dr);
+                                double ph = (0.5 * TWO_PI) * (rx * rx + ry * ry) / (lam * z);
+                                E *= cos(ph) + I * sin(ph);
                             }
                             acc += creal(E) * creal(E) + cimag(E) * cimag(E);
                         }

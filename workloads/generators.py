@@ -215,6 +215,8 @@ class Problem:
     opd_pix: Optional[np.ndarray]  # (n, n) m, or None when the pixel OPD map is not a parameter
     flat: np.ndarray  # (n_det, n_det)
     prf_sigma: float = 0.0  # s.d. of the chi^2 prior on the flat field about 1 (0: no prior)
+    focal_length: float = 0.0  # m; > 0: Fresnel regime with the detector at focal_length + focal_shift
+    focal_shift: float = 0.0  # m
 
     @property
     def n_lambda(self) -> int:
