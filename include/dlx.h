@@ -105,8 +105,20 @@ typedef struct {
                                 (Nd + 2 max|dither_px|)^2 detector and image e is the Nd x Nd
                                 window of it shifted by dither_px[e] (Sec. 3's integer dithers),
                                 which equals the model with params->dither = dither_px * pixscale
-                                at 1/n_exp of the MFT work; params->dither is then not read.
+                                (times f / z in the Fresnel regime below: the pointing offset that
+                                moves the image by whole pixels) at 1/n_exp of the MFT work;
+                                params->dither is then not read.
                                 Not accepted by the server (dlx_submit). */
+    double focal_length_m;   /* 0: Fraunhofer regime (the detector at focus; the model is angular).
+                                > 0: Fresnel regime (Sec. 1: a detector slightly out of focus adds
+                                quadratic phase factors before and after the transform): a lens of
+                                focal length f with the detector at z = f + focal_shift_m > 0;
+                                pixscale_rad is then the detector pitch over f.  The pupil gets
+                                exp(i pi |x|^2 (1/z - 1/f) / lambda) and the transform is taken at
+                                the angles r / z of the detector positions r; the factor after the
+                                transform, exp(i pi |r|^2 / (lambda z)), has modulus 1 and leaves
+                                every intensity, so it is not applied. */
+    double focal_shift_m;    /* z - f, metres; must be 0 when focal_length_m is 0 */
 } dlx_mft_desc;
 
 /* Parameters and fixed inputs of one evaluation.  Device pointers. */

@@ -53,6 +53,9 @@ class MftDesc:
     # integer-pixel dithers [n_exp][2] (x, y): one MFT per source on a larger detector, images
     # as windows of it (Sec. 3); None = dithers are the params' angles
     dither_px: Optional[Sequence] = None
+    # Fresnel regime: lens focal length and detector offset from focus (metres); 0, 0 = Fraunhofer
+    focal_length_m: float = 0.0
+    focal_shift_m: float = 0.0
 
     def to_c(self):
         lam = (C.c_double * len(self.lambdas))(*[float(x) for x in self.lambdas])
@@ -65,7 +68,8 @@ class MftDesc:
         d = N.MftDesc(self.n_pupil, self.diameter_m, self.n_det, self.pixscale_rad, self.oversample,
                       len(self.lambdas), C.cast(lam, C.POINTER(C.c_double)), self.n_src, self.n_exp, self.n_zern,
                       int(self.precision), self.psf_chunk, self.workspace_limit_bytes, float(self.prf_prior_sigma),
-                      C.cast(dpx, C.POINTER(C.c_int32)) if dpx is not None else None)
+                      C.cast(dpx, C.POINTER(C.c_int32)) if dpx is not None else None, float(self.focal_length_m),
+                      float(self.focal_shift_m))
         return d, (lam, dpx)
 
 
@@ -91,9 +95,14 @@ class Plan:
 
 
 def integer_dithers(p) -> Optional[list]:
-    """The problem's dithers in whole pixels [(x, y), ...] when every one is an integer number of
-    pixels (to 1e-6 of a pixel), else None."""
-    k = np.asarray(p.dither, dtype=np.float64) / p.pixscale
+    """The problem's dithers in whole pixels [(x, y), ...] when every one moves the image by an
+    integer number of pixels (to 1e-6 of a pixel), else None.  A pointing offset theta moves the
+    image by theta / pixscale pixels at focus and by theta z / (f pixscale) in the Fresnel regime."""
+    step = p.pixscale
+    f = float(getattr(p, "focal_length", 0.0) or 0.0)
+    if f > 0:
+        step *= f / (f + float(getattr(p, "focal_shift", 0.0) or 0.0))
+    k = np.asarray(p.dither, dtype=np.float64) / step
     r = np.rint(k)
     return r.astype(int).tolist() if np.all(np.abs(k - r) <= 1e-6) else None
 
@@ -102,6 +111,8 @@ def desc_from_problem(p, precision=DLX_BF16X3, crop: bool = False, **kw) -> MftD
     """MftDesc of a workloads.Problem-like object (duck-typed).  crop=True computes integer-pixel
     dithers as windows of one larger detector (raises if a dither is not a whole pixel)."""
     kw.setdefault("prf_prior_sigma", float(getattr(p, "prf_sigma", 0.0) or 0.0))
+    kw.setdefault("focal_length_m", float(getattr(p, "focal_length", 0.0) or 0.0))
+    kw.setdefault("focal_shift_m", float(getattr(p, "focal_shift", 0.0) or 0.0))
     if crop:
         dpx = integer_dithers(p)
         if dpx is None:

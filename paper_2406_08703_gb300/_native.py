@@ -28,7 +28,7 @@ class MftDesc(C.Structure):
                 ("oversample", C.c_int), ("n_lambda", C.c_int), ("lambda_m", C.POINTER(C.c_double)),
                 ("n_src", C.c_int), ("n_exp", C.c_int), ("n_zern", C.c_int), ("precision", C.c_int),
                 ("psf_chunk", C.c_int), ("workspace_limit_bytes", C.c_size_t), ("prf_prior_sigma", C.c_double),
-                ("dither_px", C.POINTER(C.c_int32))]
+                ("dither_px", C.POINTER(C.c_int32)), ("focal_length_m", C.c_double), ("focal_shift_m", C.c_double)]
 
 
 class Params(C.Structure):

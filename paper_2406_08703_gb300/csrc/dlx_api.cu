@@ -128,6 +128,11 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (d->n_src > kMaxSrc) return fail(DLX_ERR_RANGE, "at most 32 sources per plan");
     if (!(d->prf_prior_sigma >= 0) || !std::isfinite(d->prf_prior_sigma))
         return fail(DLX_ERR_INVALID_ARG, "prf_prior_sigma must be finite and >= 0");
+    if (!(d->focal_length_m >= 0) || !std::isfinite(d->focal_length_m) || !std::isfinite(d->focal_shift_m) ||
+        (d->focal_length_m == 0 && d->focal_shift_m != 0) ||
+        (d->focal_length_m > 0 && !(d->focal_length_m + d->focal_shift_m > 0)))
+        return fail(DLX_ERR_INVALID_ARG, "focal_length_m >= 0 (0 with focal_shift_m 0) and focal_length_m + "
+                                         "focal_shift_m > 0");
     // integer-pixel dithers: one MFT per source on a detector wide enough for every window
     int delta = 0;
     if (d->dither_px) {
@@ -179,7 +184,9 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->planes = fmt_planes(p->fmt);
     p->esz = fmt_esize(p->fmt);
     p->dx = d->diameter_m / p->ni;
-    p->du = d->pixscale_rad / p->os;
+    double du_scale;
+    fresnel_terms(d, &du_scale, &p->chirp);
+    p->du = d->pixscale_rad / p->os * du_scale;
 
     if (p->prec != DLX_FP32_SIMT) {
         std::string why;

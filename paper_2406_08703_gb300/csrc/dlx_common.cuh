@@ -324,7 +324,8 @@ struct dlx_plan {
     int *crop = nullptr;
     std::vector<int32_t> dither_px;  // host copy of desc.dither_px ([nei][2]) or empty
     int prec, fmt, planes, esz;
-    double dx, du;
+    double dx, du;   // du: the transform's angle step, (pixscale / os) f / z in the Fresnel regime
+    double chirp = 0.0;  // Fresnel regime: (1/z - 1/f) / 2, the pupil's quadratic phase is 2 pi chirp |x|^2 / lambda
     int G = 1;       // partial-intensity planes of the intensity contraction
     // tensor-core forms: the intensity contraction's work split for R active slots
     // (s2[R-1]); offsets and pieces live in s2_table (see s2_schedule.h)
@@ -407,6 +408,19 @@ struct KScope {
     KScope(dlx_plan *p, int cls, int n, cudaStream_t st);
     ~KScope();
 };
+
+// Fresnel regime of a descriptor (focal_length_m > 0, detector at z = f + focal_shift_m): the
+// factor on the transform's angle step (f / z) and the pupil chirp coefficient (1/z - 1/f) / 2;
+// (1, 0) in the Fraunhofer regime.
+inline void fresnel_terms(const dlx_mft_desc *d, double *du_scale, double *chirp) {
+    *du_scale = 1.0;
+    *chirp = 0.0;
+    if (d->focal_length_m > 0) {
+        const double f = d->focal_length_m, z = f + d->focal_shift_m;
+        *du_scale = f / z;
+        *chirp = 0.5 * (1.0 / z - 1.0 / f);
+    }
+}
 
 // ---- plan construction (dlx_api.cu)
 int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out);

@@ -144,7 +144,7 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
 __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__restrict__ opd, float2 *npart,
                            float *tpart, unsigned int *ncount, float *pscale, float *wnorm,
                            const double *__restrict__ lam, int B, int nse, int ne, int ni, double dx,
-                           float2 *__restrict__ tilt, unsigned int *qmax, unsigned int *gmax) {
+                           float2 *__restrict__ tilt, unsigned int *qmax, unsigned int *gmax, double chirp) {
     pdl_trigger();
     pdl_wait();
     extern __shared__ float c_sh[];
@@ -187,7 +187,9 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
         }
         __syncthreads();
     }
-    // tilt factors of this slot's PSFs: tilt[r B + bl][axis][n]
+    // tilt factors of this slot's PSFs: tilt[r B + bl][axis][n]; in the Fresnel regime each also
+    // carries its axis' share of the quadratic phase exp(i pi |x|^2 (1/z - 1/f) / lambda), the
+    // factor before the transform (separable: x^2 + y^2), chirp = (1/z - 1/f) / 2
     {
         const float *pos = slot_ptr(prm, PPOS, r), *dith = slot_ptr(prm, PDITHER, r);
         const double cN = 0.5 * (ni - 1);
@@ -196,7 +198,8 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
             const int bl = i / (2 * ni), ax = (i / ni) & 1, n = i - (i / ni) * ni;
             const int l = bl / nse, se = bl - l * nse, s = se / ne, e = se - s * ne;
             const double th = (double)pos[2 * s + ax] + (dith ? (double)dith[2 * e + ax] : 0.0);
-            const double t = ((double)n - cN) * dx * th / lam[l];
+            const double xn = ((double)n - cN) * dx;
+            const double t = (xn * th + chirp * xn * xn) / lam[l];
             float sn, cs;
             sincospif((float)(2.0 * (t - rint(t))), &sn, &cs);
             tl[i] = make_float2(cs, sn);
@@ -355,7 +358,7 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     const int blocks = std::max(1, std::min({work, p->sm_count * 8 / R, kNormParts}));
     cudaError_t e = launch_pdl(k_prologue, dim3(blocks, R), dim3(256), sizeof(float) * (p->nz > 0 ? p->nz : 1), st,
                                prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm,
-                               p->lam_d, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax);
+                               p->lam_d, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax, p->chirp);
     if (e != cudaSuccess) return e;
     const int groups = p->ni * (p->ldi / 8), nyl = R * p->nl;
     const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nyl - 1) / nyl));

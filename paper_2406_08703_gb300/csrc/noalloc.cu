@@ -120,7 +120,9 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     p.planes = 2;
     p.esz = 4;
     p.dx = d->diameter_m / p.ni;
-    p.du = d->pixscale_rad / p.os;
+    double du_scale;
+    dlx::fresnel_terms(d, &du_scale, &p.chirp);
+    p.du = d->pixscale_rad / p.os * du_scale;
     p.G = 1;
     p.chunk = 1;
 

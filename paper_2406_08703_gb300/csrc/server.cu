@@ -170,6 +170,8 @@ std::string bucket_key(const Req &r) {
     int hp = r.has_pix;
     put(&hp, sizeof(int));
     put(&d.prf_prior_sigma, sizeof(double));  // the plan's loss
+    put(&d.focal_length_m, sizeof(double));    // Fresnel regime
+    put(&d.focal_shift_m, sizeof(double));
     put(r.lambdas.data(), r.lambdas.size() * sizeof(double));
     return k;
 }
@@ -586,6 +588,10 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
         return fail(DLX_ERR_INVALID_ARG, "bad request shape");
     if (d.n_src > dlx::kMaxSrc) return fail(DLX_ERR_RANGE, "at most 32 sources");
     if (d.dither_px) return fail(DLX_ERR_UNSUPPORTED, "integer-pixel dither windows (dither_px) are not served");
+    if (!(d.focal_length_m >= 0) || !std::isfinite(d.focal_length_m) || !std::isfinite(d.focal_shift_m) ||
+        (d.focal_length_m == 0 && d.focal_shift_m != 0) ||
+        (d.focal_length_m > 0 && !(d.focal_length_m + d.focal_shift_m > 0)))
+        return fail(DLX_ERR_INVALID_ARG, "bad focal_length_m / focal_shift_m");
     if (!rq->transmission || !rq->weights || !rq->flux || !rq->pos || !rq->flat || !rq->data ||
         (d.n_zern > 0 && (!rq->zern_basis || !rq->zern_coeff)) || rq->n_steps < 0)
         return fail(DLX_ERR_INVALID_ARG, "missing request input");

@@ -45,7 +45,8 @@ class Server:
         lam = (C.c_double * len(p.lambdas))(*[float(x) for x in p.lambdas])
         desc = N.MftDesc(p.n_pupil, p.diameter, p.n_det, p.pixscale, p.oversample, len(p.lambdas),
                          C.cast(lam, C.POINTER(C.c_double)), len(p.flux), len(p.dither), len(p.coeff), precision, 0, 0,
-                         float(getattr(p, "prf_sigma", 0.0) or 0.0))
+                         float(getattr(p, "prf_sigma", 0.0) or 0.0), None,
+                         float(getattr(p, "focal_length", 0.0) or 0.0), float(getattr(p, "focal_shift", 0.0) or 0.0))
         arrs = dict(transmission=_f32(p.transmission), opd_fixed=_f32(p.opd_fixed),
                     zern_basis=_f32(p.basis) if len(p.coeff) else None, weights=_f32(p.weights),
                     dither=_f32(p.dither), zern_coeff=_f32(p.coeff) if len(p.coeff) else None,

@@ -48,6 +48,8 @@ def test_invalid_shapes_rejected_without_a_device(native):
     bad = [
         dict(n_pupil=1), dict(n_det=0), dict(oversample=0), dict(n_src=0), dict(n_exp=0), dict(precision=9),
         dict(diameter_m=0.0), dict(pixscale_rad=-1.0), dict(prf_prior_sigma=-0.1),
+        dict(focal_length_m=-1.0), dict(focal_shift_m=1e-3), dict(focal_length_m=1.0, focal_shift_m=-1.0),
+        dict(focal_length_m=float("nan")),
     ]
     for over in bad:
         kw = dict(n_pupil=16, diameter_m=0.1, n_det=8, pixscale_rad=1e-6, oversample=2, n_lambda=1,
@@ -63,6 +65,8 @@ def test_invalid_shapes_rejected_without_a_device(native):
     kw["prf_prior_sigma"] = 0.0
     kw["diameter_m"] = 0.1
     kw["pixscale_rad"] = 1e-6
+    kw["focal_length_m"] = 0.0
+    kw["focal_shift_m"] = 0.0
     d = native.MftDesc(**kw)
     assert lib.dlx_make_mft(C.byref(d), 0, C.byref(h)) == -6  # RANGE
     assert lib.dlx_make_mft(None, 0, C.byref(h)) == -1

@@ -280,3 +280,48 @@ def test_integer_dither_windows_match_angles_on_the_gpu():
     for k in a["grads"]:
         if b["grads"][k] is not None:
             assert rel_l2(a["grads"][k], b["grads"][k]) < 1e-5, k
+
+
+def _defocused(problem, data_seed, edge_rad, f=1.2):
+    """Fresnel regime (Sec. 1) with the detector moved from focus so that the quadratic phase reaches
+    about edge_rad at the pupil edge at the shortest wavelength; data from the oracle."""
+    R = 0.5 * problem.diameter
+    dz = edge_rad * float(np.min(problem.lambdas)) * f * f / (np.pi * R * R)
+    problem.focal_length, problem.focal_shift = f, dz
+    return W.poisson_counts(oracle.forward(problem), data_seed)
+
+
+@pytest.mark.parametrize("case", range(2))
+@pytest.mark.parametrize("form", FORMS)
+def test_fresnel_regime(case, form):
+    """The detector out of focus (quadratic phase factors around the transform, Sec. 1): model, PSF,
+    loss and every gradient against the oracle's chirp-transform-chirp definition."""
+    truth, _, start = fit_problem("custom", seed=40 + case, **RAGGED[case])
+    data = _defocused(truth, 41 + case, 3.0)
+    start.focal_length, start.focal_shift = truth.focal_length, truth.focal_shift
+    err = compare(gpu_eval(start, data, form), oracle_eval(start, data), form)
+    print(form, case, err)
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_fresnel_binary_reduced(form):
+    """Binary-star shapes (256^2 pupil, 1024^2 grid, 4 wavelengths) with a strong defocus: about 30
+    rad of quadratic phase at the pupil edge, the chirp carried in FP64-reduced tilt tables."""
+    truth, _, start = fit_problem("binary", n_lambda=4)
+    data = _defocused(truth, 45, 30.0)
+    start.focal_length, start.focal_shift = truth.focal_length, truth.focal_shift
+    err = compare(gpu_eval(start, data, form, want_psf=False), oracle_eval(start, data), form)
+    print(form, err)
+
+
+def test_fresnel_with_integer_dither_windows():
+    """Fresnel regime and integer-dither windows together, against the oracle.  Out of focus a
+    pointing offset theta moves the image by theta z / f, so the dithers that move it by whole
+    pixels are k pixscale f / z."""
+    start, _ = _crop_problem(0, 50)
+    k = np.rint(start.dither / start.pixscale)
+    _defocused(start, 51, 4.0)
+    start.dither = k * start.pixscale * start.focal_length / (start.focal_length + start.focal_shift)
+    data = W.poisson_counts(oracle.forward(start), 52)
+    err = compare(gpu_eval(start, data, "bf16x3", crop=True), oracle_eval(start, data), "bf16x3")
+    print(err)
