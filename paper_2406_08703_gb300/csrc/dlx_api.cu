@@ -309,6 +309,18 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx * p->gsplit);
     if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(float2) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
+    if (p->ns > 8) {
+        // two-pass binning: one thread per pixel for the model pass, a (blocks x source) grid for
+        // the flux gradients, each about 8 blocks of 256 threads per SM
+        p->bin_a_blocks = (int)std::max<size_t>(1, std::min<size_t>((npi + 255) / 256, (size_t)p->sm_count * 8 / R_max));
+        p->bin_b_blocks = (int)std::max<size_t>(
+            1, std::min<size_t>((npi + 255) / 256, ((size_t)p->sm_count * 8 + (size_t)p->ns * R_max - 1) /
+                                                      ((size_t)p->ns * R_max)));
+        if (e == cudaSuccess) e = plan_alloc(p, &p->red_a, sizeof(double) * p->bin_a_blocks * R_max);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->red_b, sizeof(double) * p->bin_b_blocks * kMaxSrc * R_max);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->fcount, sizeof(unsigned int) * kMaxSrc * R_max);
+        if (e == cudaSuccess) e = cudaMemset(p->fcount, 0, sizeof(unsigned int) * kMaxSrc * R_max);
+    }
     if (e == cudaSuccess && p->prec == DLX_FP32_SIMT)
         e = plan_alloc(p, &p->pos_part, sizeof(double) * 2 * Bt * p->gsplit);
     if (e == cudaSuccess) e = plan_alloc(p, &p->npart, sizeof(float2) * kNormParts * R_max);

@@ -354,8 +354,13 @@ struct dlx_plan {
     float *model_tmp = nullptr;// [R][nei][ndi*ndi]
     float *gphi = nullptr;     // [R*B][ni*ni] (2 pi / lambda) dL/dphase
     float2 *gopd = nullptr;    // [R][ni*ni] g_OPD as a compensated (hi, lo) FP32 pair
-    double *red = nullptr;     // [R][red_blocks][1 + 8] reduction partials
+    double *red = nullptr;     // [R][red_blocks][1 + kMaxSrc] reduction partials (up to 8 sources)
     int red_blocks = 0;
+    // more than 8 sources: two-pass binning (k_bin_model, k_flux_grad) and its partials
+    int bin_a_blocks = 1, bin_b_blocks = 1;
+    double *red_a = nullptr;   // [R][bin_a_blocks] loss partials
+    double *red_b = nullptr;   // [R][kMaxSrc][bin_b_blocks] flux-gradient partials
+    unsigned int *fcount = nullptr;  // [R][kMaxSrc] finished flux-gradient blocks (reset by the last)
     double *pos_part = nullptr;// CUDA-core form: [R*B][gsplit][2] position-moment partials
     float2 *zpart = nullptr;   // [R][n_zern][ceil(Ni^2 / 64)] Zernike-gradient partials (compensated pairs)
     unsigned int *bcount = nullptr;  // [R] blocks of the binning pass done (reset by the last one)

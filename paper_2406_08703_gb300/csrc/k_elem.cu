@@ -589,6 +589,281 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
     }
 }
 
+// ---------------------------------------------------------------------------
+// Many sources (more than 8): the same quantities in two passes, so that no thread
+// holds per-source arrays (the one-pass kernel above needs about 7 registers per
+// source and drops to one block per SM at 32 sources).
+//   k_bin_model:  one thread per pixel; for every image the source loop forms
+//                 m = FF sum_s F_s B_s, the NLL, GI = FF g_m and dL/dFF; the loss
+//                 partials go to red_a[r][blk] and the slot's last block sums them.
+//   k_flux_grad:  grid (blocks, source, slot); dL/dF_s = sum_{e,p} GI_e[p] B_{s,e}[p]
+//                 re-reading the source's planes, and the FP16 form's bounds Q_{s,e};
+//                 partials in red_b[r][s][blk], the last block of each (r, s) sums them.
+
+// For NC planes at once (plane indices rse[k], block corners (ry[k], rx[k]), skipped
+// where on[k] is false): v[k] = the sum over the os x os block and the G partial-
+// intensity planes, vm[k] = the largest single oversampled value of the block.  The
+// plane loop is outermost and the NC blocks innermost (unrolled), so every load of
+// one plane is in flight at once.
+template <int OS, int NC>
+__device__ __forceinline__ void bin_blocks(const float *__restrict__ Is, int G, size_t Rnse, size_t plane, int no,
+                                           int os, const size_t (&rse)[NC], const int (&ry)[NC], const int (&rx)[NC],
+                                           const bool (&on)[NC], float (&v)[NC], float (&vm)[NC]) {
+    if constexpr (OS == 0) {
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            v[k] = 0.f;
+            vm[k] = 0.f;
+            if (!on[k]) continue;
+            for (int a = 0; a < os; ++a)
+                for (int c = 0; c < os; ++c) {
+                    float q = 0.f;
+                    for (int gg = 0; gg < G; ++gg)
+                        q += __ldg(Is + ((size_t)gg * Rnse + rse[k]) * plane + (size_t)(ry[k] + a) * no +
+                                   (size_t)rx[k] + c);
+                    v[k] += q;
+                    vm[k] = fmaxf(vm[k], q);
+                }
+        }
+    } else {
+        float q[NC][OS][OS];
+#pragma unroll
+        for (int k = 0; k < NC; ++k)
+#pragma unroll
+            for (int a = 0; a < OS; ++a)
+#pragma unroll
+                for (int c = 0; c < OS; ++c) q[k][a][c] = 0.f;
+        for (int gg = 0; gg < G; ++gg) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                if (!on[k]) continue;
+                const float *src = Is + ((size_t)gg * Rnse + rse[k]) * plane + (size_t)ry[k] * no + rx[k];
+                if constexpr (OS == 4) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const float4 t = __ldg((const float4 *)(src + (size_t)a * no));
+                        q[k][a][0] += t.x;
+                        q[k][a][1] += t.y;
+                        q[k][a][2] += t.z;
+                        q[k][a][3] += t.w;
+                    }
+                } else if constexpr (OS == 2) {
+                    const float2 t0 = __ldg((const float2 *)src), t1 = __ldg((const float2 *)(src + no));
+                    q[k][0][0] += t0.x;
+                    q[k][0][1] += t0.y;
+                    q[k][1][0] += t1.x;
+                    q[k][1][1] += t1.y;
+                } else {
+                    q[k][0][0] += __ldg(src);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            v[k] = 0.f;
+            vm[k] = 0.f;
+#pragma unroll
+            for (int a = 0; a < OS; ++a) {
+                float rsum = 0.f;
+#pragma unroll
+                for (int c = 0; c < OS; ++c) {
+                    rsum += q[k][a][c];
+                    vm[k] = fmaxf(vm[k], q[k][a][c]);
+                }
+                v[k] += rsum;
+            }
+        }
+    }
+}
+
+// blocks handled together per thread: fewer for the wide oversampled blocks (registers)
+template <int OS>
+__host__ __device__ constexpr int bin_chunk() {
+    return OS == 4 ? 2 : OS == 2 ? 4 : OS == 1 ? 8 : 1;
+}
+
+template <int OS>
+__global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
+                                                   int ne, int nd, int os_rt, int no, int nem,
+                                                   const int2 *__restrict__ crop, DevParams prm,
+                                                   const int32_t *__restrict__ data, size_t dstride,
+                                                   float *__restrict__ model, size_t mstride, float *__restrict__ GI,
+                                                   DevGrads g, double *red_a, unsigned long long *clamped,
+                                                   double *loss, unsigned int *bcount, float prf_inv,
+                                                   const float *__restrict__ cot) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ df sh[32];
+    __shared__ bool s_last;
+    const int np = nd * nd, r = blockIdx.y, os = OS > 0 ? OS : os_rt;
+    const float *flux = slot_ptr(prm, PFLUX, r), *flat = slot_ptr(prm, PFLAT, r);
+    const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
+    float *mod = model + (size_t)r * mstride;
+    float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
+    const float *ct = cot ? cot + (size_t)r * ne * np : nullptr;
+    const bool grad = dat || ct;
+    const size_t plane = (size_t)no * no;
+    df acc[1] = {{0.f, 0.f}};
+    unsigned long long nclamp = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        const int py = p / nd, px = p % nd;
+        const float ff = flat[p];
+        float dff = 0.f;
+        for (int e = 0; e < ne; ++e) {
+            const int2 oc = crop ? __ldg(crop + e) : make_int2(0, 0);
+            const int em = crop ? 0 : e;
+            const int ry = (py + oc.y) * os, rx = (px + oc.x) * os;
+            float btot = 0.f;
+            constexpr int NC = bin_chunk<OS>();
+            for (int s0 = 0; s0 < ns; s0 += NC) {
+                size_t rse[NC];
+                int rys[NC], rxs[NC];
+                bool on[NC];
+                float v[NC], vm[NC];
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    on[k] = s0 + k < ns;
+                    rse[k] = (size_t)r * nse + (size_t)(s0 + k) * nem + em;
+                    rys[k] = ry;
+                    rxs[k] = rx;
+                }
+                bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm);
+#pragma unroll
+                for (int k = 0; k < NC; ++k)
+                    if (on[k]) btot = fmaf(__ldg(flux + s0 + k), v[k], btot);
+            }
+            const float m = ff * btot;
+            mod[(size_t)e * np + p] = m;
+            if (grad) {
+                float gm;
+                if (ct) {
+                    gm = __ldg(ct + (size_t)e * np + p);
+                } else {
+                    const float d = (float)dat[(size_t)e * np + p];
+                    float mc = m;
+                    if (!(mc >= 1e-30f)) {
+                        mc = 1e-30f;
+                        ++nclamp;
+                    }
+                    acc[0] = df_add(acc[0], m);
+                    acc[0] = df_add(acc[0], -d * logf(mc));
+                    gm = 1.f - d / mc;
+                }
+                GI[((size_t)r * ne + e) * np + p] = ff * gm;
+                dff = fmaf(gm, btot, dff);
+            }
+        }
+        if (dat && !ct && prf_inv > 0.f) {
+            // chi^2 log prior on the pixel response (Sec. 4): (FF - 1)^2 / (2 sigma^2)
+            const float dev = ff - 1.f;
+            acc[0] = df_add(acc[0], 0.5f * prf_inv * dev * dev);
+            dff = fmaf(prf_inv, dev, dff);
+        }
+        if (grad && dflat) dflat[p] = dff;
+    }
+    if (!grad) return;
+    block_sum<1>(acc, sh);
+    if (dat && nclamp) atomicAdd(clamped, nclamp);
+    if (threadIdx.x == 0) {
+        red_a[(size_t)r * gridDim.x + blockIdx.x] = df_to_double(acc[0]);
+        __threadfence();
+        s_last = atomicAdd(bcount + r, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(red_a + (size_t)r * gridDim.x + b);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            if (loss) loss[r] = v;
+            bcount[r] = 0;  // ready for the next launch
+        }
+    }
+}
+
+template <int OS>
+__global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is, int G, int Rnse, int nse, int ne,
+                                                   int nd, int os_rt, int no, int nem,
+                                                   const int2 *__restrict__ crop, const float *__restrict__ GI,
+                                                   DevGrads g, double *red_b, unsigned int *fcount,
+                                                   unsigned int *qmax) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ df sh[32];
+    __shared__ unsigned int s_q[kQShared];
+    __shared__ bool s_last;
+    const int np = nd * nd, s = blockIdx.y, r = blockIdx.z, os = OS > 0 ? OS : os_rt;
+    const size_t plane = (size_t)no * no;
+    if (qmax)
+        for (int i = threadIdx.x; i < kQShared; i += blockDim.x) s_q[i] = 0u;
+    __syncthreads();
+    df acc[1] = {{0.f, 0.f}};
+    // block-uniform trip count, so the warp-wide maxima below see every lane
+    for (int p0 = blockIdx.x * blockDim.x; p0 < np; p0 += gridDim.x * blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        const bool valid = p < np;
+        const int py = valid ? p / nd : 0, px = valid ? p % nd : 0;
+        constexpr int NC = bin_chunk<OS>();
+        for (int e0 = 0; e0 < ne; e0 += NC) {
+            size_t rse[NC];
+            int rys[NC], rxs[NC], ems[NC];
+            bool on[NC];
+            float v[NC], vm[NC], gi[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                const int e = e0 + k;
+                on[k] = valid && e < ne;
+                const int2 oc = (crop && e < ne) ? __ldg(crop + e) : make_int2(0, 0);
+                ems[k] = crop ? 0 : e;
+                rse[k] = (size_t)r * nse + (size_t)s * nem + ems[k];
+                rys[k] = (py + oc.y) * os;
+                rxs[k] = (px + oc.x) * os;
+                gi[k] = on[k] ? __ldg(GI + ((size_t)r * ne + e) * np + p) : 0.f;
+            }
+            bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm);
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                if (e0 + k >= ne) break;
+                if (on[k]) acc[0] = df_add(acc[0], gi[k] * v[k]);
+                if (qmax) {
+                    float qv = fabsf(gi[k]) * sqrtf(vm[k]);
+                    if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
+                    for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
+                    if ((threadIdx.x & 31) == 0) {
+                        const int em = ems[k];
+                        if (em < kQShared)
+                            atomicMax(s_q + em, __float_as_uint(qv));
+                        else
+                            atomicMax(qmax + (size_t)r * nse + s * nem + em, __float_as_uint(qv));
+                    }
+                }
+            }
+        }
+    }
+    block_sum<1>(acc, sh);  // its barriers also publish s_q
+    if (qmax)
+        for (int k = threadIdx.x; k < nem && k < kQShared; k += blockDim.x)
+            atomicMax(qmax + (size_t)r * nse + s * nem + k, s_q[k]);
+    const size_t slot = (size_t)r * kMaxSrc + s;
+    if (threadIdx.x == 0) {
+        red_b[slot * gridDim.x + blockIdx.x] = df_to_double(acc[0]);
+        __threadfence();
+        s_last = atomicAdd(fcount + slot, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(red_b + slot * gridDim.x + b);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            if (g.p[GFLUX]) g.p[GFLUX][(size_t)r * g.s[GFLUX] + s] = (float)v;
+            fcount[slot] = 0;  // ready for the next launch
+        }
+    }
+}
+
 // GI[r][P] = sum_e GIimg[r][e][P - crop[e]] over the images whose window holds big-detector pixel P
 // (fixed order over e)
 __global__ void k_crop_fold(const float *__restrict__ gimg, const int2 *__restrict__ crop, int ne, int nd,
@@ -620,13 +895,33 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
                           p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data, data_stride, model,
                           model_stride, gi, gg, p->red, p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot);
     };
-    // per-source registers for up to 8 sources, or up to kMaxSrc
     cudaError_t e;
-    if (p->ns <= 8)
+    if (p->ns <= 8) {
+        // one pass, per-source registers
         e = p->os == 4 ? go(k_bin_nll<4, 8>) : p->os == 2 ? go(k_bin_nll<2, 8>) : go(k_bin_nll<0, 8>);
-    else
-        e = p->os == 4 ? go(k_bin_nll<4, kMaxSrc>) : p->os == 2 ? go(k_bin_nll<2, kMaxSrc>) : go(k_bin_nll<0, kMaxSrc>);
+    } else {
+        auto ga = [&](auto kern) {
+            return launch_pdl(kern, dim3(p->bin_a_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse,
+                              p->ns, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data,
+                              data_stride, model, model_stride, gi, gg, p->red_a, p->clamped, loss, p->bcount,
+                              p->prf_inv, p->cot);
+        };
+        e = p->os == 4 ? ga(k_bin_model<4>) : p->os == 2 ? ga(k_bin_model<2>) : p->os == 1 ? ga(k_bin_model<1>)
+                                                                                         : ga(k_bin_model<0>);
+        const bool grad = data || p->cot;
+        if (e == cudaSuccess && grad && (gg.p[GFLUX] || p->qmax)) {
+            ++ks.n;
+            auto gb = [&](auto kern) {
+                return launch_pdl(kern, dim3(p->bin_b_blocks, p->ns, R), dim3(256), 0, st, p->Is, p->G,
+                                  R * p->nse, p->nse, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop,
+                                  (const float *)gi, gg, p->red_b, p->fcount, p->qmax);
+            };
+            e = p->os == 4 ? gb(k_flux_grad<4>) : p->os == 2 ? gb(k_flux_grad<2>) : p->os == 1 ? gb(k_flux_grad<1>)
+                                                                                             : gb(k_flux_grad<0>);
+        }
+    }
     if (e != cudaSuccess || !p->crop || !(data || p->cot)) return e;
+    ++ks.n;
     // integer dithers: the adjoint weights of the big detector are the images' weights placed back
     // at their windows and summed
     const size_t nb = (size_t)p->nd * p->nd;

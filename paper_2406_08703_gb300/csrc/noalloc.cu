@@ -138,6 +138,8 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     }
     const size_t np = (size_t)p.nd * p.nd, nq = (size_t)p.no * p.no, npx = (size_t)p.ni * p.ni;
     p.red_blocks = std::max(1, std::min((int)((np + 255) / 256), p.sm_count * 2));
+    // more than 8 sources: the model pass of the two-pass binning (no loss, no partials)
+    p.bin_a_blocks = std::max(1, std::min((int)((np + 255) / 256), p.sm_count * 8));
 
     // bytes this call needs, with the same carve as below (alignment included)
     Carve need{nullptr};

@@ -185,12 +185,15 @@ def test_adam_matches_numpy():
     assert rel_l2(T["th"].cpu().numpy(), th) < 1e-6
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16x3", "bf16x4"])
-def test_many_sources_with_prf_prior(form):
-    """12 sources (past the 8-source register path), 2 dithered exposures, and the chi^2 prior
-    on the pixel response (Sec. 4), element by element against the oracle."""
-    _, data, start = fit_problem("custom", seed=14, n_pupil=48, n_det=24, oversample=2, n_lambda=2, n_src=12,
-                                 n_exp=2, dither_px=0.5, obscuration=0.2, grating=True, n_zern_max=6)
+@pytest.mark.parametrize("os_", [1, 2, 3, 4])
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "bf16x4", "f16x3"])
+def test_many_sources_with_prf_prior(form, os_):
+    """12 sources (the two-pass binning beyond 8 sources) at every oversample path, 2 dithered
+    exposures, and the chi^2 prior on the pixel response (Sec. 4), element by element against the
+    oracle."""
+    _, data, start = fit_problem("custom", seed=14, n_pupil=48, n_det=24 if os_ < 3 else 14, oversample=os_,
+                                 n_lambda=2, n_src=12, n_exp=2, dither_px=0.5, obscuration=0.2, grating=True,
+                                 n_zern_max=6)
     start.prf_sigma = 0.1
     start.flat = W.flat_field(start.n_det, 0.1, 15)
     err = compare(gpu_eval(start, data, form, want_psf=False), oracle_eval(start, data), form)
@@ -243,6 +246,9 @@ CROP = [
          dither=[(0, 0), (5, -1), (-2, 4)]),
     # os 3 (the generic binning path), a single undithered image
     dict(n_pupil=24, n_det=10, oversample=3, n_lambda=2, n_src=1, n_exp=1, n_zern_max=3, dither=[(0, 0)]),
+    # ten sources (the two-pass binning) with windows, os 4
+    dict(n_pupil=32, n_det=12, oversample=4, n_lambda=2, n_src=10, n_exp=3, n_zern_max=4,
+         dither=[(0, 0), (2, -1), (-1, 2)]),
 ]
 
 
