@@ -215,6 +215,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     // planes of the balanced split of (tile, wavelength) jobs, for every count of
     // active slots.
     std::vector<int> s2_host;
+    std::vector<uint8_t> used_host;
     if (p->prec == DLX_FP32_SIMT) {
         long units = (long)((p->no + 63) / 64) * ((p->no + 63) / 64) * p->nse;
         p->G = (int)std::min<long>(p->nl, std::max<long>(1, (2L * p->sm_count + units - 1) / units));
@@ -239,7 +240,15 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
             s2_host.insert(s2_host.end(), off.begin(), off.end());
             while (s2_host.size() % 4) s2_host.push_back(0);
             sp.pcs = (long)s2_host.size();
-            for (const S2Piece &q : pcs) s2_host.insert(s2_host.end(), {q.seg, q.l0, q.l1, q.pz});
+            // the readers take each segment's plane count from a table, so no piece clears the
+            // planes its segment leaves unwritten
+            sp.used = (long)used_host.size();
+            used_host.resize(used_host.size() + (size_t)nseg, 0);
+            for (const S2Piece &q : pcs) {
+                s2_host.insert(s2_host.end(), {q.seg, q.l0, q.l1, (q.pz & 0xffff) | (kS2None << 16)});
+                uint8_t &u = used_host[sp.used + q.seg];
+                u = (uint8_t)std::max<int>(u, (q.pz & 0xffff) + 1);
+            }
             sp.nct = nct;
             sp.npieces = (int)pcs.size();
         }
@@ -338,6 +347,8 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
         e = plan_alloc(p, &p->s2_table, sizeof(int) * s2_host.size());
         if (e == cudaSuccess)
             e = cudaMemcpy(p->s2_table, s2_host.data(), sizeof(int) * s2_host.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->s2_used, used_host.size());
+        if (e == cudaSuccess) e = cudaMemcpy(p->s2_used, used_host.data(), used_host.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess) e = plan_alloc(p, &p->err, sizeof(int32_t));
     if (e == cudaSuccess) e = plan_alloc(p, &p->clamped, sizeof(unsigned long long));

@@ -332,7 +332,12 @@ struct dlx_plan {
     struct S2Split {
         long off = 0, pcs = 0;  // int offsets of the CTA offsets and of the pieces
         int nct = 0, npieces = 0;
+        long used = 0;          // byte offset of this split's plane counts in s2_used
     };
+    // tensor-core forms: planes each (slot, source, exposure) x 128-tile segment of the
+    // intensity writes, [rse][tile] per split; the binning and PSF passes read only those
+    // planes (the split clears none of the others).  NULL: every one of the G planes.
+    uint8_t *s2_used = nullptr;
     std::vector<S2Split> s2;
     int *s2_table = nullptr;
     int chunk = 1;   // PSFs per adjoint pass
@@ -413,6 +418,11 @@ struct KScope {
     KScope(dlx_plan *p, int cls, int n, cudaStream_t st);
     ~KScope();
 };
+
+// the plane-count table of the intensity split for R active slots, or NULL (every plane)
+inline const uint8_t *s2_used_of(const dlx_plan *p, int R) {
+    return (p->s2_used && R >= 1 && R <= (int)p->s2.size()) ? p->s2_used + p->s2[R - 1].used : nullptr;
+}
 
 // Fresnel regime of a descriptor (focal_length_m > 0, detector at z = f + focal_shift_m): the
 // factor on the transform's angle step (f / z) and the pupil chirp coefficient (1/z - 1/f) / 2;

@@ -393,7 +393,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                           int no, int nem, const int2 *__restrict__ crop, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount,
-                          float prf_inv, const float *__restrict__ cot) {
+                          float prf_inv, const float *__restrict__ cot, const uint8_t *__restrict__ used, int tn) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[32 * (1 + MAXS)];
@@ -437,6 +437,8 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                 bmax[s] = 0.f;
                 if (s < ns && valid) {
                     const size_t rse = (size_t)r * nse + s * nem + em;
+                    // planes this block's 128-tile of the intensity holds (os divides 128)
+                    const int ng = (used && OS > 0) ? used[rse * tn * tn + (ry >> 7) * tn + (rx >> 7)] : G;
                     float v = 0.f, vm = 0.f;
                     if constexpr (OS == 4 || OS == 2) {
                         // per-subpixel sums over the planes; each plane's OS row loads are in flight together
@@ -445,7 +447,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                         for (int a = 0; a < OS; ++a)
 #pragma unroll
                             for (int c = 0; c < OS; ++c) q[a][c] = 0.f;
-                        for (int gg = 0; gg < G; ++gg) {
+                        for (int gg = 0; gg < ng; ++gg) {
                             const float *src = Is + ((size_t)gg * Rnse + rse) * plane + (size_t)ry * no + rx;
                             if constexpr (OS == 4) {
                                 float4 t[4];
@@ -480,7 +482,8 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                         for (int a = 0; a < os; ++a)
                             for (int c = 0; c < os; ++c) {
                                 float q = 0.f;
-                                for (int gg = 0; gg < G; ++gg)
+                                const int ngq = used ? used[rse * tn * tn + ((ry + a) >> 7) * tn + ((rx + c) >> 7)] : G;
+                                for (int gg = 0; gg < ngq; ++gg)
                                     q += __ldg(Is + ((size_t)gg * Rnse + rse) * plane + (size_t)(ry + a) * no +
                                                (size_t)rx + c);
                                 v += q;
@@ -608,7 +611,8 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
 template <int OS, int NC>
 __device__ __forceinline__ void bin_blocks(const float *__restrict__ Is, int G, size_t Rnse, size_t plane, int no,
                                            int os, const size_t (&rse)[NC], const int (&ry)[NC], const int (&rx)[NC],
-                                           const bool (&on)[NC], float (&v)[NC], float (&vm)[NC]) {
+                                           const bool (&on)[NC], float (&v)[NC], float (&vm)[NC],
+                                           const uint8_t *__restrict__ used, int tn) {
     if constexpr (OS == 0) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
@@ -618,7 +622,9 @@ __device__ __forceinline__ void bin_blocks(const float *__restrict__ Is, int G, 
             for (int a = 0; a < os; ++a)
                 for (int c = 0; c < os; ++c) {
                     float q = 0.f;
-                    for (int gg = 0; gg < G; ++gg)
+                    const int ngq =
+                        used ? used[rse[k] * tn * tn + ((ry[k] + a) >> 7) * tn + ((rx[k] + c) >> 7)] : G;
+                    for (int gg = 0; gg < ngq; ++gg)
                         q += __ldg(Is + ((size_t)gg * Rnse + rse[k]) * plane + (size_t)(ry[k] + a) * no +
                                    (size_t)rx[k] + c);
                     v[k] += q;
@@ -633,10 +639,17 @@ __device__ __forceinline__ void bin_blocks(const float *__restrict__ Is, int G, 
             for (int a = 0; a < OS; ++a)
 #pragma unroll
                 for (int c = 0; c < OS; ++c) q[k][a][c] = 0.f;
-        for (int gg = 0; gg < G; ++gg) {
+        // planes each block's 128-tile of the intensity holds (os divides 128)
+        int ng[NC], ngmax = 0;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            ng[k] = !on[k] ? 0 : used ? used[rse[k] * tn * tn + (ry[k] >> 7) * tn + (rx[k] >> 7)] : G;
+            ngmax = max(ngmax, ng[k]);
+        }
+        for (int gg = 0; gg < ngmax; ++gg) {
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
-                if (!on[k]) continue;
+                if (gg >= ng[k]) continue;
                 const float *src = Is + ((size_t)gg * Rnse + rse[k]) * plane + (size_t)ry[k] * no + rx[k];
                 if constexpr (OS == 4) {
 #pragma unroll
@@ -690,7 +703,8 @@ __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is,
                                                    float *__restrict__ model, size_t mstride, float *__restrict__ GI,
                                                    DevGrads g, double *red_a, unsigned long long *clamped,
                                                    double *loss, unsigned int *bcount, float prf_inv,
-                                                   const float *__restrict__ cot) {
+                                                   const float *__restrict__ cot, const uint8_t *__restrict__ used,
+                                                   int tn) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
@@ -727,7 +741,7 @@ __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is,
                     rys[k] = ry;
                     rxs[k] = rx;
                 }
-                bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm);
+                bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm, used, tn);
 #pragma unroll
                 for (int k = 0; k < NC; ++k)
                     if (on[k]) btot = fmaf(__ldg(flux + s0 + k), v[k], btot);
@@ -787,7 +801,7 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
                                                    int nd, int os_rt, int no, int nem,
                                                    const int2 *__restrict__ crop, const float *__restrict__ GI,
                                                    DevGrads g, double *red_b, unsigned int *fcount,
-                                                   unsigned int *qmax) {
+                                                   unsigned int *qmax, const uint8_t *__restrict__ used, int tn) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
@@ -821,7 +835,7 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
                 rxs[k] = (px + oc.x) * os;
                 gi[k] = on[k] ? __ldg(GI + ((size_t)r * ne + e) * np + p) : 0.f;
             }
-            bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm);
+            bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm, used, tn);
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
                 if (e0 + k >= ne) break;
@@ -890,10 +904,13 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     if (g) gg = *g;
     KScope ks(p, KC_BIN, 1, st);
     float *gi = p->crop ? p->GIimg : p->GI;
+    const uint8_t *used = s2_used_of(p, R);
+    const int tn = (p->no + 127) / 128;
     auto go = [&](auto kern) {
         return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse, p->ns,
                           p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data, data_stride, model,
-                          model_stride, gi, gg, p->red, p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot);
+                          model_stride, gi, gg, p->red, p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot,
+                          used, tn);
     };
     cudaError_t e;
     if (p->ns <= 8) {
@@ -904,7 +921,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
             return launch_pdl(kern, dim3(p->bin_a_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse,
                               p->ns, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data,
                               data_stride, model, model_stride, gi, gg, p->red_a, p->clamped, loss, p->bcount,
-                              p->prf_inv, p->cot);
+                              p->prf_inv, p->cot, used, tn);
         };
         e = p->os == 4 ? ga(k_bin_model<4>) : p->os == 2 ? ga(k_bin_model<2>) : p->os == 1 ? ga(k_bin_model<1>)
                                                                                          : ga(k_bin_model<0>);
@@ -914,7 +931,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
             auto gb = [&](auto kern) {
                 return launch_pdl(kern, dim3(p->bin_b_blocks, p->ns, R), dim3(256), 0, st, p->Is, p->G,
                                   R * p->nse, p->nse, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop,
-                                  (const float *)gi, gg, p->red_b, p->fcount, p->qmax);
+                                  (const float *)gi, gg, p->red_b, p->fcount, p->qmax, used, tn);
             };
             e = p->os == 4 ? gb(k_flux_grad<4>) : p->os == 2 ? gb(k_flux_grad<2>) : p->os == 1 ? gb(k_flux_grad<1>)
                                                                                              : gb(k_flux_grad<0>);
@@ -933,18 +950,22 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
 // psf[e][y][x] = sum_s F_s sum_g Is[g][s nem + em][y + oy][x + ox]: the image-sized oversampled
 // intensity of image e (the window at crop[e] of the source's one plane with integer dithers)
 __global__ void k_psf_out(const float *__restrict__ Is, int G, int nse, int ns, int nem, int no, int ne, int noi,
-                          const int2 *__restrict__ crop, int os, const float *__restrict__ flux, float *__restrict__ psf) {
+                          const int2 *__restrict__ crop, int os, const float *__restrict__ flux, float *__restrict__ psf,
+                          const uint8_t *__restrict__ used, int tn) {
     const size_t plane = (size_t)no * no, iplane = (size_t)noi * noi, total = (size_t)ne * iplane;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
         const int e = (int)(i / iplane);
         const int y = (int)(i % iplane / noi), x = (int)(i % noi);
         const int2 o = crop ? __ldg(crop + e) : make_int2(0, 0);
         const int em = crop ? 0 : e;
-        const size_t q = (size_t)(y + o.y * os) * no + x + o.x * os;
+        const int yy = y + o.y * os, xx = x + o.x * os;
+        const size_t q = (size_t)yy * no + xx;
         float v = 0.f;
         for (int s = 0; s < ns; ++s) {
             float vs = 0.f;
-            for (int gg = 0; gg < G; ++gg) vs += Is[((size_t)gg * nse + s * nem + em) * plane + q];
+            const size_t rse = (size_t)s * nem + em;
+            const int ng = used ? used[rse * tn * tn + (yy >> 7) * tn + (xx >> 7)] : G;
+            for (int gg = 0; gg < ng; ++gg) vs += Is[((size_t)gg * nse + rse) * plane + q];
             v = fmaf(flux[s], vs, v);
         }
         psf[i] = v;
@@ -957,7 +978,7 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
     KScope ks(p, KC_BIN, 1, st);
     k_psf_out<<<blocks, 256, 0, st>>>(p->Is, p->G, p->nse, p->ns, p->ne, p->no, p->nei, noi, (const int2 *)p->crop,
-                                      p->os, prm.p[PFLUX], psf);
+                                      p->os, prm.p[PFLUX], psf, s2_used_of(p, 1), (p->no + 127) / 128);
     return cudaGetLastError();
 }
 
