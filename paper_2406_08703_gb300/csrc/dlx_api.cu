@@ -215,6 +215,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     // planes of the balanced split of (tile, wavelength) jobs, for every count of
     // active slots.
     std::vector<int> s2_host;
+    std::vector<int> fold_host;
     std::vector<uint8_t> used_host;
     if (p->prec == DLX_FP32_SIMT) {
         long units = (long)((p->no + 63) / 64) * ((p->no + 63) / 64) * p->nse;
@@ -240,15 +241,19 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
             s2_host.insert(s2_host.end(), off.begin(), off.end());
             while (s2_host.size() % 4) s2_host.push_back(0);
             sp.pcs = (long)s2_host.size();
-            // the readers take each segment's plane count from a table, so no piece clears the
-            // planes its segment leaves unwritten
-            sp.used = (long)used_host.size();
-            used_host.resize(used_host.size() + (size_t)nseg, 0);
+            // the segments written in more than one plane are folded into plane 0 after the
+            // contraction, so no piece clears the planes its segment leaves unwritten
+            std::vector<int> used((size_t)nseg, 0);
             for (const S2Piece &q : pcs) {
                 s2_host.insert(s2_host.end(), {q.seg, q.l0, q.l1, (q.pz & 0xffff) | (kS2None << 16)});
-                uint8_t &u = used_host[sp.used + q.seg];
-                u = (uint8_t)std::max<int>(u, (q.pz & 0xffff) + 1);
+                used[q.seg] = std::max(used[q.seg], (q.pz & 0xffff) + 1);
             }
+            sp.used = (long)used_host.size();
+            for (int sg = 0; sg < nseg; ++sg) used_host.push_back((uint8_t)used[sg]);
+            sp.fold = (long)fold_host.size() / 2;
+            for (int sg = 0; sg < nseg; ++sg)
+                if (used[sg] > 1) fold_host.insert(fold_host.end(), {sg, used[sg]});
+            sp.nfold = (int)(fold_host.size() / 2 - sp.fold);
             sp.nct = nct;
             sp.npieces = (int)pcs.size();
         }
@@ -349,6 +354,11 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
             e = cudaMemcpy(p->s2_table, s2_host.data(), sizeof(int) * s2_host.size(), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = plan_alloc(p, &p->s2_used, used_host.size());
         if (e == cudaSuccess) e = cudaMemcpy(p->s2_used, used_host.data(), used_host.size(), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !fold_host.empty()) {
+            e = plan_alloc(p, &p->s2_fold, sizeof(int) * fold_host.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(p->s2_fold, fold_host.data(), sizeof(int) * fold_host.size(), cudaMemcpyHostToDevice);
+        }
     }
     if (e == cudaSuccess) e = plan_alloc(p, &p->err, sizeof(int32_t));
     if (e == cudaSuccess) e = plan_alloc(p, &p->clamped, sizeof(unsigned long long));
@@ -386,6 +396,7 @@ int eval_forward(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
         DLX_CU(simt_forward(p, R, st), "simt forward");
     } else {
         DLX_CU(tc_forward(p, R, st), "tensor-core forward");
+        if (folds_planes(p)) DLX_CU(launch_plane_fold(p, R, st), "plane fold");
     }
     return DLX_OK;
 }

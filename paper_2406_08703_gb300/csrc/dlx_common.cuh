@@ -332,11 +332,16 @@ struct dlx_plan {
     struct S2Split {
         long off = 0, pcs = 0;  // int offsets of the CTA offsets and of the pieces
         int nct = 0, npieces = 0;
+        long fold = 0;          // int2 offset of this split's fold list in s2_fold
+        int nfold = 0;          // segments written in more than one plane
         long used = 0;          // byte offset of this split's plane counts in s2_used
     };
-    // tensor-core forms: planes each (slot, source, exposure) x 128-tile segment of the
-    // intensity writes, [rse][tile] per split; the binning and PSF passes read only those
-    // planes (the split clears none of the others).  NULL: every one of the G planes.
+    // Tensor-core forms: the split clears none of the planes a segment leaves unwritten.
+    // Up to 8 sources the one-pass binning and the PSF output read each segment's planes as
+    // counted in s2_used ([rse][tile] per split); beyond 8, where the binning reads the
+    // intensity twice, k_plane_fold first adds the (segment, planes written) pairs of
+    // s2_fold into plane 0 and the readers take plane 0 alone.
+    int *s2_fold = nullptr;
     uint8_t *s2_used = nullptr;
     std::vector<S2Split> s2;
     int *s2_table = nullptr;
@@ -419,9 +424,14 @@ struct KScope {
     ~KScope();
 };
 
-// the plane-count table of the intensity split for R active slots, or NULL (every plane)
-inline const uint8_t *s2_used_of(const dlx_plan *p, int R) {
-    return (p->s2_used && R >= 1 && R <= (int)p->s2.size()) ? p->s2_used + p->s2[R - 1].used : nullptr;
+// the tensor-core split's planes are folded into plane 0 after stage 2 (more than 8 sources)
+inline bool folds_planes(const dlx_plan *p) { return p->prec != DLX_FP32_SIMT && p->ns > 8; }
+// partial-intensity planes a reader adds (at most; see plane_counts)
+inline int planes_to_read(const dlx_plan *p) { return folds_planes(p) ? 1 : p->G; }
+// the plane-count table for R active slots where the readers need it, else NULL
+inline const uint8_t *plane_counts(const dlx_plan *p, int R) {
+    return (!folds_planes(p) && p->s2_used && R >= 1 && R <= (int)p->s2.size()) ? p->s2_used + p->s2[R - 1].used
+                                                                                  : nullptr;
 }
 
 // Fresnel regime of a descriptor (focal_length_m > 0, detector at z = f + focal_shift_m): the
@@ -457,6 +467,8 @@ cudaError_t launch_fisher_gram(const float *J, int n, size_t npix, const float *
                                double *work, cudaStream_t st);
 // cot = 1 - d / max(m, 1e-30) elementwise (dlx_nll_cotangent)
 cudaError_t launch_nll_cotangent(const float *m, const int32_t *d, size_t n, float *cot, cudaStream_t st);
+// adds the stage-2 split's extra planes into plane 0 (tensor-core forms; no-op otherwise)
+cudaError_t launch_plane_fold(dlx_plan *p, int R, cudaStream_t st);
 // a = (a - b) * c elementwise (the central difference of dlx_model_jvp)
 cudaError_t launch_scaled_diff(float *a, const float *b, size_t n, float c, cudaStream_t st);
 // Adam over R packed slots of n parameters each; group k of a slot is

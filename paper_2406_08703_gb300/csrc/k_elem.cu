@@ -603,16 +603,14 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
 //                 re-reading the source's planes, and the FP16 form's bounds Q_{s,e};
 //                 partials in red_b[r][s][blk], the last block of each (r, s) sums them.
 
-// For NC planes at once (plane indices rse[k], block corners (ry[k], rx[k]), skipped
-// where on[k] is false): v[k] = the sum over the os x os block and the G partial-
-// intensity planes, vm[k] = the largest single oversampled value of the block.  The
-// plane loop is outermost and the NC blocks innermost (unrolled), so every load of
-// one plane is in flight at once.
+// For NC oversampled blocks at once (top-left samples src[k] of the first partial-
+// intensity plane, skipped where on[k] is false): v[k] = the sum over the os x os block
+// and the G planes (gstride floats apart), vm[k] = the largest single oversampled value
+// of the block.  The plane loop is outermost and the NC blocks innermost (unrolled), so
+// every load of one plane is in flight at once.
 template <int OS, int NC>
-__device__ __forceinline__ void bin_blocks(const float *__restrict__ Is, int G, size_t Rnse, size_t plane, int no,
-                                           int os, const size_t (&rse)[NC], const int (&ry)[NC], const int (&rx)[NC],
-                                           const bool (&on)[NC], float (&v)[NC], float (&vm)[NC],
-                                           const uint8_t *__restrict__ used, int tn) {
+__device__ __forceinline__ void bin_blocks(const float *const (&src)[NC], int G, size_t gstride, int no, int os,
+                                           const bool (&on)[NC], float (&v)[NC], float (&vm)[NC]) {
     if constexpr (OS == 0) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
@@ -622,11 +620,7 @@ __device__ __forceinline__ void bin_blocks(const float *__restrict__ Is, int G, 
             for (int a = 0; a < os; ++a)
                 for (int c = 0; c < os; ++c) {
                     float q = 0.f;
-                    const int ngq =
-                        used ? used[rse[k] * tn * tn + ((ry[k] + a) >> 7) * tn + ((rx[k] + c) >> 7)] : G;
-                    for (int gg = 0; gg < ngq; ++gg)
-                        q += __ldg(Is + ((size_t)gg * Rnse + rse[k]) * plane + (size_t)(ry[k] + a) * no +
-                                   (size_t)rx[k] + c);
+                    for (int gg = 0; gg < G; ++gg) q += __ldg(src[k] + gg * gstride + (size_t)a * no + c);
                     v[k] += q;
                     vm[k] = fmaxf(vm[k], q);
                 }
@@ -639,35 +633,29 @@ __device__ __forceinline__ void bin_blocks(const float *__restrict__ Is, int G, 
             for (int a = 0; a < OS; ++a)
 #pragma unroll
                 for (int c = 0; c < OS; ++c) q[k][a][c] = 0.f;
-        // planes each block's 128-tile of the intensity holds (os divides 128)
-        int ng[NC], ngmax = 0;
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            ng[k] = !on[k] ? 0 : used ? used[rse[k] * tn * tn + (ry[k] >> 7) * tn + (rx[k] >> 7)] : G;
-            ngmax = max(ngmax, ng[k]);
-        }
-        for (int gg = 0; gg < ngmax; ++gg) {
+#pragma unroll 1
+        for (int gg = 0; gg < G; ++gg) {
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
-                if (gg >= ng[k]) continue;
-                const float *src = Is + ((size_t)gg * Rnse + rse[k]) * plane + (size_t)ry[k] * no + rx[k];
+                if (!on[k]) continue;
+                const float *sp = src[k] + gg * gstride;
                 if constexpr (OS == 4) {
 #pragma unroll
                     for (int a = 0; a < 4; ++a) {
-                        const float4 t = __ldg((const float4 *)(src + (size_t)a * no));
+                        const float4 t = __ldg((const float4 *)(sp + (size_t)a * no));
                         q[k][a][0] += t.x;
                         q[k][a][1] += t.y;
                         q[k][a][2] += t.z;
                         q[k][a][3] += t.w;
                     }
                 } else if constexpr (OS == 2) {
-                    const float2 t0 = __ldg((const float2 *)src), t1 = __ldg((const float2 *)(src + no));
+                    const float2 t0 = __ldg((const float2 *)sp), t1 = __ldg((const float2 *)(sp + no));
                     q[k][0][0] += t0.x;
                     q[k][0][1] += t0.y;
                     q[k][1][0] += t1.x;
                     q[k][1][1] += t1.y;
                 } else {
-                    q[k][0][0] += __ldg(src);
+                    q[k][0][0] += __ldg(sp);
                 }
             }
         }
@@ -703,48 +691,50 @@ __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is,
                                                    float *__restrict__ model, size_t mstride, float *__restrict__ GI,
                                                    DevGrads g, double *red_a, unsigned long long *clamped,
                                                    double *loss, unsigned int *bcount, float prf_inv,
-                                                   const float *__restrict__ cot, const uint8_t *__restrict__ used,
-                                                   int tn) {
+                                                   const float *__restrict__ cot) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
+    __shared__ float s_flux[kMaxSrc];
     __shared__ bool s_last;
     const int np = nd * nd, r = blockIdx.y, os = OS > 0 ? OS : os_rt;
     const float *flux = slot_ptr(prm, PFLUX, r), *flat = slot_ptr(prm, PFLAT, r);
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) s_flux[i] = flux[i];
+    __syncthreads();
     const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
     float *mod = model + (size_t)r * mstride;
     float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
     const float *ct = cot ? cot + (size_t)r * ne * np : nullptr;
     const bool grad = dat || ct;
-    const size_t plane = (size_t)no * no;
+    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane, sstride = (size_t)nem * plane;
+    const float *slot = Is + (size_t)r * nse * plane;
     df acc[1] = {{0.f, 0.f}};
     unsigned long long nclamp = 0;
+    constexpr int NC = bin_chunk<OS>();
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
         const int py = p / nd, px = p % nd;
         const float ff = flat[p];
         float dff = 0.f;
         for (int e = 0; e < ne; ++e) {
             const int2 oc = crop ? __ldg(crop + e) : make_int2(0, 0);
-            const int em = crop ? 0 : e;
-            const int ry = (py + oc.y) * os, rx = (px + oc.x) * os;
+            // first source's plane of this image, at the block's top-left sample
+            const float *base = slot + (size_t)(crop ? 0 : e) * plane + (size_t)((py + oc.y) * os) * no +
+                                (size_t)(px + oc.x) * os;
             float btot = 0.f;
-            constexpr int NC = bin_chunk<OS>();
+#pragma unroll 1
             for (int s0 = 0; s0 < ns; s0 += NC) {
-                size_t rse[NC];
-                int rys[NC], rxs[NC];
+                const float *src[NC];
                 bool on[NC];
                 float v[NC], vm[NC];
 #pragma unroll
                 for (int k = 0; k < NC; ++k) {
                     on[k] = s0 + k < ns;
-                    rse[k] = (size_t)r * nse + (size_t)(s0 + k) * nem + em;
-                    rys[k] = ry;
-                    rxs[k] = rx;
+                    src[k] = base + (size_t)(s0 + k) * sstride;
                 }
-                bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm, used, tn);
+                bin_blocks<OS, NC>(src, G, gstride, no, os, on, v, vm);
 #pragma unroll
                 for (int k = 0; k < NC; ++k)
-                    if (on[k]) btot = fmaf(__ldg(flux + s0 + k), v[k], btot);
+                    if (on[k]) btot = fmaf(s_flux[s0 + k], v[k], btot);
             }
             const float m = ff * btot;
             mod[(size_t)e * np + p] = m;
@@ -801,27 +791,29 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
                                                    int nd, int os_rt, int no, int nem,
                                                    const int2 *__restrict__ crop, const float *__restrict__ GI,
                                                    DevGrads g, double *red_b, unsigned int *fcount,
-                                                   unsigned int *qmax, const uint8_t *__restrict__ used, int tn) {
+                                                   unsigned int *qmax) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
     __shared__ unsigned int s_q[kQShared];
     __shared__ bool s_last;
     const int np = nd * nd, s = blockIdx.y, r = blockIdx.z, os = OS > 0 ? OS : os_rt;
-    const size_t plane = (size_t)no * no;
+    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane;
+    const float *src0 = Is + ((size_t)r * nse + (size_t)s * nem) * plane;  // this source's first plane
+    const float *gslot = GI + (size_t)r * ne * np;
     if (qmax)
         for (int i = threadIdx.x; i < kQShared; i += blockDim.x) s_q[i] = 0u;
     __syncthreads();
     df acc[1] = {{0.f, 0.f}};
+    constexpr int NC = bin_chunk<OS>();
     // block-uniform trip count, so the warp-wide maxima below see every lane
     for (int p0 = blockIdx.x * blockDim.x; p0 < np; p0 += gridDim.x * blockDim.x) {
         const int p = p0 + threadIdx.x;
         const bool valid = p < np;
         const int py = valid ? p / nd : 0, px = valid ? p % nd : 0;
-        constexpr int NC = bin_chunk<OS>();
+#pragma unroll 1
         for (int e0 = 0; e0 < ne; e0 += NC) {
-            size_t rse[NC];
-            int rys[NC], rxs[NC], ems[NC];
+            const float *src[NC];
             bool on[NC];
             float v[NC], vm[NC], gi[NC];
 #pragma unroll
@@ -829,13 +821,11 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
                 const int e = e0 + k;
                 on[k] = valid && e < ne;
                 const int2 oc = (crop && e < ne) ? __ldg(crop + e) : make_int2(0, 0);
-                ems[k] = crop ? 0 : e;
-                rse[k] = (size_t)r * nse + (size_t)s * nem + ems[k];
-                rys[k] = (py + oc.y) * os;
-                rxs[k] = (px + oc.x) * os;
-                gi[k] = on[k] ? __ldg(GI + ((size_t)r * ne + e) * np + p) : 0.f;
+                src[k] = src0 + (size_t)(crop ? 0 : e) * plane + (size_t)((py + oc.y) * os) * no +
+                         (size_t)(px + oc.x) * os;
+                gi[k] = on[k] ? __ldg(gslot + (size_t)e * np + p) : 0.f;
             }
-            bin_blocks<OS, NC>(Is, G, Rnse, plane, no, os, rse, rys, rxs, on, v, vm, used, tn);
+            bin_blocks<OS, NC>(src, G, gstride, no, os, on, v, vm);
 #pragma unroll
             for (int k = 0; k < NC; ++k) {
                 if (e0 + k >= ne) break;
@@ -845,7 +835,7 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
                     if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
                     for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
                     if ((threadIdx.x & 31) == 0) {
-                        const int em = ems[k];
+                        const int em = crop ? 0 : e0 + k;
                         if (em < kQShared)
                             atomicMax(s_q + em, __float_as_uint(qv));
                         else
@@ -878,6 +868,36 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
     }
 }
 
+// Partial-intensity planes of the tensor-core split: the few (slot, source, exposure)
+// x 128-tile segments whose wavelengths were cut over several CTAs (fold[i] = (segment,
+// planes written)) are added into plane 0 in plane order, so every later reader takes
+// plane 0 alone.  Grid: (segments, 4) blocks stepping over the tile's samples.
+__global__ void k_plane_fold(float *__restrict__ Is, const int2 *__restrict__ fold, int tn, int no, size_t Rnse) {
+    pdl_trigger();
+    pdl_wait();
+    const int2 f = __ldg(fold + blockIdx.x);
+    const int tt = tn * tn, rse = f.x / tt, tile = f.x % tt;
+    const int m0 = (tile / tn) * 128, n0 = (tile % tn) * 128;
+    const int rows = min(128, no - m0), cols = min(128, no - n0);
+    const size_t plane = (size_t)no * no;
+    float *p0 = Is + (size_t)rse * plane;
+    for (int i = blockIdx.y * blockDim.x + threadIdx.x; i < rows * cols; i += gridDim.y * blockDim.x) {
+        const size_t o = (size_t)(m0 + i / cols) * no + n0 + i % cols;
+        float v = p0[o];
+        for (int gg = 1; gg < f.y; ++gg) v += p0[gg * Rnse * plane + o];
+        p0[o] = v;
+    }
+}
+
+cudaError_t launch_plane_fold(dlx_plan *p, int R, cudaStream_t st) {
+    if (p->s2.empty() || R < 1 || R > (int)p->s2.size()) return cudaSuccess;
+    const dlx_plan::S2Split &sp = p->s2[R - 1];
+    if (sp.nfold == 0) return cudaSuccess;
+    KScope ks(p, KC_BIN, 1, st);
+    return launch_pdl(k_plane_fold, dim3(sp.nfold, 4), dim3(256), 0, st, p->Is, (const int2 *)p->s2_fold + sp.fold,
+                      (p->no + 127) / 128, p->no, (size_t)R * p->nse);
+}
+
 // GI[r][P] = sum_e GIimg[r][e][P - crop[e]] over the images whose window holds big-detector pixel P
 // (fixed order over e)
 __global__ void k_crop_fold(const float *__restrict__ gimg, const int2 *__restrict__ crop, int ne, int nd,
@@ -904,13 +924,12 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     if (g) gg = *g;
     KScope ks(p, KC_BIN, 1, st);
     float *gi = p->crop ? p->GIimg : p->GI;
-    const uint8_t *used = s2_used_of(p, R);
-    const int tn = (p->no + 127) / 128;
+    const int G = planes_to_read(p);
     auto go = [&](auto kern) {
-        return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse, p->ns,
+        return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->ns,
                           p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data, data_stride, model,
                           model_stride, gi, gg, p->red, p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot,
-                          used, tn);
+                          plane_counts(p, R), (p->no + 127) / 128);
     };
     cudaError_t e;
     if (p->ns <= 8) {
@@ -918,10 +937,10 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
         e = p->os == 4 ? go(k_bin_nll<4, 8>) : p->os == 2 ? go(k_bin_nll<2, 8>) : go(k_bin_nll<0, 8>);
     } else {
         auto ga = [&](auto kern) {
-            return launch_pdl(kern, dim3(p->bin_a_blocks, R), dim3(256), 0, st, p->Is, p->G, R * p->nse, p->nse,
+            return launch_pdl(kern, dim3(p->bin_a_blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse,
                               p->ns, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data,
                               data_stride, model, model_stride, gi, gg, p->red_a, p->clamped, loss, p->bcount,
-                              p->prf_inv, p->cot, used, tn);
+                              p->prf_inv, p->cot);
         };
         e = p->os == 4 ? ga(k_bin_model<4>) : p->os == 2 ? ga(k_bin_model<2>) : p->os == 1 ? ga(k_bin_model<1>)
                                                                                          : ga(k_bin_model<0>);
@@ -929,9 +948,9 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
         if (e == cudaSuccess && grad && (gg.p[GFLUX] || p->qmax)) {
             ++ks.n;
             auto gb = [&](auto kern) {
-                return launch_pdl(kern, dim3(p->bin_b_blocks, p->ns, R), dim3(256), 0, st, p->Is, p->G,
+                return launch_pdl(kern, dim3(p->bin_b_blocks, p->ns, R), dim3(256), 0, st, p->Is, G,
                                   R * p->nse, p->nse, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop,
-                                  (const float *)gi, gg, p->red_b, p->fcount, p->qmax, used, tn);
+                                  (const float *)gi, gg, p->red_b, p->fcount, p->qmax);
             };
             e = p->os == 4 ? gb(k_flux_grad<4>) : p->os == 2 ? gb(k_flux_grad<2>) : p->os == 1 ? gb(k_flux_grad<1>)
                                                                                              : gb(k_flux_grad<0>);
@@ -977,8 +996,9 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
     const size_t total = (size_t)noi * noi * p->nei;
     int blocks = (int)std::min<size_t>((total + 255) / 256, (size_t)p->sm_count * 16);
     KScope ks(p, KC_BIN, 1, st);
-    k_psf_out<<<blocks, 256, 0, st>>>(p->Is, p->G, p->nse, p->ns, p->ne, p->no, p->nei, noi, (const int2 *)p->crop,
-                                      p->os, prm.p[PFLUX], psf, s2_used_of(p, 1), (p->no + 127) / 128);
+    k_psf_out<<<blocks, 256, 0, st>>>(p->Is, planes_to_read(p), p->nse, p->ns, p->ne, p->no, p->nei, noi,
+                                      (const int2 *)p->crop, p->os, prm.p[PFLUX], psf, plane_counts(p, 1),
+                                      (p->no + 127) / 128);
     return cudaGetLastError();
 }
 
