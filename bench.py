@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--laplace", action="store_true",
                     help="time the Laplace-approximation errors instead (Sec. 4: the likelihood Hessian over "
                          "positions, fluxes and Zernikes, inverted) on --workload (default paper)")
+    ap.add_argument("--crop", action="store_true",
+                    help="main line: compute whole-pixel dithers as windows of one larger detector per source "
+                         "(Sec. 3), as --fit and --laplace do by default")
     ap.add_argument("--no-crop", action="store_true",
                     help="--fit / --laplace: compute every image's PSFs, not windows of one larger detector per "
                          "source, even where the dithers are whole pixels")
@@ -115,6 +118,7 @@ def max_over_ranks(dist, x):
 
 
 N_LAMBDAS = 0  # set from --lambdas
+CROP = False  # set from --crop
 
 
 def make_inputs(workload, seed_offset=0):
@@ -189,7 +193,8 @@ def run_form(P, torch, workload, form, steps, warmup, device, timing=True):
     step), so the roofline's kernel time is measured inside the timed region
     without slowing the rest of it."""
     truth, start, data = make_inputs(workload)
-    plan = P.dlx_make_mft(P.desc_from_problem(start, P.PRECISIONS[form]), device=device)
+    crop = CROP and start.n_exp > 1 and P.integer_dithers(start) is not None
+    plan = P.dlx_make_mft(P.desc_from_problem(start, P.PRECISIONS[form], crop=crop), device=device)
     prm = P.params_from_problem(start, device=f"cuda:{device}")
     dt = torch.as_tensor(data, device=f"cuda:{device}")
     grads = P.empty_grads(plan)
@@ -595,9 +600,10 @@ def reference_arm(args, rank, world):
 
 
 def main():
-    global N_LAMBDAS
+    global N_LAMBDAS, CROP
     args = parse()
     N_LAMBDAS = args.lambdas
+    CROP = args.crop
     rank, world, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, rank, world)
@@ -646,7 +652,7 @@ def main():
     kt = r["kt"]
     classes = {k: v for k, v in kt.items() if isinstance(v, dict)}
     dom = r["dom"]
-    ni, no, B = info.n_pupil, info.n_out, info.n_psf
+    ni, no, B = info.n_pupil, info.n_mft_out, info.n_psf
     alg = {  # algorithmic FLOP per launch (8 per complex MAC), one launch per class per eval
         "stage1": 8.0 * B * no * ni * ni, "stage2_intensity": 8.0 * B * no * no * ni,
         "adjoint_field": 8.0 * B * no * no * ni, "adjoint_stage2T": 8.0 * B * ni * no * no,
@@ -660,10 +666,10 @@ def main():
     nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16x3sa": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
     # DRAM bytes (read + written) of the contractions of the BF16x3 form from one ncu capture of
     # this build on the 8-wavelength case (16 PSFs), scaled by the PSF count, in which their
-    # traffic grows (the adjoint 1^T splits K differently at that size and is left out); any
-    # other kernel or form has no capture of the current code
-    traffic_16 = {"stage1": 25.59e6, "stage2_intensity": 51.81e6, "adjoint_field": 129.95e6,
-                  "adjoint_stage2T": 172.03e6}
+    # traffic grows (the adjoint 1^T splits K differently at that size and is left out; stage 2
+    # has written no zero planes since, so its capture is out of date); any other kernel or
+    # form has no capture of the current code
+    traffic_16 = {"stage1": 25.59e6, "adjoint_field": 129.95e6, "adjoint_stage2T": 172.03e6}
     traffic = (traffic_16[dom] / 16 * B if (args.form == "bf16x3" and dom in traffic_16 and
                                             args.workload == "binary") else None)
     roof = None
