@@ -307,6 +307,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
             off[2 * k + 1] = delta - d->dither_px[2 * k + 1];
         }
         if (e == cudaSuccess) e = plan_alloc(p, &p->GIimg, sizeof(float) * p->nei * npi * R_max);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->Swin, sizeof(float) * np * R_max);
         if (e == cudaSuccess) e = plan_alloc(p, &p->crop, sizeof(int) * 2 * p->nei);
         if (e == cudaSuccess) e = cudaMemcpy(p->crop, off.data(), sizeof(int) * 2 * p->nei, cudaMemcpyHostToDevice);
     }
@@ -323,9 +324,9 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->gphi, sizeof(float) * Bt * npx * p->gsplit);
     if (e == cudaSuccess) e = plan_alloc(p, &p->gopd, sizeof(float2) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->red, sizeof(double) * p->red_blocks * (1 + kMaxSrc) * R_max);
-    if (p->ns > 8) {
-        // two-pass binning: one thread per pixel for the model pass, a (blocks x source) grid for
-        // the flux gradients, each about 8 blocks of 256 threads per SM
+    if (p->ns > 8 || d->dither_px) {
+        // two-pass binning (and the window passes): one thread per pixel for the model pass, a
+        // (blocks x source) grid for the flux gradients, each about 8 blocks of 256 threads per SM
         p->bin_a_blocks = (int)std::max<size_t>(1, std::min<size_t>((npi + 255) / 256, (size_t)p->sm_count * 8 / R_max));
         p->bin_b_blocks = (int)std::max<size_t>(
             1, std::min<size_t>((npi + 255) / 256, ((size_t)p->sm_count * 8 + (size_t)p->ns * R_max - 1) /

@@ -361,6 +361,7 @@ struct dlx_plan {
     float *Is = nullptr;       // [G][R*nse][no][no] per-source intensity partials
     float *GI = nullptr;       // [R][ne][nd*nd] FF * dL/dm on the MFT's detector
     float *GIimg = nullptr;    // integer dithers: [R][nei][ndi*ndi] the images' FF * dL/dm
+    float *Swin = nullptr;     // integer dithers: [R][nd*nd] sum_s F_s B_s on the big detector
     float *model_tmp = nullptr;// [R][nei][ndi*ndi]
     float *gphi = nullptr;     // [R*B][ni*ni] (2 pi / lambda) dL/dphase
     float2 *gopd = nullptr;    // [R][ni*ni] g_OPD as a compensated (hi, lo) FP32 pair
@@ -424,8 +425,9 @@ struct KScope {
     ~KScope();
 };
 
-// the tensor-core split's planes are folded into plane 0 after stage 2 (more than 8 sources)
-inline bool folds_planes(const dlx_plan *p) { return p->prec != DLX_FP32_SIMT && p->ns > 8; }
+// the tensor-core split's planes are folded into plane 0 after stage 2 (more than 8 sources,
+// or integer-dither windows)
+inline bool folds_planes(const dlx_plan *p) { return p->prec != DLX_FP32_SIMT && (p->ns > 8 || p->crop); }
 // partial-intensity planes a reader adds (at most; see plane_counts)
 inline int planes_to_read(const dlx_plan *p) { return folds_planes(p) ? 1 : p->G; }
 // the plane-count table for R active slots where the readers need it, else NULL

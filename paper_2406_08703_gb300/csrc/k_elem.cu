@@ -868,6 +868,182 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Integer-dither windows.  Every image is a window of the same per-source planes, so
+//   k_win_sum:   S[r][P] = sum_s F_s B_s[P] once on the big detector (one thread per pixel);
+//   k_win_nll:   m_e[p] = FF[p] S[p + crop[e]], the NLL, GI_e = FF g_m and dL/dFF per image
+//                pixel (loss partials as in k_bin_model);
+//   k_crop_fold: GI[P] = sum_e GI_e[P - crop[e]] (also the adjoint's weight map);
+//   k_win_flux:  dL/dF_s = sum_P GI[P] B_s[P], one pass over each source's plane, and the
+//                FP16 form's bound Q_s = max |GI| sqrt(I_s) of the weights the adjoint uses.
+template <int OS>
+__global__ void __launch_bounds__(256) k_win_sum(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
+                                                 int ndb, int os_rt, int no, DevParams prm, float *__restrict__ S) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ float s_flux[kMaxSrc];
+    const int r = blockIdx.y, os = OS > 0 ? OS : os_rt;
+    const float *flux = slot_ptr(prm, PFLUX, r);
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) s_flux[i] = flux[i];
+    __syncthreads();
+    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane, npb = (size_t)ndb * ndb;
+    const float *slot = Is + (size_t)r * nse * plane;
+    constexpr int NC = bin_chunk<OS>();
+    for (size_t P = blockIdx.x * (size_t)blockDim.x + threadIdx.x; P < npb; P += (size_t)gridDim.x * blockDim.x) {
+        const int py = (int)(P / ndb), px = (int)(P % ndb);
+        const float *base = slot + (size_t)(py * os) * no + (size_t)px * os;
+        float btot = 0.f;
+#pragma unroll 1
+        for (int s0 = 0; s0 < ns; s0 += NC) {
+            const float *src[NC];
+            bool on[NC];
+            float v[NC], vm[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                on[k] = s0 + k < ns;
+                src[k] = base + (size_t)(s0 + k) * plane;
+            }
+            bin_blocks<OS, NC>(src, G, gstride, no, os, on, v, vm);
+#pragma unroll
+            for (int k = 0; k < NC; ++k)
+                if (on[k]) btot = fmaf(s_flux[s0 + k], v[k], btot);
+        }
+        S[(size_t)r * npb + P] = btot;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_win_nll(const float *__restrict__ S, int ndb, int ne, int nd,
+                                                 const int2 *__restrict__ crop, DevParams prm,
+                                                 const int32_t *__restrict__ data, size_t dstride,
+                                                 float *__restrict__ model, size_t mstride, float *__restrict__ GI,
+                                                 DevGrads g, double *red_a, unsigned long long *clamped,
+                                                 double *loss, unsigned int *bcount, float prf_inv,
+                                                 const float *__restrict__ cot) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ df sh[32];
+    __shared__ bool s_last;
+    const int np = nd * nd, r = blockIdx.y;
+    const float *flat = slot_ptr(prm, PFLAT, r), *Sr = S + (size_t)r * ndb * ndb;
+    const int32_t *dat = data ? data + (size_t)r * dstride : nullptr;
+    float *mod = model + (size_t)r * mstride;
+    float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
+    const float *ct = cot ? cot + (size_t)r * ne * np : nullptr;
+    const bool grad = dat || ct;
+    df acc[1] = {{0.f, 0.f}};
+    unsigned long long nclamp = 0;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < np; p += gridDim.x * blockDim.x) {
+        const int py = p / nd, px = p % nd;
+        const float ff = flat[p];
+        float dff = 0.f;
+        for (int e = 0; e < ne; ++e) {
+            const int2 oc = __ldg(crop + e);
+            const float btot = __ldg(Sr + (size_t)(py + oc.y) * ndb + px + oc.x);
+            const float m = ff * btot;
+            mod[(size_t)e * np + p] = m;
+            if (grad) {
+                float gm;
+                if (ct) {
+                    gm = __ldg(ct + (size_t)e * np + p);
+                } else {
+                    const float d = (float)dat[(size_t)e * np + p];
+                    float mc = m;
+                    if (!(mc >= 1e-30f)) {
+                        mc = 1e-30f;
+                        ++nclamp;
+                    }
+                    acc[0] = df_add(acc[0], m);
+                    acc[0] = df_add(acc[0], -d * logf(mc));
+                    gm = 1.f - d / mc;
+                }
+                GI[((size_t)r * ne + e) * np + p] = ff * gm;
+                dff = fmaf(gm, btot, dff);
+            }
+        }
+        if (dat && !ct && prf_inv > 0.f) {
+            // chi^2 log prior on the pixel response (Sec. 4): (FF - 1)^2 / (2 sigma^2)
+            const float dev = ff - 1.f;
+            acc[0] = df_add(acc[0], 0.5f * prf_inv * dev * dev);
+            dff = fmaf(prf_inv, dev, dff);
+        }
+        if (grad && dflat) dflat[p] = dff;
+    }
+    if (!grad) return;
+    block_sum<1>(acc, sh);
+    if (dat && nclamp) atomicAdd(clamped, nclamp);
+    if (threadIdx.x == 0) {
+        red_a[(size_t)r * gridDim.x + blockIdx.x] = df_to_double(acc[0]);
+        __threadfence();
+        s_last = atomicAdd(bcount + r, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(red_a + (size_t)r * gridDim.x + b);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            if (loss) loss[r] = v;
+            bcount[r] = 0;  // ready for the next launch
+        }
+    }
+}
+
+template <int OS>
+__global__ void __launch_bounds__(256) k_win_flux(const float *__restrict__ Is, int G, int Rnse, int nse, int ndb,
+                                                  int os_rt, int no, const float *__restrict__ GI, DevGrads g,
+                                                  double *red_b, unsigned int *fcount, unsigned int *qmax) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ df sh[32];
+    __shared__ unsigned int s_q;
+    __shared__ bool s_last;
+    const int s = blockIdx.y, r = blockIdx.z, os = OS > 0 ? OS : os_rt;
+    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane, npb = (size_t)ndb * ndb;
+    const float *src0 = Is + ((size_t)r * nse + s) * plane;
+    const float *gr = GI + (size_t)r * npb;
+    if (threadIdx.x == 0) s_q = 0u;
+    __syncthreads();
+    df acc[1] = {{0.f, 0.f}};
+    // block-uniform trip count, so the warp-wide maxima below see every lane
+    for (size_t P0 = (size_t)blockIdx.x * blockDim.x; P0 < npb; P0 += (size_t)gridDim.x * blockDim.x) {
+        const size_t P = P0 + threadIdx.x;
+        const bool valid = P < npb;
+        const int py = valid ? (int)(P / ndb) : 0, px = valid ? (int)(P % ndb) : 0;
+        const float *src[1] = {src0 + (size_t)(py * os) * no + (size_t)px * os};
+        const bool on[1] = {valid};
+        float v[1], vm[1];
+        bin_blocks<OS, 1>(src, G, gstride, no, os, on, v, vm);
+        const float gi = valid ? __ldg(gr + P) : 0.f;
+        if (valid) acc[0] = df_add(acc[0], gi * v[0]);
+        if (qmax) {
+            float qv = fabsf(gi) * sqrtf(vm[0]);
+            if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
+            for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
+            if ((threadIdx.x & 31) == 0) atomicMax(&s_q, __float_as_uint(qv));
+        }
+    }
+    block_sum<1>(acc, sh);  // its barriers also publish s_q
+    if (qmax && threadIdx.x == 0) atomicMax(qmax + (size_t)r * nse + s, s_q);
+    const size_t slot = (size_t)r * kMaxSrc + s;
+    if (threadIdx.x == 0) {
+        red_b[slot * gridDim.x + blockIdx.x] = df_to_double(acc[0]);
+        __threadfence();
+        s_last = atomicAdd(fcount + slot, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        double v = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(red_b + slot * gridDim.x + b);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) {
+            if (g.p[GFLUX]) g.p[GFLUX][(size_t)r * g.s[GFLUX] + s] = (float)v;
+            fcount[slot] = 0;  // ready for the next launch
+        }
+    }
+}
+
 // Partial-intensity planes of the tensor-core split: the few (slot, source, exposure)
 // x 128-tile segments whose wavelengths were cut over several CTAs (fold[i] = (segment,
 // planes written)) are added into plane 0 in plane order, so every later reader takes
@@ -925,6 +1101,36 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     KScope ks(p, KC_BIN, 1, st);
     float *gi = p->crop ? p->GIimg : p->GI;
     const int G = planes_to_read(p);
+    if (p->crop) {
+        // integer-dither windows: one source sum on the big detector, then the images
+        const size_t npb = (size_t)p->nd * p->nd;
+        const int bs = (int)std::max<size_t>(1, std::min<size_t>((npb + 255) / 256, (size_t)p->sm_count * 8 / R));
+        auto gs = [&](auto kern) {
+            return launch_pdl(kern, dim3(bs, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->ns, p->nd,
+                              p->os, p->no, prm, p->Swin);
+        };
+        cudaError_t e = p->os == 4 ? gs(k_win_sum<4>) : p->os == 2 ? gs(k_win_sum<2>) : p->os == 1 ? gs(k_win_sum<1>)
+                                                                                                 : gs(k_win_sum<0>);
+        ++ks.n;
+        if (e == cudaSuccess)
+            e = launch_pdl(k_win_nll, dim3(p->bin_a_blocks, R), dim3(256), 0, st, (const float *)p->Swin, p->nd,
+                           p->nei, p->ndi, (const int2 *)p->crop, prm, data, data_stride, model, model_stride,
+                           p->GIimg, gg, p->red_a, p->clamped, loss, p->bcount, p->prf_inv, p->cot);
+        if (e != cudaSuccess || !(data || p->cot)) return e;
+        ++ks.n;
+        e = launch_pdl(k_crop_fold, dim3(bs, R), dim3(256), 0, st, (const float *)p->GIimg, (const int2 *)p->crop,
+                       p->nei, p->ndi, p->GI, p->nd);
+        if (e != cudaSuccess || !(gg.p[GFLUX] || p->qmax)) return e;
+        ++ks.n;
+        const int bf = (int)std::max<size_t>(
+            1, std::min<size_t>((npb + 255) / 256, ((size_t)p->sm_count * 8 + (size_t)p->ns * R - 1) / ((size_t)p->ns * R)));
+        auto gf = [&](auto kern) {
+            return launch_pdl(kern, dim3(bf, p->ns, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->nd, p->os,
+                              p->no, (const float *)p->GI, gg, p->red_b, p->fcount, p->qmax);
+        };
+        return p->os == 4 ? gf(k_win_flux<4>) : p->os == 2 ? gf(k_win_flux<2>) : p->os == 1 ? gf(k_win_flux<1>)
+                                                                                          : gf(k_win_flux<0>);
+    }
     auto go = [&](auto kern) {
         return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->ns,
                           p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data, data_stride, model,
