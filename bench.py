@@ -666,10 +666,10 @@ def main():
     nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16x3sa": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
     # DRAM bytes (read + written) of the contractions of the BF16x3 form from one ncu capture of
     # this build on the 8-wavelength case (16 PSFs), scaled by the PSF count, in which their
-    # traffic grows (the adjoint 1^T splits K differently at that size and is left out; stage 2
-    # has written no zero planes since, so its capture is out of date); any other kernel or
-    # form has no capture of the current code
-    traffic_16 = {"stage1": 25.59e6, "adjoint_field": 129.95e6, "adjoint_stage2T": 172.03e6}
+    # traffic grows (the adjoint 1^T splits K differently at that size and is left out); any
+    # other kernel or form has no capture of the current code
+    traffic_16 = {"stage1": 25.25e6, "stage2_intensity": 50.74e6, "adjoint_field": 126.48e6,
+                  "adjoint_stage2T": 166.53e6}
     traffic = (traffic_16[dom] / 16 * B if (args.form == "bf16x3" and dom in traffic_16 and
                                             args.workload == "binary") else None)
     roof = None
