@@ -390,7 +390,7 @@ constexpr int kQShared = 64;  // (source, exposure) maxima kept in shared memory
 
 template <int OS, int MAXS>
 __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse, int ns, int ne, int nd, int os_rt,
-                          int no, int nem, const int2 *__restrict__ crop, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
+                          int no, DevParams prm, const int32_t *__restrict__ data, size_t dstride,
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount,
                           float prf_inv, const float *__restrict__ cot, const uint8_t *__restrict__ used, int tn) {
@@ -426,17 +426,13 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
         for (int e = 0; e < ne; ++e) {
             float bs[MAXS], bmax[MAXS];
             float btot = 0.f;
-            // image e is the window at crop[e] of the one MFT plane per source (integer dithers),
-            // or the source's own plane of exposure e
-            const int2 oc = crop ? __ldg(crop + e) : make_int2(0, 0);
-            const int em = crop ? 0 : e;
-            const int ry = (py + oc.y) * os, rx = (px + oc.x) * os;
+            const int ry = py * os, rx = px * os;
 #pragma unroll
             for (int s = 0; s < MAXS; ++s) {
                 bs[s] = 0.f;
                 bmax[s] = 0.f;
                 if (s < ns && valid) {
-                    const size_t rse = (size_t)r * nse + s * nem + em;
+                    const size_t rse = (size_t)r * nse + s * ne + e;
                     // planes this block's 128-tile of the intensity holds (os divides 128)
                     const int ng = (used && OS > 0) ? used[rse * tn * tn + (ry >> 7) * tn + (rx >> 7)] : G;
                     float v = 0.f, vm = 0.f;
@@ -530,7 +526,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                     if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
                     for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
                     if ((threadIdx.x & 31) == 0) {
-                        const int k = s * nem + em;
+                        const int k = s * ne + e;
                         if (k < kQShared)
                             atomicMax(s_q + k, __float_as_uint(qv));
                         else
@@ -685,8 +681,7 @@ __host__ __device__ constexpr int bin_chunk() {
 
 template <int OS>
 __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
-                                                   int ne, int nd, int os_rt, int no, int nem,
-                                                   const int2 *__restrict__ crop, DevParams prm,
+                                                   int ne, int nd, int os_rt, int no, DevParams prm,
                                                    const int32_t *__restrict__ data, size_t dstride,
                                                    float *__restrict__ model, size_t mstride, float *__restrict__ GI,
                                                    DevGrads g, double *red_a, unsigned long long *clamped,
@@ -706,7 +701,7 @@ __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is,
     float *dflat = g.p[GFLAT] ? g.p[GFLAT] + (size_t)r * g.s[GFLAT] : nullptr;
     const float *ct = cot ? cot + (size_t)r * ne * np : nullptr;
     const bool grad = dat || ct;
-    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane, sstride = (size_t)nem * plane;
+    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane, sstride = (size_t)ne * plane;
     const float *slot = Is + (size_t)r * nse * plane;
     df acc[1] = {{0.f, 0.f}};
     unsigned long long nclamp = 0;
@@ -716,10 +711,8 @@ __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is,
         const float ff = flat[p];
         float dff = 0.f;
         for (int e = 0; e < ne; ++e) {
-            const int2 oc = crop ? __ldg(crop + e) : make_int2(0, 0);
-            // first source's plane of this image, at the block's top-left sample
-            const float *base = slot + (size_t)(crop ? 0 : e) * plane + (size_t)((py + oc.y) * os) * no +
-                                (size_t)(px + oc.x) * os;
+            // first source's plane of this exposure, at the block's top-left sample
+            const float *base = slot + (size_t)e * plane + (size_t)(py * os) * no + (size_t)px * os;
             float btot = 0.f;
 #pragma unroll 1
             for (int s0 = 0; s0 < ns; s0 += NC) {
@@ -788,8 +781,7 @@ __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is,
 
 template <int OS>
 __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is, int G, int Rnse, int nse, int ne,
-                                                   int nd, int os_rt, int no, int nem,
-                                                   const int2 *__restrict__ crop, const float *__restrict__ GI,
+                                                   int nd, int os_rt, int no, const float *__restrict__ GI,
                                                    DevGrads g, double *red_b, unsigned int *fcount,
                                                    unsigned int *qmax) {
     pdl_trigger();
@@ -799,7 +791,7 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
     __shared__ bool s_last;
     const int np = nd * nd, s = blockIdx.y, r = blockIdx.z, os = OS > 0 ? OS : os_rt;
     const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane;
-    const float *src0 = Is + ((size_t)r * nse + (size_t)s * nem) * plane;  // this source's first plane
+    const float *src0 = Is + ((size_t)r * nse + (size_t)s * ne) * plane;  // this source's first plane
     const float *gslot = GI + (size_t)r * ne * np;
     if (qmax)
         for (int i = threadIdx.x; i < kQShared; i += blockDim.x) s_q[i] = 0u;
@@ -820,9 +812,7 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
             for (int k = 0; k < NC; ++k) {
                 const int e = e0 + k;
                 on[k] = valid && e < ne;
-                const int2 oc = (crop && e < ne) ? __ldg(crop + e) : make_int2(0, 0);
-                src[k] = src0 + (size_t)(crop ? 0 : e) * plane + (size_t)((py + oc.y) * os) * no +
-                         (size_t)(px + oc.x) * os;
+                src[k] = src0 + (size_t)e * plane + (size_t)(py * os) * no + (size_t)px * os;
                 gi[k] = on[k] ? __ldg(gslot + (size_t)e * np + p) : 0.f;
             }
             bin_blocks<OS, NC>(src, G, gstride, no, os, on, v, vm);
@@ -835,11 +825,11 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
                     if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
                     for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
                     if ((threadIdx.x & 31) == 0) {
-                        const int em = crop ? 0 : e0 + k;
-                        if (em < kQShared)
-                            atomicMax(s_q + em, __float_as_uint(qv));
+                        const int e = e0 + k;
+                        if (e < kQShared)
+                            atomicMax(s_q + e, __float_as_uint(qv));
                         else
-                            atomicMax(qmax + (size_t)r * nse + s * nem + em, __float_as_uint(qv));
+                            atomicMax(qmax + (size_t)r * nse + s * ne + e, __float_as_uint(qv));
                     }
                 }
             }
@@ -847,8 +837,8 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
     }
     block_sum<1>(acc, sh);  // its barriers also publish s_q
     if (qmax)
-        for (int k = threadIdx.x; k < nem && k < kQShared; k += blockDim.x)
-            atomicMax(qmax + (size_t)r * nse + s * nem + k, s_q[k]);
+        for (int k = threadIdx.x; k < ne && k < kQShared; k += blockDim.x)
+            atomicMax(qmax + (size_t)r * nse + s * ne + k, s_q[k]);
     const size_t slot = (size_t)r * kMaxSrc + s;
     if (threadIdx.x == 0) {
         red_b[slot * gridDim.x + blockIdx.x] = df_to_double(acc[0]);
@@ -1099,7 +1089,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     DevGrads gg{};
     if (g) gg = *g;
     KScope ks(p, KC_BIN, 1, st);
-    float *gi = p->crop ? p->GIimg : p->GI;
+    float *gi = p->GI;
     const int G = planes_to_read(p);
     if (p->crop) {
         // integer-dither windows: one source sum on the big detector, then the images
@@ -1133,7 +1123,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     }
     auto go = [&](auto kern) {
         return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->ns,
-                          p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data, data_stride, model,
+                          p->ne, p->nd, p->os, p->no, prm, data, data_stride, model,
                           model_stride, gi, gg, p->red, p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot,
                           plane_counts(p, R), (p->no + 127) / 128);
     };
@@ -1144,7 +1134,7 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     } else {
         auto ga = [&](auto kern) {
             return launch_pdl(kern, dim3(p->bin_a_blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse,
-                              p->ns, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop, prm, data,
+                              p->ns, p->ne, p->nd, p->os, p->no, prm, data,
                               data_stride, model, model_stride, gi, gg, p->red_a, p->clamped, loss, p->bcount,
                               p->prf_inv, p->cot);
         };
@@ -1155,21 +1145,14 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
             ++ks.n;
             auto gb = [&](auto kern) {
                 return launch_pdl(kern, dim3(p->bin_b_blocks, p->ns, R), dim3(256), 0, st, p->Is, G,
-                                  R * p->nse, p->nse, p->nei, p->ndi, p->os, p->no, p->ne, (const int2 *)p->crop,
-                                  (const float *)gi, gg, p->red_b, p->fcount, p->qmax);
+                                  R * p->nse, p->nse, p->ne, p->nd, p->os, p->no, (const float *)gi, gg, p->red_b,
+                                  p->fcount, p->qmax);
             };
             e = p->os == 4 ? gb(k_flux_grad<4>) : p->os == 2 ? gb(k_flux_grad<2>) : p->os == 1 ? gb(k_flux_grad<1>)
                                                                                              : gb(k_flux_grad<0>);
         }
     }
-    if (e != cudaSuccess || !p->crop || !(data || p->cot)) return e;
-    ++ks.n;
-    // integer dithers: the adjoint weights of the big detector are the images' weights placed back
-    // at their windows and summed
-    const size_t nb = (size_t)p->nd * p->nd;
-    const int blocks = (int)std::min<size_t>((nb + 255) / 256, (size_t)p->sm_count * 8);
-    return launch_pdl(k_crop_fold, dim3(blocks, R), dim3(256), 0, st, (const float *)p->GIimg,
-                      (const int2 *)p->crop, p->nei, p->ndi, p->GI, p->nd);
+    return e;
 }
 
 // psf[e][y][x] = sum_s F_s sum_g Is[g][s nem + em][y + oy][x + ox]: the image-sized oversampled
