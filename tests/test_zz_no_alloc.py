@@ -55,6 +55,28 @@ def test_noalloc_forward_matches_planned_forward_twice():
         assert np.max(np.abs(got - want)) <= TOL * want.max()
 
 
+def test_noalloc_many_sources_matches_planned_forward():
+    """Twelve sources, past the eight that the one-pass binning holds in registers."""
+    import torch
+
+    import paper_2406_08703_gb300 as P
+
+    P.load()
+    p = W.perturbed_start(W.make_problem("custom", seed=31, n_pupil=32, n_det=24, oversample=2, n_lambda=2,
+                                         n_src=12, n_exp=2, dither_px=0.5, n_zern_max=4), 32)
+    prm = P.params_from_problem(p)
+    desc = P.desc_from_problem(p, P.DLX_FP32_SIMT)
+    out = torch.full((p.n_exp, p.n_det, p.n_det), float("nan"), device="cuda")
+    for _ in range(2):
+        P.dlx_forward_noalloc(desc, prm, out)
+        plan = P.dlx_make_mft(desc)
+        ref = P.dlx_forward(plan, prm)
+        torch.cuda.synchronize()
+        got, want = out.double().cpu().numpy(), ref.double().cpu().numpy()
+        plan.close()
+        assert np.max(np.abs(got - want)) <= TOL * want.max()
+
+
 def test_noalloc_rejects_shapes_beyond_the_scratch():
     import paper_2406_08703_gb300 as P
     from paper_2406_08703_gb300._native import DlxError
