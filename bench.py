@@ -239,39 +239,64 @@ def run_form(P, torch, workload, form, steps, warmup, device, timing=True):
 
 
 def e2e_run(P, torch, r, steps, device):
-    """Same call through the public API with host inputs: H2D of the step's inputs
-    from pinned memory, the evaluation, D2H of loss and gradients, per step."""
-    plan, start, data = r["plan"], r["start"], r["data"]
+    """Same call through the public API with host inputs: every step copies its inputs from
+    pinned host memory, evaluates, and reads its loss and gradients back to the host.  Steps
+    are pipelined two deep on three streams, as a caller evaluating a stream of problems would
+    run them: step i+1's upload and step i-1's read-back overlap step i's evaluation, and the
+    host waits for each step's own read-back before it counts the step as done."""
+    plan, data = r["plan"], r["data"]
     host = {k: (None if v is None else v.cpu().pin_memory()) for k, v in r["prm"].items()}
-    dev = {k: (None if v is None else torch.empty_like(v)) for k, v in r["prm"].items()}
     hdata = torch.as_tensor(data).pin_memory()
-    ddata = torch.empty_like(hdata, device=f"cuda:{device}")
-    grads = P.empty_grads(plan)
-    hgrads = {k: (None if v is None else torch.empty(v.shape, dtype=v.dtype).pin_memory()) for k, v in grads.items()}
-    loss = torch.empty(1, dtype=torch.float64, device=f"cuda:{device}")
-    hloss = torch.empty(1, dtype=torch.float64).pin_memory()
-    stream = torch.cuda.current_stream(device)
+    dev_name = f"cuda:{device}"
+    up, comp, down = (torch.cuda.Stream(device) for _ in range(3))
+    bufs = []
+    for _ in range(2):
+        grads = P.empty_grads(plan)
+        bufs.append(dict(
+            dev={k: (None if v is None else torch.empty_like(v)) for k, v in r["prm"].items()},
+            ddata=torch.empty_like(hdata, device=dev_name), grads=grads,
+            loss=torch.empty(1, dtype=torch.float64, device=dev_name),
+            hgrads={k: (None if v is None else torch.empty(v.shape, dtype=v.dtype).pin_memory())
+                    for k, v in grads.items()},
+            hloss=torch.empty(1, dtype=torch.float64).pin_memory(),
+            uploaded=torch.cuda.Event(), evaluated=torch.cuda.Event(), read=torch.cuda.Event(), used=False))
     h2d = sum(v.numel() * v.element_size() for v in host.values() if v is not None) + hdata.numel() * 4
-    d2h = 8 + sum(v.numel() * v.element_size() for v in hgrads.values() if v is not None)
+    d2h = 8 + sum(v.numel() * v.element_size() for v in bufs[0]["hgrads"].values() if v is not None)
 
-    def step():
-        for k, v in host.items():
-            if v is not None:
-                dev[k].copy_(v, non_blocking=True)
-        ddata.copy_(hdata, non_blocking=True)
-        P.dlx_loss_grad(plan, dev, ddata, loss=loss, grads=grads, stream=stream)
-        hloss.copy_(loss, non_blocking=True)
-        for k, v in grads.items():
-            if v is not None:
-                hgrads[k].copy_(v, non_blocking=True)
-        stream.synchronize()
+    def enqueue(i):
+        b = bufs[i % 2]
+        if b["used"]:  # the buffers of step i - 2: its evaluation read them, its read-back emptied them
+            up.wait_event(b["evaluated"])
+            comp.wait_event(b["read"])
+        with torch.cuda.stream(up):
+            for k, v in host.items():
+                if v is not None:
+                    b["dev"][k].copy_(v, non_blocking=True)
+            b["ddata"].copy_(hdata, non_blocking=True)
+            b["uploaded"].record(up)
+        comp.wait_event(b["uploaded"])
+        P.dlx_loss_grad(plan, b["dev"], b["ddata"], loss=b["loss"], grads=b["grads"], stream=comp)
+        b["evaluated"].record(comp)
+        down.wait_event(b["evaluated"])
+        with torch.cuda.stream(down):
+            b["hloss"].copy_(b["loss"], non_blocking=True)
+            for k, v in b["grads"].items():
+                if v is not None:
+                    b["hgrads"][k].copy_(v, non_blocking=True)
+            b["read"].record(down)
+        b["used"] = True
 
-    for _ in range(3):
-        step()
+    def run(n):
+        enqueue(0)
+        for i in range(n):
+            if i + 1 < n:
+                enqueue(i + 1)
+            bufs[i % 2]["read"].synchronize()  # step i's loss and gradients are on the host
+
+    run(3)
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
-    for _ in range(steps):
-        step()
+    run(steps)
     torch.cuda.synchronize(device)
     dt = (time.perf_counter() - t0) / steps
     return dict(s_per_step=dt, h2d=h2d, d2h=d2h)
@@ -712,7 +737,8 @@ def main():
     # e2e through the public API with host buffers
     e = e2e_run(P, torch, r, max(3, args.steps // 3), device)
     line["e2e"] = dict(value=world / max_over_ranks(dist, e["s_per_step"]), unit="evals/s",
-                       h2d_bytes_per_step=e["h2d"], d2h_bytes_per_step=e["d2h"])
+                       h2d_bytes_per_step=e["h2d"], d2h_bytes_per_step=e["d2h"],
+                       pipeline="two steps deep: upload, evaluation and read-back on their own streams")
     r["plan"].close()
 
     if not args.no_forms and rank == 0:
