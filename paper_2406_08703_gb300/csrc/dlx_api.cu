@@ -332,7 +332,10 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
             1, std::min<size_t>((npi + 255) / 256, ((size_t)p->sm_count * 8 + (size_t)p->ns * R_max - 1) /
                                                       ((size_t)p->ns * R_max)));
         if (e == cudaSuccess) e = plan_alloc(p, &p->red_a, sizeof(double) * p->bin_a_blocks * R_max);
-        if (e == cudaSuccess) e = plan_alloc(p, &p->red_b, sizeof(double) * p->bin_b_blocks * kMaxSrc * R_max);
+        // the window flux pass has (column blocks x row blocks) partials per source, most at R = 1
+        const int nb_win = d->dither_px ? ((p->nd + 127) / 128) * win_flux_rows(p, 1) : 0;
+        const size_t nb_flux = (size_t)std::max(p->bin_b_blocks, nb_win);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->red_b, sizeof(double) * nb_flux * kMaxSrc * R_max);
         if (e == cudaSuccess) e = plan_alloc(p, &p->fcount, sizeof(unsigned int) * kMaxSrc * R_max);
         if (e == cudaSuccess) e = cudaMemset(p->fcount, 0, sizeof(unsigned int) * kMaxSrc * R_max);
     }

@@ -428,6 +428,11 @@ struct KScope {
 // the tensor-core split's planes are folded into plane 0 after stage 2 (more than 8 sources,
 // or integer-dither windows)
 inline bool folds_planes(const dlx_plan *p) { return p->prec != DLX_FP32_SIMT && (p->ns > 8 || p->crop); }
+// row blocks of k_win_flux: about 16 blocks of 128 threads per SM over columns x rows x sources
+inline int win_flux_rows(const dlx_plan *p, int R) {
+    const int cx = (p->nd + 127) / 128;
+    return std::max(1, std::min(p->nd, p->sm_count * 16 / (cx * p->ns * R)));
+}
 // partial-intensity planes a reader adds (at most; see plane_counts)
 inline int planes_to_read(const dlx_plan *p) { return folds_planes(p) ? 1 : p->G; }
 // the plane-count table for R active slots where the readers need it, else NULL

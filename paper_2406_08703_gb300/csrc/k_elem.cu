@@ -866,22 +866,27 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
 //   k_crop_fold: GI[P] = sum_e GI_e[P - crop[e]] (also the adjoint's weight map);
 //   k_win_flux:  dL/dF_s = sum_P GI[P] B_s[P], one pass over each source's plane, and the
 //                FP16 form's bound Q_s = max |GI| sqrt(I_s) of the weights the adjoint uses.
+// 2-D indexing for the big-detector passes: a thread owns one column px = blockIdx.x *
+// blockDim.x + threadIdx.x and walks rows py = blockIdx.y + k * gridDim.y, so no pixel index
+// is divided; source (and slot) come from blockIdx.z.
 template <int OS>
-__global__ void __launch_bounds__(256) k_win_sum(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
+__global__ void __launch_bounds__(128) k_win_sum(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
                                                  int ndb, int os_rt, int no, DevParams prm, float *__restrict__ S) {
     pdl_trigger();
     pdl_wait();
     __shared__ float s_flux[kMaxSrc];
-    const int r = blockIdx.y, os = OS > 0 ? OS : os_rt;
+    const int r = blockIdx.z, os = OS > 0 ? OS : os_rt;
     const float *flux = slot_ptr(prm, PFLUX, r);
     for (int i = threadIdx.x; i < ns; i += blockDim.x) s_flux[i] = flux[i];
     __syncthreads();
-    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane, npb = (size_t)ndb * ndb;
-    const float *slot = Is + (size_t)r * nse * plane;
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    if (px >= ndb) return;
+    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane;
+    const float *slot = Is + (size_t)r * nse * plane + (size_t)px * os;
+    float *Sr = S + (size_t)r * ndb * ndb + px;
     constexpr int NC = bin_chunk<OS>();
-    for (size_t P = blockIdx.x * (size_t)blockDim.x + threadIdx.x; P < npb; P += (size_t)gridDim.x * blockDim.x) {
-        const int py = (int)(P / ndb), px = (int)(P % ndb);
-        const float *base = slot + (size_t)(py * os) * no + (size_t)px * os;
+    for (int py = blockIdx.y; py < ndb; py += gridDim.y) {
+        const float *base = slot + (size_t)(py * os) * no;
         float btot = 0.f;
 #pragma unroll 1
         for (int s0 = 0; s0 < ns; s0 += NC) {
@@ -898,7 +903,7 @@ __global__ void __launch_bounds__(256) k_win_sum(const float *__restrict__ Is, i
             for (int k = 0; k < NC; ++k)
                 if (on[k]) btot = fmaf(s_flux[s0 + k], v[k], btot);
         }
-        S[(size_t)r * npb + P] = btot;
+        Sr[(size_t)py * ndb] = btot;
     }
 }
 
@@ -926,28 +931,45 @@ __global__ void __launch_bounds__(256) k_win_nll(const float *__restrict__ S, in
         const int py = p / nd, px = p % nd;
         const float ff = flat[p];
         float dff = 0.f;
-        for (int e = 0; e < ne; ++e) {
-            const int2 oc = __ldg(crop + e);
-            const float btot = __ldg(Sr + (size_t)(py + oc.y) * ndb + px + oc.x);
-            const float m = ff * btot;
-            mod[(size_t)e * np + p] = m;
-            if (grad) {
-                float gm;
-                if (ct) {
-                    gm = __ldg(ct + (size_t)e * np + p);
-                } else {
-                    const float d = (float)dat[(size_t)e * np + p];
-                    float mc = m;
-                    if (!(mc >= 1e-30f)) {
-                        mc = 1e-30f;
-                        ++nclamp;
-                    }
-                    acc[0] = df_add(acc[0], m);
-                    acc[0] = df_add(acc[0], -d * logf(mc));
-                    gm = 1.f - d / mc;
+        constexpr int EC = 4;  // images per chunk, their loads issued together
+        for (int e0 = 0; e0 < ne; e0 += EC) {
+            float bt[EC], dv[EC];
+#pragma unroll
+            for (int k = 0; k < EC; ++k) {
+                const int e = e0 + k;
+                bt[k] = 0.f;
+                dv[k] = 0.f;
+                if (e < ne) {
+                    const int2 oc = __ldg(crop + e);
+                    bt[k] = __ldg(Sr + (size_t)(py + oc.y) * ndb + px + oc.x);
+                    if (dat && !ct) dv[k] = (float)__ldg(dat + (size_t)e * np + p);
                 }
-                GI[((size_t)r * ne + e) * np + p] = ff * gm;
-                dff = fmaf(gm, btot, dff);
+            }
+#pragma unroll
+            for (int k = 0; k < EC; ++k) {
+                const int e = e0 + k;
+                if (e >= ne) break;
+                const float btot = bt[k];
+                const float m = ff * btot;
+                mod[(size_t)e * np + p] = m;
+                if (grad) {
+                    float gm;
+                    if (ct) {
+                        gm = __ldg(ct + (size_t)e * np + p);
+                    } else {
+                        const float d = dv[k];
+                        float mc = m;
+                        if (!(mc >= 1e-30f)) {
+                            mc = 1e-30f;
+                            ++nclamp;
+                        }
+                        acc[0] = df_add(acc[0], m);
+                        acc[0] = df_add(acc[0], -d * logf(mc));
+                        gm = 1.f - d / mc;
+                    }
+                    GI[((size_t)r * ne + e) * np + p] = ff * gm;
+                    dff = fmaf(gm, btot, dff);
+                }
             }
         }
         if (dat && !ct && prf_inv > 0.f) {
@@ -980,52 +1002,64 @@ __global__ void __launch_bounds__(256) k_win_nll(const float *__restrict__ S, in
 }
 
 template <int OS>
-__global__ void __launch_bounds__(256) k_win_flux(const float *__restrict__ Is, int G, int Rnse, int nse, int ndb,
-                                                  int os_rt, int no, const float *__restrict__ GI, DevGrads g,
-                                                  double *red_b, unsigned int *fcount, unsigned int *qmax) {
+__global__ void __launch_bounds__(128) k_win_flux(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
+                                                  int ndb, int os_rt, int no, const float *__restrict__ GI,
+                                                  DevGrads g, double *red_b, unsigned int *fcount,
+                                                  unsigned int *qmax) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
     __shared__ unsigned int s_q;
     __shared__ bool s_last;
-    const int s = blockIdx.y, r = blockIdx.z, os = OS > 0 ? OS : os_rt;
-    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane, npb = (size_t)ndb * ndb;
-    const float *src0 = Is + ((size_t)r * nse + s) * plane;
-    const float *gr = GI + (size_t)r * npb;
+    const int s = blockIdx.z % ns, r = blockIdx.z / ns, os = OS > 0 ? OS : os_rt;
+    const size_t plane = (size_t)no * no, gstride = (size_t)Rnse * plane;
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool col = px < ndb;
+    const float *src0 = Is + ((size_t)r * nse + s) * plane + (size_t)(col ? px : 0) * os;
+    const float *gr = GI + (size_t)r * ndb * ndb + (col ? px : 0);
     if (threadIdx.x == 0) s_q = 0u;
     __syncthreads();
     df acc[1] = {{0.f, 0.f}};
-    // block-uniform trip count, so the warp-wide maxima below see every lane
-    for (size_t P0 = (size_t)blockIdx.x * blockDim.x; P0 < npb; P0 += (size_t)gridDim.x * blockDim.x) {
-        const size_t P = P0 + threadIdx.x;
-        const bool valid = P < npb;
-        const int py = valid ? (int)(P / ndb) : 0, px = valid ? (int)(P % ndb) : 0;
-        const float *src[1] = {src0 + (size_t)(py * os) * no + (size_t)px * os};
-        const bool on[1] = {valid};
-        float v[1], vm[1];
-        bin_blocks<OS, 1>(src, G, gstride, no, os, on, v, vm);
-        const float gi = valid ? __ldg(gr + P) : 0.f;
-        if (valid) acc[0] = df_add(acc[0], gi * v[0]);
-        if (qmax) {
-            float qv = fabsf(gi) * sqrtf(vm[0]);
-            if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
-            for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
-            if ((threadIdx.x & 31) == 0) atomicMax(&s_q, __float_as_uint(qv));
+    // NC rows per thread and pass, all their loads in flight; the trip count is the same for
+    // every thread of the block, so the warp-wide maxima below see every lane
+    constexpr int NC = bin_chunk<OS>();
+    for (int py0 = blockIdx.y; py0 < ndb; py0 += gridDim.y * NC) {
+        const float *src[NC];
+        bool on[NC];
+        float v[NC], vm[NC], gi[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const int py = py0 + k * gridDim.y;
+            on[k] = col && py < ndb;
+            src[k] = src0 + (size_t)((on[k] ? py : 0) * os) * no;
+            gi[k] = on[k] ? __ldg(gr + (size_t)py * ndb) : 0.f;
+        }
+        bin_blocks<OS, NC>(src, G, gstride, no, os, on, v, vm);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (on[k]) acc[0] = df_add(acc[0], gi[k] * v[k]);
+            if (qmax) {
+                float qv = fabsf(gi[k]) * sqrtf(vm[k]);
+                if (!(qv < 3.0e38f)) qv = 3.0e38f;  // NaN / inf in the model: keep the bound finite
+                for (int o = 16; o > 0; o >>= 1) qv = fmaxf(qv, __shfl_xor_sync(0xffffffffu, qv, o));
+                if ((threadIdx.x & 31) == 0) atomicMax(&s_q, __float_as_uint(qv));
+            }
         }
     }
     block_sum<1>(acc, sh);  // its barriers also publish s_q
     if (qmax && threadIdx.x == 0) atomicMax(qmax + (size_t)r * nse + s, s_q);
     const size_t slot = (size_t)r * kMaxSrc + s;
+    const int nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
     if (threadIdx.x == 0) {
-        red_b[slot * gridDim.x + blockIdx.x] = df_to_double(acc[0]);
+        red_b[slot * nblk + bid] = df_to_double(acc[0]);
         __threadfence();
-        s_last = atomicAdd(fcount + slot, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(fcount + slot, 1u) == nblk - 1;
     }
     __syncthreads();
     if (s_last && threadIdx.x < 32) {
         __threadfence();
         double v = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += 32) v += __ldcg(red_b + slot * gridDim.x + b);
+        for (int b = threadIdx.x; b < nblk; b += 32) v += __ldcg(red_b + slot * nblk + b);
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (threadIdx.x == 0) {
             if (g.p[GFLUX]) g.p[GFLUX][(size_t)r * g.s[GFLUX] + s] = (float)v;
@@ -1073,7 +1107,7 @@ __global__ void k_crop_fold(const float *__restrict__ gimg, const int2 *__restri
     const int r = blockIdx.y;
     const size_t npb = (size_t)nb * nb, np = (size_t)nd * nd;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < npb; q += (size_t)gridDim.x * blockDim.x) {
-        const int y = (int)(q / nb), x = (int)(q % nb);
+        const int y = (int)((unsigned)q / (unsigned)nb), x = (int)((unsigned)q % (unsigned)nb);  // 32-bit division
         float v = 0.f;
         for (int e = 0; e < ne; ++e) {
             const int2 o = __ldg(crop + e);
@@ -1093,11 +1127,12 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     const int G = planes_to_read(p);
     if (p->crop) {
         // integer-dither windows: one source sum on the big detector, then the images
-        const size_t npb = (size_t)p->nd * p->nd;
-        const int bs = (int)std::max<size_t>(1, std::min<size_t>((npb + 255) / 256, (size_t)p->sm_count * 8 / R));
+        const dim3 tb(128);
+        const int cx = (p->nd + 127) / 128;
+        const int ry = std::max(1, std::min(p->nd, p->sm_count * 16 / (cx * R)));
         auto gs = [&](auto kern) {
-            return launch_pdl(kern, dim3(bs, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->ns, p->nd,
-                              p->os, p->no, prm, p->Swin);
+            return launch_pdl(kern, dim3(cx, ry, R), tb, 0, st, p->Is, G, R * p->nse, p->nse, p->ns, p->nd, p->os,
+                              p->no, prm, p->Swin);
         };
         cudaError_t e = p->os == 4 ? gs(k_win_sum<4>) : p->os == 2 ? gs(k_win_sum<2>) : p->os == 1 ? gs(k_win_sum<1>)
                                                                                                  : gs(k_win_sum<0>);
@@ -1108,15 +1143,16 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
                            p->GIimg, gg, p->red_a, p->clamped, loss, p->bcount, p->prf_inv, p->cot);
         if (e != cudaSuccess || !(data || p->cot)) return e;
         ++ks.n;
+        const size_t npb = (size_t)p->nd * p->nd;
+        const int bs = (int)std::max<size_t>(1, std::min<size_t>((npb + 255) / 256, (size_t)p->sm_count * 8 / R));
         e = launch_pdl(k_crop_fold, dim3(bs, R), dim3(256), 0, st, (const float *)p->GIimg, (const int2 *)p->crop,
                        p->nei, p->ndi, p->GI, p->nd);
         if (e != cudaSuccess || !(gg.p[GFLUX] || p->qmax)) return e;
         ++ks.n;
-        const int bf = (int)std::max<size_t>(
-            1, std::min<size_t>((npb + 255) / 256, ((size_t)p->sm_count * 8 + (size_t)p->ns * R - 1) / ((size_t)p->ns * R)));
+        const int fy = win_flux_rows(p, R);
         auto gf = [&](auto kern) {
-            return launch_pdl(kern, dim3(bf, p->ns, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->nd, p->os,
-                              p->no, (const float *)p->GI, gg, p->red_b, p->fcount, p->qmax);
+            return launch_pdl(kern, dim3(cx, fy, p->ns * R), tb, 0, st, p->Is, G, R * p->nse, p->nse, p->ns, p->nd,
+                              p->os, p->no, (const float *)p->GI, gg, p->red_b, p->fcount, p->qmax);
         };
         return p->os == 4 ? gf(k_win_flux<4>) : p->os == 2 ? gf(k_win_flux<2>) : p->os == 1 ? gf(k_win_flux<1>)
                                                                                           : gf(k_win_flux<0>);
