@@ -37,13 +37,13 @@ def _cuda():
     P.load()
 
 
-def _gpu(problem, form, data=None, kinds=("fisher",)):
+def _gpu(problem, form, data=None, kinds=("fisher",), crop=False):
     import torch
 
     import paper_2406_08703_gb300 as P
     from paper_2406_08703_gb300.laplace import Laplace
 
-    plan = P.dlx_make_mft(P.desc_from_problem(problem, P.PRECISIONS[form]))
+    plan = P.dlx_make_mft(P.desc_from_problem(problem, P.PRECISIONS[form], crop=crop))
     prm = P.params_from_problem(problem)
     lp = Laplace(plan)
     J = lp.jacobian(prm).double().cpu().numpy()
@@ -223,3 +223,27 @@ def test_paper_full_size_sampled(form):
     res = OL.sigma(H)  # raises if H is singular
     assert np.all(np.linalg.eigvalsh(H / np.sqrt(np.outer(np.diag(H), np.diag(H)))) > 0)
     assert np.all(res >= (1 - 1e-9) / np.sqrt(np.diag(H)))
+
+
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_integer_dither_windows_against_oracle(form):
+    """The Laplace passes on a window plan (integer dithers, Sec. 3): the tangent forwards, the
+    cotangent pass of the window NLL and the one-source plans of the same windows, against the
+    oracle's per-exposure model with the same dithers as angles."""
+    import oracle
+    from oracle import laplace as OL
+
+    p = aberrated_problem()
+    k = np.array([(0, 0), (2, -1), (-1, 2)], dtype=np.float64)
+    p.dither = k * p.pixscale
+    data = np.random.default_rng(19).poisson(oracle.forward(p)).astype(np.int32)
+    Jref, labs_ref = OL.jacobian(p)
+    ref = {kd: OL.information(p, data if kd != "fisher" else None, kd)[0] for kd in ("fisher", "hessian")}
+    J, out, labs = _gpu(p, form, data, kinds=("fisher", "hessian"), crop=True)
+    assert labs == labs_ref
+    ej = float(np.max(np.abs(J - Jref).max(axis=1) / np.abs(Jref).max(axis=1)))
+    errs = {kd: _rel(out[kd], ref[kd]) for kd in out}
+    print(form, "windows: J", ej, "info", errs)
+    assert ej < TOL[form]["J"]
+    assert errs["fisher"] < TOL[form]["info"]
+    assert errs["hessian"] < TOL[form]["hess"]
