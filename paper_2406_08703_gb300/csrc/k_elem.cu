@@ -1071,7 +1071,7 @@ __global__ void __launch_bounds__(128) k_win_flux(const float *__restrict__ Is, 
 // Partial-intensity planes of the tensor-core split: the few (slot, source, exposure)
 // x 128-tile segments whose wavelengths were cut over several CTAs (fold[i] = (segment,
 // planes written)) are added into plane 0 in plane order, so every later reader takes
-// plane 0 alone.  Grid: (segments, 4) blocks stepping over the tile's samples.
+// plane 0 alone.  Grid: (segments, 16) blocks stepping over the tile's samples.
 __global__ void k_plane_fold(float *__restrict__ Is, const int2 *__restrict__ fold, int tn, int no, size_t Rnse) {
     pdl_trigger();
     pdl_wait();
@@ -1094,7 +1094,7 @@ cudaError_t launch_plane_fold(dlx_plan *p, int R, cudaStream_t st) {
     const dlx_plan::S2Split &sp = p->s2[R - 1];
     if (sp.nfold == 0) return cudaSuccess;
     KScope ks(p, KC_BIN, 1, st);
-    return launch_pdl(k_plane_fold, dim3(sp.nfold, 4), dim3(256), 0, st, p->Is, (const int2 *)p->s2_fold + sp.fold,
+    return launch_pdl(k_plane_fold, dim3(sp.nfold, 16), dim3(256), 0, st, p->Is, (const int2 *)p->s2_fold + sp.fold,
                       (p->no + 127) / 128, p->no, (size_t)R * p->nse);
 }
 
