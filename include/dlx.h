@@ -107,8 +107,8 @@ typedef struct {
                                 which equals the model with params->dither = dither_px * pixscale
                                 (times f / z in the Fresnel regime below: the pointing offset that
                                 moves the image by whole pixels) at 1/n_exp of the MFT work;
-                                params->dither is then not read.
-                                Not accepted by the server (dlx_submit). */
+                                params->dither is then not read (nor a request's dither
+                                in dlx_submit). */
     double focal_length_m;   /* 0: Fraunhofer regime (the detector at focus; the model is angular).
                                 > 0: Fresnel regime (Sec. 1: a detector slightly out of focus adds
                                 quadratic phase factors before and after the transform): a lens of

@@ -45,6 +45,7 @@ struct Req {
     uint64_t ticket = 0;
     dlx_mft_desc desc{};
     std::vector<double> lambdas;
+    std::vector<int32_t> dither_px;  // integer-pixel dithers (windows), or empty
     bool has_pix = false;
     std::vector<float> T, opd_fixed, basis, weights, dither, coeff, pix, flux, pos, flat;
     std::vector<int32_t> data;
@@ -109,7 +110,7 @@ struct Bucket {
         d.s[dlx::PFLUX] = n_theta;
         d.p[dlx::PPOS] = theta + off[4];
         d.s[dlx::PPOS] = n_theta;
-        d.p[dlx::PDITHER] = dither;
+        d.p[dlx::PDITHER] = (plan && plan->crop) ? nullptr : dither;  // windows read no dither angles
         d.s[dlx::PDITHER] = 2 * (size_t)ne;
         d.p[dlx::PFLAT] = theta + off[2];
         d.s[dlx::PFLAT] = n_theta;
@@ -173,6 +174,9 @@ std::string bucket_key(const Req &r) {
     put(&d.focal_length_m, sizeof(double));    // Fresnel regime
     put(&d.focal_shift_m, sizeof(double));
     put(r.lambdas.data(), r.lambdas.size() * sizeof(double));
+    const int nwin = (int)r.dither_px.size();
+    put(&nwin, sizeof(int));
+    put(r.dither_px.data(), r.dither_px.size() * sizeof(int32_t));
     return k;
 }
 
@@ -185,13 +189,19 @@ size_t theta_size(const dlx_mft_desc &d, bool has_pix) {
 // parameters, gradient and Adam state.  The same arithmetic as make_plan's
 // allocations, used for admission before anything is allocated.
 size_t bucket_bytes(const dlx_mft_desc &d, bool has_pix, int cap) {
-    const size_t ni = d.n_pupil, nd = d.n_det, no = (size_t)d.n_det * d.oversample, nl = d.n_lambda;
-    const size_t ldi = (ni + 7) / 8 * 8, ldo = (no + 7) / 8 * 8, B = nl * d.n_src * d.n_exp, Bt = B * cap;
+    // integer-dither windows: the MFT runs once per source on a detector wider by 2 max|dither|
+    size_t delta = 0;
+    if (d.dither_px)
+        for (int k = 0; k < 2 * d.n_exp; ++k) delta = std::max<size_t>(delta, (size_t)std::abs(d.dither_px[k]));
+    const size_t ne_mft = d.dither_px ? 1 : (size_t)d.n_exp;
+    const size_t ni = d.n_pupil, nd = d.n_det, no = ((size_t)d.n_det + 2 * delta) * d.oversample, nl = d.n_lambda;
+    const size_t ldi = (ni + 7) / 8 * 8, ldo = (no + 7) / 8 * 8, B = nl * d.n_src * ne_mft, Bt = B * cap;
     const int fmt = dlx::fmt_of_prec(d.precision);
     const size_t pe = (size_t)dlx::fmt_planes(fmt) * dlx::fmt_esize(fmt);
     size_t b = pe * (nl * no * ldi + nl * ni * ldo + Bt * ni * ldi + Bt * no * ldi + Bt * no * ldo + Bt * ni * ldo);
-    b += 4 * (Bt * ni * ni) + 8 * (Bt * 2 * ni) + 4 * (size_t)d.n_src * d.n_exp * cap * no * no * 2;
+    b += 4 * (Bt * ni * ni) + 8 * (Bt * 2 * ni) + 4 * (size_t)d.n_src * ne_mft * cap * no * no * 2;
     b += 16 * (size_t)cap * ni * ni + 8 * (size_t)cap * d.n_exp * nd * nd;
+    if (d.dither_px) b += 4 * (size_t)cap * (d.n_exp * nd * nd + 2 * (no / d.oversample) * (no / d.oversample));
     const size_t nth = theta_size(d, has_pix);
     b += (size_t)cap * 4 * (ni * ni * (1 + 1 + d.n_zern) + nl + 2 * d.n_exp + d.n_exp * nd * nd + 4 * nth + 5);
     return b + (64u << 20);  // reduction partials, tables, allocator rounding
@@ -241,6 +251,7 @@ int create_bucket(dlx_server *s, const Req &r, Bucket **out) {
     if (b->bytes > free_budget) return DLX_ERR_NOMEM;
     dlx_mft_desc pd = d;
     pd.lambda_m = r.lambdas.data();
+    pd.dither_px = r.dither_px.empty() ? nullptr : r.dither_px.data();
     pd.psf_chunk = 0;
     pd.workspace_limit_bytes = 0;
     int rc = dlx::make_plan(&pd, s->device, cap, &b->plan);
@@ -587,7 +598,9 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
         d.n_zern < 0 || !d.lambda_m || d.precision < DLX_FP32_SIMT || d.precision > DLX_BF16X3SA)
         return fail(DLX_ERR_INVALID_ARG, "bad request shape");
     if (d.n_src > dlx::kMaxSrc) return fail(DLX_ERR_RANGE, "at most 32 sources");
-    if (d.dither_px) return fail(DLX_ERR_UNSUPPORTED, "integer-pixel dither windows (dither_px) are not served");
+    if (d.dither_px)
+        for (int k = 0; k < 2 * d.n_exp; ++k)
+            if (d.dither_px[k] < -4096 || d.dither_px[k] > 4096) return fail(DLX_ERR_RANGE, "|dither_px| <= 4096");
     if (!(d.focal_length_m >= 0) || !std::isfinite(d.focal_length_m) || !std::isfinite(d.focal_shift_m) ||
         (d.focal_length_m == 0 && d.focal_shift_m != 0) ||
         (d.focal_length_m > 0 && !(d.focal_length_m + d.focal_shift_m > 0)))
@@ -599,6 +612,8 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
     q->desc = d;
     q->lambdas.assign(d.lambda_m, d.lambda_m + d.n_lambda);
     q->desc.lambda_m = nullptr;
+    if (d.dither_px) q->dither_px.assign(d.dither_px, d.dither_px + 2 * (size_t)d.n_exp);
+    q->desc.dither_px = q->dither_px.empty() ? nullptr : q->dither_px.data();  // the request's own copy
     q->has_pix = rq->opd_pix != nullptr;
     const size_t npx = (size_t)d.n_pupil * d.n_pupil, np = (size_t)d.n_det * d.n_det;
     auto cp = [](std::vector<float> &dst, const float *src, size_t n) {

@@ -40,12 +40,23 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, problem, data, n_steps: int = 10, lr: Optional[dict] = None, precision: int = N.DLX_BF16X3) -> int:
+    def submit(self, problem, data, n_steps: int = 10, lr: Optional[dict] = None, precision: int = N.DLX_BF16X3,
+               crop: bool = False) -> int:
+        """crop=True serves whole-pixel dithers as windows of one larger detector per source."""
         p = problem
         lam = (C.c_double * len(p.lambdas))(*[float(x) for x in p.lambdas])
+        dpx = None
+        if crop:
+            from . import integer_dithers
+
+            k = integer_dithers(p)
+            if k is None:
+                raise ValueError("crop=True needs dithers of whole pixels")
+            dpx = (C.c_int32 * (2 * len(k)))(*[int(v) for row in k for v in row])
         desc = N.MftDesc(p.n_pupil, p.diameter, p.n_det, p.pixscale, p.oversample, len(p.lambdas),
                          C.cast(lam, C.POINTER(C.c_double)), len(p.flux), len(p.dither), len(p.coeff), precision, 0, 0,
-                         float(getattr(p, "prf_sigma", 0.0) or 0.0), None,
+                         float(getattr(p, "prf_sigma", 0.0) or 0.0),
+                         C.cast(dpx, C.POINTER(C.c_int32)) if dpx is not None else None,
                          float(getattr(p, "focal_length", 0.0) or 0.0), float(getattr(p, "focal_shift", 0.0) or 0.0))
         arrs = dict(transmission=_f32(p.transmission), opd_fixed=_f32(p.opd_fixed),
                     zern_basis=_f32(p.basis) if len(p.coeff) else None, weights=_f32(p.weights),

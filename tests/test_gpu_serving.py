@@ -37,11 +37,11 @@ SHAPE_A = dict(n_pupil=64, n_det=32, oversample=2, n_lambda=3, n_src=2, n_zern_m
 SHAPE_B = dict(n_pupil=48, n_det=24, oversample=4, n_lambda=2, n_src=1, n_zern_max=4)
 
 
-def _serve(P, reqs, n_steps=3, max_slots=8, budget=0, form="bf16x4"):
+def _serve(P, reqs, n_steps=3, max_slots=8, budget=0, form="bf16x4", crop=False):
     from paper_2406_08703_gb300.server import result_shapes
 
     srv = P.dlx_server_create(0, budget, max_slots)
-    tickets = [srv.submit(p, d, n_steps=n_steps, lr=LR, precision=P.PRECISIONS[form]) for p, d in reqs]
+    tickets = [srv.submit(p, d, n_steps=n_steps, lr=LR, precision=P.PRECISIONS[form], crop=crop) for p, d in reqs]
     out = [srv.poll(t, timeout_s=120.0, shapes=result_shapes(p)) for t, (p, _) in zip(tickets, reqs)]
     stats = srv.stats()
     srv.close()
@@ -72,6 +72,39 @@ def test_single_evaluation_matches_direct_call(P):
     assert rel_l2(res[0]["g_zern"], grads["d_zern"].cpu().numpy()) < 1e-6
     assert rel_l2(res[0]["g_flat"], grads["d_flat"].cpu().numpy()) < 1e-6
     assert res[0]["steps_done"] == 1
+
+
+def _window_request(seed, n_src=3):
+    """Whole-pixel dithers (the paper's windows, Sec. 3), small: three exposures."""
+    truth = W.make_problem("custom", seed=seed, n_pupil=40, n_det=20, oversample=2, n_lambda=2, n_src=n_src, n_exp=3,
+                           n_zern_max=5)
+    truth.dither = np.array([(0, 0), (2, -1), (-1, 3)], dtype=np.float64) * truth.pixscale
+    data = W.poisson_counts(oracle.forward(truth), seed + 1)
+    return W.perturbed_start(truth, seed + 2), data
+
+
+def test_windows_served_alone_in_the_mix_and_as_a_plan(P):
+    """Integer-dither window requests: one evaluation equals the window plan's loss and gradient,
+    and K Adam steps give the same result alone and among other window requests of its shape
+    (slots of one bucket)."""
+    import torch
+
+    a = _window_request(110)
+    one, _ = _serve(P, [a], n_steps=0, crop=True)
+    plan = P.dlx_make_mft(P.desc_from_problem(a[0], P.DLX_BF16X4, crop=True))
+    loss, grads, _ = P.dlx_loss_grad(plan, P.params_from_problem(a[0]), torch.as_tensor(a[1], device="cuda"))
+    torch.cuda.synchronize()
+    assert one[0]["loss"] == pytest.approx(loss.item(), rel=1e-9)
+    for k, gk in (("g_zern", "d_zern"), ("g_flat", "d_flat"), ("g_flux", "d_flux"), ("g_pos", "d_pos")):
+        assert rel_l2(one[0][k], grads[gk].cpu().numpy()) < 1e-6, k
+    alone, _ = _serve(P, [a], n_steps=3, crop=True)
+    others = [_window_request(120 + i) for i in range(2)]
+    mixed, stats = _serve(P, [others[0], a, others[1]], n_steps=3, crop=True)
+    assert stats["grouped_launches"] > 0
+    x, y = alone[0], mixed[1]
+    assert x["loss"] == pytest.approx(y["loss"], rel=1e-9)
+    for k in ("zern_coeff", "flux", "pos", "flat", "g_zern", "g_flat", "g_pos"):
+        assert rel_l2(y[k], x[k]) < 1e-6, k
 
 
 def test_adam_steps_match_manual_loop(P):
