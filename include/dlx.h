@@ -27,6 +27,11 @@
  * outputs are valid once the stream has completed.  Every call returns a
  * dlx_status; no exception crosses the ABI.  dlx_last_error() gives a
  * thread-local message for the last failing call on the calling thread.
+ *
+ * A plan holds one evaluation's workspaces: calls on the same plan must be
+ * issued by one host thread at a time and on one stream (or with the caller
+ * ordering the streams), since each call's work reuses them; different plans
+ * are independent.  The server (dlx_server_*) is thread-safe.
  */
 #ifndef DLX_H
 #define DLX_H
