@@ -247,3 +247,23 @@ def test_integer_dither_windows_against_oracle(form):
     assert ej < TOL[form]["J"]
     assert errs["fisher"] < TOL[form]["info"]
     assert errs["hessian"] < TOL[form]["hess"]
+
+
+def test_fresnel_regime_against_oracle():
+    """The Laplace passes in the Fresnel regime (Sec. 1): the tangent phasors carry the pupil chirp
+    through the same tilt tables; J and the Fisher matrix against the oracle's differences."""
+    import oracle
+    from oracle import laplace as OL
+
+    p = aberrated_problem()
+    # detector moved so the pupil chirp reaches about 3 rad at the edge: pi R^2 dz / (f^2 lambda)
+    f = 1.0
+    p.focal_length, p.focal_shift = f, 3.0 * LAM * f * f / (np.pi * (0.5 * p.diameter) ** 2)
+    Jref, labs_ref = OL.jacobian(p)
+    ref = OL.information(p, None, "fisher")[0]
+    J, out, labs = _gpu(p, "fp32")
+    ej = float(np.max(np.abs(J - Jref).max(axis=1) / np.abs(Jref).max(axis=1)))
+    err = _rel(out["fisher"], ref)
+    print("fresnel: J", ej, "fisher", err, "focal shift", p.focal_shift)
+    assert labs == labs_ref
+    assert ej < TOL["fp32"]["J"] and err < TOL["fp32"]["info"]

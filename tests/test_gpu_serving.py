@@ -107,6 +107,25 @@ def test_windows_served_alone_in_the_mix_and_as_a_plan(P):
         assert rel_l2(y[k], x[k]) < 1e-6, k
 
 
+def test_fresnel_request_matches_direct_call(P):
+    """A request in the Fresnel regime (Sec. 1): focal length and focus offset key its bucket and
+    reach its plan; one evaluation equals the direct call."""
+    import torch
+
+    p, d = _request(130, **SHAPE_B)
+    p.focal_length, p.focal_shift = 1.2, 2e-4
+    res, _ = _serve(P, [(p, d)], n_steps=0)
+    plan = P.dlx_make_mft(P.desc_from_problem(p, P.DLX_BF16X4))
+    loss, grads, _ = P.dlx_loss_grad(plan, P.params_from_problem(p), torch.as_tensor(d, device="cuda"))
+    torch.cuda.synchronize()
+    assert res[0]["loss"] == pytest.approx(loss.item(), rel=1e-9)
+    assert rel_l2(res[0]["g_zern"], grads["d_zern"].cpu().numpy()) < 1e-6
+    q = p.copy()
+    q.focal_length, q.focal_shift = 0.0, 0.0
+    res0, _ = _serve(P, [(q, d)], n_steps=0)
+    assert abs(res0[0]["loss"] - res[0]["loss"]) > 1e-6 * abs(res[0]["loss"])  # the defocus is not dropped
+
+
 def test_adam_steps_match_manual_loop(P):
     import torch
 
