@@ -155,13 +155,17 @@ __device__ __forceinline__ void store_cplx8(void *base, size_t pstride, size_t i
 
 // Stochastic splitting (BF16x3 form).  hi = SR(x) and lo = SR(x - hi), where SR
 // rounds to bf16 up or down in magnitude with probability proportional to the
-// distance (add 16 random bits below the kept bits of the fp32 pattern, then
-// truncate), so E[hi + lo] = x and the errors of different elements are
-// independent and zero-mean: the products that a three-product split drops, and
-// the rounding of the kept ones, then add up like sqrt(K) instead of K in a
-// coherent sum.  The random bits come from a counter-based hash of the element's
-// index and a per-operand seed (the 32-bit finaliser of MurmurHash3), so results
-// are reproducible.
+// distance (add random bits below the kept bits of the fp32 pattern, then
+// truncate), so E[hi + lo] = x up to the randomness' granularity and the errors
+// of different elements are independent and zero-mean: the products that a
+// three-product split drops, and the rounding of the kept ones, then add up like
+// sqrt(K) instead of K in a coherent sum.  A split takes 8 random bits per
+// rounding: the bias left by that granularity is at most 2^-8 ulp, which puts the
+// coherent part of the dropped lo*lo products near 2^-30 and that of lo's own
+// rounding near 2^-23 of a sum's size, so one 32-bit hash serves both parts of
+// both components of a complex element.  The bits come from a counter-based hash
+// of the element's index and a per-operand seed (the 32-bit finaliser of
+// MurmurHash3), so results are reproducible.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
     h *= 0x85ebca6bu;
@@ -175,27 +179,27 @@ __device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, uint32_t r16) {
     if ((u & 0x7f800000u) != 0x7f800000u) u += r16;  // finite values only
     return __ushort_as_bfloat16((unsigned short)(u >> 16));
 }
-// 64 random bits for element `gidx` of the operand with seed `seed` (two
-// finaliser rounds; the index's high word, zero for operands below 2^32
-// elements, is folded in by a multiply)
-__device__ __forceinline__ uint2 sr_bits(uint64_t gidx, uint32_t seed) {
+// 32 random bits for element `gidx` of the operand with seed `seed` (one finaliser
+// round; the index's high word, zero for operands below 2^32 elements, is folded in
+// by a multiply)
+__device__ __forceinline__ uint32_t sr_word(uint64_t gidx, uint32_t seed) {
     const uint32_t k = (uint32_t)gidx ^ seed ^ ((uint32_t)(gidx >> 32) * 0x9e3779b9u);
-    const uint32_t h1 = fmix32(k);
-    return make_uint2(h1, fmix32(h1 ^ 0x7f4a7c15u));
+    return fmix32(k);
 }
+// x = hi + lo with 8 random bits per rounding: bits 0-7 of r for hi, bits 8-15 for lo
 __device__ __forceinline__ void split_sr(float x, uint32_t r, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
-    hi = bf16_sr(x, r & 0xffffu);
-    lo = bf16_sr(x - __bfloat162float(hi), r >> 16);  // x - hi is exact in fp32
+    hi = bf16_sr(x, (r & 0xffu) << 8);
+    lo = bf16_sr(x - __bfloat162float(hi), r & 0xff00u);  // x - hi is exact in fp32
 }
 
 // store_cplx for the BF16X4 layout with stochastic splitting (element index gidx)
 __device__ __forceinline__ void store_cplx_sr(void *base, size_t pstride, size_t idx, float re, float im, uint64_t gidx,
                                               uint32_t seed) {
     __nv_bfloat16 *p = (__nv_bfloat16 *)base;
-    const uint2 r = sr_bits(gidx, seed);
+    const uint32_t r = sr_word(gidx, seed);
     __nv_bfloat16 rh, rl, ih, il;
-    split_sr(re, r.x, rh, rl);
-    split_sr(im, r.y, ih, il);
+    split_sr(re, r, rh, rl);
+    split_sr(im, r >> 16, ih, il);
     p[idx] = rh;
     p[pstride + idx] = rl;
     p[2 * pstride + idx] = ih;
@@ -209,9 +213,9 @@ __device__ __forceinline__ void store_cplx8_sr(void *base, size_t pstride, size_
     __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const uint2 r = sr_bits(gidx + q, seed);
-        split_sr(re[q], r.x, rh[q], rl[q]);
-        split_sr(im[q], r.y, ih[q], il[q]);
+        const uint32_t r = sr_word(gidx + q, seed);
+        split_sr(re[q], r, rh[q], rl[q]);
+        split_sr(im[q], r >> 16, ih[q], il[q]);
     }
     *(uint4 *)p = *(const uint4 *)rh;
     *(uint4 *)(p + pstride) = *(const uint4 *)rl;

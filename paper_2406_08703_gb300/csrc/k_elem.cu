@@ -105,10 +105,10 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const
         if constexpr (F == FMT_BF16X4) {
             if (ah_hi) {
                 __nv_bfloat16 *ah = (__nv_bfloat16 *)amatH + (size_t)l * 2 * ni * ldo;
-                const uint2 rb = sr_bits(((size_t)l * ni + n) * ldo + k, sr ^ 0x68e31da4u);
+                const uint32_t rb = sr_word(((size_t)l * ni + n) * ldo + k, sr ^ 0x68e31da4u);
                 const size_t o = (size_t)n * ldo + k;
-                ah[o] = bf16_sr(re, rb.x & 0xffffu);
-                ah[(size_t)ni * ldo + o] = bf16_sr(-im, rb.y & 0xffffu);
+                ah[o] = bf16_sr(re, rb & 0xffffu);
+                ah[(size_t)ni * ldo + o] = bf16_sr(-im, rb >> 16);
                 continue;
             }
         }

@@ -434,9 +434,9 @@ __device__ __forceinline__ void stage_row16_sr(uint8_t *stg, int r, int h, const
         __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const uint2 rb = sr_bits(gidx + 8 * q + i, seed);
-            split_sr(re[8 * q + i], rb.x, rh[i], rl[i]);
-            split_sr(im[8 * q + i], rb.y, ih[i], il[i]);
+            const uint32_t rb = sr_word(gidx + 8 * q + i, seed);
+            split_sr(re[8 * q + i], rb, rh[i], rl[i]);
+            split_sr(im[8 * q + i], rb >> 16, ih[i], il[i]);
         }
         const int g = (2 * h + q) ^ ((r >> 1) & 3);
         uint8_t *p = stg + r * 64 + g * 16;
