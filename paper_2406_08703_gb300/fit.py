@@ -33,12 +33,48 @@ def paper_schedule(lr: dict, epochs_psf: int = 100, epochs_prf: int = 50) -> lis
     return [(epochs_psf, psf), (epochs_prf, {"flat": lr["flat"]})]
 
 
+def new_state(params: dict, groups=GROUPS) -> dict:
+    """Adam state of every group: {group: [m, v, steps]} (device tensors shaped like the parameter)."""
+    import torch
+
+    return {g: [torch.zeros_like(params[GROUPS[g][0]]), torch.zeros_like(params[GROUPS[g][0]]), 0]
+            for g in groups if params.get(GROUPS[g][0]) is not None}
+
+
+def checkpoint(params: dict, state: dict) -> dict:
+    """Host copy of a fit: every parameter tensor and each group's Adam moments and step count.
+    `restore` turns it back into device tensors; continuing from it repeats the uninterrupted fit
+    bit for bit (every kernel here sums in a fixed order)."""
+    out = {"param/" + k: v.detach().cpu().numpy().copy() for k, v in params.items() if v is not None}
+    for g, (m, v, t) in state.items():
+        out["m/" + g] = m.detach().cpu().numpy().copy()
+        out["v/" + g] = v.detach().cpu().numpy().copy()
+        out["t/" + g] = t
+    return out
+
+
+def restore(ckpt: dict, device: str = "cuda") -> tuple:
+    """(params, state) as device tensors from `checkpoint`'s host copy."""
+    import torch
+
+    params = {k[6:]: torch.as_tensor(v, device=device).clone() for k, v in ckpt.items() if k.startswith("param/")}
+    state = {}
+    for k, v in ckpt.items():
+        if k.startswith("m/"):
+            g = k[2:]
+            state[g] = [torch.as_tensor(v, device=device).clone(), torch.as_tensor(ckpt["v/" + g], device=device).clone(),
+                        int(ckpt["t/" + g])]
+    return params, state
+
+
 def staged_fit(plan, params: dict, data, stages: Sequence, stream=None, beta1: float = 0.9, beta2: float = 0.999,
-               eps: float = 1e-8, losses: Optional[object] = None) -> object:
+               eps: float = 1e-8, losses: Optional[object] = None, state: Optional[dict] = None) -> object:
     """Runs the stages in place on `params` (float32 device tensors, updated in
-    place).  `stages` is a list of (n_epochs, {group: learning rate}).  Returns
-    the float64 device tensor of the loss of every epoch (evaluated before that
-    epoch's update)."""
+    place).  `stages` is a list of (n_epochs, {group: learning rate}).  `state`
+    (from `new_state`, or `restore` of a checkpoint) carries each group's Adam
+    moments and step count across calls and is updated in place; without it a
+    fresh state is used.  Returns the float64 device tensor of the loss of every
+    epoch (evaluated before that epoch's update)."""
     import torch
 
     n_total = sum(int(n) for n, _ in stages)
@@ -52,7 +88,11 @@ def staged_fit(plan, params: dict, data, stages: Sequence, stream=None, beta1: f
         if params.get(GROUPS[g][0]) is None:
             raise ValueError(f"group {g!r} has no parameter tensor")
     grads = empty_grads(plan)
-    state = {g: [torch.zeros_like(params[GROUPS[g][0]]), torch.zeros_like(params[GROUPS[g][0]]), 0] for g in used}
+    if state is None:
+        state = new_state(params, used)
+    for g in used:
+        if g not in state:
+            state[g] = new_state(params, [g])[g]
     i = 0
     for n, lrs in stages:
         for _ in range(int(n)):
