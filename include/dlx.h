@@ -319,6 +319,16 @@ typedef struct {
     const int32_t *data;        /* host [n_exp][Nd][Nd] */
     int n_steps;                /* K Adam steps */
     float lr[5];                /* learning rates: zern, opd_pix, flat, flux, pos (0 freezes a group) */
+    /* Optional resume state; NULL / 0 start a fresh fit.  The Adam moments are in
+     * the packed parameter order [zern_coeff | opd_pix (only when fitted) | flat |
+     * flux | pos], n_state = n_zern + (opd_pix ? Ni*Ni : 0) + Nd*Nd + 3 n_src
+     * floats each (NULL = zeros); adam_step >= 0 is the number of Adam steps
+     * already taken, which sets the bias correction of the next one.  Fed the
+     * parameters, moments and step count of a dlx_result, a request continues
+     * that fit bit for bit: K1 steps and then K2 more equal K1 + K2 in one. */
+    const float *adam_m;        /* host [n_state] or NULL */
+    const float *adam_v;        /* host [n_state] or NULL */
+    int adam_step;
 } dlx_request;
 
 /* Result of a finished request, copied into caller-owned HOST buffers (any may be NULL). */
@@ -328,6 +338,8 @@ typedef struct {
     float *g_zern, *g_opd_pix, *g_flux, *g_pos, *g_flat;      /* gradient of the last evaluation */
     double queued_s, latency_s; /* submit -> admit, submit -> done */
     int steps_done;
+    float *adam_m, *adam_v;     /* Adam moments after the last step, packed as in dlx_request, or NULL */
+    int adam_step;              /* the request's adam_step + K: feed back to continue the fit */
 } dlx_result;
 
 typedef struct {

@@ -55,13 +55,15 @@ class KernelTimes(C.Structure):
 class Request(C.Structure):
     _fields_ = [("desc", MftDesc)] + [(k, C.c_void_p) for k in (
         "transmission", "opd_fixed", "zern_basis", "weights", "dither", "zern_coeff", "opd_pix", "flux", "pos",
-        "flat", "data")] + [("n_steps", C.c_int), ("lr", C.c_float * 5)]
+        "flat", "data")] + [("n_steps", C.c_int), ("lr", C.c_float * 5), ("adam_m", C.c_void_p),
+                            ("adam_v", C.c_void_p), ("adam_step", C.c_int)]
 
 
 class Result(C.Structure):
     _fields_ = [("loss", C.c_double)] + [(k, C.c_void_p) for k in (
         "zern_coeff", "opd_pix", "flux", "pos", "flat", "g_zern", "g_opd_pix", "g_flux", "g_pos", "g_flat")] + [
-        ("queued_s", C.c_double), ("latency_s", C.c_double), ("steps_done", C.c_int)]
+        ("queued_s", C.c_double), ("latency_s", C.c_double), ("steps_done", C.c_int), ("adam_m", C.c_void_p),
+        ("adam_v", C.c_void_p), ("adam_step", C.c_int)]
 
 
 class ServerStats(C.Structure):

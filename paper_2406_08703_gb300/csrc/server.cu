@@ -51,6 +51,8 @@ struct Req {
     std::vector<int32_t> data;
     int n_steps = 0;
     float lr[5] = {0, 0, 0, 0, 0};
+    std::vector<float> m_in, v_in;  // resume state (empty = zeros)
+    int step_in = 0;
     clk::time_point t_submit, t_admit, t_done;
     int status = DLX_PENDING;
     bool done = false;
@@ -59,7 +61,7 @@ struct Req {
     int slot = -1;
     // results (copied out of the bucket, which may be released before the poll)
     double loss = 0;
-    std::vector<float> theta_out, grad_out;
+    std::vector<float> theta_out, grad_out, m_out, v_out;
     int off[6] = {0};
 };
 
@@ -314,9 +316,11 @@ void upload(Bucket *b, int r, Req *q, bool poison) {
     if (poison) th[b->off[3]] = NAN;  // host-side fault injection: a bad input, no device fault
     h2d(b->theta + r * b->n_theta, th.data(), 4 * b->n_theta);
     cudaStreamSynchronize(st);  // th is a local buffer
-    cudaMemsetAsync(b->m + r * b->n_theta, 0, 4 * b->n_theta, st);
-    cudaMemsetAsync(b->v + r * b->n_theta, 0, 4 * b->n_theta, st);
-    cudaMemsetAsync(b->step + r, 0, sizeof(int), st);
+    if (!q->m_in.empty()) h2d(b->m + r * b->n_theta, q->m_in.data(), 4 * b->n_theta);
+    else cudaMemsetAsync(b->m + r * b->n_theta, 0, 4 * b->n_theta, st);
+    if (!q->v_in.empty()) h2d(b->v + r * b->n_theta, q->v_in.data(), 4 * b->n_theta);
+    else cudaMemsetAsync(b->v + r * b->n_theta, 0, 4 * b->n_theta, st);
+    h2d(b->step + r, &q->step_in, sizeof(int));
     float lr[5];
     for (int k = 0; k < 5; ++k) lr[k] = q->n_steps > 0 ? q->lr[k] : 0.f;
     if (!b->has_pix) lr[1] = 0.f;
@@ -509,6 +513,10 @@ void worker_loop(dlx_server *s) {
                                    cudaMemcpyDeviceToHost);
                         cudaMemcpy(q->grad_out.data(), b->grad + r * b->n_theta, 4 * b->n_theta,
                                    cudaMemcpyDeviceToHost);
+                        q->m_out.resize(b->n_theta);
+                        q->v_out.resize(b->n_theta);
+                        cudaMemcpy(q->m_out.data(), b->m + r * b->n_theta, 4 * b->n_theta, cudaMemcpyDeviceToHost);
+                        cudaMemcpy(q->v_out.data(), b->v + r * b->n_theta, 4 * b->n_theta, cudaMemcpyDeviceToHost);
                     }
                     finish(s, q, status);
                     const int last = b->active - 1;
@@ -529,7 +537,10 @@ void copy_out(const Req *q, dlx_result *out) {
     out->queued_s = secs(q->t_submit, q->t_admit);
     out->latency_s = secs(q->t_submit, q->t_done);
     out->steps_done = q->steps_done;
+    out->adam_step = q->step_in + q->n_steps;  // K = 0 evaluates with every rate at zero: no Adam step
     if (q->theta_out.empty()) return;
+    if (out->adam_m) memcpy(out->adam_m, q->m_out.data(), 4 * q->m_out.size());
+    if (out->adam_v) memcpy(out->adam_v, q->v_out.data(), 4 * q->v_out.size());
     const dlx_mft_desc &d = q->desc;
     const int *off = q->off;
     auto cp = [&](float *dst, const std::vector<float> &src, int o, size_t n) {
@@ -608,6 +619,8 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
     if (!rq->transmission || !rq->weights || !rq->flux || !rq->pos || !rq->flat || !rq->data ||
         (d.n_zern > 0 && (!rq->zern_basis || !rq->zern_coeff)) || rq->n_steps < 0)
         return fail(DLX_ERR_INVALID_ARG, "missing request input");
+    if (rq->adam_step < 0 || rq->adam_step > (1 << 30) - rq->n_steps)
+        return fail(DLX_ERR_INVALID_ARG, "adam_step must be >= 0 (and adam_step + n_steps < 2^30)");
     auto q = std::make_unique<Req>();
     q->desc = d;
     q->lambdas.assign(d.lambda_m, d.lambda_m + d.n_lambda);
@@ -632,6 +645,10 @@ int dlx_submit(dlx_server *s, const dlx_request *rq, uint64_t *ticket) {
     q->data.assign(rq->data, rq->data + (size_t)d.n_exp * np);
     q->n_steps = rq->n_steps;
     for (int k = 0; k < 5; ++k) q->lr[k] = rq->lr[k];
+    const size_t nth = theta_size(d, q->has_pix);
+    cp(q->m_in, rq->adam_m, nth);
+    cp(q->v_in, rq->adam_v, nth);
+    q->step_in = rq->adam_step;
     const size_t need = bucket_bytes(d, q->has_pix, 1);
     std::lock_guard<std::mutex> lk(s->mu);
     s->stats.submitted++;

@@ -41,8 +41,10 @@ class Server:
             pass
 
     def submit(self, problem, data, n_steps: int = 10, lr: Optional[dict] = None, precision: int = N.DLX_BF16X3,
-               crop: bool = False) -> int:
-        """crop=True serves whole-pixel dithers as windows of one larger detector per source."""
+               crop: bool = False, state: Optional[dict] = None) -> int:
+        """crop=True serves whole-pixel dithers as windows of one larger detector per source.
+        state = a poll result's {"adam_m", "adam_v", "adam_step"} (with the problem's parameters set to
+        that result's) continues that fit exactly; None starts a fresh one."""
         p = problem
         lam = (C.c_double * len(p.lambdas))(*[float(x) for x in p.lambdas])
         dpx = None
@@ -68,6 +70,16 @@ class Server:
         for k, a in arrs.items():
             setattr(req, k, None if a is None else a.ctypes.data)
         req.n_steps = n_steps
+        if state is not None:
+            n = state_size(p)
+            for k in ("adam_m", "adam_v"):
+                a = _f32(state.get(k))
+                if a is not None:
+                    if a.size != n:
+                        raise ValueError(f"{k} has {a.size} values, the packed parameters {n}")
+                    arrs[k] = a
+                    setattr(req, k, a.ctypes.data)
+            req.adam_step = int(state.get("adam_step", 0))
         lr = lr or {}
         for i, g in enumerate(_GROUPS):
             req.lr[i] = float(lr.get(g, 0.0))
@@ -76,17 +88,20 @@ class Server:
         return t.value
 
     def poll(self, ticket: int, timeout_s: float = 0.0, shapes: Optional[dict] = None):
-        """Returns None while pending, else a dict with the final parameters, gradient and timings."""
+        """Returns None while pending, else a dict with the final parameters, gradient and timings
+        (and the Adam state when `shapes` holds "adam_m" / "adam_v", see result_shapes(state=True))."""
         sh = shapes or {}
         out = {k: np.zeros(v, np.float32) for k, v in sh.items()}
         res = N.Result()
-        for k in ("zern_coeff", "opd_pix", "flux", "pos", "flat", "g_zern", "g_opd_pix", "g_flux", "g_pos", "g_flat"):
+        for k in ("zern_coeff", "opd_pix", "flux", "pos", "flat", "g_zern", "g_opd_pix", "g_flux", "g_pos", "g_flat",
+                  "adam_m", "adam_v"):
             setattr(res, k, out[k].ctypes.data if k in out else None)
         rc = N.load().dlx_poll(self.handle, ticket, timeout_s, C.byref(res))
         if rc == N.DLX_PENDING:
             return None
         N.check(rc, "dlx_poll")
-        out.update(loss=res.loss, queued_s=res.queued_s, latency_s=res.latency_s, steps_done=res.steps_done)
+        out.update(loss=res.loss, queued_s=res.queued_s, latency_s=res.latency_s, steps_done=res.steps_done,
+                   adam_step=res.adam_step)
         return out
 
     def stats(self) -> dict:
@@ -98,11 +113,21 @@ class Server:
         N.check(N.load().dlx_server_inject_fault(self.handle, kind), "dlx_server_inject_fault")
 
 
-def result_shapes(problem) -> dict:
+def state_size(problem) -> int:
+    """Length of the packed Adam moments [zern_coeff | opd_pix (when fitted) | flat | flux | pos]."""
+    p = problem
+    ni = p.n_pupil * p.n_pupil if p.opd_pix is not None else 0
+    return len(p.coeff) + ni + p.n_det * p.n_det + 3 * len(p.flux)
+
+
+def result_shapes(problem, state: bool = False) -> dict:
     p = problem
     nz, ni, nd, ns = len(p.coeff), p.n_pupil, p.n_det, len(p.flux)
-    return dict(zern_coeff=(max(nz, 1),), opd_pix=(ni, ni), flux=(ns,), pos=(ns, 2), flat=(nd, nd),
-                g_zern=(max(nz, 1),), g_opd_pix=(ni, ni), g_flux=(ns,), g_pos=(ns, 2), g_flat=(nd, nd))
+    sh = dict(zern_coeff=(max(nz, 1),), opd_pix=(ni, ni), flux=(ns,), pos=(ns, 2), flat=(nd, nd),
+              g_zern=(max(nz, 1),), g_opd_pix=(ni, ni), g_flux=(ns,), g_pos=(ns, 2), g_flat=(nd, nd))
+    if state:
+        sh.update(adam_m=(state_size(p),), adam_v=(state_size(p),))
+    return sh
 
 
 def dlx_server_create(device: int = 0, hbm_budget: int = 0, max_slots: int = 16) -> Server:

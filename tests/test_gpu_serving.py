@@ -146,6 +146,49 @@ def test_adam_steps_match_manual_loop(P):
         assert rel_l2(res[0][k], prm[k].cpu().numpy()) < 1e-5, k
 
 
+def test_resumed_request_continues_bitwise(P):
+    """K1 steps, then K2 more from the returned parameters and Adam state, equal K1 + K2 in one request."""
+    import dataclasses
+
+    from paper_2406_08703_gb300.server import result_shapes, state_size
+
+    p, d = _request(75, **SHAPE_A)
+    sh = result_shapes(p, state=True)
+    form = P.PRECISIONS["bf16x3"]
+
+    def run(prob, k, state=None):
+        srv = P.dlx_server_create(0, 0, 2)
+        t = srv.submit(prob, d, n_steps=k, lr=LR, precision=form, state=state)
+        r = srv.poll(t, timeout_s=120.0, shapes=sh)
+        srv.close()
+        return r
+
+    whole = run(p, 6)
+    first = run(p, 2)
+    assert first["adam_step"] == 2 and whole["adam_step"] == 6
+    n = state_size(p)
+    assert first["adam_m"].shape == (n,) and np.count_nonzero(first["adam_v"]) > n // 4
+    mid = dataclasses.replace(p, coeff=first["zern_coeff"][:len(p.coeff)].copy(), opd_pix=first["opd_pix"].copy(),
+                              flux=first["flux"].copy(), pos=first["pos"].copy(), flat=first["flat"].copy())
+    st = {k: first[k] for k in ("adam_m", "adam_v", "adam_step")}
+    second = run(mid, 4, st)
+    assert second["adam_step"] == 6 and second["steps_done"] == 4
+    assert second["loss"] == whole["loss"]
+    for k in ("zern_coeff", "opd_pix", "flux", "pos", "flat", "g_zern", "g_opd_pix", "g_flat", "g_pos", "adam_m",
+              "adam_v"):
+        assert np.array_equal(second[k], whole[k]), k
+    # an evaluation (K = 0) takes no Adam step and hands the state back unchanged
+    ev = run(mid, 0, st)
+    assert ev["adam_step"] == 2
+    assert np.array_equal(ev["adam_m"], first["adam_m"]) and np.array_equal(ev["adam_v"], first["adam_v"])
+    srv = P.dlx_server_create(0, 0, 1)
+    with pytest.raises(Exception):
+        srv.submit(mid, d, n_steps=1, lr=LR, precision=form, state=dict(st, adam_step=-1))
+    with pytest.raises(ValueError):
+        srv.submit(mid, d, n_steps=1, lr=LR, precision=form, state=dict(st, adam_m=st["adam_m"][:-1]))
+    srv.close()
+
+
 def test_admission_respects_budget_and_all_complete(P):
     reqs = [_request(80 + i, **(SHAPE_A if i % 2 else SHAPE_B)) for i in range(6)]
     from paper_2406_08703_gb300.server import result_shapes
