@@ -274,6 +274,37 @@ int dlx_loss_grad(dlx_plan *plan, const dlx_params *params, const int32_t *data,
  * when a device-side bounded wait expired; the flag is cleared by this call). */
 int dlx_plan_diagnostics(dlx_plan *plan, int64_t *clamped, int32_t *device_error);
 
+/* Checked mode, a stand-in for a device memory checker (the library checks its own
+ * calls).  Level 1: before any launch, every device array an entry point reads or
+ * writes must be device memory of the plan's device (or managed memory), aligned
+ * for its element type (4 bytes; 8 for doubles) and, where the driver reports the
+ * allocation holding it, lie inside that allocation for the full size the shapes
+ * imply (a sub-allocation of a caching allocator is checked against its whole
+ * block); a failure returns INVALID_ARG naming the argument and launches nothing.
+ * Level 2 also synchronises the stream after each kernel class (not while the
+ * stream is being captured) and returns CUDA, or TIMEOUT when a device-side
+ * bounded wait expired, naming the class.  0 (the default) checks nothing.  The
+ * level is process-wide; the environment variable DLX_CHECKS sets it when the
+ * library is first used.  Errors: INVALID_ARG (level outside 0..2). */
+int dlx_set_checks(int level);
+int dlx_get_checks(void);
+/* Level 1's test of one array: device memory of `device`, 4-byte aligned, and
+ * `bytes` inside its allocation.  Launches nothing. */
+int dlx_check_buffer(const void *ptr, size_t bytes, int device);
+/* The level-1 checks of a dlx_loss_grad call with these arguments, whatever the
+ * level; launches nothing. */
+int dlx_check_loss_grad_args(dlx_plan *plan, const dlx_params *params, const int32_t *data, const double *loss,
+                             const dlx_grads *grads, const float *model_opt);
+
+/* Test hook for the device-side bounded waits (no fault, no hang): kind 1 makes
+ * CTA 0 of the plan's next tensor-core contraction withhold its first operand
+ * copy, so the wait for it expires after 1 s; the CTA stops its work, frees its
+ * tensor memory and returns, the device error flag is raised
+ * (dlx_plan_diagnostics), and that call's results are undefined.  The plan and
+ * the context stay usable.  Errors: INVALID_ARG (other kinds, the FP32 form,
+ * which has no such waits). */
+int dlx_plan_inject_fault(dlx_plan *plan, int kind);
+
 /* Per-kernel-class device time of the evaluations issued on this plan while
  * timing is enabled: CUDA events are recorded on the launching stream around
  * each timed class of launch (so the times include no host gaps), and every

@@ -396,6 +396,26 @@ def dlx_plan_diagnostics(plan: Plan):
     return dict(clamped=c.value, device_error=e.value)
 
 
+def dlx_set_checks(level: int) -> None:
+    """Checked mode of the library (process-wide): 0 off, 1 argument checks before every launch,
+    2 also a synchronising check after every kernel class."""
+    N.check(load().dlx_set_checks(int(level)), "dlx_set_checks")
+
+
+def dlx_get_checks() -> int:
+    return int(load().dlx_get_checks())
+
+
+def dlx_check_buffer(ptr: int, nbytes: int, device: int = 0) -> int:
+    """Status of the checked mode's test of one device array (0 = OK); launches nothing."""
+    return int(load().dlx_check_buffer(C.c_void_p(ptr), nbytes, device))
+
+
+def dlx_plan_inject_fault(plan: Plan, kind: int = 1) -> None:
+    """Test hook: the next tensor-core contraction's bounded wait expires (device error flag)."""
+    N.check(load().dlx_plan_inject_fault(plan.handle, kind), "dlx_plan_inject_fault")
+
+
 def dlx_plan_set_timing(plan: Plan, enable: bool = True, classes=None) -> None:
     """Times every kernel class (enable=True), none (False), or only the named ones."""
     if not enable:

@@ -93,6 +93,12 @@ SIGNATURES = {
                                 C.c_void_p, C.c_void_p]),
     "dlx_plan_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "dlx_plan_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "dlx_set_checks": (C.c_int, [C.c_int]),
+    "dlx_get_checks": (C.c_int, []),
+    "dlx_check_buffer": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int]),
+    "dlx_check_loss_grad_args": (C.c_int, [C.c_void_p, C.POINTER(Params), C.c_void_p, C.c_void_p,
+                                           C.POINTER(Grads), C.c_void_p]),
+    "dlx_plan_inject_fault": (C.c_int, [C.c_void_p, C.c_int]),
     "dlx_plan_get_timing": (C.c_int, [C.c_void_p, C.POINTER(KernelTimes)]),
     "dlx_adam": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_float, C.c_float,
                            C.c_float, C.c_float, C.c_int, C.c_void_p]),

@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 
 #include "dlx_common.cuh"
@@ -62,6 +63,26 @@ void plan_free(dlx_plan *p) {
     p->allocs.clear();
 }
 
+// Level-1 checks of a call's device arrays (list of pointer, bytes, alignment, name,
+// optional), after those of its dlx_params; clears the plan's level-2 record.
+struct Buf {
+    const void *ptr;
+    size_t bytes, align;
+    const char *name;
+    bool optional;
+};
+int check_call(dlx_plan *p, const dlx_params *prm, std::initializer_list<Buf> bufs,
+               const dlx_grads *g = nullptr, const char *gname = "grads") {
+    p->check_rc = 0;
+    p->check_msg.clear();
+    if (dlx::check_level() < 1) return DLX_OK;
+    int rc = dlx::check_params(p, prm);
+    for (const Buf &b : bufs)
+        if (!rc) rc = dlx::check_buffer(b.ptr, b.bytes, b.align, p->device, b.name, b.optional);
+    if (!rc) rc = dlx::check_grads(p, g, gname);
+    return rc;
+}
+
 int validate_params(const dlx_plan *p, const dlx_params *prm) {
     if (!prm) return fail(DLX_ERR_INVALID_ARG, "params is NULL");
     if (!prm->transmission || !prm->weights || !prm->flux || !prm->pos || !prm->flat)
@@ -103,7 +124,10 @@ KScope::~KScope() {
         cudaEventRecord(b, st);
         p->events[cls]++;
     }
+    if (check_level() >= 2) class_check(p, cls, st);
 }
+
+const char *class_name(int cls) { return (cls >= 0 && cls < KC_N) ? kClassNames[cls] : "?"; }
 
 void free_plan(dlx_plan *p) {
     if (!p) return;
@@ -508,12 +532,13 @@ int dlx_forward(dlx_plan *p, const dlx_params *prm, float *model, void *stream) 
     if (!p || !model) return fail(DLX_ERR_INVALID_ARG, "plan/model is NULL");
     int rc = validate_params(p, prm);
     if (rc) return rc;
+    if ((rc = check_call(p, prm, {{model, dlx::image_bytes(p), 4, "model", false}}))) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const dlx::DevParams d = dev_params(p, prm);
-    if ((rc = dlx::eval_forward(p, d, 1, st))) return rc;
+    if ((rc = dlx::eval_forward(p, d, 1, st))) return dlx::checked_status(p, rc);
     DLX_CU(dlx::launch_bin_nll(p, d, 1, nullptr, 0, model, 0, nullptr, nullptr, st), "bin");
-    return DLX_OK;
+    return dlx::checked_status(p, DLX_OK);
 }
 
 int dlx_model_jvp(dlx_plan *p, const dlx_params *prm, const float *t_map, uint32_t src_mask, double alpha, float *jvp,
@@ -522,6 +547,11 @@ int dlx_model_jvp(dlx_plan *p, const dlx_params *prm, const float *t_map, uint32
     if (!(alpha > 0) || !std::isfinite(alpha)) return fail(DLX_ERR_INVALID_ARG, "alpha must be finite and > 0");
     int rc = validate_params(p, prm);
     if (rc) return rc;
+    if ((rc = check_call(p, prm,
+                         {{t_map, 4 * (size_t)p->ni * p->ni, 4, "t_map", false},
+                          {jvp, dlx::image_bytes(p), 4, "jvp", false},
+                          {work, dlx::image_bytes(p), 4, "work", false}})))
+        return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const dlx::DevParams d = dev_params(p, prm);
@@ -540,15 +570,16 @@ int dlx_model_jvp(dlx_plan *p, const dlx_params *prm, const float *t_map, uint32
     p->tan_map = nullptr;
     p->tan_coef = 0.f;
     p->tan_mask = 0;
-    if (rc) return rc;
+    if (rc) return dlx::checked_status(p, rc);
     DLX_CU(dlx::launch_scaled_diff(jvp, work, (size_t)p->nei * p->ndi * p->ndi, (float)(0.5 / alpha), st), "jvp");
-    return DLX_OK;
+    return dlx::checked_status(p, DLX_OK);
 }
 
 int dlx_model_vjp(dlx_plan *p, const dlx_params *prm, const float *cot, const dlx_grads *g, void *stream) {
     if (!p || !cot || !g) return fail(DLX_ERR_INVALID_ARG, "plan/cot/grads is NULL");
     int rc = validate_params(p, prm);
     if (rc) return rc;
+    if ((rc = check_call(p, prm, {{cot, dlx::image_bytes(p), 4, "cot", false}}, g))) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const dlx::DevParams d = dev_params(p, prm);
@@ -556,7 +587,7 @@ int dlx_model_vjp(dlx_plan *p, const dlx_params *prm, const float *cot, const dl
     p->cot = cot;
     rc = dlx::eval_loss_grad(p, d, 1, nullptr, 0, nullptr, &dg, nullptr, 0, st);
     p->cot = nullptr;
-    return rc;
+    return dlx::checked_status(p, rc);
 }
 
 int dlx_model_vjp_jvp(dlx_plan *p, const dlx_params *prm, const float *cot, const float *t_map, uint32_t src_mask,
@@ -569,6 +600,12 @@ int dlx_model_vjp_jvp(dlx_plan *p, const dlx_params *prm, const float *cot, cons
         if (gp[k] && !wp[k]) return fail(DLX_ERR_INVALID_ARG, "work lacks an array that grads has");
     int rc = validate_params(p, prm);
     if (rc) return rc;
+    if ((rc = check_call(p, prm,
+                         {{cot, dlx::image_bytes(p), 4, "cot", false},
+                          {t_map, 4 * (size_t)p->ni * p->ni, 4, "t_map", false}},
+                         g)) ||
+        (dlx::check_level() >= 1 && (rc = dlx::check_grads(p, work, "work"))))
+        return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const dlx::DevParams d = dev_params(p, prm);
@@ -592,16 +629,24 @@ int dlx_model_vjp_jvp(dlx_plan *p, const dlx_params *prm, const float *cot, cons
     p->tan_map = nullptr;
     p->tan_coef = 0.f;
     p->tan_mask = 0;
-    if (rc) return rc;
+    if (rc) return dlx::checked_status(p, rc);
     const size_t n[5] = {(size_t)p->nz, (size_t)p->ni * p->ni, (size_t)p->ndi * p->ndi, (size_t)p->ns,
                          (size_t)2 * p->ns};
     for (int k = 0; k < 5; ++k)
         if (gp[k]) DLX_CU(dlx::launch_scaled_diff((float *)gp[k], wp[k], n[k], (float)(0.5 / alpha), st), "vjp_jvp");
-    return DLX_OK;
+    return dlx::checked_status(p, DLX_OK);
 }
 
 int dlx_nll_cotangent(const float *model, const int32_t *data, size_t n, float *cot, void *stream) {
     if (!model || !data || !cot) return fail(DLX_ERR_INVALID_ARG, "model/data/cot is NULL");
+    if (dlx::check_level() >= 1) {
+        int dev = 0, rc;
+        cudaGetDevice(&dev);
+        if ((rc = dlx::check_buffer(model, 4 * n, 4, dev, "model", false)) ||
+            (rc = dlx::check_buffer(data, 4 * n, 4, dev, "data", false)) ||
+            (rc = dlx::check_buffer(cot, 4 * n, 4, dev, "cot", false)))
+            return rc;
+    }
     DLX_CU(dlx::launch_nll_cotangent(model, data, n, cot, (cudaStream_t)stream), "nll_cotangent");
     return DLX_OK;
 }
@@ -611,6 +656,17 @@ int dlx_fisher_gram(const float *J, int n_par, size_t n_pix, const float *model,
     if (!J || !model || !F || !work) return fail(DLX_ERR_INVALID_ARG, "J/model/F/work is NULL");
     if (n_par < 1 || n_par > DLX_GRAM_MAX_PAR) return fail(DLX_ERR_RANGE, "n_par must be 1..DLX_GRAM_MAX_PAR");
     if (n_pix == 0) return fail(DLX_ERR_INVALID_ARG, "n_pix is 0");
+    if (dlx::check_level() >= 1) {
+        int dev = 0, rc;
+        cudaGetDevice(&dev);
+        const size_t np2 = (size_t)n_par * n_par, tri = (size_t)n_par * (n_par + 1) / 2;
+        if ((rc = dlx::check_buffer(J, 4 * (size_t)n_par * n_pix, 4, dev, "J", false)) ||
+            (rc = dlx::check_buffer(model, 4 * n_pix, 4, dev, "model", false)) ||
+            (rc = dlx::check_buffer(data, 4 * n_pix, 4, dev, "data", true)) ||
+            (rc = dlx::check_buffer(F, 8 * np2, 8, dev, "F", false)) ||
+            (rc = dlx::check_buffer(work, 8 * DLX_GRAM_BLOCKS * tri, 8, dev, "work", false)))
+            return rc;
+    }
     DLX_CU(dlx::launch_fisher_gram(J, n_par, n_pix, model, data, F, work, (cudaStream_t)stream), "fisher_gram");
     return DLX_OK;
 }
@@ -619,12 +675,14 @@ int dlx_psf(dlx_plan *p, const dlx_params *prm, float *psf_os, void *stream) {
     if (!p || !psf_os) return fail(DLX_ERR_INVALID_ARG, "plan/psf is NULL");
     int rc = validate_params(p, prm);
     if (rc) return rc;
+    const size_t noi = (size_t)p->ndi * p->os;
+    if ((rc = check_call(p, prm, {{psf_os, 4 * (size_t)p->nei * noi * noi, 4, "psf_os", false}}))) return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     const dlx::DevParams d = dev_params(p, prm);
-    if ((rc = dlx::eval_forward(p, d, 1, st))) return rc;
+    if ((rc = dlx::eval_forward(p, d, 1, st))) return dlx::checked_status(p, rc);
     DLX_CU(dlx::launch_psf_out(p, d, psf_os, st), "psf");
-    return DLX_OK;
+    return dlx::checked_status(p, DLX_OK);
 }
 
 int dlx_loss_grad(dlx_plan *p, const dlx_params *prm, const int32_t *data, double *loss, const dlx_grads *g,
@@ -632,12 +690,18 @@ int dlx_loss_grad(dlx_plan *p, const dlx_params *prm, const int32_t *data, doubl
     if (!p || !data || !loss) return fail(DLX_ERR_INVALID_ARG, "plan/data/loss is NULL");
     int rc = validate_params(p, prm);
     if (rc) return rc;
+    if ((rc = check_call(p, prm,
+                         {{data, dlx::image_bytes(p), 4, "data", false},
+                          {loss, sizeof(double), 8, "loss", false},
+                          {model_opt, dlx::image_bytes(p), 4, "model", true}},
+                         g)))
+        return rc;
     DeviceGuard guard(p->device);
     cudaStream_t st = (cudaStream_t)stream;
     DLX_CU(cudaMemsetAsync(p->clamped, 0, sizeof(unsigned long long), st), "memset");
     const dlx::DevParams d = dev_params(p, prm);
     const dlx::DevGrads dg = dev_grads(g);
-    return dlx::eval_loss_grad(p, d, 1, data, 0, loss, g ? &dg : nullptr, model_opt, 0, st);
+    return dlx::checked_status(p, dlx::eval_loss_grad(p, d, 1, data, 0, loss, g ? &dg : nullptr, model_opt, 0, st));
 }
 
 int dlx_plan_diagnostics(dlx_plan *p, int64_t *clamped, int32_t *device_error) {
@@ -686,6 +750,15 @@ int dlx_adam(float *theta, const float *grad, float *m, float *v, size_t n, floa
              float eps, int t, void *stream) {
     if (n && (!theta || !grad || !m || !v)) return fail(DLX_ERR_INVALID_ARG, "NULL array");
     if (t < 1) return fail(DLX_ERR_INVALID_ARG, "Adam step t is 1-based");
+    if (dlx::check_level() >= 1 && n) {
+        int dev = 0, rc;
+        cudaGetDevice(&dev);
+        if ((rc = dlx::check_buffer(theta, 4 * n, 4, dev, "theta", false)) ||
+            (rc = dlx::check_buffer(grad, 4 * n, 4, dev, "grad", false)) ||
+            (rc = dlx::check_buffer(m, 4 * n, 4, dev, "m", false)) ||
+            (rc = dlx::check_buffer(v, 4 * n, 4, dev, "v", false)))
+            return rc;
+    }
     DLX_CU(dlx::launch_adam(theta, grad, m, v, n, lr, beta1, beta2, eps, t, (cudaStream_t)stream), "adam");
     return DLX_OK;
 }

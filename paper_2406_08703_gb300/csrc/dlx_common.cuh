@@ -408,6 +408,10 @@ struct dlx_plan {
     size_t pool_next = 0;
     int64_t launches[16] = {};
     int64_t events[16] = {};
+    // checked mode, level 2: the first kernel class that failed in the current call
+    int check_rc = 0;
+    std::string check_msg;
+    int inject = 0;  // test hook (dlx_plan_inject_fault): 1 = withhold an operand copy in the next contraction
 };
 
 namespace dlx {
@@ -417,6 +421,21 @@ constexpr int kNormParts = 1024;  // maximum blocks of the OPD / pupil-power pas
 
 enum KClass { KC_MATRICES = 0, KC_PROLOGUE, KC_STAGE1, KC_STAGE2, KC_BIN, KC_LOSS, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1,
               KC_GRAD, KC_ADAM, KC_N };
+
+// Checked mode (dlx_set_checks): the process-wide level, and the level-2 check after a
+// kernel class (synchronises the stream unless it is being captured; records the first
+// failure in p->check_rc / p->check_msg).
+int check_level();
+void class_check(dlx_plan *p, int cls, cudaStream_t st);
+const char *class_name(int cls);
+// Level-1 checks: one array (NULL passes when `optional`), the arrays of dlx_params and of
+// dlx_grads for plan p, and the bytes of one [nei][ndi][ndi] image set of 4-byte elements.
+int check_buffer(const void *ptr, size_t bytes, size_t align, int device, const char *name, bool optional);
+int check_params(const dlx_plan *p, const dlx_params *q);
+int check_grads(const dlx_plan *p, const dlx_grads *g, const char *what);
+size_t image_bytes(const dlx_plan *p);
+// A call's status after its launches: a level-2 failure recorded on the plan replaces OK.
+int checked_status(dlx_plan *p, int rc);
 
 // Scope around one class of launches on stream st: counts the `n` kernels it
 // launches and, when the plan's timing is on, records events around them.

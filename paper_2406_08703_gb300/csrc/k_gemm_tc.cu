@@ -95,6 +95,7 @@ struct TcArgs {
     int grid;         // CTAs (0: min(units, SMs))
     uint32_t sr;      // BF16x3 forms: stochastic split (seed) of the operand this launch writes, else 0
     int p4;           // BF16x3sa adjoint 1^T: the phasor is a four-plane split
+    int stall;        // test hook: CTA 0 withholds its first operand copy (its waits expire, bounded)
     int32_t *err;
 };
 
@@ -589,6 +590,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             ok = false;
                             break;
                         }
+                        // test hook: the stage is never filled, so the MMA warp's wait for it expires
+                        if (a.stall && blockIdx.x == 0 && it == 0) continue;
                         const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
                         mbar_expect_tx(full0 + 8 * s, C::STAGE_BYTES);
                         tma_load4(st, &mapA, kb * C::KB, J.a_row, 0, J.a_batch, full0 + 8 * s);
@@ -1072,6 +1075,8 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
     a.KB = Cfg<F>::KB;
     if (a.ksplit < 1) a.ksplit = 1;
     if (a.units <= 0) return cudaSuccess;
+    a.stall = p->inject == 1 ? 1 : 0;
+    p->inject = 0;
     const int grid = a.grid > 0 ? a.grid : std::min(a.units, p->sm_count);
     static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
     KScope ks(p, cls_of[KIND], 1, st);

@@ -359,6 +359,7 @@ int issue_step(Bucket *b, int R) {
     const dlx::DevParams prm = b->params();
     const dlx::DevGrads g = b->grads();
     int rc = dlx::eval_loss_grad(b->plan, prm, R, b->data, b->sz_data(), b->loss, &g, nullptr, 0, b->stream);
+    rc = dlx::checked_status(b->plan, rc);  // checked mode, level 2 (eager steps only)
     if (rc) return rc;
     k_step_inc<<<(R + 127) / 128, 128, 0, b->stream>>>(b->step, R);
     cudaError_t e = dlx::launch_adam_slots(b->theta, b->grad, b->m, b->v, b->n_theta, R, b->off_d, b->lr, b->step,
