@@ -693,8 +693,8 @@ def main():
     # this build on the 8-wavelength case (16 PSFs), scaled by the PSF count, in which their
     # traffic grows (the adjoint 1^T splits K differently at that size and is left out); any
     # other kernel or form has no capture of the current code
-    traffic_16 = {"stage1": 25.25e6, "stage2_intensity": 50.74e6, "adjoint_field": 126.48e6,
-                  "adjoint_stage2T": 166.53e6}
+    traffic_16 = {"stage1": 25.22e6, "stage2_intensity": 50.56e6, "adjoint_field": 126.70e6,
+                  "adjoint_stage2T": 165.03e6}
     traffic = (traffic_16[dom] / 16 * B if (args.form == "bf16x3" and dom in traffic_16 and
                                             args.workload == "binary") else None)
     roof = None
