@@ -405,7 +405,15 @@ def serving_run(P, reqs, form, n_steps, rate=None, seed=0):
     stats = srv.stats()
     srv.close()
     evals = len(reqs) * max(1, n_steps)
+    # algorithmic MFT work of the served evaluations (8 FLOP per complex MAC): forward stage 1 and
+    # stage 2, the recomputed field, and the adjoint's two stages, per PSF
+    flop = 0.0
+    for k, p, d in reqs:
+        ni, no = p.n_pupil, p.n_det * p.oversample
+        s1, s2 = 8.0 * no * ni * ni, 8.0 * no * no * ni
+        flop += max(1, n_steps) * p.n_lambda * p.n_src * p.n_exp * (2 * s1 + 3 * s2)
     return dict(evals_per_s=evals / wall, requests_per_s=len(reqs) / wall, wall_s=wall,
+                tflops_algorithmic=flop / wall / 1e12,
                 p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
                 grouped_launches=int(stats["grouped_launches"]), graph_launches=int(stats["graph_launches"]))
 
