@@ -29,17 +29,16 @@ int level_from_env() {
 }
 
 PFN_cuMemGetAddressRange_v3020 range_fn() {
-    static PFN_cuMemGetAddressRange_v3020 fn = nullptr;
-    static bool looked = false;
-    if (!looked) {
+    // looked up once per process (thread-safe static initialisation)
+    static const PFN_cuMemGetAddressRange_v3020 fn = []() -> PFN_cuMemGetAddressRange_v3020 {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuMemGetAddressRange_v3020)p;
-        looked = true;
-    }
+            return (PFN_cuMemGetAddressRange_v3020)p;
+        return nullptr;
+    }();
     return fn;
 }
 

@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "dlx_common.cuh"
 
@@ -996,15 +997,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
+    // looked up once per process (thread-safe static initialisation)
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
         cudaDriverEntryPointQueryResult q;
         void *p = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -1039,12 +1041,14 @@ bool make_map(dlx_plan *p, Operand &o, std::string *why, bool hi_view = false) {
 template <int F, int MODE, int KIND>
 cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operand *Cout, TcArgs &a,
                    cudaStream_t st) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    // the shared-memory attribute is a property of the kernel on each device: set once per device
+    static std::atomic<uint64_t> attr_set{0};
+    const uint64_t dev_bit = 1ull << (p->device & 63);
+    if (!(attr_set.load(std::memory_order_acquire) & dev_bit)) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F, MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              Cfg<F>::SMEM);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_set.fetch_or(dev_bit, std::memory_order_release);
     }
     a.err = p->err;
     a.nl = p->nl;
