@@ -179,7 +179,7 @@ int dlx_forward(dlx_plan *plan, const dlx_params *params, float *model, void *cu
  * s, every exposure) multiplied by exp(i alpha (2 pi / lambda) t[n]), i.e. the
  * derivative along a change of optical path t (metres, device float [Ni][Ni]).
  * t = a Zernike basis map with every bit set gives dm/dc_j; t = the pupil x or y
- * coordinate (n - (Ni-1)/2) Ni/D for one source gives dm/dtheta_x or theta_y of
+ * coordinate (n - (Ni-1)/2) D/Ni for one source gives dm/dtheta_x or theta_y of
  * that source.  The model is a quadratic form of the phasor, so the central
  * difference (m(P (1 + i a)) - m(P (1 - i a))) / (2 alpha), a = alpha (2 pi /
  * lambda) t, is the derivative itself for any alpha > 0; alpha only sets the
