@@ -52,6 +52,8 @@ def lib():
         _lib.orc_loss_grad.argtypes = [C.POINTER(_Problem), cp, cp, cp, cp, cp, cp, cp, cp]
         _lib.orc_loss_grad.restype = C.c_long
         _lib.orc_model_at.argtypes = [C.POINTER(_Problem), C.c_int, cp, cp, cp]
+        _lib.orc_set_threads.argtypes = [C.c_int]
+        _lib.orc_set_threads.restype = C.c_int
     return _lib
 
 
@@ -188,5 +190,7 @@ def model_at(p, e_idx, p_idx):
     return out
 
 
-def set_threads(n: int) -> None:
-    os.environ["OMP_NUM_THREADS"] = str(n)
+def set_threads(n: int) -> int:
+    """Threads of the oracle's parallel loops (n < 1: one per processor); returns the count in use."""
+    os.environ["OMP_NUM_THREADS"] = str(n) if n > 0 else str(os.cpu_count() or 1)
+    return int(lib().orc_set_threads(int(n)))

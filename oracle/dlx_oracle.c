@@ -46,8 +46,23 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
+
+/* Threads of the OpenMP loops below (n < 1: one per processor); returns the number the next
+ * parallel loop will use.  Timing control for the benchmark's CPU baseline, no arithmetic. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 typedef struct {
     int n_pupil;
