@@ -174,10 +174,13 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
     h ^= h >> 16;
     return h;
 }
-__device__ __forceinline__ __nv_bfloat16 bf16_sr(float x, uint32_t r16) {
-    uint32_t u = __float_as_uint(x);
-    if ((u & 0x7f800000u) != 0x7f800000u) u += r16;  // finite values only
-    return __ushort_as_bfloat16((unsigned short)(u >> 16));
+// Two stochastic roundings to bf16 in one conversion (cvt.rs, sm_100 family): the upper half
+// of the result is `a` with bits 31:16 of `rb` added below its kept bits (to the magnitude
+// bits of the fp32 pattern) and truncated, the lower half `b` with bits 15:0.
+__device__ __forceinline__ uint32_t cvt_bf16x2_sr(float a, float b, uint32_t rb) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(a), "f"(b), "r"(rb));
+    return d;
 }
 // 32 random bits for element `gidx` of the operand with seed `seed` (one finaliser
 // round; the index's high word, zero for operands below 2^32 elements, is folded in
@@ -186,41 +189,55 @@ __device__ __forceinline__ uint32_t sr_word(uint64_t gidx, uint32_t seed) {
     const uint32_t k = (uint32_t)gidx ^ seed ^ ((uint32_t)(gidx >> 32) * 0x9e3779b9u);
     return fmix32(k);
 }
-// x = hi + lo with 8 random bits per rounding: bits 0-7 of r for hi, bits 8-15 for lo
-__device__ __forceinline__ void split_sr(float x, uint32_t r, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
-    hi = bf16_sr(x, (r & 0xffu) << 8);
-    lo = bf16_sr(x - __bfloat162float(hi), r & 0xff00u);  // x - hi is exact in fp32
+// Split of one complex element, re + i im = (re_hi + re_lo) + i (im_hi + im_lo), with 8 random
+// bits of r per rounding: bits 0-7 round re_hi, 8-15 re_lo, 16-23 im_hi, 24-31 im_lo (each
+// placed at the top of its 16-bit addend).  Returns the packed pairs hi = (re_hi | im_hi << 16)
+// and lo = (re_lo | im_lo << 16); x - hi is exact in fp32.
+__device__ __forceinline__ void split_sr_cplx(float re, float im, uint32_t r, uint32_t &hi, uint32_t &lo) {
+    hi = cvt_bf16x2_sr(im, re, ((r & 0x00ff0000u) << 8) | ((r & 0x000000ffu) << 8));
+    const float re_h = __uint_as_float(hi << 16), im_h = __uint_as_float(hi & 0xffff0000u);
+    lo = cvt_bf16x2_sr(im - im_h, re - re_h, r & 0xff00ff00u);
 }
+// Packs the low (re) halves and the high (im) halves of two split pairs: (x0.re | x1.re << 16)
+// and (x0.im | x1.im << 16).
+__device__ __forceinline__ uint32_t pack_re(uint32_t x0, uint32_t x1) { return __byte_perm(x0, x1, 0x5410); }
+__device__ __forceinline__ uint32_t pack_im(uint32_t x0, uint32_t x1) { return __byte_perm(x0, x1, 0x7632); }
 
 // store_cplx for the BF16X4 layout with stochastic splitting (element index gidx)
 __device__ __forceinline__ void store_cplx_sr(void *base, size_t pstride, size_t idx, float re, float im, uint64_t gidx,
                                               uint32_t seed) {
-    __nv_bfloat16 *p = (__nv_bfloat16 *)base;
-    const uint32_t r = sr_word(gidx, seed);
-    __nv_bfloat16 rh, rl, ih, il;
-    split_sr(re, r, rh, rl);
-    split_sr(im, r >> 16, ih, il);
-    p[idx] = rh;
-    p[pstride + idx] = rl;
-    p[2 * pstride + idx] = ih;
-    p[3 * pstride + idx] = il;
+    unsigned short *p = (unsigned short *)base;
+    uint32_t hi, lo;
+    split_sr_cplx(re, im, sr_word(gidx, seed), hi, lo);
+    p[idx] = (unsigned short)hi;
+    p[pstride + idx] = (unsigned short)lo;
+    p[2 * pstride + idx] = (unsigned short)(hi >> 16);
+    p[3 * pstride + idx] = (unsigned short)(lo >> 16);
+}
+
+// Eight split elements (element q has index gidx + q) as four packed 16-byte rows: re_hi,
+// re_lo, im_hi, im_lo.
+__device__ __forceinline__ void split8_sr(const float (&re)[8], const float (&im)[8], uint64_t gidx, uint32_t seed,
+                                          uint4 &rh, uint4 &rl, uint4 &ih, uint4 &il) {
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) split_sr_cplx(re[q], im[q], sr_word(gidx + q, seed), hi[q], lo[q]);
+    rh = make_uint4(pack_re(hi[0], hi[1]), pack_re(hi[2], hi[3]), pack_re(hi[4], hi[5]), pack_re(hi[6], hi[7]));
+    rl = make_uint4(pack_re(lo[0], lo[1]), pack_re(lo[2], lo[3]), pack_re(lo[4], lo[5]), pack_re(lo[6], lo[7]));
+    ih = make_uint4(pack_im(hi[0], hi[1]), pack_im(hi[2], hi[3]), pack_im(hi[4], hi[5]), pack_im(hi[6], hi[7]));
+    il = make_uint4(pack_im(lo[0], lo[1]), pack_im(lo[2], lo[3]), pack_im(lo[4], lo[5]), pack_im(lo[6], lo[7]));
 }
 
 // store_cplx8 for the BF16X4 layout with stochastic splitting; element q has index gidx + q
 __device__ __forceinline__ void store_cplx8_sr(void *base, size_t pstride, size_t idx, const float (&re)[8],
                                                const float (&im)[8], uint64_t gidx, uint32_t seed) {
     __nv_bfloat16 *p = (__nv_bfloat16 *)base + idx;
-    __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const uint32_t r = sr_word(gidx + q, seed);
-        split_sr(re[q], r, rh[q], rl[q]);
-        split_sr(im[q], r >> 16, ih[q], il[q]);
-    }
-    *(uint4 *)p = *(const uint4 *)rh;
-    *(uint4 *)(p + pstride) = *(const uint4 *)rl;
-    *(uint4 *)(p + 2 * pstride) = *(const uint4 *)ih;
-    *(uint4 *)(p + 3 * pstride) = *(const uint4 *)il;
+    uint4 rh, rl, ih, il;
+    split8_sr(re, im, gidx, seed, rh, rl, ih, il);
+    *(uint4 *)p = rh;
+    *(uint4 *)(p + pstride) = rl;
+    *(uint4 *)(p + 2 * pstride) = ih;
+    *(uint4 *)(p + 3 * pstride) = il;
 }
 
 // Read back the value an operand represents (hi + lo).

@@ -104,11 +104,12 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const
         }
         if constexpr (F == FMT_BF16X4) {
             if (ah_hi) {
-                __nv_bfloat16 *ah = (__nv_bfloat16 *)amatH + (size_t)l * 2 * ni * ldo;
+                unsigned short *ah = (unsigned short *)amatH + (size_t)l * 2 * ni * ldo;
                 const uint32_t rb = sr_word(((size_t)l * ni + n) * ldo + k, sr ^ 0x68e31da4u);
                 const size_t o = (size_t)n * ldo + k;
-                ah[o] = bf16_sr(re, rb & 0xffffu);
-                ah[(size_t)ni * ldo + o] = bf16_sr(-im, rb >> 16);
+                const uint32_t d = cvt_bf16x2_sr(-im, re, rb);  // re with bits 15:0, -im with 31:16
+                ah[o] = (unsigned short)d;
+                ah[(size_t)ni * ldo + o] = (unsigned short)(d >> 16);
                 continue;
             }
         }

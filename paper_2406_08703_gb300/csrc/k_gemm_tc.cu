@@ -433,39 +433,34 @@ __device__ __forceinline__ void stage_row16_sr(uint8_t *stg, int r, int h, const
                                                uint64_t gidx, uint32_t seed) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        __align__(16) __nv_bfloat16 rh[8], ih[8], rl[8], il[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t rb = sr_word(gidx + 8 * q + i, seed);
-            split_sr(re[8 * q + i], rb, rh[i], rl[i]);
-            split_sr(im[8 * q + i], rb >> 16, ih[i], il[i]);
-        }
+        uint4 rh, rl, ih, il;
+        split8_sr(*(const float(*)[8])(re + 8 * q), *(const float(*)[8])(im + 8 * q), gidx + 8 * q, seed, rh, rl,
+                  ih, il);
         const int g = (2 * h + q) ^ ((r >> 1) & 3);
         uint8_t *p = stg + r * 64 + g * 16;
-        *(uint4 *)(p) = *(uint4 *)rh;
-        *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)rl;
-        *(uint4 *)(p + 2 * PLANE_BYTES) = *(uint4 *)ih;
-        *(uint4 *)(p + 3 * PLANE_BYTES) = *(uint4 *)il;
+        *(uint4 *)(p) = rh;
+        *(uint4 *)(p + PLANE_BYTES) = rl;
+        *(uint4 *)(p + 2 * PLANE_BYTES) = ih;
+        *(uint4 *)(p + 3 * PLANE_BYTES) = il;
     }
 }
 
 // stage_row16 of a two-plane (re, im) bf16 operand with stochastic rounding (the
-// BF16x3sa adjoint); element i of the row has global index gidx + i.
+// BF16x3sa adjoint); element i of the row has global index gidx + i: 16 random bits
+// per rounding, bits 15:0 of the element's word for re and 31:16 for im.
 __device__ __forceinline__ void stage_row16_hi_sr(uint8_t *stg, int r, int h, const float (&re)[CW],
                                                   const float (&im)[CW], uint64_t gidx, uint32_t seed) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        __align__(16) __nv_bfloat16 rh[8], ih[8];
+        uint32_t d[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const uint32_t rb = fmix32((uint32_t)(gidx + 8 * q + i) ^ seed ^ ((uint32_t)(gidx >> 32) * 0x9e3779b9u));
-            rh[i] = bf16_sr(re[8 * q + i], rb & 0xffffu);
-            ih[i] = bf16_sr(im[8 * q + i], rb >> 16);
-        }
+        for (int i = 0; i < 8; ++i)
+            d[i] = cvt_bf16x2_sr(im[8 * q + i], re[8 * q + i], sr_word(gidx + 8 * q + i, seed));
         const int g = (2 * h + q) ^ ((r >> 1) & 3);
         uint8_t *p = stg + r * 64 + g * 16;
-        *(uint4 *)(p) = *(uint4 *)rh;
-        *(uint4 *)(p + PLANE_BYTES) = *(uint4 *)ih;
+        *(uint4 *)(p) = make_uint4(pack_re(d[0], d[1]), pack_re(d[2], d[3]), pack_re(d[4], d[5]), pack_re(d[6], d[7]));
+        *(uint4 *)(p + PLANE_BYTES) =
+            make_uint4(pack_im(d[0], d[1]), pack_im(d[2], d[3]), pack_im(d[4], d[5]), pack_im(d[6], d[7]));
     }
 }
 
