@@ -80,6 +80,10 @@ typedef enum {
                           noise of about 2^-8 / sqrt(K) of each contraction's terms instead of
                           the split's bias-free 2^-16; the PSF and loss are those of DLX_BF16X3 */
 } dlx_prec;
+/* The BF16 split forms (BF16X3, BF16X4, BF16X3SA) keep about 17 significant bits per operand,
+ * whose representation error a contraction averages down over its terms only: below 32 pupil
+ * samples per side their PSF misses 1e-5 of its peak, so plans of such pupils run DLX_F16X3
+ * (22 bits) instead, and dlx_plan_info.precision reports the form that runs. */
 
 typedef struct dlx_plan dlx_plan;
 typedef struct dlx_server dlx_server;

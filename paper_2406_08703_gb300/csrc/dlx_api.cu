@@ -201,6 +201,12 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->ldi = round8(p->ni);
     p->ldo = round8(p->no);
     p->prec = d->precision;
+    // a 16-bit split (hi + lo BF16 carry about 17 significant bits) leaves each operand a
+    // representation error near 2^-17 that a contraction averages down only over its terms: with
+    // fewer than 32 pupil samples the PSF misses 1e-5 of its peak (measured 1.0-3.2e-5 at 5 and
+    // 17 samples), so those plans run the 22-bit FP16 split
+    if (p->ni < kMinBf16Pupil && (p->prec == DLX_BF16X3 || p->prec == DLX_BF16X4 || p->prec == DLX_BF16X3SA))
+        p->prec = DLX_F16X3;
     p->fmt = fmt_of_prec(p->prec);
     p->sr = (p->prec == DLX_BF16X3 || p->prec == DLX_BF16X3SA) ? 0x6d2b79f5u : 0u;  // stochastic split
     p->adj1 = (p->prec == DLX_BF16X3SA);

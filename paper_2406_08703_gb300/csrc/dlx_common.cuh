@@ -434,6 +434,7 @@ struct dlx_plan {
 namespace dlx {
 
 constexpr int kMaxSrc = 32;  // sources per plan
+constexpr int kMinBf16Pupil = 32;  // smallest pupil (samples per side) the BF16 split forms run at
 constexpr int kNormParts = 1024;  // maximum blocks of the OPD / pupil-power pass
 
 enum KClass { KC_MATRICES = 0, KC_PROLOGUE, KC_STAGE1, KC_STAGE2, KC_BIN, KC_LOSS, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1,

@@ -508,16 +508,19 @@ void worker_loop(dlx_server *s) {
                     if (status == DLX_OK) {
                         q->loss = losses[i][r];
                         memcpy(q->off, b->off, sizeof(q->off));
-                        q->theta_out.resize(b->n_theta);
-                        q->grad_out.resize(b->n_theta);
-                        cudaMemcpy(q->theta_out.data(), b->theta + r * b->n_theta, 4 * b->n_theta,
-                                   cudaMemcpyDeviceToHost);
-                        cudaMemcpy(q->grad_out.data(), b->grad + r * b->n_theta, 4 * b->n_theta,
-                                   cudaMemcpyDeviceToHost);
-                        q->m_out.resize(b->n_theta);
-                        q->v_out.resize(b->n_theta);
-                        cudaMemcpy(q->m_out.data(), b->m + r * b->n_theta, 4 * b->n_theta, cudaMemcpyDeviceToHost);
-                        cudaMemcpy(q->v_out.data(), b->v + r * b->n_theta, 4 * b->n_theta, cudaMemcpyDeviceToHost);
+                        // parameters, gradient and Adam moments of the slot to the request
+                        const size_t o = r * b->n_theta, nb = 4 * b->n_theta;
+                        std::vector<float> *dst[4] = {&q->theta_out, &q->grad_out, &q->m_out, &q->v_out};
+                        const float *src[4] = {b->theta + o, b->grad + o, b->m + o, b->v + o};
+                        cudaError_t ce2 = cudaSuccess;
+                        for (int k = 0; k < 4 && ce2 == cudaSuccess; ++k) {
+                            dst[k]->resize(b->n_theta);
+                            ce2 = cudaMemcpy(dst[k]->data(), src[k], nb, cudaMemcpyDeviceToHost);
+                        }
+                        if (ce2 != cudaSuccess) {
+                            status = DLX_ERR_CUDA;
+                            for (auto *d : dst) d->clear();
+                        }
                     }
                     finish(s, q, status);
                     const int last = b->active - 1;
