@@ -3,10 +3,13 @@
 // Every contraction is C[m][n] = sum_k A[m][k] B[n][k] over complex operands
 // stored as re/im FP32 planes with both operands contiguous in k.  A 256-thread
 // block owns a 64 x 64 output tile; each thread holds a 4 x 4 complex
-// register tile (rows ty + 16 i, columns tx + 16 j) so that stores of
-// neighbouring threads are contiguous.  Operand tiles of 16 k are staged in
-// shared memory transposed to [k][row] (padded by one word against bank
-// conflicts).  The epilogues are the same as in the tensor-core form.
+// register tile (rows 4 ty + i, columns 4 tx + j), read per k from shared memory
+// as four 16-byte vectors (re and im of its four rows and of its four columns),
+// so that 64 FMAs take four shared-memory loads and sixteen threads store 64
+// contiguous floats of a row.  Operand tiles of 16 k are staged in shared memory
+// transposed to [k][row] (rows padded to 68 words: 16-byte aligned, and the
+// transposing stores spread over the banks).  The epilogues are the same as in
+// the tensor-core form.
 #include "dlx_common.cuh"
 
 namespace dlx {
@@ -14,47 +17,65 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
 
+constexpr int PAD = 4;  // row padding of the staged tiles (keeps float4 reads aligned)
+
 struct SimtSmem {
-    float ar[BK][BM + 1], ai[BK][BM + 1], br[BK][BN + 1], bi[BK][BN + 1];
+    __align__(16) float ar[BK][BM + PAD];
+    __align__(16) float ai[BK][BM + PAD];
+    __align__(16) float br[BK][BN + PAD];
+    __align__(16) float bi[BK][BN + PAD];
 };
 
-// Accumulates the tile (m0, n0) of A . B^T into (cr, ci).
+// Accumulates the tile (m0, n0) of A . B^T into (cr, ci).  PF: load the next k-block from
+// global memory while the current one is multiplied (16 more registers; measured faster for
+// stage 1 and the adjoint 2^T and 1^T, no faster for the recomputed field, and stage 2, which
+// also holds the spectral sum, spilled with it).
+template <bool PF>
 __device__ __forceinline__ void simt_tile(const float *__restrict__ A, size_t a_ps, int lda, int M,
                                           const float *__restrict__ Bm, size_t b_ps, int ldb, int N, int K, int m0,
                                           int n0, float (&cr)[4][4], float (&ci)[4][4], SimtSmem &sm) {
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    constexpr int NR = (BM * BK) / NT;  // staged elements per thread and array
+    // the next k-block's operands are loaded into registers while the current one is
+    // multiplied out of shared memory
+    float vr[NR], vi[NR], wr[NR], wi[NR];
+    auto fetch = [&](int k0) {
 #pragma unroll
-        for (int r = 0; r < (BM * BK) / NT; ++r) {
-            int idx = tid + r * NT, row = idx / BK, kk = idx % BK, gk = k0 + kk;
-            float vr = 0.f, vi = 0.f, wr = 0.f, wi = 0.f;
-            int gm = m0 + row, gn = n0 + row;
+        for (int r = 0; r < NR; ++r) {
+            const int idx = tid + r * NT, row = idx / BK, kk = idx % BK, gk = k0 + kk;
+            const int gm = m0 + row, gn = n0 + row;
+            vr[r] = vi[r] = wr[r] = wi[r] = 0.f;
             if (gm < M && gk < K) {
-                size_t o = (size_t)gm * lda + gk;
-                vr = A[o];
-                vi = A[a_ps + o];
+                const size_t o = (size_t)gm * lda + gk;
+                vr[r] = A[o];
+                vi[r] = A[a_ps + o];
             }
             if (gn < N && gk < K) {
-                size_t o = (size_t)gn * ldb + gk;
-                wr = Bm[o];
-                wi = Bm[b_ps + o];
+                const size_t o = (size_t)gn * ldb + gk;
+                wr[r] = Bm[o];
+                wi[r] = Bm[b_ps + o];
             }
-            sm.ar[kk][row] = vr;
-            sm.ai[kk][row] = vi;
-            sm.br[kk][row] = wr;
-            sm.bi[kk][row] = wi;
+        }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        if (!PF && k0 > 0) fetch(k0);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int idx = tid + r * NT, row = idx / BK, kk = idx % BK;
+            sm.ar[kk][row] = vr[r];
+            sm.ai[kk][row] = vi[r];
+            sm.br[kk][row] = wr[r];
+            sm.bi[kk][row] = wi[r];
         }
         __syncthreads();
+        if (PF && k0 + BK < K) fetch(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            float a_r[4], a_i[4], b_r[4], b_i[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                a_r[i] = sm.ar[kk][ty + 16 * i];
-                a_i[i] = sm.ai[kk][ty + 16 * i];
-                b_r[i] = sm.br[kk][tx + 16 * i];
-                b_i[i] = sm.bi[kk][tx + 16 * i];
-            }
+            const float4 ar4 = *(const float4 *)&sm.ar[kk][4 * ty], ai4 = *(const float4 *)&sm.ai[kk][4 * ty];
+            const float4 br4 = *(const float4 *)&sm.br[kk][4 * tx], bi4 = *(const float4 *)&sm.bi[kk][4 * tx];
+            const float a_r[4] = {ar4.x, ar4.y, ar4.z, ar4.w}, a_i[4] = {ai4.x, ai4.y, ai4.z, ai4.w};
+            const float b_r[4] = {br4.x, br4.y, br4.z, br4.w}, b_i[4] = {bi4.x, bi4.y, bi4.z, bi4.w};
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -77,7 +98,7 @@ __device__ __forceinline__ void zero(float (&c)[4][4]) {
 }
 
 // Stage 1: T1t[b][kx][ny] = sum_nx A(l)[kx][nx] P[b][ny][nx].
-__global__ void __launch_bounds__(NT) k_simt_stage1(const float *amat, const float *P, float *T1t, int ni, int no,
+__global__ void __launch_bounds__(NT, 2) k_simt_stage1(const float *amat, const float *P, float *T1t, int ni, int no,
                                                     int ldi, int nse, int B) {
     __shared__ SimtSmem sm;
     const int b = blockIdx.z, l = (b % B) / nse, m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -85,14 +106,14 @@ __global__ void __launch_bounds__(NT) k_simt_stage1(const float *amat, const flo
     zero(cr);
     zero(ci);
     const size_t aps = (size_t)no * ldi, pps = (size_t)ni * ldi;
-    simt_tile(amat + (size_t)l * 2 * aps, aps, ldi, no, P + (size_t)b * 2 * pps, pps, ldi, ni, ni, m0, n0, cr, ci, sm);
+    simt_tile<true>(amat + (size_t)l * 2 * aps, aps, ldi, no, P + (size_t)b * 2 * pps, pps, ldi, ni, ni, m0, n0, cr, ci, sm);
     float *out = T1t + (size_t)b * 2 * aps;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            int m = m0 + 4 * ty + i, n = n0 + 4 * tx + j;
             if (m < no && n < ni) {
                 out[(size_t)m * ldi + n] = cr[i][j];
                 out[aps + (size_t)m * ldi + n] = ci[i][j];
@@ -101,7 +122,7 @@ __global__ void __launch_bounds__(NT) k_simt_stage1(const float *amat, const flo
 }
 
 // Stage 2 + intensity: Is[g][r nse + se][ky][kx] = sum_{l in group g} w_l |sum_ny A(l)[ky][ny] T1t[b][kx][ny]|^2.
-__global__ void __launch_bounds__(NT) k_simt_stage2(const float *amat, const float *T1t, const float *wnorm, float *Is,
+__global__ void __launch_bounds__(NT, 2) k_simt_stage2(const float *amat, const float *T1t, const float *wnorm, float *Is,
                                                     int ni, int no, int ldi, int nse, int nl, int G, int tiles_n,
                                                     int B) {
     __shared__ SimtSmem sm;
@@ -116,7 +137,7 @@ __global__ void __launch_bounds__(NT) k_simt_stage2(const float *amat, const flo
         zero(cr);
         zero(ci);
         const int b = r * B + l * nse + se;
-        simt_tile(amat + (size_t)l * 2 * aps, aps, ldi, no, T1t + (size_t)b * 2 * aps, aps, ldi, no, ni, m0, n0, cr,
+        simt_tile<false>(amat + (size_t)l * 2 * aps, aps, ldi, no, T1t + (size_t)b * 2 * aps, aps, ldi, no, ni, m0, n0, cr,
                   ci, sm);
         const float w = wnorm[(size_t)r * nl + l];
 #pragma unroll
@@ -130,14 +151,14 @@ __global__ void __launch_bounds__(NT) k_simt_stage2(const float *amat, const flo
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            int m = m0 + 4 * ty + i, n = n0 + 4 * tx + j;
             if (m < no && n < no) out[(size_t)m * no + n] = acc[i][j];
         }
 }
 
 // Adjoint, recomputed field: E^T[kx][ky] = sum_ny T1t[b][kx][ny] A(l)[ky][ny];
 // GEt[z][kx][ky] = 2 w_l F_s GI[e][bin(ky,kx)] E^T[kx][ky]  (dL/dRe E + i dL/dIm E).
-__global__ void __launch_bounds__(NT) k_simt_grad_field(const float *amat, const float *T1t, const float *wnorm,
+__global__ void __launch_bounds__(NT, 2) k_simt_grad_field(const float *amat, const float *T1t, const float *wnorm,
                                                         DevParams prm, const float *GI, float *GEt, int ni, int no,
                                                         int ldi, int ldo, int nl, int nse, int ne, int nd, int os,
                                                         int B, int b0, int tiles_n) {
@@ -149,7 +170,7 @@ __global__ void __launch_bounds__(NT) k_simt_grad_field(const float *amat, const
     float cr[4][4], ci[4][4];
     zero(cr);
     zero(ci);
-    simt_tile(T1t + (size_t)b * 2 * aps, aps, ldi, no, amat + (size_t)l * 2 * aps, aps, ldi, no, ni, m0, n0, cr, ci,
+    simt_tile<false>(T1t + (size_t)b * 2 * aps, aps, ldi, no, amat + (size_t)l * 2 * aps, aps, ldi, no, ni, m0, n0, cr, ci,
               sm);
     const float c = 2.f * wnorm[(size_t)r * nl + l] * slot_ptr(prm, PFLUX, r)[s];
     const float *gi = GI + ((size_t)r * ne + e) * nd * nd;
@@ -160,7 +181,7 @@ __global__ void __launch_bounds__(NT) k_simt_grad_field(const float *amat, const
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int kx = m0 + ty + 16 * i, ky = n0 + tx + 16 * j;
+            int kx = m0 + 4 * ty + i, ky = n0 + 4 * tx + j;
             if (kx < no && ky < no) {
                 float f = c * gi[(ky / os) * nd + kx / os];
                 out[(size_t)kx * ldo + ky] = f * cr[i][j];
@@ -170,7 +191,7 @@ __global__ void __launch_bounds__(NT) k_simt_grad_field(const float *amat, const
 }
 
 // Adjoint stage 2^T: GT1[z][ny][kx] = sum_ky AH(l)[ny][ky] GEt[z][kx][ky].
-__global__ void __launch_bounds__(NT) k_simt_adj2(const float *amatH, const float *GEt, float *GT1, int ni, int no,
+__global__ void __launch_bounds__(NT, 2) k_simt_adj2(const float *amatH, const float *GEt, float *GT1, int ni, int no,
                                                   int ldo, int nse, int B, int b0) {
     __shared__ SimtSmem sm;
     const int z = blockIdx.z, b = b0 + z, l = (b % B) / nse, m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
@@ -178,7 +199,7 @@ __global__ void __launch_bounds__(NT) k_simt_adj2(const float *amatH, const floa
     float cr[4][4], ci[4][4];
     zero(cr);
     zero(ci);
-    simt_tile(amatH + (size_t)l * 2 * hps, hps, ldo, ni, GEt + (size_t)z * 2 * gps, gps, ldo, no, no, m0, n0, cr, ci,
+    simt_tile<true>(amatH + (size_t)l * 2 * hps, hps, ldo, ni, GEt + (size_t)z * 2 * gps, gps, ldo, no, no, m0, n0, cr, ci,
               sm);
     float *out = GT1 + (size_t)z * 2 * hps;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -186,7 +207,7 @@ __global__ void __launch_bounds__(NT) k_simt_adj2(const float *amatH, const floa
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int m = m0 + ty + 16 * i, n = n0 + tx + 16 * j;
+            int m = m0 + 4 * ty + i, n = n0 + 4 * tx + j;
             if (m < ni && n < no) {
                 out[(size_t)m * ldo + n] = cr[i][j];
                 out[hps + (size_t)m * ldo + n] = ci[i][j];
@@ -196,7 +217,7 @@ __global__ void __launch_bounds__(NT) k_simt_adj2(const float *amatH, const floa
 
 // Adjoint stage 1^T + phase gradient: G_P[ny][nx] = sum_kx GT1[z][ny][kx] AH(l)[nx][kx];
 // gphi[b][ny][nx] = (2 pi / lambda_l) Im(G_P conj(P[b][ny][nx])).
-__global__ void __launch_bounds__(NT) k_simt_adj1(const float *amatH, const float *GT1, const float *P,
+__global__ void __launch_bounds__(NT, 2) k_simt_adj1(const float *amatH, const float *GT1, const float *P,
                                                   const double *lam, float *gphi, int ni, int no, int ldi, int ldo,
                                                   int nse, int B, int b0) {
     __shared__ SimtSmem sm;
@@ -205,7 +226,7 @@ __global__ void __launch_bounds__(NT) k_simt_adj1(const float *amatH, const floa
     float cr[4][4], ci[4][4];
     zero(cr);
     zero(ci);
-    simt_tile(GT1 + (size_t)z * 2 * hps, hps, ldo, ni, amatH + (size_t)l * 2 * hps, hps, ldo, ni, no, m0, n0, cr, ci,
+    simt_tile<true>(GT1 + (size_t)z * 2 * hps, hps, ldo, ni, amatH + (size_t)l * 2 * hps, hps, ldo, ni, no, m0, n0, cr, ci,
               sm);
     const float k2 = (float)(6.283185307179586476925286766559 / lam[l]);
     const float *pb = P + (size_t)b * 2 * pps;
@@ -215,7 +236,7 @@ __global__ void __launch_bounds__(NT) k_simt_adj1(const float *amatH, const floa
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int ny = m0 + ty + 16 * i, nx = n0 + tx + 16 * j;
+            int ny = m0 + 4 * ty + i, nx = n0 + 4 * tx + j;
             if (ny < ni && nx < ni) {
                 float pr = pb[(size_t)ny * ldi + nx], pi = pb[pps + (size_t)ny * ldi + nx];
                 out[(size_t)ny * ni + nx] = k2 * (ci[i][j] * pr - cr[i][j] * pi);
