@@ -294,19 +294,24 @@ int create_bucket(dlx_server *s, const Req &r, Bucket **out) {
     return DLX_OK;
 }
 
-// Upload a request's inputs into slot `r` of its bucket (asynchronous on the bucket stream).
-void upload(Bucket *b, int r, Req *q, bool poison) {
+// Upload a request's inputs into slot `r` of its bucket on the bucket stream; returns the
+// first CUDA error of the copies (the slot is then not used).
+cudaError_t upload(Bucket *b, int r, Req *q, bool poison) {
     cudaStream_t st = b->stream;
+    cudaError_t err = cudaSuccess;
+    auto keep = [&](cudaError_t e) {
+        if (err == cudaSuccess) err = e;
+    };
     auto h2d = [&](void *dst, const void *src, size_t bytes) {
-        if (bytes) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+        if (bytes) keep(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
     };
     h2d(b->T + r * b->sz_T(), q->T.data(), 4 * b->sz_T());
     if (!q->opd_fixed.empty()) h2d(b->opd_fixed + r * b->sz_T(), q->opd_fixed.data(), 4 * b->sz_T());
-    else cudaMemsetAsync(b->opd_fixed + r * b->sz_T(), 0, 4 * b->sz_T(), st);
+    else keep(cudaMemsetAsync(b->opd_fixed + r * b->sz_T(), 0, 4 * b->sz_T(), st));
     if (b->nz) h2d(b->basis + r * b->sz_basis(), q->basis.data(), 4 * b->sz_basis());
     h2d(b->weights + (size_t)r * b->nl, q->weights.data(), 4 * b->nl);
     if (!q->dither.empty()) h2d(b->dither + (size_t)r * 2 * b->ne, q->dither.data(), 8 * b->ne);
-    else cudaMemsetAsync(b->dither + (size_t)r * 2 * b->ne, 0, 8 * b->ne, st);
+    else keep(cudaMemsetAsync(b->dither + (size_t)r * 2 * b->ne, 0, 8 * b->ne, st));
     std::vector<float> th(b->n_theta, 0.f);
     std::copy(q->coeff.begin(), q->coeff.end(), th.begin() + b->off[0]);
     if (b->has_pix) std::copy(q->pix.begin(), q->pix.end(), th.begin() + b->off[1]);
@@ -315,18 +320,19 @@ void upload(Bucket *b, int r, Req *q, bool poison) {
     std::copy(q->pos.begin(), q->pos.end(), th.begin() + b->off[4]);
     if (poison) th[b->off[3]] = NAN;  // host-side fault injection: a bad input, no device fault
     h2d(b->theta + r * b->n_theta, th.data(), 4 * b->n_theta);
-    cudaStreamSynchronize(st);  // th is a local buffer
+    keep(cudaStreamSynchronize(st));  // th is a local buffer
     if (!q->m_in.empty()) h2d(b->m + r * b->n_theta, q->m_in.data(), 4 * b->n_theta);
-    else cudaMemsetAsync(b->m + r * b->n_theta, 0, 4 * b->n_theta, st);
+    else keep(cudaMemsetAsync(b->m + r * b->n_theta, 0, 4 * b->n_theta, st));
     if (!q->v_in.empty()) h2d(b->v + r * b->n_theta, q->v_in.data(), 4 * b->n_theta);
-    else cudaMemsetAsync(b->v + r * b->n_theta, 0, 4 * b->n_theta, st);
+    else keep(cudaMemsetAsync(b->v + r * b->n_theta, 0, 4 * b->n_theta, st));
     h2d(b->step + r, &q->step_in, sizeof(int));
     float lr[5];
     for (int k = 0; k < 5; ++k) lr[k] = q->n_steps > 0 ? q->lr[k] : 0.f;
     if (!b->has_pix) lr[1] = 0.f;
     h2d(b->lr + 5 * r, lr, sizeof(lr));
     h2d(b->data + r * b->sz_data(), q->data.data(), 4 * b->sz_data());
-    cudaStreamSynchronize(st);
+    keep(cudaStreamSynchronize(st));
+    return err;
 }
 
 // Move slot `from` into slot `to` (device-to-device), keeping slots contiguous.
@@ -459,10 +465,17 @@ void worker_loop(dlx_server *s) {
             const bool poison = s->fault_next == 2;
             if (poison) s->fault_next = 0;
             lk.unlock();
-            upload(b, r, q, poison);
+            const cudaError_t ue = upload(b, r, q, poison);
             lk.lock();
-            s->stats.admitted++;
             it = s->queue.erase(it);
+            if (ue != cudaSuccess) {  // the slot (the last one) is given back unused
+                cudaGetLastError();
+                b->slot_req[r] = nullptr;
+                b->active--;
+                finish(s, q, DLX_ERR_CUDA);
+                continue;
+            }
+            s->stats.admitted++;
         }
         int active = 0;
         for (auto &kv : s->buckets) active += kv.second->active;
