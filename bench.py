@@ -302,10 +302,37 @@ def e2e_run(P, torch, r, steps, device):
     return dict(s_per_step=dt, h2d=h2d, d2h=d2h)
 
 
-def cpu_baseline(workload, budget_s=20.0):
+def sample_parity(P, torch, sub, data, form, ref):
+    """The GPU path against the oracle's result on the timed sample (the same inputs on both
+    sides): model max error of the peak, loss relative error, worst gradient group's relative
+    L2 error."""
+    plan = P.dlx_make_mft(P.desc_from_problem(sub, P.PRECISIONS[form]))
+    prm = P.params_from_problem(sub)
+    dt = torch.as_tensor(np.ascontiguousarray(data, dtype=np.int32), device="cuda")
+    model = torch.empty((sub.n_exp, sub.n_det, sub.n_det), device="cuda")
+    loss, g, _ = P.dlx_loss_grad(plan, prm, dt, model=model)
+    torch.cuda.synchronize()
+    m = model.double().cpu().numpy()
+    gmap = dict(coeff="d_zern", opd_pix="d_opd_pix", flat="d_flat", flux="d_flux", pos="d_pos")
+    worst, which = 0.0, None
+    for k, gk in gmap.items():
+        if g.get(gk) is None or ref[k].size == 0 or not np.any(ref[k]):
+            continue
+        e = float(np.linalg.norm(g[gk].double().cpu().numpy() - ref[k]) / np.linalg.norm(ref[k]))
+        if e > worst:
+            worst, which = e, k
+    out = dict(form=form, model_max_err_of_peak=float(np.max(np.abs(m - ref["model"])) / np.max(ref["model"])),
+               loss_rel_err=abs(loss.item() - ref["loss"]) / abs(ref["loss"]), grad_rel_l2_worst=worst,
+               grad_worst_group=which, effective_precision=int(plan.info.precision))
+    plan.close()
+    return out
+
+
+def cpu_baseline(workload, budget_s=20.0, form=None):
     """The FP64 oracle as it stands, on this host's cores, on a bounded sample of the
     workload: the same model restricted to its first few wavelengths (all sources and
-    exposures); evals/s scaled by the sampled share of the PSFs."""
+    exposures); evals/s scaled by the sampled share of the PSFs.  With `form`, the GPU path
+    is also compared with the oracle's result on that sample."""
     import oracle
 
     truth, start, data = make_inputs(workload)
@@ -314,7 +341,7 @@ def cpu_baseline(workload, budget_s=20.0):
     sub.lambdas, sub.weights = start.lambdas[:nsub], start.weights[:nsub]
     oracle.lib()
     cores = oracle.set_threads(0)  # one thread per host core
-    oracle.loss_grad(sub, data)  # warm (thread pool, page-in)
+    ref = oracle.loss_grad(sub, data)  # warm (thread pool, page-in); kept for the parity check
     t0, n = time.perf_counter(), 0
     while True:
         oracle.loss_grad(sub, data)
@@ -329,7 +356,14 @@ def cpu_baseline(workload, budget_s=20.0):
     oracle.loss_grad(sub, data)
     dt1 = time.perf_counter() - t1
     oracle.set_threads(0)
-    return dict(value=frac / dt, unit="evals/s", cores=cores, kind="oracle",
+    parity = None
+    if form is not None:
+        import torch
+
+        import paper_2406_08703_gb300 as P
+
+        parity = sample_parity(P, torch, sub, data, form, ref)
+    return dict(value=frac / dt, unit="evals/s", cores=cores, kind="oracle", parity_on_sample=parity,
                 sample=f"{nsub} of {start.n_lambda} wavelengths (all sources and exposures), {n} runs, "
                        f"{dt:.2f} s each; value scaled by {frac:.4f} of the PSFs",
                 single_core=dict(value=frac / dt1, unit="evals/s", cores=1, sample=f"the same sample, 1 run, "
@@ -782,7 +816,7 @@ def main():
         line["forms"] = forms
 
     if not args.no_cpu and rank == 0 and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.workload)
+        line["cpu_baseline"] = cpu_baseline(args.workload, form=args.form)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
