@@ -49,6 +49,9 @@ def test_invalid_shapes_rejected_without_a_device(native):
         dict(n_pupil=1), dict(n_det=0), dict(oversample=0), dict(n_src=0), dict(n_exp=0), dict(precision=9),
         dict(diameter_m=0.0), dict(pixscale_rad=-1.0), dict(prf_prior_sigma=-0.1),
         dict(focal_length_m=-1.0), dict(focal_shift_m=1e-3), dict(focal_length_m=1.0, focal_shift_m=-1.0),
+        dict(n_lambda=0), dict(n_zern=-1), dict(lambda_m=None),
+        dict(lambda_m=C.cast((C.c_double * 1)(-595e-9), C.POINTER(C.c_double))),
+        dict(lambda_m=C.cast((C.c_double * 1)(float("inf")), C.POINTER(C.c_double))),
         dict(focal_length_m=float("nan")),
     ]
     for over in bad:
