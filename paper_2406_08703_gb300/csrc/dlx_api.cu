@@ -45,8 +45,6 @@ int cuda_fail(cudaError_t e, const char *where) {
         if (_e != cudaSuccess) return cuda_fail(_e, where); \
     } while (0)
 
-int round8(int x) { return (x + 7) / 8 * 8; }
-
 template <class T>
 cudaError_t plan_alloc(dlx_plan *p, T **ptr, size_t bytes) {
     void *q = nullptr;
@@ -198,8 +196,8 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->nz = d->n_zern;
     p->nse = p->ns * p->ne;
     p->B = p->nl * p->nse;
-    p->ldi = round8(p->ni);
-    p->ldo = round8(p->no);
+    p->ldi = dlx::operand_ld(p->ni);
+    p->ldo = dlx::operand_ld(p->no);
     p->prec = d->precision;
     // a 16-bit split (hi + lo BF16 carry about 17 significant bits) leaves each operand a
     // representation error near 2^-17 that a contraction averages down only over its terms: with

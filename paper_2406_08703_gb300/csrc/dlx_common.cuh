@@ -2,8 +2,9 @@
 //
 // Operand layout.  Every complex matrix that feeds a contraction is stored as
 // P planes of a row-major [rows][ld] array, plane-major, where ld is the
-// contraction length rounded up to a multiple of 8 (16-byte rows for the
-// tensor-memory-access engine; padding columns stay zero).  The planes depend
+// contraction length rounded up to a multiple of 64 (operand_ld: the 64-byte row
+// chunks the tensor-memory-access engine reads stay aligned; padding columns stay
+// zero).  The planes depend
 // on the arithmetic form:
 //   FMT_F32    : re, im                     (float)         -- CUDA-core FP32 form
 //   FMT_BF16X4 : re_hi, re_lo, im_hi, im_lo (bf16)          -- BF16x3 and BF16x4 forms
@@ -434,6 +435,11 @@ struct dlx_plan {
 namespace dlx {
 
 constexpr int kMaxSrc = 32;  // sources per plan
+// Row length of the operand planes: a multiple of 64 elements, so that every 64-byte row chunk a
+// TMA box reads starts on a 64-byte boundary (with 1064-element rows, 2128-byte pitch, the chunks of
+// odd rows straddled 32-byte sectors and the L2 served the adjoint contractions at 1.3 sectors
+// per request instead of 2).  The padding columns are zero.
+inline int operand_ld(int n) { return (n + 63) / 64 * 64; }
 constexpr int kMinBf16Pupil = 32;  // smallest pupil (samples per side) the BF16 split forms run at
 constexpr int kNormParts = 1024;  // maximum blocks of the OPD / pupil-power pass
 

@@ -197,7 +197,7 @@ size_t bucket_bytes(const dlx_mft_desc &d, bool has_pix, int cap) {
         for (int k = 0; k < 2 * d.n_exp; ++k) delta = std::max<size_t>(delta, (size_t)std::abs(d.dither_px[k]));
     const size_t ne_mft = d.dither_px ? 1 : (size_t)d.n_exp;
     const size_t ni = d.n_pupil, nd = d.n_det, no = ((size_t)d.n_det + 2 * delta) * d.oversample, nl = d.n_lambda;
-    const size_t ldi = (ni + 7) / 8 * 8, ldo = (no + 7) / 8 * 8, B = nl * d.n_src * ne_mft, Bt = B * cap;
+    const size_t ldi = dlx::operand_ld((int)ni), ldo = dlx::operand_ld((int)no), B = nl * d.n_src * ne_mft, Bt = B * cap;
     const int fmt = dlx::fmt_of_prec(d.precision);
     const size_t pe = (size_t)dlx::fmt_planes(fmt) * dlx::fmt_esize(fmt);
     size_t b = pe * (nl * no * ldi + nl * ni * ldo + Bt * ni * ldi + Bt * no * ldi + Bt * no * ldo + Bt * ni * ldo);
