@@ -3,17 +3,21 @@
 One step = one dlx_loss_grad over the whole model (every wavelength x source x
 exposure PSF: phasor, two-sided MFT, intensity, binning, flat field, Poisson
 NLL, and the full adjoint to the Zernike, pixel-OPD, flat-field, flux and
-position gradients).  The default workload is the binary-star polychromatic
-fit: 256^2 pupil, 32 wavelengths x 2 stars = 64 PSFs onto a 1024^2 oversampled
-grid (256^2 detector, oversample 4), synthetic seeded inputs.
+position gradients).  The default workload is the million-parameter
+calibration: 512^2 pupil with Zernikes 2-36 and a 512^2 pixel OPD map, 16
+wavelengths x 8 dithered exposures of one star = 128 PSFs onto a 2048^2
+oversampled grid (1024^2 detector, oversample 2), synthetic seeded inputs.  The
+binary-star fit (256^2 pupil, 32 wavelengths x 2 stars onto 1024^2) is timed
+beside it under the key "binary".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--form bf16x3] [--impl reference]
 
 Prints one JSON line (rank 0).  `value` is device-timed (CUDA events on the
 launching stream, inputs resident); `e2e` times the same call with host inputs
 copied in from pinned memory and the loss and gradients copied back.  The
-reference arm (--impl reference) times the FP64 CPU oracle on a bounded sample
-of the same workload on this host's cores.
+reference arm (--impl reference) times the FP64 CPU oracle on this host's cores,
+each step one bounded sample of the same workload (the whole evaluation where
+it takes seconds, else one wavelength x exposure slice of it).
 """
 
 from __future__ import annotations
@@ -55,11 +59,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "bf16x3sa", "bf16x4", "f16x3", "tf32x3", "bf16", "fp32"])
     ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
-    ap.add_argument("--workload", default="binary")
+    ap.add_argument("--workload", default="calib")
     ap.add_argument("--lambdas", type=int, default=0,
                     help="use only this many of the workload's wavelengths (same per-PSF shapes; profiling captures)")
     ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side FP32 / other-form lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-binary", action="store_true",
+                    help="skip the binary-star workload timed beside the main one")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="time the steps without the per-kernel-class events (no roofline line)")
     ap.add_argument("--serving", action="store_true",
@@ -119,6 +125,40 @@ def max_over_ranks(dist, x):
 
 N_LAMBDAS = 0  # set from --lambdas
 CROP = False  # set from --crop
+
+
+def dither_windows(problem):
+    """The whole-pixel dither steps of an in-focus problem, or None (the crop shapes of --crop)."""
+    k = np.asarray(problem.dither, dtype=np.float64) / problem.pixscale
+    r = np.rint(k)
+    return r.astype(int) if problem.focal_length == 0 and np.all(np.abs(k - r) <= 1e-6) else None
+
+
+def shapes(problem, crop):
+    """PSFs per evaluation and MFT output samples per side (crop: one PSF per source and
+    wavelength on a detector wide enough for every window)."""
+    k = dither_windows(problem) if crop and problem.n_exp > 1 else None
+    if k is None:
+        return problem.n_psf, problem.n_det * problem.oversample
+    return problem.n_lambda * problem.n_src, (problem.n_det + 2 * int(np.max(np.abs(k)))) * problem.oversample
+
+
+def streams_past_l2(problem, crop):
+    """True when a step streams more than 256 MB (twice the 129 MB L2): the phasors and the
+    first-stage products of every PSF in the four-plane 16-bit split, 64-padded rows."""
+    B, no = shapes(problem, crop)
+    ldi = -(-problem.n_pupil // 64) * 64
+    return B * 8 * (problem.n_pupil + no) * ldi > (256 << 20)
+
+
+def workload_config(workload, problem, crop, world):
+    """The `config` of both arms' JSON lines: the workload and its sizes, and the L2 policy."""
+    B, no = shapes(problem, crop)
+    big = streams_past_l2(problem, crop)
+    return dict(workload=workload_name(workload), psfs_per_eval=B, pupil=problem.n_pupil, mft_out=no,
+                parallelism=f"replicas x{world}" if world > 1 else "single",
+                l2=("no flush: per-step working set > 129 MB L2" if big
+                    else "256 MB write before every step (working set below the 129 MB L2)"))
 
 
 def make_inputs(workload, seed_offset=0):
@@ -216,9 +256,9 @@ def run_form(P, torch, workload, form, steps, warmup, device, timing=True):
         dom = max((k for k in kt_all if k in CONTRACTIONS), key=lambda k: kt_all[k], default=None)
         P.dlx_plan_set_timing(plan, dom is not None, classes=[dom] if dom else None)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    # a step whose working set fits in the 129 MB L2 is preceded by a 256 MB write (outside its events)
+    # a step that streams less than twice the 129 MB L2 is preceded by a 256 MB write (outside its events)
     flush = (torch.empty(64 << 20, dtype=torch.float32, device=f"cuda:{device}")
-             if plan.info.workspace_bytes < (256 << 20) else None)
+             if not streams_past_l2(start, crop) else None)
     torch.cuda.synchronize(device)
     for i in range(steps):
         if flush is not None:
@@ -302,10 +342,14 @@ def e2e_run(P, torch, r, steps, device):
     return dict(s_per_step=dt, h2d=h2d, d2h=d2h)
 
 
+GMAP = dict(coeff="d_zern", opd_pix="d_opd_pix", flat="d_flat", flux="d_flux", pos="d_pos")
+
+
 def sample_parity(P, torch, sub, data, form, ref):
     """The GPU path against the oracle's result on the timed sample (the same inputs on both
-    sides): model max error of the peak, loss relative error, worst gradient group's relative
-    L2 error."""
+    sides), element by element: model max error of the peak, loss relative error, and per
+    gradient group the relative L2 error and the largest element error of the group's largest
+    element."""
     plan = P.dlx_make_mft(P.desc_from_problem(sub, P.PRECISIONS[form]))
     prm = P.params_from_problem(sub)
     dt = torch.as_tensor(np.ascontiguousarray(data, dtype=np.int32), device="cuda")
@@ -313,32 +357,55 @@ def sample_parity(P, torch, sub, data, form, ref):
     loss, g, _ = P.dlx_loss_grad(plan, prm, dt, model=model)
     torch.cuda.synchronize()
     m = model.double().cpu().numpy()
-    gmap = dict(coeff="d_zern", opd_pix="d_opd_pix", flat="d_flat", flux="d_flux", pos="d_pos")
-    worst, which = 0.0, None
-    for k, gk in gmap.items():
+    worst, which, groups = 0.0, None, {}
+    for k, gk in GMAP.items():
         if g.get(gk) is None or ref[k].size == 0 or not np.any(ref[k]):
             continue
-        e = float(np.linalg.norm(g[gk].double().cpu().numpy() - ref[k]) / np.linalg.norm(ref[k]))
+        a, b = g[gk].double().cpu().numpy(), ref[k]
+        e = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        groups[k] = dict(rel_l2=e, max_err_of_max=float(np.max(np.abs(a - b)) / np.max(np.abs(b))))
         if e > worst:
             worst, which = e, k
     out = dict(form=form, model_max_err_of_peak=float(np.max(np.abs(m - ref["model"])) / np.max(ref["model"])),
                loss_rel_err=abs(loss.item() - ref["loss"]) / abs(ref["loss"]), grad_rel_l2_worst=worst,
-               grad_worst_group=which, effective_precision=int(plan.info.precision))
+               grad_worst_group=which, grads=groups, effective_precision=int(plan.info.precision))
     plan.close()
     return out
 
 
-def cpu_baseline(workload, budget_s=20.0, form=None):
-    """The FP64 oracle as it stands, on this host's cores, on a bounded sample of the
-    workload: the same model restricted to its first few wavelengths (all sources and
-    exposures); evals/s scaled by the sampled share of the PSFs.  With `form`, the GPU path
-    is also compared with the oracle's result on that sample."""
+# a whole evaluation whose MFT work (forward and adjoint) is below this many complex multiply-adds
+# takes seconds on the host's cores, and is the oracle's sample as it stands
+ORACLE_WHOLE_CMAC = 5e10
+
+
+def oracle_sample(workload):
+    """The oracle's bounded sample of a workload and the share of the evaluation's PSFs it holds.
+    The whole evaluation where its MFT work is below ORACLE_WHOLE_CMAC (tiny, binary: seconds on
+    the host), else one (wavelength, exposure) slice -- the first wavelength and the first exposure
+    with every source -- whose cost is that share of the evaluation's (every PSF costs the same;
+    the binning and likelihood are a small part)."""
+    truth, start, data = make_inputs(workload)
+    ni, no = start.n_pupil, start.n_det * start.oversample
+    cmac = 2.0 * start.n_psf * (no * ni * ni + no * no * ni)
+    if cmac <= ORACLE_WHOLE_CMAC:
+        return start, data, 1.0, f"the whole evaluation ({start.n_psf} PSFs)", start
+    sub = start.copy()
+    sub.lambdas, sub.weights = start.lambdas[:1], start.weights[:1]
+    sub.dither = start.dither[:1]
+    frac = 1.0 / (start.n_lambda * start.n_exp)
+    desc = (f"one (wavelength, exposure) slice: the first of {start.n_lambda} wavelengths and the first of "
+            f"{start.n_exp} exposures with all {start.n_src} source(s), {sub.n_psf} of {start.n_psf} PSFs at full "
+            f"size; evals/s = {frac:.6f} / seconds per slice (extrapolated by the PSF count)")
+    return sub, data[:1], frac, desc, start
+
+
+def cpu_baseline(workload, budget_s=12.0, form=None):
+    """The FP64 oracle as it stands, on this host's cores, on the bounded sample of the workload
+    (oracle_sample), timed for about budget_s; the same sample once on one core.  With `form`, the
+    GPU path is also compared with the oracle's result on that sample."""
     import oracle
 
-    truth, start, data = make_inputs(workload)
-    nsub = 2
-    sub = start.copy()
-    sub.lambdas, sub.weights = start.lambdas[:nsub], start.weights[:nsub]
+    sub, data, frac, desc, _ = oracle_sample(workload)
     oracle.lib()
     cores = oracle.set_threads(0)  # one thread per host core
     ref = oracle.loss_grad(sub, data)  # warm (thread pool, page-in); kept for the parity check
@@ -346,10 +413,9 @@ def cpu_baseline(workload, budget_s=20.0, form=None):
     while True:
         oracle.loss_grad(sub, data)
         n += 1
-        if time.perf_counter() - t0 > budget_s or n >= 20:
+        if (time.perf_counter() - t0 > budget_s and n >= 2) or n >= 20:
             break
     dt = (time.perf_counter() - t0) / n
-    frac = nsub / start.n_lambda
     # the same sample once on one core
     oracle.set_threads(1)
     t1 = time.perf_counter()
@@ -364,10 +430,9 @@ def cpu_baseline(workload, budget_s=20.0, form=None):
 
         parity = sample_parity(P, torch, sub, data, form, ref)
     return dict(value=frac / dt, unit="evals/s", cores=cores, kind="oracle", parity_on_sample=parity,
-                sample=f"{nsub} of {start.n_lambda} wavelengths (all sources and exposures), {n} runs, "
-                       f"{dt:.2f} s each; value scaled by {frac:.4f} of the PSFs",
-                single_core=dict(value=frac / dt1, unit="evals/s", cores=1, sample=f"the same sample, 1 run, "
-                                                                                  f"{dt1:.2f} s"))
+                seconds_per_sample=dt, sample=f"{desc}; {n} timed runs of {dt:.2f} s",
+                single_core=dict(value=frac / dt1, unit="evals/s", cores=1,
+                                 sample=f"the same sample, 1 run, {dt1:.2f} s"))
 
 
 SERVING_METRIC = "serving: fit requests (K Adam fwd+grad steps each) evals/s and p50/p99 request latency"
@@ -644,15 +709,15 @@ def laplace_bench(args):
 
 
 def reference_arm(args, rank, world):
-    """--impl reference: the FP64 CPU oracle timed on this host, rank 0 only."""
+    """--impl reference: the FP64 CPU oracle timed on this host, rank 0 only.  Each step is one
+    oracle run of the workload's bounded sample (oracle_sample); `ms_per_step` is that run's
+    measured time, and `value` the evaluations per second it implies (the sample's share of the
+    PSFs over the seconds per step)."""
     if rank != 0:
         return
     import oracle
 
-    truth, start, data = make_inputs(args.workload)
-    nsub = 1
-    sub = start.copy()
-    sub.lambdas, sub.weights = start.lambdas[:nsub], start.weights[:nsub]
+    sub, data, frac, desc, start = oracle_sample(args.workload)
     oracle.lib()
     cores = oracle.set_threads(0)  # one thread per host core
     for _ in range(args.warmup):
@@ -661,17 +726,81 @@ def reference_arm(args, rank, world):
     for _ in range(args.steps):
         oracle.loss_grad(sub, data)
     dt = (time.perf_counter() - t0) / args.steps
-    frac = nsub / start.n_lambda
     value = frac / dt
     line = dict(impl="reference", metric=METRIC, value=value, unit="evals/s", n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * dt / frac, higher_is_better=True, scaling="weak",
+                warmup=args.warmup, ms_per_step=1e3 * dt, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
-                config=dict(workload=workload_name(args.workload), sample=f"{nsub} of {start.n_lambda} wavelengths per step"),
-                cpu_baseline=dict(value=value, unit="evals/s", cores=cores, kind="oracle",
-                                  sample=f"each step: {nsub} of {start.n_lambda} wavelengths x all sources; "
-                                         f"value scaled by {frac:.4f}"),
+                config=workload_config(args.workload, start, CROP, world),
+                step=f"one oracle run of {desc}",
+                cpu_baseline=dict(value=value, unit="evals/s", cores=cores, kind="oracle", sample=desc),
                 e2e=dict(value=value, unit="evals/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
+
+
+# algorithmic FLOP per launch of each contraction class (8 per complex MAC), one launch per class per eval
+def contraction_flop(B, ni, no):
+    return {"stage1": 8.0 * B * no * ni * ni, "stage2_intensity": 8.0 * B * no * no * ni,
+            "adjoint_field": 8.0 * B * no * no * ni, "adjoint_stage2T": 8.0 * B * ni * no * no,
+            "adjoint_stage1T": 8.0 * B * ni * ni * no}
+
+
+# DRAM bytes (read + written) per launch of the BF16x3 form's contractions, from one-pass ncu
+# captures of this build on reduced cases (the binary-star shapes with 8 of 32 wavelengths, 16
+# PSFs; the calibration shapes with 2 of 16 wavelengths, 16 PSFs), scaled to a full launch by the
+# PSF count, in which their traffic grows (every PSF's operands are distinct and the A(lambda)
+# blocks are per wavelength); none for a kernel or form without a capture of the current code
+TRAFFIC_16 = {
+    "binary": {"stage1": 25.24e6, "stage2_intensity": 50.82e6, "adjoint_field": 126.51e6,
+               "adjoint_stage2T": 166.42e6},
+    "calib": {},
+}
+
+
+def roofline(r, form, workload, clk, peaks):
+    """Roofline of the dominant contraction of a run_form result: algorithmic FLOP per launch over
+    its mean event-timed launch in the timed region, against the measured tensor peak that
+    matches the clocks sampled during the run."""
+    kt, dom, info = r["kt"], r["dom"], r["info"]
+    classes = {k: v for k, v in kt.items() if isinstance(v, dict)}
+    ni, no, B = info.n_pupil, info.n_mft_out, info.n_psf
+    alg = contraction_flop(B, ni, no)
+    if dom not in alg or classes[dom]["events"] <= 0:
+        return None
+    # tensor instructions per algorithmic product: forward contractions of BF16x4 take 4, its adjoint 3
+    adj = dom.startswith("adjoint")
+    split = {"bf16x4": 3.0 if adj else 4.0, "bf16x3sa": 1.0 if adj else 3.0, "f16x3": 3.0, "bf16x3": 3.0,
+             "tf32x3": 3.0, "bf16": 1.0, "fp32": 1.0}[form]
+    nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16x3sa": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
+    t16 = TRAFFIC_16.get(workload, {}).get(dom) if form == "bf16x3" and not N_LAMBDAS else None
+    traffic = t16 / 16 * B if t16 else None
+    per_launch_ms = classes[dom]["ms"] / max(classes[dom]["events"], 1)
+    achieved = alg[dom] / (per_launch_ms / 1e3) / 1e12
+    if form == "fp32":
+        peak = 152 * 128 * 2 * (clk["sm_mhz"] or 1920.0) * 1e6 / 1e12
+        return dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                    traffic=None, kernel=dom, peak_source="152 SMs x 128 FP32 lanes x 2 x median SM clock")
+    # the burst peak while the sampled clocks stayed at their maximum with no power cap (the
+    # kernel ran as cuBLAS did for the burst figure), else the sustained one
+    capped = ("sw_power_cap" in (clk.get("reasons") or []) or
+              (clk.get("sm_mhz") or 0) < 0.97 * (clk.get("sm_max_mhz") or 0))
+    key = "bf16_tflops_sustained" if capped else "bf16_tflops"
+    if key in peaks:
+        base, src, tag = peaks[key], f"MEASURED_PEAKS.json {key}", " (of measured)"
+    else:
+        base, src = (1700.0, "recipe fallback 1.7 PFLOP/s sustained") if capped else \
+            (1900.0, "recipe fallback 1.9 PFLOP/s burst")
+        tag = " (of fallback)"
+    peak = base * nom_ratio[form]
+    return dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
+                traffic=traffic, traffic_unit="bytes per launch", kernel=dom,
+                executed_tflops=achieved * split, executed_frac=achieved * split / peak,
+                peak_source=src + (" x nominal tf32/bf16 ratio 1.1/2.25" if form == "tf32x3" else "") + tag)
+
+
+DTYPES = {"f16x3": "f16x3 split (fp32 accumulate)", "bf16x4": "bf16x4 split (fp32 accumulate)",
+          "bf16x3sa": "bf16x3 stochastic split, bf16 stochastic adjoint (fp32 accumulate)",
+          "bf16x3": "bf16x3 split (fp32 accumulate)", "tf32x3": "tf32x3 split (fp32 accumulate)",
+          "bf16": "bf16 (fp32 accumulate)", "fp32": "f32"}
 
 
 def main():
@@ -722,75 +851,18 @@ def main():
     info = r["info"]
     evals_per_s = world * args.steps / (total_ms / 1e3)
     ms_step = total_ms / args.steps
-
-    # roofline of the dominant contraction (its device time measured with events in the timed region)
-    kt = r["kt"]
-    classes = {k: v for k, v in kt.items() if isinstance(v, dict)}
-    dom = r["dom"]
-    ni, no, B = info.n_pupil, info.n_mft_out, info.n_psf
-    alg = {  # algorithmic FLOP per launch (8 per complex MAC), one launch per class per eval
-        "stage1": 8.0 * B * no * ni * ni, "stage2_intensity": 8.0 * B * no * no * ni,
-        "adjoint_field": 8.0 * B * no * no * ni, "adjoint_stage2T": 8.0 * B * ni * no * no,
-        "adjoint_stage1T": 8.0 * B * ni * ni * no,
-    }
-    # tensor instructions per algorithmic product: forward contractions of BF16x4 take 4, its adjoint 3
-    adj = (dom or "").startswith("adjoint")
-    split = {"bf16x4": 3.0 if adj else 4.0, "bf16x3sa": 1.0 if adj else 3.0, "f16x3": 3.0, "bf16x3": 3.0, "tf32x3": 3.0,
-             "bf16": 1.0,
-             "fp32": 1.0}[args.form]
-    nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16x3sa": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
-    # DRAM bytes (read + written) of the contractions of the BF16x3 form from one ncu capture of
-    # this build on the 8-wavelength case (16 PSFs), scaled by the PSF count, in which their
-    # traffic grows (the adjoint 1^T splits K differently at that size and is left out); any
-    # other kernel or form has no capture of the current code
-    traffic_16 = {"stage1": 25.24e6, "stage2_intensity": 50.82e6, "adjoint_field": 126.51e6,
-                  "adjoint_stage2T": 166.42e6}
-    traffic = (traffic_16[dom] / 16 * B if (args.form == "bf16x3" and dom in traffic_16 and
-                                            args.workload == "binary") else None)
-    roof = None
-    if dom in alg and classes[dom]["events"] > 0:
-        per_launch_ms = classes[dom]["ms"] / max(classes[dom]["events"], 1)
-        achieved = alg[dom] / (per_launch_ms / 1e3) / 1e12
-        if args.form == "fp32":
-            peak = 152 * 128 * 2 * (clk["sm_mhz"] or 1920.0) * 1e6 / 1e12
-            roof = dict(bound="alu", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                        traffic=None, kernel=dom, peak_source="152 SMs x 128 FP32 lanes x 2 x median SM clock")
-        else:
-            # the burst peak while the sampled clocks stayed at their maximum with no power cap (the
-            # kernel ran as cuBLAS did for the burst figure), else the sustained one
-            capped = ("sw_power_cap" in (clk.get("reasons") or []) or
-                      (clk.get("sm_mhz") or 0) < 0.97 * (clk.get("sm_max_mhz") or 0))
-            key = "bf16_tflops_sustained" if capped else "bf16_tflops"
-            if key in peaks:
-                base, src = peaks[key], f"MEASURED_PEAKS.json {key}"
-                tag = " (of measured)"
-            else:
-                base, src = (1700.0, "recipe fallback 1.7 PFLOP/s sustained") if capped else \
-                    (1900.0, "recipe fallback 1.9 PFLOP/s burst")
-                tag = " (of fallback)"
-            peak = base * nom_ratio[args.form]
-            roof = dict(bound="tensor", achieved=achieved, peak=peak, unit="TFLOP/s", frac=achieved / peak,
-                        traffic=traffic, traffic_unit="bytes per launch", kernel=dom,
-                        executed_tflops=achieved * split, executed_frac=achieved * split / peak,
-                        peak_source=src + (" x nominal tf32/bf16 ratio 1.1/2.25" if args.form == "tf32x3" else "")
-                        + tag)
-
+    B = info.n_psf
+    crop = CROP and r["start"].n_exp > 1 and P.integer_dithers(r["start"]) is not None
     line = dict(metric=METRIC, value=evals_per_s, unit="evals/s", n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=ms_step, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype={"f16x3": "f16x3 split (fp32 accumulate)", "bf16x4": "bf16x4 split (fp32 accumulate)",
-                       "bf16x3sa": "bf16x3 stochastic split, bf16 stochastic adjoint (fp32 accumulate)", "bf16x3": "bf16x3 split (fp32 accumulate)",
-                       "tf32x3": "tf32x3 split (fp32 accumulate)",
-                       "bf16": "bf16 (fp32 accumulate)", "fp32": "f32"}[args.form],
-                data="synthetic",
-                config=dict(workload=workload_name(args.workload), form=args.form, psfs_per_eval=B, pupil=ni, mft_out=no,
-                            parallelism="replicas" if world > 1 else "single",
-                            l2=("256 MB write before every step (working set below the 129 MB L2)" if r["l2_flush"]
-                                else "no flush: per-step working set > 129 MB L2"),
-                            working_set_mb=round(info.workspace_bytes / 2**20)),
+                dtype=DTYPES[args.form], data="synthetic",
+                config=workload_config(args.workload, r["start"], crop, world),
+                form=args.form, working_set_mb=round(info.workspace_bytes / 2**20),
                 psf_evals_per_s=evals_per_s * B,
                 latency_ms=dict(p50=float(np.percentile(ms, 50)), p99=float(np.percentile(ms, 99))),
                 tflops_algorithmic=evals_per_s / world * info.flop_loss_grad / 1e12,
-                gpu_launches=int(kt["total_launches"]), clocks=clk, roofline=roof,
+                gpu_launches=int(r["kt"]["total_launches"]), clocks=clk,
+                roofline=roofline(r, args.form, args.workload, clk, peaks),
                 kernels=({k: round(v, 4) for k, v in r["kt_all"].items()} if r["kt_all"] else {}),
                 wall_s=wall, device_error=r["diag"]["device_error"])
 
@@ -800,6 +872,7 @@ def main():
                        h2d_bytes_per_step=e["h2d"], d2h_bytes_per_step=e["d2h"],
                        pipeline="two steps deep: upload, evaluation and read-back on their own streams")
     r["plan"].close()
+    del r
 
     if not args.no_forms and rank == 0:
         forms = {}
@@ -811,9 +884,27 @@ def main():
                 forms[f] = dict(value=1e3 / float(rf["ms"].mean()), p50_ms=float(np.percentile(rf["ms"], 50)),
                                 p99_ms=float(np.percentile(rf["ms"], 99)))
                 rf["plan"].close()
+                del rf
             except Exception as ex:  # report, do not hide
                 forms[f] = dict(error=str(ex))
         line["forms"] = forms
+
+    if not args.no_binary and args.workload != "binary" and rank == 0:
+        # the binary-star fit (256^2 pupil, 32 wavelengths x 2 stars onto 1024^2), timed the same way
+        clk_b = Clocks(device)
+        clk_b.start()
+        rb = run_form(P, torch, "binary", args.form, args.steps, args.warmup, device,
+                      timing=not args.no_kernel_timing)
+        cb = clk_b.stop()
+        msb = rb["ms"]
+        line["binary"] = dict(
+            workload=workload_name("binary"), value=1e3 * len(msb) / float(msb.sum()), unit="evals/s",
+            ms_per_step=float(msb.mean()), steps=len(msb),
+            latency_ms=dict(p50=float(np.percentile(msb, 50)), p99=float(np.percentile(msb, 99))),
+            roofline=roofline(rb, args.form, "binary", cb, peaks),
+            kernels=({k: round(v, 4) for k, v in rb["kt_all"].items()} if rb["kt_all"] else {}), clocks=cb)
+        rb["plan"].close()
+        del rb
 
     if not args.no_cpu and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, form=args.form)

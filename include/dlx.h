@@ -250,15 +250,28 @@ int dlx_fisher_gram(const float *J, int n_par, size_t n_pix, const float *model,
  * file-scope device array of 16 MiB that every GPU loading the library holds
  * until the process exits.  Arguments are dlx_forward's, with `desc` in place
  * of a plan (desc->lambda_m is host memory, read during the call).
- * Limits: at most 32 sources and 256 wavelengths, and the working memory of
+ * Limits: dlx_make_mft's checks of the descriptor (INVALID_ARG, RANGE), at most
+ * 32 sources and 256 wavelengths, no dither_px windows (UNSUPPORTED), and the
+ * working memory of
  *   8*nl + 8*nl + 8*B*Ni + 4*Ni^2 + 8*nl*No*Ni8 + 8*nl*Ni*No8 + 8*B*Ni*Ni8
- *   + 8*B*No*Ni8 + 4*nS*nE*No^2 + reduction partials   (bytes, Ni8/No8 = sizes rounded up to 8)
+ *   + 8*B*No*Ni8 + 4*nS*nE*No^2 + reduction partials   (bytes, Ni8/No8 = sizes rounded up to 8,
+ *   each of the 16 regions starting on a 256-byte boundary)
  * must fit in 16 MiB; larger shapes return DLX_ERR_RANGE with the byte count.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  Every call on a device shares the array and overwrites
- * it, so calls whose work overlaps on the GPU (other streams or threads) race:
- * serialise them.  Asynchronous on the stream like dlx_forward. */
+ * Under dlx_set_checks(1) the parameter arrays and `model` are checked as for
+ * dlx_forward before anything runs.
+ * When memory is taken: CUDA loads a library's device code and its device arrays
+ * when they are first used (lazy loading, the default), so the first call on a
+ * device loads the 16 MiB array and the kernels the call runs; a later call that
+ * needs a kernel no earlier call ran (more than 8 sources, for one) loads that
+ * kernel too.  Make the first calls, with the shapes the caller will use, before
+ * reserving the device's memory, or have everything loaded when the context is
+ * created by setting CUDA_MODULE_LOADING=EAGER in the environment.  Make the first
+ * call on a device before any stream capture.  Every call looks up the array's
+ * device address (cudaGetSymbolAddress) on the calling thread's current device,
+ * which must be the device of the arrays passed in.  Every call on a device
+ * shares the array and overwrites it, so calls whose work overlaps on the GPU
+ * (other streams or threads) race: serialise them.  Asynchronous on the stream
+ * like dlx_forward. */
 int dlx_forward_noalloc(const dlx_mft_desc *desc, const dlx_params *params, float *model, void *cuda_stream);
 
 /* The flux-weighted oversampled intensity before binning and flat field,
@@ -382,6 +395,10 @@ typedef struct {
     int active, queued;
     size_t hbm_in_use, hbm_budget;
     uint64_t evals, graph_launches, grouped_launches;
+    /* admissions into a bucket where another request had already taken steps (a slot
+     * refilled mid-flight), and finished slots refilled by moving the bucket's last
+     * active slot down into them */
+    uint64_t midflight_admits, slot_moves;
 } dlx_server_stats;
 
 /* Create a continuous-batching fit server on `device` with its own stream and

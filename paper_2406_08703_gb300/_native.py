@@ -70,7 +70,7 @@ class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("admitted", C.c_uint64), ("completed", C.c_uint64),
                 ("rejected", C.c_uint64), ("active", C.c_int), ("queued", C.c_int), ("hbm_in_use", C.c_size_t),
                 ("hbm_budget", C.c_size_t), ("evals", C.c_uint64), ("graph_launches", C.c_uint64),
-                ("grouped_launches", C.c_uint64)]
+                ("grouped_launches", C.c_uint64), ("midflight_admits", C.c_uint64), ("slot_moves", C.c_uint64)]
 
 
 # Every symbol include/dlx.h declares, with (restype, argtypes).

@@ -135,11 +135,10 @@ void free_plan(dlx_plan *p) {
     delete p;
 }
 
-int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
-    if (!d || !out) return fail(DLX_ERR_INVALID_ARG, "desc/out is NULL");
-    *out = nullptr;
+int check_desc(const dlx_mft_desc *d, int *delta_out) {
+    if (!d) return fail(DLX_ERR_INVALID_ARG, "desc is NULL");
     if (d->n_pupil < 2 || d->n_det < 1 || d->oversample < 1 || d->n_lambda < 1 || d->n_src < 1 || d->n_exp < 1 ||
-        d->n_zern < 0 || R_max < 1)
+        d->n_zern < 0)
         return fail(DLX_ERR_INVALID_ARG, "sizes must be positive (n_pupil >= 2)");
     if (!(d->diameter_m > 0) || !(d->pixscale_rad > 0)) return fail(DLX_ERR_INVALID_ARG, "diameter and pixscale > 0");
     if (!d->lambda_m) return fail(DLX_ERR_INVALID_ARG, "lambda_m is NULL");
@@ -168,6 +167,21 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     const long long no_ll = nd_mft * d->oversample;
     if (d->n_pupil > 8192 || no_ll > 16384)
         return fail(DLX_ERR_RANGE, "n_pupil <= 8192 and (n_det + 2 max|dither_px|) * oversample <= 16384");
+    // PSF and Zernike counts stay far inside the 32-bit index arithmetic
+    if (d->n_zern > 4096 || (long long)d->n_lambda * d->n_src * d->n_exp > (1LL << 24))
+        return fail(DLX_ERR_RANGE, "n_zern <= 4096 and n_lambda * n_src * n_exp <= 2^24");
+    if (delta_out) *delta_out = delta;
+    return DLX_OK;
+}
+
+int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
+    if (!d || !out) return fail(DLX_ERR_INVALID_ARG, "desc/out is NULL");
+    *out = nullptr;
+    if (R_max < 1) return fail(DLX_ERR_INVALID_ARG, "R_max must be >= 1");
+    int delta = 0;
+    if (int rc = check_desc(d, &delta)) return rc;
+    const long long nd_mft = (long long)d->n_det + 2LL * delta;
+    const long long no_ll = nd_mft * d->oversample;
 
     DeviceGuard guard(device);
     cudaDeviceProp prop;

@@ -11,8 +11,10 @@
 //   FMT_BF16X2 : re, im                     (bf16)          -- plain BF16 form
 //   FMT_TF32X4 : re_hi, re_lo, im_hi, im_lo (tf32 in fp32)  -- TF32x3 form
 //   FMT_F16X4  : re_hi, re_lo, im_hi, im_lo (fp16)          -- FP16x3 form
-// hi = round(x), lo = round(x - hi).  Which split products a contraction forms
-// (three, or four with lo*lo) is chosen by the tensor-core kernel per form.
+// hi = x rounded to 8 significant bits, lo = x - hi rounded to the element type
+// (8 significant bits in BF16, 11 in FP16 and TF32; see split_hi8).  Which split
+// products a contraction forms (three, or four with lo*lo) is chosen by the
+// tensor-core kernel per form.
 // FP16 operands hold x times a power of two that keeps |x| <= 1 (see the
 // scale helpers below), so hi and lo stay inside FP16's exponent range.
 #pragma once
@@ -37,17 +39,32 @@ __host__ __device__ constexpr int fmt_esize(int f) {
     return (f == FMT_BF16X4 || f == FMT_BF16X2 || f == FMT_F16X4) ? 2 : 4;
 }
 
-// 16-bit element type of a 16-bit form and its round-to-nearest conversions.
+// The hi part of every split keeps 8 significant bits (round to nearest), whatever
+// the element type.  The tensor core adds an instruction's products to its FP32
+// accumulator after aligning them to it and keeps about 24 bits, truncating: a
+// 16-bit hi*hi product (8 x 8 bits) loses nothing beside a sum up to 2^8 times its
+// size, whereas the 22-bit products of 11-bit parts (FP16, TF32) lose low bits as
+// soon as the sum is 4 times larger, and at a coherent PSF peak those losses add
+// up (measured 1.5-1.9e-5 of the peak over a 512-long contraction with full-width
+// FP16 and TF32 hi parts).  With an 8-bit hi the lo part of FP16 and TF32 carries
+// the next 11 bits, so hi + lo represent x to about 2^-21 (BF16: 2^-17).
+__device__ __forceinline__ float split_hi8(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// 16-bit element type of a 16-bit form and its round-to-nearest conversions;
+// `hi` rounds the hi part of a split.
 template <int F>
 struct H16 {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ T from(float x) { return __float2bfloat16_rn(x); }
+    static __device__ __forceinline__ T hi(float x) { return __float2bfloat16_rn(x); }
     static __device__ __forceinline__ float to(T x) { return __bfloat162float(x); }
 };
 template <>
 struct H16<FMT_F16X4> {
     using T = __half;
     static __device__ __forceinline__ T from(float x) { return __float2half_rn(x); }
+    // 8 significant bits are exact in FP16 inside its normal range (operands are scaled to |x| <= 1)
+    static __device__ __forceinline__ T hi(float x) { return __float2half_rn(split_hi8(x)); }
     static __device__ __forceinline__ float to(T x) { return __half2float(x); }
 };
 
@@ -80,7 +97,7 @@ __device__ __forceinline__ void store_cplx(void *base, size_t pstride, size_t id
     } else if constexpr (F == FMT_BF16X4 || F == FMT_F16X4) {
         using H = H16<F>;
         typename H::T *p = (typename H::T *)base;
-        const typename H::T rh = H::from(re), ih = H::from(im);
+        const typename H::T rh = H::hi(re), ih = H::hi(im);
         p[idx] = rh;
         p[pstride + idx] = H::from(re - H::to(rh));
         p[2 * pstride + idx] = ih;
@@ -91,7 +108,7 @@ __device__ __forceinline__ void store_cplx(void *base, size_t pstride, size_t id
         p[pstride + idx] = __float2bfloat16_rn(im);
     } else {
         float *p = (float *)base;
-        float rh = tf32_round(re), ih = tf32_round(im);
+        float rh = split_hi8(re), ih = split_hi8(im);
         p[idx] = rh;
         p[pstride + idx] = tf32_round(re - rh);
         p[2 * pstride + idx] = ih;
@@ -109,8 +126,8 @@ __device__ __forceinline__ void store_cplx8(void *base, size_t pstride, size_t i
         float hr[8], hi[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            hr[q] = (F == FMT_F32) ? re[q] : tf32_round(re[q]);
-            hi[q] = (F == FMT_F32) ? im[q] : tf32_round(im[q]);
+            hr[q] = (F == FMT_F32) ? re[q] : split_hi8(re[q]);
+            hi[q] = (F == FMT_F32) ? im[q] : split_hi8(im[q]);
         }
         auto put = [&](float *d, const float *v) {
             ((float4 *)d)[0] = make_float4(v[0], v[1], v[2], v[3]);
@@ -137,8 +154,8 @@ __device__ __forceinline__ void store_cplx8(void *base, size_t pstride, size_t i
         __align__(16) typename H::T rh[8], ih[8], rl[8], il[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            rh[q] = H::from(re[q]);
-            ih[q] = H::from(im[q]);
+            rh[q] = H::hi(re[q]);
+            ih[q] = H::hi(im[q]);
             rl[q] = H::from(re[q] - H::to(rh[q]));
             il[q] = H::from(im[q] - H::to(ih[q]));
         }
@@ -502,6 +519,9 @@ inline void fresnel_terms(const dlx_mft_desc *d, double *du_scale, double *chirp
 }
 
 // ---- plan construction (dlx_api.cu)
+// Validates a descriptor (sizes, ranges, wavelengths, precision, Fresnel terms, dithers):
+// DLX_OK, or the status with dlx_last_error set; *delta_out = max |dither_px| (may be NULL).
+int check_desc(const dlx_mft_desc *d, int *delta_out);
 int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out);
 void free_plan(dlx_plan *p);
 

@@ -341,8 +341,8 @@ __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const flo
             }
             char *pb = (char *)P + (size_t)bg * Pl * ps * es;
             if constexpr (F == FMT_BF16X4) {
-                if (sr) {  // BF16x3 form: stochastic split
-                    store_cplx8_sr(pb, ps, (size_t)ny * ldi + nx0, re, im, ((size_t)bg * ni + ny) * ldi + nx0,
+                if (sr) {  // BF16x3 form: stochastic split, random bits keyed by the slot-local PSF index
+                    store_cplx8_sr(pb, ps, (size_t)ny * ldi + nx0, re, im, ((size_t)(bg - r * B) * ni + ny) * ldi + nx0,
                                    sr ^ 0x1b873593u);
                     continue;
                 }

@@ -354,8 +354,8 @@ __device__ __forceinline__ void store_row(void *base, size_t ps, size_t off, con
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const float x = re[8 * q + i], y = im[8 * q + i];
-                    rh[i] = H::from(x);
-                    ih[i] = H::from(y);
+                    rh[i] = H::hi(x);
+                    ih[i] = H::hi(y);
                     rl[i] = H::from(x - H::to(rh[i]));
                     il[i] = H::from(y - H::to(ih[i]));
                 }
@@ -378,9 +378,9 @@ __device__ __forceinline__ void store_row(void *base, size_t ps, size_t off, con
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     const float x = re[4 * q + i], y = im[4 * q + i];
-                    hp[i] = tf32_round(x);
+                    hp[i] = split_hi8(x);
                     lp[i] = tf32_round(x - hp[i]);
-                    hip[i] = tf32_round(y);
+                    hip[i] = split_hi8(y);
                     lip[i] = tf32_round(y - hip[i]);
                 }
                 *(float4 *)(p + 4 * q) = h;
@@ -408,8 +408,8 @@ __device__ __forceinline__ void stage_row16(uint8_t *stg, int r, int h, const fl
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const float x = re[8 * q + i], y = im[8 * q + i];
-            rh[i] = H::from(x);
-            ih[i] = H::from(y);
+            rh[i] = H::hi(x);
+            ih[i] = H::hi(y);
             rl[i] = H::from(x - H::to(rh[i]));
             il[i] = H::from(y - H::to(ih[i]));
         }
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         if constexpr (KIND == KS1 && F == FMT_BF16X4) {
                             if (a.sr) {
                                 const int n = J.n0 + c0;
-                                stage_row16_sr(stg, row, h, er, ei, ((size_t)J.b * a.M + m) * a.out_ld + n,
+                                stage_row16_sr(stg, row, h, er, ei, ((size_t)(J.b % a.B) * a.M + m) * a.out_ld + n,
                                                a.sr ^ 0xcc9e2d51u);
                                 staged = true;
                             }
@@ -820,7 +820,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         if constexpr ((KIND == KGE || KIND == KGT1) && F == FMT_BF16X2) {
                             if (a.sr) {  // BF16x3sa adjoint: stochastically rounded hi parts only
                                 const int n = J.n0 + c0;
-                                stage_row16_hi_sr(stg, row, h, er, ei, ((size_t)J.b * a.M + m) * a.out_ld + n,
+                                stage_row16_hi_sr(stg, row, h, er, ei, ((size_t)(J.b % a.B) * a.M + m) * a.out_ld + n,
                                                   a.sr);
                                 staged = true;
                             }

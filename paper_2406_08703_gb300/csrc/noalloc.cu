@@ -13,14 +13,12 @@
 // CUDA-core form.
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "dlx_common.cuh"
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB per GPU
-constexpr int kMaxDevices = 64;
 constexpr int kMaxLambdas = 256;
 
 // Working memory shared by every call on a device.  In host code this name is
@@ -28,29 +26,37 @@ constexpr int kMaxLambdas = 256;
 // cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on `device` (which must be current),
-// looked up on the first call per device.
-int scratch_address(int device, void **out) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (device < 0 || device >= kMaxDevices) {
-        dlx_set_error("device index out of range");
-        return DLX_ERR_INVALID_ARG;
+// Device address of the scratch array on the current device, looked up on every
+// call (a lookup is cheap, and a cached address would go stale if the device's
+// context were reset and the array reloaded elsewhere).
+int scratch_address(void **out) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        dlx_set_error(std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") +
+                      cudaGetErrorString(e));
+        return DLX_ERR_CUDA;
     }
-    if (!g_scratch_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            dlx_set_error(std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") +
-                          cudaGetErrorString(e));
-            return DLX_ERR_CUDA;
-        }
-        g_scratch_addr[device] = p;
-    }
-    *out = g_scratch_addr[device];
+    *out = p;
     return DLX_OK;
+}
+
+// The wavelength tables travel as a kernel argument (by value), so the call copies
+// nothing from host memory with cudaMemcpy.
+struct LamTable {
+    double lam[kMaxLambdas];
+    int n;
+};
+
+// lam_d[l] = lambda_l, invlam[l] = 1/lambda_l rounded to float (as a plan stores them),
+// and the reset of the normalisation's block counter.
+__global__ void k_noalloc_tables(const LamTable t, double *lam_d, float *invlam, unsigned int *ncount) {
+    const int l = threadIdx.x;
+    if (l < t.n) {
+        lam_d[l] = t.lam[l];
+        invlam[l] = (float)(1.0 / t.lam[l]);
+    }
+    if (l == 0) *ncount = 0u;
 }
 
 // Bump layout inside the scratch array, 256-byte aligned regions.
@@ -69,31 +75,26 @@ struct Carve {
 }  // namespace
 
 extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm, float *model, void *stream) {
-    if (!d || !prm || !model || !d->lambda_m) {
-        dlx_set_error("desc, params, model and desc->lambda_m are required");
+    if (!d || !prm || !model) {
+        dlx_set_error("desc, params and model are required");
         return DLX_ERR_INVALID_ARG;
     }
-    if (d->n_pupil < 2 || d->n_det < 1 || d->oversample < 1 || d->n_lambda < 1 || d->n_src < 1 || d->n_exp < 1 ||
-        d->n_zern < 0 || !(d->diameter_m > 0) || !(d->pixscale_rad > 0)) {
-        dlx_set_error("sizes must be positive (n_pupil >= 2), diameter and pixscale > 0");
-        return DLX_ERR_INVALID_ARG;
-    }
+    // the plan's own checks: sizes, ranges, wavelengths, Fresnel terms
+    if (int rc = dlx::check_desc(d, nullptr)) return rc;
     if (!prm->transmission || !prm->weights || !prm->flux || !prm->pos || !prm->flat ||
         (d->n_zern > 0 && (!prm->zern_basis || !prm->zern_coeff))) {
         dlx_set_error("transmission, weights, flux, pos, flat (and the Zernike arrays when n_zern > 0) are required");
         return DLX_ERR_INVALID_ARG;
     }
-    for (int l = 0; l < d->n_lambda; ++l)
-        if (!(d->lambda_m[l] > 0) || !std::isfinite(d->lambda_m[l])) {
-            dlx_set_error("wavelengths must be finite and > 0");
-            return DLX_ERR_INVALID_ARG;
-        }
     if (d->dither_px) {
         dlx_set_error("dlx_forward_noalloc: integer-pixel dither windows (dither_px) need a plan");
         return DLX_ERR_UNSUPPORTED;
     }
-    if (d->n_src > dlx::kMaxSrc || d->n_lambda > kMaxLambdas) {
-        dlx_set_error("dlx_forward_noalloc: at most 32 sources and 256 wavelengths");
+    // the scratch holds at least 8 * Ni * Ni8 bytes of phasor per PSF, so more than 2^17 PSFs never fit
+    const long long B_ll = (long long)d->n_lambda * d->n_src * d->n_exp;
+    if (d->n_lambda > kMaxLambdas || B_ll > (1LL << 17)) {
+        dlx_set_error("dlx_forward_noalloc: at most 256 wavelengths and 2^17 PSFs, and the working memory must fit "
+                      "the fixed 16 MiB scratch");
         return DLX_ERR_RANGE;
     }
 
@@ -136,6 +137,12 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
         dlx_set_error("cudaDeviceGetAttribute failed");
         return DLX_ERR_CUDA;
     }
+    if (dlx::check_level() >= 1) {
+        // checked mode: every array is device memory of this device, aligned, and large enough
+        int rc = dlx::check_params(&p, prm);
+        if (!rc) rc = dlx::check_buffer(model, sizeof(float) * (size_t)p.ne * p.nd * p.nd, 4, dev, "model", false);
+        if (rc) return rc;
+    }
     const size_t np = (size_t)p.nd * p.nd, nq = (size_t)p.no * p.no, npx = (size_t)p.ni * p.ni;
     p.red_blocks = std::max(1, std::min((int)((np + 255) / 256), p.sm_count * 2));
     // more than 8 sources: the model pass of the two-pass binning (no loss, no partials)
@@ -166,7 +173,7 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     }
 
     void *base = nullptr;
-    int rc = scratch_address(dev, &base);
+    int rc = scratch_address(&base);
     if (rc) return rc;
     Carve c{(char *)base};
     p.lam_d = c.take<double>(p.nl);
@@ -191,15 +198,11 @@ extern "C" int dlx_forward_noalloc(const dlx_mft_desc *d, const dlx_params *prm,
     // cleared; the tables below are rewritten on every call because another call
     // may have left a different shape in the array.
     cudaStream_t st = (cudaStream_t)stream;
-    double lam[kMaxLambdas];
-    float inv[kMaxLambdas];
-    for (int l = 0; l < p.nl; ++l) {
-        lam[l] = d->lambda_m[l];
-        inv[l] = (float)(1.0 / d->lambda_m[l]);
-    }
-    cudaError_t e = cudaMemcpyAsync(p.lam_d, lam, sizeof(double) * p.nl, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.ncount, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(p.invlam, inv, sizeof(float) * p.nl, cudaMemcpyHostToDevice, st);
+    LamTable tab{};
+    tab.n = p.nl;
+    for (int l = 0; l < p.nl; ++l) tab.lam[l] = d->lambda_m[l];
+    k_noalloc_tables<<<1, kMaxLambdas, 0, st>>>(tab, p.lam_d, p.invlam, p.ncount);
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = dlx::launch_mft_matrices(&p, st);
     if (e != cudaSuccess) {
         dlx_set_error(std::string("dlx_forward_noalloc: ") + cudaGetErrorString(e));

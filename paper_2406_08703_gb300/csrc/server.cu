@@ -457,6 +457,11 @@ void worker_loop(dlx_server *s) {
                 ++it;
                 continue;
             }
+            for (int k = 0; k < b->active; ++k)
+                if (b->slot_req[k] && b->slot_req[k]->steps_done > 0) {
+                    s->stats.midflight_admits++;
+                    break;
+                }
             const int r = b->active++;
             b->slot_req[r] = q;
             q->bucket = b;
@@ -537,7 +542,10 @@ void worker_loop(dlx_server *s) {
                     }
                     finish(s, q, status);
                     const int last = b->active - 1;
-                    if (r != last) move_slot(b, last, r);
+                    if (r != last) {
+                        move_slot(b, last, r);
+                        s->stats.slot_moves++;
+                    }
                     b->slot_req[last] = nullptr;
                     b->active--;
                     cudaStreamSynchronize(b->stream);

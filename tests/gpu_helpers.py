@@ -6,32 +6,31 @@ import numpy as np
 import oracle
 import workloads as W
 
-# Tolerances per arithmetic form (PSF max error relative to the peak, loss
-# relative error, gradient relative L2 error per parameter group).  The FP32
-# form, BF16x4 (the split form that keeps the hi*hi products in their own
-# accumulator and includes lo*lo) and BF16x3 (three products of a stochastically
-# rounded split, hi*hi apart in stage 2) must meet 1e-5 of peak on the PSF.
-# TF32x3 is measured at up to ~1.9e-5 at coherent PSF peaks (a 512-long
-# contraction takes 64 tensor instructions per accumulator at k = 8 each) and is
-# bounded at 2e-5.  FP16x3 (FP16 hi + lo carry 22 significant bits, so lo*lo is below
-# 2^-22 and three products suffice) has the most accurate operands, but its
-# 22-bit hi*hi products overflow the ~24-bit window in which the tensor core
-# aligns them to a growing FP32 accumulator, so coherent sums lose low bits:
-# measured 1.6e-6 of peak at a 64 pupil, 4.2e-6 at 256 and 1.5e-5 at 512; the
-# PSF is bounded at 2e-5 and the gradients at the FP32 bound.
-# BF16x3sa shares BF16x3's forward; its adjoint contracts the stochastically
-# rounded hi parts alone, so its gradients carry zero-mean noise of about
-# 2^-8 / sqrt(K) per contraction: measured 3e-4 (binary-star workload) to 1.5e-3
-# (64 pupil) relative L2, bounded at 3e-3.
+# Tolerances per arithmetic form: PSF max error relative to the peak, loss relative
+# error, gradient relative L2 error per parameter group (`grad`) and the largest
+# error of any gradient element relative to the group's largest element
+# (`grad_max`).  Every split form and the FP32 form meet 1e-5 of the peak on the PSF.
+# The hi part of every split keeps 8 significant bits, so its hi*hi products fit the
+# tensor core's accumulator alignment window; TF32x3 and FP16x3 carry the next 11
+# bits in lo (measured up to 7.1e-6 and 7.3e-6 of the peak, 1.6e-6 / 1.1e-6 on a
+# coherent 512-long contraction, where full-width hi parts measured 1.9e-5 / 1.5e-5).
+# Gradients (worst over the GPU parity cases, relative L2 / element of group max):
+# FP32 2.3e-6 / 2.1e-6; FP16x3, TF32x3 and BF16x4 (round-to-nearest splits) up to
+# 4.5e-5; BF16x3 up to 6.5e-4 / 7.0e-4: its stochastic split removes the coherent
+# bias at the PSF peak but leaves a noise floor about four times the
+# round-to-nearest split's, and gradients that weigh the faint PSF wings (flux and
+# flat through 1 - d/m) see it.  BF16x3sa shares BF16x3's forward; its adjoint
+# contracts the stochastically rounded hi parts alone, so its gradients carry
+# zero-mean noise of about 2^-8 / sqrt(K) per contraction: up to 2.2e-3 / 4.1e-3.
 # Plain BF16 is reported as measured and only bounded loosely here.
 TOL = {
-    "f16x3": dict(psf=2e-5, loss=1e-6, grad=1e-4),
-    "fp32": dict(psf=1e-5, loss=1e-6, grad=1e-4),
-    "tf32x3": dict(psf=2e-5, loss=1e-6, grad=1e-4),
-    "bf16x4": dict(psf=1e-5, loss=1e-6, grad=1e-3),
-    "bf16x3": dict(psf=1e-5, loss=1e-6, grad=1e-3),
-    "bf16x3sa": dict(psf=1e-5, loss=1e-6, grad=3e-3),
-    "bf16": dict(psf=5e-3, loss=1e-3, grad=5e-2),
+    "fp32": dict(psf=1e-5, loss=1e-6, grad=1e-5, grad_max=1e-5),
+    "f16x3": dict(psf=1e-5, loss=1e-6, grad=1e-4, grad_max=1e-4),
+    "tf32x3": dict(psf=1e-5, loss=1e-6, grad=1e-4, grad_max=1e-4),
+    "bf16x4": dict(psf=1e-5, loss=1e-6, grad=1e-4, grad_max=1e-4),
+    "bf16x3": dict(psf=1e-5, loss=1e-6, grad=1e-3, grad_max=1e-3),
+    "bf16x3sa": dict(psf=1e-5, loss=1e-6, grad=3e-3, grad_max=6e-3),
+    "bf16": dict(psf=1e-2, loss=1e-3, grad=5e-2, grad_max=5e-2),
 }
 
 
@@ -93,6 +92,10 @@ def compare(out, ref, precision, groups=("coeff", "opd_pix", "flat", "flux", "po
     for g in groups:
         if ref[g].size:
             err[g] = rel_l2(out["grads"][gmap[g]], ref[g])
+            top = float(np.max(np.abs(ref[g])))
+            if top > 0:  # element by element: the largest error against the group's largest element
+                err[g + "_max"] = float(np.max(np.abs(out["grads"][gmap[g]] - ref[g]))) / top
+    print("compare", precision, err)
     assert out["diag"]["device_error"] == 0
     assert err.get("psf", 0) <= tol["psf"], err
     assert err["model"] <= tol["psf"], err
@@ -101,4 +104,6 @@ def compare(out, ref, precision, groups=("coeff", "opd_pix", "flat", "flux", "po
     for g in groups:
         if g in err:
             assert err[g] <= tol["grad"], (g, err)
+        if g + "_max" in err:
+            assert err[g + "_max"] <= tol["grad_max"], (g, err)
     return err

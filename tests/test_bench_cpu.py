@@ -36,3 +36,31 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_print_nothing():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_reference_arm_timed_steps_fit_the_run():
+    """ms_per_step is the measured time of one step (one oracle run of the sample), so the
+    steps' total fits inside the process's own wall time."""
+    import time
+
+    t0 = time.perf_counter()
+    d = json.loads(_run({})[0])
+    wall = time.perf_counter() - t0
+    assert d["steps"] * d["ms_per_step"] / 1e3 <= wall
+
+
+def test_calibration_sample_is_one_wavelength_exposure_slice():
+    """The million-parameter calibration is sampled as one (wavelength, exposure) slice of its
+    128 PSFs at full size; the binary-star evaluation is taken whole."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    sub, data, frac, desc, start = bench.oracle_sample("calib")
+    assert start.n_psf == 128 and sub.n_psf == 1 and frac == 1.0 / 128
+    assert sub.n_pupil == 512 and sub.n_det * sub.oversample == 2048 and data.shape == (1, 1024, 1024)
+    assert "slice" in desc
+    cfg = bench.workload_config("calib", start, False, 1)
+    assert (cfg["psfs_per_eval"], cfg["pupil"], cfg["mft_out"]) == (128, 512, 2048)
+    assert cfg["l2"].startswith("no flush")
+    _, _, frac_b, _, start_b = bench.oracle_sample("binary")
+    assert frac_b == 1.0 and start_b.n_psf == 64

@@ -58,6 +58,37 @@ def test_ragged_shapes(case, form):
     compare(out, oracle_eval(start, data), form)
 
 
+def _long_problem(case):
+    """512-long contractions (the two-sided MFT of Sec. 3 over a 512^2 pupil) onto a small
+    detector, so the oracle checks every output."""
+    if case == 0:
+        # evaluated at an unaberrated hard-edged pupil and an on-axis star: every phasor sample is the
+        # same, so the rounding of the operands and of the accumulation adds up coherently at the PSF
+        # peak.  The data come from an aberrated, shifted star of another flux, so that every gradient
+        # carries signal (at the data's own truth they are Poisson noise, sums that nearly cancel)
+        p = W.make_problem("custom", seed=70, n_pupil=512, n_det=24, oversample=2, zern_rms=0.0)
+        p.transmission = W.aperture(512, p.diameter, 0.0, oversample=1)
+        truth = p.copy()
+        truth.coeff = 20e-9 * np.random.default_rng(71).standard_normal(p.n_zern)
+        truth.pos = truth.pos + 0.3 * p.pixscale
+        truth.flux = 1.2 * p.flux
+        truth.flat = W.flat_field(p.n_det, 0.05, 72)
+        return p, W.poisson_counts(oracle.forward(truth), 73)
+    truth, data, start = fit_problem("custom", seed=72, n_pupil=512, n_det=32, oversample=2, n_lambda=2, n_src=2,
+                                     obscuration=0.2, grating=True, n_zern_max=8, opd_pix_rms=5e-9)
+    return start, data
+
+
+@pytest.mark.parametrize("case", range(2))
+@pytest.mark.parametrize("form", FORMS)
+def test_long_contractions(case, form):
+    """K = 512 in both forward contractions and the adjoint 1^T: model, PSF, loss and every
+    gradient element against the oracle."""
+    p, data = _long_problem(case)
+    err = compare(gpu_eval(p, data, form), oracle_eval(p, data), form)
+    print(form, case, err)
+
+
 @pytest.fixture(scope="module")
 def binary_reduced():
     truth, data, start = fit_problem("binary", n_lambda=4)

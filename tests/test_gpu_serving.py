@@ -60,6 +60,43 @@ def test_same_result_alone_and_in_the_mix(P):
         assert rel_l2(y[k], x[k]) < 1e-6, k
 
 
+def test_mid_flight_admission_gives_the_solo_result(P):
+    """Continuous batching: six same-shape requests with uneven step counts on a server with two
+    slots, in the default BF16x3 form.  As a request finishes, a queued one is admitted into the
+    freed slot while the other slot's request is still stepping, and when the finished request sat
+    below the last active slot, that slot's request (inputs, parameters, Adam state) is moved down
+    into the freed one mid-fit.  Every request's loss, parameters and gradients equal its run alone
+    (one slot, same K): the split's random bits follow the PSF's index inside its slot, and the
+    reductions have a fixed order per slot, so only the stage-2 work split, which depends on the
+    active-slot count, may reorder sums (within 1e-6)."""
+    from paper_2406_08703_gb300.server import result_shapes
+
+    ks = [2, 40, 9, 3, 7, 4]
+    reqs = [_request(140 + i, **SHAPE_A) for i in range(len(ks))]
+    form = P.PRECISIONS["bf16x3"]
+    keys = ("zern_coeff", "opd_pix", "flux", "pos", "flat", "g_zern", "g_opd_pix", "g_flat", "g_flux", "g_pos")
+
+    def run(batch):
+        srv = P.dlx_server_create(0, 0, 2)
+        tickets = [srv.submit(p, d, n_steps=k, lr=LR, precision=form) for (p, d), k in batch]
+        out = [srv.poll(t, timeout_s=120.0, shapes=result_shapes(p)) for t, ((p, _), _) in zip(tickets, batch)]
+        stats = srv.stats()
+        srv.close()
+        return out, stats
+
+    mixed, stats = run(list(zip(reqs, ks)))
+    assert stats["completed"] == len(ks) and stats["grouped_launches"] > 0
+    assert stats["midflight_admits"] >= 1, stats  # a slot was refilled next to a running fit
+    assert stats["slot_moves"] >= 1, stats  # a running fit was moved down into a freed slot
+    for i, (rq, k) in enumerate(zip(reqs, ks)):
+        (alone,), _ = run([(rq, k)])
+        y = mixed[i]
+        assert y["steps_done"] == k and alone["steps_done"] == k
+        assert y["loss"] == pytest.approx(alone["loss"], rel=1e-9), i
+        for key in keys:
+            assert rel_l2(y[key], alone[key]) < 1e-6, (i, key)
+
+
 def test_single_evaluation_matches_direct_call(P):
     import torch
 
