@@ -431,7 +431,7 @@ def dlx_plan_set_timing(plan: Plan, enable: bool = True, classes=None) -> None:
 
 
 KERNEL_CLASSES = ("mft_matrices", "prologue", "stage1", "stage2_intensity", "bin_nll", "loss", "adjoint_field",
-                  "adjoint_stage2T", "adjoint_stage1T", "grad_reduce", "adam")
+                  "adjoint_stage2T", "adjoint_stage1T", "grad_reduce", "adam", "adjoint_field_scale")
 
 
 def dlx_plan_get_timing_names():

@@ -96,7 +96,7 @@ namespace dlx {
 
 static const char *kClassNames[KC_N] = {"mft_matrices", "prologue",      "stage1",          "stage2_intensity",
                                         "bin_nll",      "loss",          "adjoint_field",   "adjoint_stage2T",
-                                        "adjoint_stage1T", "grad_reduce", "adam"};
+                                        "adjoint_stage1T", "grad_reduce", "adam", "adjoint_field_scale"};
 
 static cudaEvent_t pool_get(dlx_plan *p) {
     if (p->pool_next < p->pool.size()) return p->pool[p->pool_next++];
@@ -339,6 +339,15 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->tilt, sizeof(float2) * Bt * 2 * p->ni);
     if (e == cudaSuccess) e = plan_alloc(p, &p->opd, sizeof(float) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->Is, sizeof(float) * (size_t)p->G * p->nse * R_max * nq);
+    // the fields stage 2 keeps for the adjoint (instead of its recomputation), when the adjoint
+    // takes every PSF at once and a workspace limit leaves room for them
+    const size_t ef_bytes = sizeof(float) * 2 * (size_t)Bt * p->no * p->ldo;
+    if (e == cudaSuccess && field_kept(p->fmt, p->adj1, p->chunk, Bt) &&
+        (d->workspace_limit_bytes == 0 || d->workspace_limit_bytes >= (size_t)Bt * per_psf + ef_bytes)) {
+        e = plan_alloc(p, &p->Ef, ef_bytes);
+        if (e == cudaSuccess) e = cudaMemset(p->Ef, 0, ef_bytes);
+        if (e == cudaSuccess) e = plan_alloc(p, &p->GIt, sizeof(float) * p->ne * np * R_max);
+    }
     if (e == cudaSuccess) e = plan_alloc(p, &p->GI, sizeof(float) * p->ne * np * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->model_tmp, sizeof(float) * p->nei * npi * R_max);
     if (d->dither_px) {
@@ -449,6 +458,14 @@ int eval_forward(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
 
 int eval_loss_grad(dlx_plan *p, const DevParams &prm, int R, const int32_t *data, size_t data_stride, double *loss,
                    const DevGrads *g, float *model, size_t model_stride, cudaStream_t st) {
+    const bool pupil = g && (g->p[GZERN] || g->p[GPIX] || g->p[GPOS]);
+    // stage 2 keeps each PSF's field for the adjoint when a pupil gradient is wanted and the
+    // adjoint operand holds every PSF; the flag lives for this evaluation only
+    struct KeepField {
+        dlx_plan *p;
+        ~KeepField() { p->keep_field = false; }
+    } keep{p};
+    p->keep_field = pupil && keeps_field(p, R);
     int rc = eval_forward(p, prm, R, st);
     if (rc) return rc;
     if (!model) {
@@ -456,7 +473,6 @@ int eval_loss_grad(dlx_plan *p, const DevParams &prm, int R, const int32_t *data
         model_stride = (size_t)p->nei * p->ndi * p->ndi;
     }
     DLX_CU(launch_bin_nll(p, prm, R, data, data_stride, model, model_stride, g, loss, st), "bin+nll+loss");
-    const bool pupil = g && (g->p[GZERN] || g->p[GPIX] || g->p[GPOS]);
     if (pupil) {
         const int Bt = R * p->B;
         for (int b0 = 0; b0 < Bt; b0 += p->chunk) {

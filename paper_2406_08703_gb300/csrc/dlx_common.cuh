@@ -398,6 +398,8 @@ struct dlx_plan {
     float2 *tilt = nullptr;    // [R*B][2][ni]
     float *opd = nullptr;      // [R][ni*ni]
     float *Is = nullptr;       // [G][R*nse][no][no] per-source intensity partials
+    float *Ef = nullptr;       // [R*B][re, im][no][ldo] fp32 fields kept by stage 2 for the adjoint, or NULL
+    float *GIt = nullptr;      // [R][ne][nd][nd] GI transposed (x rows, y columns), with Ef
     float *GI = nullptr;       // [R][ne][nd*nd] FF * dL/dm on the MFT's detector
     float *GIimg = nullptr;    // integer dithers: [R][nei][ndi*ndi] the images' FF * dL/dm
     float *Swin = nullptr;     // integer dithers: [R][nd*nd] sum_s F_s B_s on the big detector
@@ -417,6 +419,9 @@ struct dlx_plan {
     float *mom = nullptr;      // tensor-core forms: [R*B][gsplit][tiles][8 warps][2] position moments
     uint32_t sr = 0;           // BF16x3 forms: stochastic splitting of the forward operands (seed base), else 0
     bool adj1 = false;         // BF16x3sa: the adjoint contracts the stochastic hi parts only (2-plane bf16)
+    // set by eval_loss_grad for one evaluation: stage 2 also writes every PSF's field E into the
+    // adjoint-field operand (GEt) and the adjoint scales it in place instead of recomputing it
+    bool keep_field = false;
     float prf_inv = 0.f;       // 1 / sigma^2 of the chi^2 prior on the flat field, 0 = none
     // forward-mode derivative (dlx_model_jvp): while tan_map is set, the phasors of the sources
     // in tan_mask are multiplied by (1 + i tan_coef (2 pi / lambda) tan_map[n])
@@ -461,7 +466,7 @@ constexpr int kMinBf16Pupil = 32;  // smallest pupil (samples per side) the BF16
 constexpr int kNormParts = 1024;  // maximum blocks of the OPD / pupil-power pass
 
 enum KClass { KC_MATRICES = 0, KC_PROLOGUE, KC_STAGE1, KC_STAGE2, KC_BIN, KC_LOSS, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1,
-              KC_GRAD, KC_ADAM, KC_N };
+              KC_GRAD, KC_ADAM, KC_FIELD_SCALE, KC_N };
 
 // Checked mode (dlx_set_checks): the process-wide level, and the level-2 check after a
 // kernel class (synchronises the stream unless it is being captured; records the first
@@ -543,6 +548,13 @@ cudaError_t launch_fisher_gram(const float *J, int n, size_t npix, const float *
 cudaError_t launch_nll_cotangent(const float *m, const int32_t *d, size_t n, float *cot, cudaStream_t st);
 // adds the stage-2 split's extra planes into plane 0 (tensor-core forms; no-op otherwise)
 cudaError_t launch_plane_fold(dlx_plan *p, int R, cudaStream_t st);
+// Whether an evaluation of R slots keeps the fields stage 2 forms for the adjoint: plans of the
+// BF16 split forms (not BF16x3sa) whose adjoint operand holds every PSF at once allocate Ef.
+inline bool keeps_field(const dlx_plan *p, int R) { return p->Ef != nullptr && p->chunk >= R * p->B; }
+// Whether a plan of this form, PSF count and adjoint chunk allocates Ef.
+inline bool field_kept(int fmt, bool adj1, int chunk, int Bt) { return fmt == FMT_BF16X4 && !adj1 && chunk >= Bt; }
+// The adjoint field from the kept fields: GEt[z] = split(2 w F GI o Ef[b0 + z]) (z < nb).
+cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st);
 // a = (a - b) * c elementwise (the central difference of dlx_model_jvp)
 cudaError_t launch_scaled_diff(float *a, const float *b, size_t n, float c, cudaStream_t st);
 // Adam over R packed slots of n parameters each; group k of a slot is

@@ -1401,6 +1401,102 @@ __global__ void k_grad_final(const float2 *__restrict__ zpart, int nz, int nzb, 
     }
 }
 
+// The adjoint field from the fields stage 2 kept (the chain rule of the Poisson likelihood,
+// Sec. 4, through I = sum_l w_l F_s |E|^2): GEt[z][kx][ky] = 2 w_l F_s GI[e][ky/os][kx/os] E[kx][ky]
+// for the chunk-local PSF z = b - b0, b = (r, l, s, e), from Ef (fp32, [b][re, im][kx][ky]) into
+// the four-plane BF16 split, rounded to nearest -- the values and the split that the recomputing
+// contraction's epilogue writes.  One warp per row (z, kx) at a time: the row's constants are
+// formed once, and each lane takes 8-element vectors 256 columns apart (two 16-byte loads per
+// plane in, one 16-byte store per plane out, four vectors in flight); padding columns ky >= No
+// get zeros.
+__device__ __forceinline__ void field_scale_vec(const float *er, const float *ei, __nv_bfloat16 *p, size_t ps,
+                                                const float *gi, float c, int k0, int no, int os, int bmax) {
+    const float4 a0 = __ldg((const float4 *)(er + k0)), a1 = __ldg((const float4 *)(er + k0) + 1);
+    const float4 c0 = __ldg((const float4 *)(ei + k0)), c1 = __ldg((const float4 *)(ei + k0) + 1);
+    const float xr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float xi[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
+    int brow = k0 / os, brem = k0 - brow * os;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const bool in = k0 + q < no;
+        const float f = in ? c * __ldg(gi + min(brow, bmax)) : 0.f;
+        const float x = in ? xr[q] * f : 0.f, y = in ? xi[q] * f : 0.f;
+        rh[q] = __float2bfloat16_rn(x);
+        rl[q] = __float2bfloat16_rn(x - __bfloat162float(rh[q]));
+        ih[q] = __float2bfloat16_rn(y);
+        il[q] = __float2bfloat16_rn(y - __bfloat162float(ih[q]));
+        if (++brem == os) {
+            brem = 0;
+            ++brow;
+        }
+    }
+    *(uint4 *)(p + k0) = *(const uint4 *)rh;
+    *(uint4 *)(p + ps + k0) = *(const uint4 *)rl;
+    *(uint4 *)(p + 2 * ps + k0) = *(const uint4 *)ih;
+    *(uint4 *)(p + 3 * ps + k0) = *(const uint4 *)il;
+}
+
+__global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ Ef, __nv_bfloat16 *__restrict__ ge,
+                                                     const float *__restrict__ GIt, DevParams prm,
+                                                     const float *__restrict__ wnorm, int b0, int nb, int B, int nl,
+                                                     int nse, int ne, int no, int ldo, int nd, int os) {
+    pdl_trigger();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5, nrows = nb * no;
+    const size_t ps = (size_t)no * ldo;
+    const int bmax = (no - 1) / os;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += nwarps) {
+        const int z = row / no, kx = row - z * no, b = b0 + z;
+        const int r = b / B, rem = b - r * B, l = rem / nse, se = rem - l * nse, s = se / ne, e = se - s * ne;
+        const float c = 2.f * __ldg(wnorm + r * nl + l) * __ldg(slot_ptr(prm, PFLUX, r) + s);
+        const float *gi = GIt + (((size_t)r * ne + e) * nd + kx / os) * nd;  // row x = kx / os, along y
+        const float *er = Ef + (size_t)b * 2 * ps + (size_t)kx * ldo, *ei = er + ps;
+        __nv_bfloat16 *p = ge + (size_t)z * 4 * ps + (size_t)kx * ldo;
+        int k0 = 8 * lane;
+        for (; k0 + 3 * 256 < ldo; k0 += 4 * 256) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) field_scale_vec(er, ei, p, ps, gi, c, k0 + u * 256, no, os, bmax);
+        }
+        for (; k0 < ldo; k0 += 256) field_scale_vec(er, ei, p, ps, gi, c, k0, no, os, bmax);
+    }
+}
+
+// GIt[k][x][y] = GI[k][y][x] for the R * ne weight maps, through 32 x 32 tiles in shared memory
+// (the field scaling reads the weights along y).
+__global__ void k_gi_transpose(const float *__restrict__ GI, float *__restrict__ GIt, int nd) {
+    __shared__ float t[32][33];
+    pdl_trigger();
+    pdl_wait();
+    const size_t base = (size_t)blockIdx.z * nd * nd;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int y = y0 + j, x = x0 + threadIdx.x;
+        if (y < nd && x < nd) t[j][threadIdx.x] = GI[base + (size_t)y * nd + x];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int x = x0 + j, y = y0 + threadIdx.x;
+        if (y < nd && x < nd) GIt[base + (size_t)x * nd + y] = t[threadIdx.x][j];
+    }
+}
+
+cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st) {
+    if (nb <= 0) return cudaSuccess;
+    KScope ks(p, KC_FIELD_SCALE, 2, st);
+    const int R = (b0 + nb + p->B - 1) / p->B;  // slots whose weight maps the PSFs use
+    const int tiles = (p->nd + 31) / 32;
+    cudaError_t e = launch_pdl(k_gi_transpose, dim3(tiles, tiles, R * p->ne), dim3(32, 8), 0, st,
+                               (const float *)p->GI, p->GIt, p->nd);
+    if (e != cudaSuccess) return e;
+    const int rows = nb * p->no;
+    const int blocks = std::max(1, std::min((rows + 7) / 8, p->sm_count * 8));
+    return launch_pdl(k_field_scale, dim3(blocks), dim3(256), 0, st, (const float *)p->Ef,
+                      (__nv_bfloat16 *)p->GEt.ptr, (const float *)p->GIt, prm, (const float *)p->wnorm, b0, nb, p->B,
+                      p->nl, p->nse, p->ne, p->no, p->ldo, p->nd, p->os);
+}
+
 cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st) {
     const int npx = p->ni * p->ni, nzb = (npx + 63) / 64;
     DevGrads gg{};

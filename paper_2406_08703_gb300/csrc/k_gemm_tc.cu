@@ -523,6 +523,22 @@ __device__ __forceinline__ void load_row(const void *base, size_t ps, size_t off
     }
 }
 
+// Stage 2 keeping the field for the adjoint: the 16 values E[ky = m][kx = n0 + i] of this
+// thread's row go transposed into Ef[b][re, im][kx][ky] (fp32).  The 32 lanes of a warp hold 32
+// consecutive rows, so every store instruction writes 128 contiguous bytes of one column.
+__device__ __forceinline__ void store_field_t(const TcArgs &a, int b, int m, int n0, const float (&er)[CW],
+                                              const float (&ei)[CW]) {
+    if (m >= a.M) return;
+    float *o = (float *)a.out + (size_t)b * 2 * a.out_ps + (size_t)n0 * a.out_ld + m;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+        if (n0 + i < a.N) {
+            o[(size_t)i * a.out_ld] = er[i];
+            o[a.out_ps + (size_t)i * a.out_ld] = ei[i];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ the kernel
 template <int F, int MODE, int KIND>
 __global__ void __launch_bounds__(NTHREADS, 1)
@@ -834,8 +850,46 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
+                if constexpr (KIND == KS2) {
+                    // stage 2: four 16-column chunks of this warp's accumulator half; the accumulators
+                    // are handed back to the MMA warp once the last chunk is loaded, before its |E|^2
+                    // sums and field stores (holding two chunks at once would spill registers)
+                    auto ld_chunk = [&](int cc, float (&er)[CW], float (&ei)[CW]) {
+                        const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + 64 * h + CW * cc;
+                        tmem_ld16(ta, er);
+                        tmem_ld16(ta + 128, ei);
+                        if constexpr (MODE != FAST) {
+                            float t[CW];
+                            tmem_ld16(ta + 256, t);
 #pragma unroll
-                for (int cc = 0; cc < (TMA_OUT ? 0 : 64 / CW); ++cc) {
+                            for (int i = 0; i < CW; ++i) er[i] += t[i];
+                            tmem_ld16(ta + 384, t);
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) ei[i] += t[i];
+                        }
+                    };
+                    auto use_chunk = [&](int cc, const float (&er)[CW], const float (&ei)[CW]) {
+#pragma unroll
+                        for (int i = 0; i < CW; ++i)
+                            acc[CW * cc + i] = fmaf(w, er[i] * er[i] + ei[i] * ei[i], acc[CW * cc + i]);
+                        if constexpr (F == FMT_BF16X4) {  // the field kept for the adjoint
+                            if (a.out) store_field_t(a, J.b, m, J.n0 + 64 * h + CW * cc, er, ei);
+                        }
+                    };
+                    float er[CW], ei[CW];
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc) {
+                        ld_chunk(cc, er, ei);
+                        use_chunk(cc, er, ei);
+                    }
+                    ld_chunk(3, er, ei);
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+                    use_chunk(3, er, ei);
+                }
+#pragma unroll
+                for (int cc = 0; cc < ((TMA_OUT || KIND == KS2) ? 0 : 64 / CW); ++cc) {
                     const int c0 = 64 * h + CW * cc;
                     const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + c0;
                     float er[CW], ei[CW];
@@ -853,9 +907,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const int n0 = J.n0 + c0;
                     const int nvalid = min(CW, a.N - n0);
                     if constexpr (KIND == KS2) {
-#pragma unroll
-                        for (int i = 0; i < CW; ++i)
-                            acc[CW * cc + i] = fmaf(w, er[i] * er[i] + ei[i] * ei[i], acc[CW * cc + i]);
                     } else {
                         if (m < a.M && nvalid > 0) {
                             if constexpr (KIND == KGE) {
@@ -917,9 +968,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+                if constexpr (KIND != KS2) {  // stage 2 handed its accumulators back above
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+                }
                 if constexpr (F == FMT_F16X4 && KIND == KGE) {
                     // max |GEt'| of this PSF (non-negative floats order as their bits)
                     if (!(gmx < 3.0e38f)) gmx = 3.0e38f;
@@ -1109,6 +1162,11 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     c.s2pc = (const int4 *)(p->s2_table + sp.pcs);
     c.grid = sp.nct;
     c.units = sp.npieces;
+    if (p->keep_field) {  // E of every PSF, transposed: Ef[b][re, im][kx][ky]
+        c.out = p->Ef;
+        c.out_ld = p->ldo;
+        c.out_ps = (size_t)p->no * p->ldo;
+    }
     return launch<F, MODE2, KS2>(p, p->amat, p->T1t, nullptr, c, st);
 }
 
@@ -1133,7 +1191,9 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
         T1.tmap = p->T1t.tmap_hi;
         Am.tmap = p->amat.tmap_hi;
     }
-    cudaError_t e = launch<F, FAST, KGE>(p, T1, Am, &p->GEt, a, st);
+    // the field kept by stage 2 (BF16 split forms) is scaled and split; otherwise it is recomputed
+    cudaError_t e = p->keep_field ? launch_field_scale(p, prm, b0, nb, st)
+                                  : launch<F, FAST, KGE>(p, T1, Am, &p->GEt, a, st);
     if (e != cudaSuccess) return e;
     // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No)
     TcArgs b{};

@@ -202,6 +202,9 @@ size_t bucket_bytes(const dlx_mft_desc &d, bool has_pix, int cap) {
     const size_t pe = (size_t)dlx::fmt_planes(fmt) * dlx::fmt_esize(fmt);
     size_t b = pe * (nl * no * ldi + nl * ni * ldo + Bt * ni * ldi + Bt * no * ldi + Bt * no * ldo + Bt * ni * ldo);
     b += 4 * (Bt * ni * ni) + 8 * (Bt * 2 * ni) + 4 * (size_t)d.n_src * ne_mft * cap * no * no * 2;
+    // the fields stage 2 keeps for the adjoint (the bucket's plan takes every PSF in one chunk)
+    if (dlx::field_kept(fmt, d.precision == DLX_BF16X3SA, (int)Bt, (int)Bt))
+        b += 8 * Bt * no * ldo + 4 * (size_t)cap * ne_mft * (no / d.oversample) * (no / d.oversample);
     b += 16 * (size_t)cap * ni * ni + 8 * (size_t)cap * d.n_exp * nd * nd;
     if (d.dither_px) b += 4 * (size_t)cap * (d.n_exp * nd * nd + 2 * (no / d.oversample) * (no / d.oversample));
     const size_t nth = theta_size(d, has_pix);

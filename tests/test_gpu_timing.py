@@ -45,11 +45,11 @@ def test_class_timing_counts_and_masks():
             assert v["events"] >= 3 and v["ms"] > 0, k
 
     # one class: only it carries events
-    P.dlx_plan_set_timing(plan, True, classes=["adjoint_field"])
+    P.dlx_plan_set_timing(plan, True, classes=["adjoint_stage2T"])
     P.dlx_loss_grad(plan, prm, data)
     one = P.dlx_plan_get_timing(plan)
-    assert one["adjoint_field"]["events"] == 1 and one["adjoint_field"]["ms"] > 0
-    assert all(v["events"] == 0 for k, v in one.items() if isinstance(v, dict) and k != "adjoint_field")
+    assert one["adjoint_stage2T"]["events"] == 1 and one["adjoint_stage2T"]["ms"] > 0
+    assert all(v["events"] == 0 for k, v in one.items() if isinstance(v, dict) and k != "adjoint_stage2T")
 
     # reading reset everything
     again = P.dlx_plan_get_timing(plan)
