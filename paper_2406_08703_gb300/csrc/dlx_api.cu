@@ -321,7 +321,8 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     op_alloc(p->GT1, p->chunk, p->ni, p->ldo, adj_planes);
     const size_t npx = (size_t)p->ni * p->ni, np = (size_t)p->nd * p->nd, nq = (size_t)p->no * p->no;
     const size_t npi = (size_t)p->ndi * p->ndi;
-    p->red_blocks = std::max(1, std::min((int)((npi + 255) / 256), std::max(1, p->sm_count * 2 / R_max)));
+    // blocks of the one-pass binning: up to eight per SM, so that enough loads are in flight
+    p->red_blocks = std::max(1, std::min((int)((npi + 255) / 256), std::max(1, p->sm_count * 8 / R_max)));
     if (e == cudaSuccess) e = plan_alloc(p, &p->lam_d, sizeof(double) * p->nl);
     if (e == cudaSuccess) e = plan_alloc(p, &p->wnorm, sizeof(float) * p->nl * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->pscale, sizeof(float) * 2 * R_max);

@@ -151,7 +151,6 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
     extern __shared__ float c_sh[];
     __shared__ df sh[32];
     __shared__ bool s_last;
-    __shared__ float s_part[4][64];
     const int r = blockIdx.y;
     const float *fixed = slot_ptr(prm, POPDF, r), *basis = slot_ptr(prm, PBASIS, r);
     const float *coeff = slot_ptr(prm, PCOEFF, r), *pix = slot_ptr(prm, POPDPIX, r), *T = slot_ptr(prm, PT, r);
@@ -164,29 +163,28 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
         for (int i = tid; i < B; i += nthr) gmax[(size_t)r * B + i] = 0u;
     df t2[1] = {{0.f, 0.f}};
     float tmax = 0.f;
-    // 64 pupil pixels per block and pass, 4 threads per pixel: thread group k sums the
-    // Zernike terms j = k, k + 4, ... (all its loads in flight), group 0 adds the four
-    // partial sums in a fixed order
-    const int lpx = threadIdx.x & 63, grp = threadIdx.x >> 6;
-    for (int i0 = blockIdx.x * 64; i0 < npx; i0 += gridDim.x * 64) {  // block-uniform trip count
-        const int i = i0 + lpx;
-        float v = 0.f;
-        if (i < npx) {
-#pragma unroll 4
-            for (int j = grp; j < nz; j += 4) v = fmaf(c_sh[j], __ldg(basis + (size_t)j * npx + i), v);
+    // one thread per pupil pixel: the Zernike terms go into eight partial sums (eight basis
+    // loads in flight), added in a fixed order
+    for (int i = tid; i < npx; i += nthr) {
+        float part[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) part[q] = 0.f;
+        int j = 0;
+        for (; j + 7 < nz; j += 8) {
+            float z[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) z[q] = __ldg(basis + (size_t)(j + q) * npx + i);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) part[q] = fmaf(c_sh[j + q], z[q], part[q]);
         }
-        s_part[grp][lpx] = v;
-        __syncthreads();
-        if (grp == 0 && i < npx) {
-            float o = fixed ? fixed[i] : 0.f;
-            o += (s_part[0][lpx] + s_part[1][lpx]) + (s_part[2][lpx] + s_part[3][lpx]);
-            if (pix) o += pix[i];
-            opd[(size_t)r * npx + i] = o;
-            const float t = T[i];
-            t2[0] = df_add(t2[0], t * t);
-            tmax = fmaxf(tmax, fabsf(t));
-        }
-        __syncthreads();
+        for (int q = 0; j < nz; ++j, ++q) part[q] = fmaf(c_sh[j], __ldg(basis + (size_t)j * npx + i), part[q]);
+        float o = fixed ? __ldg(fixed + i) : 0.f;
+        o += ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
+        if (pix) o += __ldg(pix + i);
+        opd[(size_t)r * npx + i] = o;
+        const float t = __ldg(T + i);
+        t2[0] = df_add(t2[0], t * t);
+        tmax = fmaxf(tmax, fabsf(t));
     }
     // tilt factors of this slot's PSFs: tilt[r B + bl][axis][n]; in the Fresnel regime each also
     // carries its axis' share of the quadratic phase exp(i pi |x|^2 (1/z - 1/f) / lambda), the
@@ -355,7 +353,7 @@ __global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const flo
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
     const int npx = p->ni * p->ni;
     KScope ks(p, KC_PROLOGUE, 2, st);
-    const int work = std::max((npx + 63) / 64, (p->B * 2 * p->ni + 255) / 256);
+    const int work = std::max((npx + 255) / 256, (p->B * 2 * p->ni + 255) / 256);
     const int blocks = std::max(1, std::min({work, p->sm_count * 8 / R, kNormParts}));
     cudaError_t e = launch_pdl(k_prologue, dim3(blocks, R), dim3(256), sizeof(float) * (p->nz > 0 ? p->nz : 1), st,
                                prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm,
@@ -424,6 +422,7 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
         const int py = valid ? p / nd : 0, px = valid ? p % nd : 0;
         const float ff = valid ? flat[p] : 0.f;
         float dff = 0.f;
+#pragma unroll 2
         for (int e = 0; e < ne; ++e) {
             float bs[MAXS], bmax[MAXS];
             float btot = 0.f;
@@ -1166,8 +1165,13 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
     };
     cudaError_t e;
     if (p->ns <= 8) {
-        // one pass, per-source registers
-        e = p->os == 4 ? go(k_bin_nll<4, 8>) : p->os == 2 ? go(k_bin_nll<2, 8>) : go(k_bin_nll<0, 8>);
+        // one pass, per-source registers (sized for 1, 2 or 8 sources)
+        if (p->ns == 1)
+            e = p->os == 4 ? go(k_bin_nll<4, 1>) : p->os == 2 ? go(k_bin_nll<2, 1>) : go(k_bin_nll<0, 1>);
+        else if (p->ns == 2)
+            e = p->os == 4 ? go(k_bin_nll<4, 2>) : p->os == 2 ? go(k_bin_nll<2, 2>) : go(k_bin_nll<0, 2>);
+        else
+            e = p->os == 4 ? go(k_bin_nll<4, 8>) : p->os == 2 ? go(k_bin_nll<2, 8>) : go(k_bin_nll<0, 8>);
     } else {
         auto ga = [&](auto kern) {
             return launch_pdl(kern, dim3(p->bin_a_blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse,
@@ -1237,17 +1241,25 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
 // g_OPD[r][n] = sum_{b in slot r} gphi[b][n] (compensated);  dL/dOPD_pix = g_OPD;
 // and the Zernike partials <Z_j, g_OPD> over the block's 64 pupil pixels
 // (zpart[r][j][block], compensated pairs).  A block covers 64 pupil pixels with 4
-// threads per pixel, each summing every 4th entry (8 loads in flight); the 4
-// partial sums are combined in a fixed order.  For the Zernike partials the 64
-// threads of group k take the terms j = k, k + 4, ...
-__global__ void k_gopd_zern(const float *__restrict__ gphi, int B, int npx, float2 *__restrict__ gopd, DevGrads g,
-                            DevParams prm, int nz, float2 *__restrict__ zpart) {
+// threads per pixel, each summing every 4th entry of the pixel's column of gphi (8
+// loads in flight); the 4 partial sums are combined in a fixed order.  For the
+// Zernike partials the threads of group k take the terms j = k, k + 4, ..., up to 32
+// of them at a time: every warp sums each term over its 32 pixels (basis loads all in
+// flight first), and after one barrier 32 threads per group add the group's two
+// warps.  All sums are compensated FP32 pairs (about 44 significant bits), the reading
+// of "FP64 gradient reductions" applied here, in a fixed order, so every run gives
+// the same bits.
+constexpr int kGopdPx = 64;  // pupil pixels per block of k_gopd_zern
+__global__ void __launch_bounds__(256) k_gopd_zern(const float *__restrict__ gphi, int B, int npx,
+                                                   float2 *__restrict__ gopd, DevGrads g, DevParams prm, int nz,
+                                                   float2 *__restrict__ zpart) {
     pdl_trigger();
     pdl_wait();
     __shared__ df sh[4][64];
-    __shared__ df shz[8];
+    __shared__ df shz[8][32];
     const int r = blockIdx.y, px = threadIdx.x & 63, grp = threadIdx.x >> 6, lane = threadIdx.x & 31;
-    const int n = blockIdx.x * 64 + px;
+    const int wid = threadIdx.x >> 5;
+    const int n = blockIdx.x * kGopdPx + px;
     df acc{0.f, 0.f};
     if (n < npx) {
         const float *src = gphi + (size_t)r * B * npx + n;
@@ -1270,34 +1282,30 @@ __global__ void k_gopd_zern(const float *__restrict__ gphi, int B, int npx, floa
     }
     if (!zpart) return;
     const float *basis = slot_ptr(prm, PBASIS, r);
-    // the basis values of this thread's terms (up to 16 per group) are loaded up front
-    constexpr int ZQ = 16;
-    float zb[ZQ];
+    const int ng = (nz + 3) / 4;  // terms of the group with the most
+    for (int q0 = 0; q0 < ng; q0 += 32) {  // block-uniform
+        float zb[32];
 #pragma unroll
-    for (int q = 0; q < ZQ; ++q) {
-        const int j = 4 * q + grp;
-        zb[q] = (j < nz && n < npx) ? __ldg(basis + (size_t)j * npx + n) : 0.f;
-    }
-    auto partial = [&](int j, float z) {
-        df v{0.f, 0.f};
-        if (j < nz && n < npx) v = df_add(df_add(v, z * t.hi), z * t.lo);
-        v = warp_sum(v);
-        if (lane == 0) shz[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (px == 0 && j < nz) {
-            const df w = df_add(shz[2 * grp], shz[2 * grp + 1]);
-            zpart[((size_t)r * nz + j) * gridDim.x + blockIdx.x] = make_float2(w.hi, w.lo);
+        for (int q = 0; q < 32; ++q) {
+            const int j = 4 * (q0 + q) + grp;
+            zb[q] = (q0 + q < ng && j < nz && n < npx) ? __ldg(basis + (size_t)j * npx + n) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            if (q0 + q >= ng) break;  // block-uniform
+            df v = df_add(df{zb[q] * t.hi, 0.f}, zb[q] * t.lo);
+            v = warp_sum(v);
+            if (lane == q) shz[wid][q] = v;
         }
         __syncthreads();
-    };
-#pragma unroll
-    for (int q = 0; q < ZQ; ++q) {
-        if (4 * q >= nz) break;  // uniform
-        partial(4 * q + grp, zb[q]);
-    }
-    for (int j0 = 4 * ZQ; j0 < nz; j0 += 4) {
-        const int j = j0 + grp;
-        partial(j, (j < nz && n < npx) ? __ldg(basis + (size_t)j * npx + n) : 0.f);
+        if ((threadIdx.x & 32) == 0) {  // first warp of each group: lanes = terms
+            const int q = lane, j = 4 * (q0 + q) + grp;
+            if (q0 + q < ng && j < nz) {
+                const df w = df_add(shz[2 * grp][q], shz[2 * grp + 1][q]);
+                zpart[((size_t)r * nz + j) * gridDim.x + blockIdx.x] = make_float2(w.hi, w.lo);
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1498,7 +1506,7 @@ cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb
 }
 
 cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st) {
-    const int npx = p->ni * p->ni, nzb = (npx + 63) / 64;
+    const int npx = p->ni * p->ni, nzb = (npx + kGopdPx - 1) / kGopdPx;
     DevGrads gg{};
     if (g) gg = *g;
     const bool zern = gg.p[GZERN] && p->nz > 0, pos_tc = gg.p[GPOS] && p->mom, pos_simt = gg.p[GPOS] && !p->mom;

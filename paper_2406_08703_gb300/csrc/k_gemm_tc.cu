@@ -525,7 +525,9 @@ __device__ __forceinline__ void load_row(const void *base, size_t ps, size_t off
 
 // Stage 2 keeping the field for the adjoint: the 16 values E[ky = m][kx = n0 + i] of this
 // thread's row go transposed into Ef[b][re, im][kx][ky] (fp32).  The 32 lanes of a warp hold 32
-// consecutive rows, so every store instruction writes 128 contiguous bytes of one column.
+// consecutive rows, so every store instruction writes 128 contiguous bytes of one column.  (Marking
+// the stores evict-first cut the contraction's operand re-reads but made the scaling pass, which
+// then found none of the field in L2, slower by more: not kept.)
 __device__ __forceinline__ void store_field_t(const TcArgs &a, int b, int m, int n0, const float (&er)[CW],
                                               const float (&ei)[CW]) {
     if (m >= a.M) return;
@@ -761,6 +763,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if constexpr (KIND == KGT1) osc = f16_sigma2(a, J);
                     if constexpr (KIND == KGP) k2 /= al * al * f16_gamma(a, J) * f16_sigma2(a, J) * pi;
                 }
+                bool released = false;  // accumulators already handed back to the MMA warp
                 if constexpr (TMA_OUT) {
                     // four rounds of one 32-column box: warp (q, h) fills rows 32q.., columns 16h..,
                     // one thread stores the box; rows and columns past the tensor are clipped by TMA
@@ -782,14 +785,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     };
                     if constexpr (KIND == KGE) gi_round(0, gcur);
-                    for (int t = 0; t < 4; ++t) {
-                        if (J.n0 + 32 * t >= a.out_ld) break;  // uniform over the epilogue warps
-                        const int c0 = 32 * t + 16 * h;
-                        const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + c0;
-                        if constexpr (KIND == KGE) {
-                            if (t < 3) gi_round(t + 1, gnxt);
-                        }
-                        float er[CW], ei[CW];
+                    // one accumulator buffer (stage 1 with hi*hi apart): rounds 2 and 3 are loaded
+                    // together and the accumulators handed back to the MMA warp before their work
+                    constexpr bool kEarly = (KIND == KS1 && MODE != FAST);
+                    auto ld_round = [&](int t, float (&er)[CW], float (&ei)[CW]) {
+                        const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + 32 * t + 16 * h;
                         tmem_ld16(ta, er);
                         tmem_ld16(ta + 128, ei);
                         if constexpr (MODE != FAST) {
@@ -800,6 +800,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             tmem_ld16(ta + 384, tt);
 #pragma unroll
                             for (int i = 0; i < CW; ++i) ei[i] += tt[i];
+                        }
+                    };
+                    float pre_r[2][CW], pre_i[2][CW];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (J.n0 + 32 * t >= a.out_ld) break;  // uniform over the epilogue warps
+                        const int c0 = 32 * t + 16 * h;
+                        if constexpr (KIND == KGE) {
+                            if (t < 3) gi_round(t + 1, gnxt);
+                        }
+                        float er[CW], ei[CW];
+                        if (kEarly && t >= 2) {
+                            if (t == 2) {
+                                ld_round(2, pre_r[0], pre_i[0]);
+                                if (J.n0 + 96 < a.out_ld) ld_round(3, pre_r[1], pre_i[1]);
+                                tc_fence_before();
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+                                released = true;
+                            }
+#pragma unroll
+                            for (int i = 0; i < CW; ++i) {
+                                er[i] = pre_r[t - 2][i];
+                                ei[i] = pre_i[t - 2][i];
+                            }
+                        } else {
+                            ld_round(t, er, ei);
                         }
                         if constexpr (KIND == KGE) {
 #pragma unroll
@@ -968,7 +995,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                         }
                     }
                 }
-                if constexpr (KIND != KS2) {  // stage 2 handed its accumulators back above
+                if (KIND != KS2 && !released) {  // stage 2 handed its accumulators back above
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
