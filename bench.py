@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "bf16x3sa", "bf16x4", "f16x3", "tf32x3", "bf16", "fp32"])
     ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
-    ap.add_argument("--workload", default="calib")
+    ap.add_argument("--workload", default=None,
+                    help="workload of the main line (default calib) or of --fit / --laplace (default paper)")
     ap.add_argument("--lambdas", type=int, default=0,
                     help="use only this many of the workload's wavelengths (same per-PSF shapes; profiling captures)")
     ap.add_argument("--no-forms", action="store_true", help="skip the side-by-side FP32 / other-form lines")
@@ -584,7 +585,7 @@ def fit_bench(args):
     P.load()
     import workloads as W
 
-    wl = args.workload if args.workload != "binary" else "paper"
+    wl = args.workload or "paper"
     truth = W.make_problem(wl)
     start = W.perturbed_start(truth, 81)
     data = W.synthetic_counts((start.n_exp, start.n_det, start.n_det), float(np.sum(truth.flux)) * start.n_exp,
@@ -645,7 +646,7 @@ def laplace_bench(args):
     P.load()
     import workloads as W
 
-    wl = args.workload if args.workload != "binary" else "paper"
+    wl = args.workload or "paper"
     truth = W.make_problem(wl)
     crop = use_crop(P, truth, args)
     plan = P.dlx_make_mft(P.desc_from_problem(truth, P.PRECISIONS[args.form], crop=crop))
@@ -744,15 +745,15 @@ def contraction_flop(B, ni, no):
             "adjoint_stage1T": 8.0 * B * ni * ni * no}
 
 
-# DRAM bytes (read + written) per launch of the BF16x3 form's contractions, from one-pass ncu
-# captures of this build on reduced cases (the binary-star shapes with 8 of 32 wavelengths, 16
-# PSFs; the calibration shapes with 2 of 16 wavelengths, 16 PSFs), scaled to a full launch by the
-# PSF count, in which their traffic grows (every PSF's operands are distinct and the A(lambda)
-# blocks are per wavelength); none for a kernel or form without a capture of the current code
+# DRAM bytes (read + written) per launch of the BF16x3 form's contractions, from ncu captures of
+# this build on reduced cases of 16 PSFs (the calibration shapes with 2 of 16 wavelengths, the
+# binary-star shapes with 8 of 32), scaled to a full launch by the PSF count, in which their
+# traffic grows (every PSF's operands are distinct and the A(lambda) blocks are per wavelength);
+# none for a kernel or form without a capture of the current code
 TRAFFIC_16 = {
-    "binary": {"stage1": 25.24e6, "stage2_intensity": 50.82e6, "adjoint_field": 126.51e6,
-               "adjoint_stage2T": 166.42e6},
-    "calib": {},
+    "binary": {},
+    "calib": {"stage1": 131.47e6, "stage2_intensity": 983.86e6, "adjoint_stage2T": 889.08e6,
+              "adjoint_stage1T": 198.35e6},
 }
 
 
@@ -806,6 +807,9 @@ DTYPES = {"f16x3": "f16x3 split (fp32 accumulate)", "bf16x4": "bf16x4 split (fp3
 def main():
     global N_LAMBDAS, CROP
     args = parse()
+    fit_like = args.fit or args.laplace
+    if args.workload is None and not fit_like:
+        args.workload = "calib"
     N_LAMBDAS = args.lambdas
     CROP = args.crop
     rank, world, local = dist_env()

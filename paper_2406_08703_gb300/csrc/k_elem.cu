@@ -137,7 +137,8 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
 //    partials go to npart[r][block] (and max |T| to tpart), and the last block
 //    of the slot to finish combines them in a fixed order into
 //    pscale[r] = (1 / sqrt(sum T^2), pi_r), pi_r the FP16 operand scale of the
-//    phasor (2^-ceil(log2 max |T_hat|));
+//    phasor (2^-ceil(log2 max |T_hat|)); sum T^2 is carried in compensated FP32
+//    pairs, per block and across blocks (fixed order);
 //  * clears the slot's FP16 scale maxima (qmax, gmax) of the adjoint;
 //  * the separable tilt factors exp(i 2 pi x_n theta / lambda) of every PSF and
 //    axis, theta = pos[s] + dither[e], with the argument reduced in FP64;
@@ -385,6 +386,10 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
 // order-independent.
 // OS > 0 fixes the oversample at compile time (unrolled, vector loads of the
 // os-wide row segments); OS = 0 takes it from `os_rt`.
+// Precision (the reading of the target's FP64 loss and gradient reductions): the
+// per-pixel loss and flux terms are summed in compensated FP32 pairs (about 44
+// significant bits) within a block, each block partial is converted to FP64 once,
+// and the last block adds the partials in FP64 in block order.
 constexpr int kQShared = 64;  // (source, exposure) maxima kept in shared memory
 
 template <int OS, int MAXS>
@@ -598,6 +603,8 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
 //   k_flux_grad:  grid (blocks, source, slot); dL/dF_s = sum_{e,p} GI_e[p] B_{s,e}[p]
 //                 re-reading the source's planes, and the FP16 form's bounds Q_{s,e};
 //                 partials in red_b[r][s][blk], the last block of each (r, s) sums them.
+// Precision: per-pixel terms are summed in compensated FP32 pairs within a block, block
+// partials converted to FP64 once and added in FP64 in block order by the last block.
 
 // For NC oversampled blocks at once (top-left samples src[k] of the first partial-
 // intensity plane, skipped where on[k] is false): v[k] = the sum over the os x os block
@@ -868,7 +875,8 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
 //                FP16 form's bound Q_s = max |GI| sqrt(I_s) of the weights the adjoint uses.
 // 2-D indexing for the big-detector passes: a thread owns one column px = blockIdx.x *
 // blockDim.x + threadIdx.x and walks rows py = blockIdx.y + k * gridDim.y, so no pixel index
-// is divided; source (and slot) come from blockIdx.z.
+// is divided; source (and slot) come from blockIdx.z.  Loss and flux sums: compensated FP32
+// pairs within a block, FP64 across block partials in block order (as in k_bin_nll).
 template <int OS>
 __global__ void __launch_bounds__(128) k_win_sum(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
                                                  int ndb, int os_rt, int no, DevParams prm, float *__restrict__ S) {
@@ -1355,7 +1363,8 @@ __global__ void k_pos_final(const double *part, int nsplit, int B, int nl, int n
     if (lane == 0) g.p[GPOS][(size_t)r * g.s[GPOS] + 2 * s + ax] = (float)v;
 }
 
-// Final sums of the gradient reductions, grid (n_zern + n_src, R), fixed order:
+// Final sums of the gradient reductions, grid (n_zern + n_src, R), fixed order, in
+// compensated FP32 pairs (the Zernike partials arrive as pairs; about 44 significant bits):
 // block j < n_zern: dL/dc_j = sum of the Zernike partials of slot r;
 // block n_zern + s (tensor-core forms): dL/dtheta_s from the position moments the
 // adjoint 1^T epilogue reduced per (PSF, K split, tile, warp), over wavelengths and
@@ -1586,7 +1595,8 @@ cudaError_t launch_scaled_diff(float *a, const float *b, size_t n, float c, cuda
 // triangle.  Each block takes 32-pixel chunks (rows padded to 33 floats so the
 // threads of a warp, which share i and run over consecutive j, hit distinct
 // banks), sums a chunk in FP32 and adds it to its FP64 partials; a second kernel
-// adds the block partials in block order, so the result does not depend on timing.
+// adds the block partials in block order, so the result does not depend on timing
+// (FP32 over 32 products, FP64 beyond).
 constexpr int kGramChunk = 32, kGramPad = 33, kGramPairsPerThread = (DLX_GRAM_MAX_PAR * (DLX_GRAM_MAX_PAR + 1) / 2 + 255) / 256;
 
 __global__ void __launch_bounds__(256) k_fisher_gram(const float *__restrict__ J, int n, size_t npix,
