@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-binary", action="store_true",
                     help="skip the binary-star workload timed beside the main one")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the short serving measurement added to the main line")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="time the steps without the per-kernel-class events (no roofline line)")
     ap.add_argument("--serving", action="store_true",
@@ -909,6 +911,18 @@ def main():
             kernels=({k: round(v, 4) for k, v in rb["kt_all"].items()} if rb["kt_all"] else {}), clocks=cb)
         rb["plan"].close()
         del rb
+
+    if not args.no_serving and rank == 0:
+        # the fit server on a short mixed-size request stream (the full sweep: --serving)
+        reqs = serving_requests(60, args.serving_shapes)
+        sat = serving_run(P, reqs, args.form, 10)
+        poi = serving_run(P, reqs, args.form, 10, rate=0.75 * sat["requests_per_s"], seed=7)
+        keep = ("evals_per_s", "requests_per_s", "p50_ms", "p99_ms", "tflops_algorithmic", "grouped_launches",
+                "graph_launches")
+        line["serving"] = dict(
+            workload=f"60 fit requests of {args.serving_shapes} mixed shapes (pupil 128-512, detector 64-512, "
+                     "oversample 2-4, 1-64 wavelengths, 1-3 stars), K=10 Adam steps each",
+            saturated={k: sat[k] for k in keep}, poisson_075={k: poi[k] for k in keep})
 
     if not args.no_cpu and rank == 0 and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, form=args.form)
