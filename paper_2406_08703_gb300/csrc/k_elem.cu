@@ -1166,7 +1166,14 @@ cudaError_t launch_bin_nll(dlx_plan *p, const DevParams &prm, int R, const int32
                                                                                           : gf(k_win_flux<0>);
     }
     auto go = [&](auto kern) {
-        return launch_pdl(kern, dim3(p->red_blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->ns,
+        // one wave of resident blocks (a grid of several waves left SMs idle in its last one); each
+        // block strides over the pixels, so any grid covers them
+        static const int per_sm = [&] {
+            int n = 0;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, 256, 0) == cudaSuccess && n > 0 ? n : 1;
+        }();
+        const int blocks = std::max(1, std::min(p->red_blocks, per_sm * p->sm_count / R));
+        return launch_pdl(kern, dim3(blocks, R), dim3(256), 0, st, p->Is, G, R * p->nse, p->nse, p->ns,
                           p->ne, p->nd, p->os, p->no, prm, data, data_stride, model,
                           model_stride, gi, gg, p->red, p->clamped, p->qmax, loss, p->bcount, p->prf_inv, p->cot,
                           plane_counts(p, R), (p->no + 127) / 128);
@@ -1251,23 +1258,25 @@ cudaError_t launch_psf_out(dlx_plan *p, const DevParams &prm, float *psf, cudaSt
 // (zpart[r][j][block], compensated pairs).  A block covers 64 pupil pixels with 4
 // threads per pixel, each summing every 4th entry of the pixel's column of gphi (8
 // loads in flight); the 4 partial sums are combined in a fixed order.  For the
-// Zernike partials the threads of group k take the terms j = k, k + 4, ..., up to 32
-// of them at a time: every warp sums each term over its 32 pixels (basis loads all in
-// flight first), and after one barrier 32 threads per group add the group's two
-// warps.  All sums are compensated FP32 pairs (about 44 significant bits), the reading
-// of "FP64 gradient reductions" applied here, in a fixed order, so every run gives
-// the same bits.
-constexpr int kGopdPx = 64;  // pupil pixels per block of k_gopd_zern
+// Zernike partials the block takes up to 64 terms at a time: their basis rows over
+// the block's pixels are staged in shared memory (coalesced 256-byte row loads), each
+// thread forms the partial sum of one (term, 8-pixel group) pair, and one thread per
+// term adds the term's eight group sums in order.  All sums are compensated FP32 pairs
+// (about 44 significant bits), the reading of "FP64 gradient reductions" applied here,
+// in a fixed order, so every run gives the same bits.
+constexpr int kGopdPx = 64;     // pupil pixels per block of k_gopd_zern
+constexpr int kGopdTerms = 64;  // Zernike terms per pass of its partial sums
 __global__ void __launch_bounds__(256) k_gopd_zern(const float *__restrict__ gphi, int B, int npx,
                                                    float2 *__restrict__ gopd, DevGrads g, DevParams prm, int nz,
                                                    float2 *__restrict__ zpart) {
     pdl_trigger();
     pdl_wait();
-    __shared__ df sh[4][64];
-    __shared__ df shz[8][32];
-    const int r = blockIdx.y, px = threadIdx.x & 63, grp = threadIdx.x >> 6, lane = threadIdx.x & 31;
-    const int wid = threadIdx.x >> 5;
-    const int n = blockIdx.x * kGopdPx + px;
+    __shared__ df sh[4][kGopdPx];
+    __shared__ df ts[kGopdPx];
+    __shared__ float zs[kGopdTerms][kGopdPx + 1];  // row stride 65: a warp's terms fall in distinct banks
+    __shared__ df part[8 * kGopdTerms];
+    const int r = blockIdx.y, px = threadIdx.x & 63, grp = threadIdx.x >> 6;
+    const int nb0 = blockIdx.x * kGopdPx, n = nb0 + px;
     df acc{0.f, 0.f};
     if (n < npx) {
         const float *src = gphi + (size_t)r * B * npx + n;
@@ -1283,37 +1292,53 @@ __global__ void __launch_bounds__(256) k_gopd_zern(const float *__restrict__ gph
     }
     sh[grp][px] = acc;
     __syncthreads();
-    const df t = df_add(df_add(sh[0][px], sh[1][px]), df_add(sh[2][px], sh[3][px]));
-    if (grp == 0 && n < npx) {
-        gopd[(size_t)r * npx + n] = make_float2(t.hi, t.lo);
-        if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = t.hi + t.lo;
+    if (grp == 0) {
+        const df t = df_add(df_add(sh[0][px], sh[1][px]), df_add(sh[2][px], sh[3][px]));
+        ts[px] = t;  // zero beyond the pupil's last pixel
+        if (n < npx) {
+            gopd[(size_t)r * npx + n] = make_float2(t.hi, t.lo);
+            if (g.p[GPIX]) g.p[GPIX][(size_t)r * g.s[GPIX] + n] = t.hi + t.lo;
+        }
     }
     if (!zpart) return;
     const float *basis = slot_ptr(prm, PBASIS, r);
-    const int ng = (nz + 3) / 4;  // terms of the group with the most
-    for (int q0 = 0; q0 < ng; q0 += 32) {  // block-uniform
-        float zb[32];
+    const int nvalid = min(kGopdPx, npx - nb0);
+    for (int j0 = 0; j0 < nz; j0 += kGopdTerms) {  // block-uniform
+        const int nzc = min(kGopdTerms, nz - j0);
+        __syncthreads();  // ts written; zs and part free
+        // every thread's basis loads in flight together (blockDim.x = 256: four term rows per pass)
+        float zv[kGopdTerms / 4];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int j = 4 * (q0 + q) + grp;
-            zb[q] = (q0 + q < ng && j < nz && n < npx) ? __ldg(basis + (size_t)j * npx + n) : 0.f;
+        for (int k = 0; k < kGopdTerms / 4; ++k) {
+            const int jj = 4 * k + (threadIdx.x >> 6), c = threadIdx.x & 63;
+            zv[k] = (jj < nzc && c < nvalid) ? __ldg(basis + (size_t)(j0 + jj) * npx + nb0 + c) : 0.f;
         }
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            if (q0 + q >= ng) break;  // block-uniform
-            df v = df_add(df{zb[q] * t.hi, 0.f}, zb[q] * t.lo);
-            v = warp_sum(v);
-            if (lane == q) shz[wid][q] = v;
+        for (int k = 0; k < kGopdTerms / 4; ++k) {
+            const int jj = 4 * k + (threadIdx.x >> 6);
+            if (jj < nzc) zs[jj][threadIdx.x & 63] = zv[k];
         }
         __syncthreads();
-        if ((threadIdx.x & 32) == 0) {  // first warp of each group: lanes = terms
-            const int q = lane, j = 4 * (q0 + q) + grp;
-            if (q0 + q < ng && j < nz) {
-                const df w = df_add(shz[2 * grp][q], shz[2 * grp + 1][q]);
-                zpart[((size_t)r * nz + j) * gridDim.x + blockIdx.x] = make_float2(w.hi, w.lo);
+        // pair i = (term i mod nzc, pixel group i / nzc): sum over the group's 8 pixels
+        for (int i = threadIdx.x; i < nzc * 8; i += blockDim.x) {
+            const int jj = i % nzc, c0 = 8 * (i / nzc);
+            df v{0.f, 0.f};
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float z = zs[jj][c0 + c];
+                const df t = ts[c0 + c];
+                v = df_add(v, z * t.hi);
+                v = df_add(v, z * t.lo);
             }
+            part[i] = v;
         }
         __syncthreads();
+        if (threadIdx.x < nzc) {
+            df w = part[threadIdx.x];
+#pragma unroll
+            for (int gq = 1; gq < 8; ++gq) w = df_add(w, part[gq * nzc + threadIdx.x]);
+            zpart[((size_t)r * nz + j0 + threadIdx.x) * gridDim.x + blockIdx.x] = make_float2(w.hi, w.lo);
+        }
     }
 }
 
