@@ -878,9 +878,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 if constexpr (KIND == KS2) {
-                    // stage 2: four 16-column chunks of this warp's accumulator half; the accumulators
-                    // are handed back to the MMA warp once the last chunk is loaded, before its |E|^2
-                    // sums and field stores (holding two chunks at once would spill registers)
+                    // stage 2: four 16-column chunks of this warp's accumulator half; chunks 2 and 3 are
+                    // loaded together and the accumulators handed back to the MMA warp before their
+                    // |E|^2 sums and field stores (a third chunk held would spill far more registers
+                    // than the 44 bytes this costs at the 168-register limit of ten warps)
                     auto ld_chunk = [&](int cc, float (&er)[CW], float (&ei)[CW]) {
                         const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + buf * 256 + 64 * h + CW * cc;
                         tmem_ld16(ta, er);
@@ -903,16 +904,18 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             if (a.out) store_field_t(a, J.b, m, J.n0 + 64 * h + CW * cc, er, ei);
                         }
                     };
-                    float er[CW], ei[CW];
+                    float er[CW], ei[CW], er2[CW], ei2[CW];
 #pragma unroll
-                    for (int cc = 0; cc < 3; ++cc) {
+                    for (int cc = 0; cc < 2; ++cc) {
                         ld_chunk(cc, er, ei);
                         use_chunk(cc, er, ei);
                     }
+                    ld_chunk(2, er2, ei2);
                     ld_chunk(3, er, ei);
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+                    use_chunk(2, er2, ei2);
                     use_chunk(3, er, ei);
                 }
 #pragma unroll

@@ -58,6 +58,16 @@ def test_ragged_shapes(case, form):
     compare(out, oracle_eval(start, data), form)
 
 
+@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+def test_many_zernike_terms(form):
+    """80 Zernike terms (more than the 64 a block of the gradient reduction sums at a time) over a
+    37^2 pupil (1369 pixels: a partial last block of 64): every Zernike gradient element."""
+    _, data, start = fit_problem("custom", seed=90, n_pupil=37, n_det=20, oversample=2, n_lambda=2, n_src=1,
+                                 n_exp=2, dither_px=0.5, n_zern_max=80, obscuration=0.1)
+    assert start.n_zern == 80
+    compare(gpu_eval(start, data, form), oracle_eval(start, data), form)
+
+
 def _long_problem(case):
     """512-long contractions (the two-sided MFT of Sec. 3 over a 512^2 pupil) onto a small
     detector, so the oracle checks every output."""
