@@ -159,7 +159,8 @@ typedef struct {
     int psf_chunk;             /* PSFs per adjoint pass */
     size_t workspace_bytes;    /* device memory held by the plan */
     double flop_forward;       /* algorithmic MFT FLOP of one forward (8 per complex MAC) */
-    double flop_loss_grad;     /* algorithmic MFT FLOP of one loss+gradient incl. recomputation */
+    double flop_loss_grad;     /* algorithmic MFT FLOP of one loss+gradient, with the field's
+                                  recomputation where the plan does not keep stage 2's fields */
     int gemm_tiles_stage2;     /* output tiles of the dominant contraction */
     int n_mft_out;             /* the MFT's output grid per side: n_out, or (Nd + 2 max|dither_px|) * os */
 } dlx_plan_info;

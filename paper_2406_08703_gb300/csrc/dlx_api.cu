@@ -556,8 +556,9 @@ int dlx_plan_get_info(const dlx_plan *p, dlx_plan_info *o) {
     const double ni = p->ni, no = p->no;
     const double s1 = 8.0 * no * ni * ni, s2 = 8.0 * no * no * ni;
     o->flop_forward = p->B * (s1 + s2);
-    // forward (s1 + s2) + recomputed field (s2) + adjoint stage 2^T (s2) + adjoint stage 1^T (s1)
-    o->flop_loss_grad = p->B * (2 * s1 + 3 * s2);
+    // forward (s1 + s2) + adjoint stage 2^T (s2) + adjoint stage 1^T (s1), and the recomputed field
+    // (s2) where the plan does not keep the fields of stage 2
+    o->flop_loss_grad = p->B * (2 * s1 + (p->Ef ? 2 : 3) * s2);
     int t = (p->prec == DLX_FP32_SIMT) ? 64 : 128;
     o->gemm_tiles_stage2 = ((p->no + t - 1) / t) * ((p->no + t - 1) / t) * p->nse * p->G;
     return DLX_OK;
