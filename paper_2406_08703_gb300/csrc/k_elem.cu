@@ -254,9 +254,10 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
 // T_hat exp(i 2 pi OPD / lambda) is formed once and multiplied by the tilt of
 // each source and exposure of that wavelength (16- or 32-byte stores per
 // plane); columns from Ni up to the padded row length are written as zeros.
-// Grid: x over the eight-column groups, y over (slot, wavelength).
+// Grid: x over the eight-column groups, y over (slot, wavelength).  Four blocks per SM (64
+// registers, a few spilled in the BF16 split form) measured faster than three at 79 registers.
 template <int F>
-__global__ void k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
+__global__ void __launch_bounds__(256, 4) k_phasor(DevParams prm, const float *__restrict__ opd, const float2 *__restrict__ tilt,
                          const float *__restrict__ invlam, const float *__restrict__ pscale, int B, int nl, int nse,
                          int ne, int ni, int ldi, void *P, uint32_t sr, const float *__restrict__ tmap, float tcoef,
                          uint32_t tmask) {
