@@ -102,7 +102,8 @@ typedef struct {
     int n_exp;               /* exposures (known dithers), >= 1 */
     int n_zern;              /* Zernike basis terms, >= 0 */
     int precision;           /* dlx_prec */
-    int psf_chunk;           /* PSFs per adjoint pass (per-wavelength recomputation batch);
+    int psf_chunk;           /* PSFs per adjoint pass (per-wavelength recomputation batch;
+                                all PSFs at once lets the BF16 split forms keep stage 2's fields);
                                 0 = automatic from workspace_limit_bytes */
     size_t workspace_limit_bytes; /* 0 = no limit; bounds the adjoint workspace */
     double prf_prior_sigma;  /* > 0: the loss adds the chi^2 log prior on the pixel response
@@ -266,10 +267,10 @@ int dlx_fisher_gram(const float *J, int n_par, size_t n_pix, const float *model,
  * needs a kernel no earlier call ran (more than 8 sources, for one) loads that
  * kernel too.  Make the first calls, with the shapes the caller will use, before
  * reserving the device's memory, or have everything loaded when the context is
- * created by setting CUDA_MODULE_LOADING=EAGER in the environment.  Make the first
- * call on a device before any stream capture.  Every call looks up the array's
- * device address (cudaGetSymbolAddress) on the calling thread's current device,
- * which must be the device of the arrays passed in.  Every call on a device
+ * created by setting CUDA_MODULE_LOADING=EAGER in the environment.  Every call
+ * looks up the array's device address (cudaGetSymbolAddress) on the calling
+ * thread's current device, which must be the device of the arrays passed in.
+ * Every call on a device
  * shares the array and overwrites it, so calls whose work overlaps on the GPU
  * (other streams or threads) race: serialise them.  Asynchronous on the stream
  * like dlx_forward. */
@@ -281,9 +282,12 @@ int dlx_psf(dlx_plan *plan, const dlx_params *params, float *psf_os, void *cuda_
 
 /* Loss and gradient (Sec. 4): *loss (device, one double) = sum (m - d ln max(m, 1e-30)),
  * gradients into `grads`, and the model into `model_opt` ([n_exp][Nd][Nd], may be NULL).
- * `data` is device int32 [n_exp][Nd][Nd] photon counts.  The adjoint recomputes
- * each PSF's field from the stored first-stage product instead of storing all
- * complex fields, psf_chunk PSFs at a time. */
+ * `data` is device int32 [n_exp][Nd][Nd] photon counts.  When a pupil gradient is
+ * wanted, the BF16 split forms (BF16x3, BF16x4) whose adjoint takes every PSF in one
+ * pass (psf_chunk at least the PSF count, with the workspace to hold them) keep each
+ * PSF's field from stage 2 and form the adjoint field from it; the other forms and
+ * smaller psf_chunk recompute each PSF's field from the stored first-stage product,
+ * psf_chunk PSFs at a time. */
 int dlx_loss_grad(dlx_plan *plan, const dlx_params *params, const int32_t *data, double *loss,
                   const dlx_grads *grads, float *model_opt, void *cuda_stream);
 
