@@ -419,8 +419,8 @@ struct dlx_plan {
     float *mom = nullptr;      // tensor-core forms: [R*B][gsplit][tiles][8 warps][2] position moments
     uint32_t sr = 0;           // BF16x3 forms: stochastic splitting of the forward operands (seed base), else 0
     bool adj1 = false;         // BF16x3sa: the adjoint contracts the stochastic hi parts only (2-plane bf16)
-    // set by eval_loss_grad for one evaluation: stage 2 also writes every PSF's field E into the
-    // adjoint-field operand (GEt) and the adjoint scales it in place instead of recomputing it
+    // set by eval_loss_grad for one evaluation: stage 2 also writes every PSF's field E (Ef) and
+    // the adjoint forms its field operand from it instead of recomputing it
     bool keep_field = false;
     float prf_inv = 0.f;       // 1 / sigma^2 of the chi^2 prior on the flat field, 0 = none
     // forward-mode derivative (dlx_model_jvp): while tan_map is set, the phasors of the sources
