@@ -222,6 +222,13 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     p->fmt = fmt_of_prec(p->prec);
     p->sr = (p->prec == DLX_BF16X3 || p->prec == DLX_BF16X3SA) ? 0x6d2b79f5u : 0u;  // stochastic split
     p->adj1 = (p->prec == DLX_BF16X3SA);
+    // the FP16 split form runs the forward contractions mirror-paired (pair_layout)
+    p->paired = (p->fmt == FMT_F16X4);
+    if (p->paired) {
+        p->hn = (p->ni + 1) / 2;
+        p->hp = pair_half(p->ni);
+        p->ldk = operand_ld(2 * p->hp);
+    }
     p->prf_inv = d->prf_prior_sigma > 0 ? (float)(1.0 / (d->prf_prior_sigma * d->prf_prior_sigma)) : 0.f;
     p->planes = fmt_planes(p->fmt);
     p->esz = fmt_esize(p->fmt);
@@ -313,10 +320,16 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     };
     // BF16x3sa: the adjoint-only operands (AH, GEt, GT1) hold the stochastic hi parts alone
     const int adj_planes = p->adj1 ? 2 : p->planes;
-    op_alloc(p->amat, p->nl, p->no, p->ldi, p->planes);
+    if (p->paired) {
+        op_alloc(p->amat, p->nl, p->no, p->ldk, 2);
+        op_alloc(p->Pp, Bt, 2 * p->hp, p->ldk, p->planes);
+        op_alloc(p->T1t, Bt, p->no, p->ldk, p->planes);
+    } else {
+        op_alloc(p->amat, p->nl, p->no, p->ldi, p->planes);
+        op_alloc(p->T1t, Bt, p->no, p->ldi, p->planes);
+    }
     op_alloc(p->amatH, p->nl, p->ni, p->ldo, adj_planes);
     op_alloc(p->P, Bt, p->ni, p->ldi, p->planes);
-    op_alloc(p->T1t, Bt, p->no, p->ldi, p->planes);
     op_alloc(p->GEt, p->chunk, p->no, p->ldo, adj_planes);
     op_alloc(p->GT1, p->chunk, p->ni, p->ldo, adj_planes);
     const size_t npx = (size_t)p->ni * p->ni, np = (size_t)p->nd * p->nd, nq = (size_t)p->no * p->no;

@@ -387,6 +387,14 @@ struct dlx_plan {
     int chunk = 1;   // PSFs per adjoint pass
     int gsplit = 1;  // K splits of the adjoint 1^T contraction: gphi holds [R*B][gsplit][ni*ni]
     dlx::Operand amat, amatH, P, T1t, GEt, GT1;
+    // Mirror-paired forward (the FP16 split form, see pair_layout below): amat holds [Re A | Im A]
+    // over the first half of the pupil axis in two planes (hi, lo), Pp the phasor's mirror sums
+    // and differences along both pupil axes, and T1t the first-stage product in the same paired
+    // layout along its pupil axis; P keeps the plain phasor for the adjoint 1^T epilogue.
+    bool paired = false;
+    int hn = 0, hp = 0;        // pair indices ceil(Ni/2), and that count rounded up to 16
+    int ldk = 0;               // row length of the paired operands: operand_ld(2 hp)
+    dlx::Operand Pp;
     double *lam_d = nullptr;   // [nl]
     float *wnorm = nullptr;    // [R][nl] weights / sum(weights)
     float *pscale = nullptr;   // [R][2] 1/sqrt(sum T^2), FP16 phasor scale pi_r
@@ -463,6 +471,32 @@ constexpr int kMaxSrc = 32;  // sources per plan
 // per request instead of 2).  The padding columns are zero.
 inline int operand_ld(int n) { return (n + 63) / 64 * 64; }
 constexpr int kMinBf16Pupil = 32;  // smallest pupil (samples per side) the BF16 split forms run at
+
+// Mirror pairing of the forward contractions (the two-sided MFT of Sec. 3 on the centred grids
+// x_n = (n - (Ni-1)/2) dx, u_k = (k - (No-1)/2) du).  Since x_{Ni-1-n} = -x_n, the matrix has
+// A[k][Ni-1-n] = conj(A[k][n]), so for any row v along the pupil axis, with j < hn = ceil(Ni/2),
+// m = Ni-1-j, S_j = v_j + v_m, D_j = v_j - v_m (S = v_j, D = 0 for the middle of an odd axis,
+// where A is real):
+//   sum_n A[k][n] v_n = sum_j a[k][j] S_j + i b[k][j] D_j,   a = Re A, b = Im A,
+// so  Re = sum_j a S_re - b D_im  and  Im = sum_j a S_im + b D_re.  Each is a real contraction of
+// the matrix row [a | b] (length 2 hp, each half padded with zeros to hp = hn rounded up to 16)
+// with a varying row [S_re | D_im] or [S_im | D_re], the second half of the first one subtracted:
+// six tensor-core products per 16-wide step of a (hi, lo) split instead of twelve for the complex
+// product, on the same operand bytes.  The sums and differences are rounded to the split in place
+// of the samples, at up to twice their modulus, which raises the split's representation error by
+// a factor near 1.4: the FP16 split (about 2^-20) absorbs that, the BF16 split (2^-17, BF16x3
+// already near 1e-5 of the PSF peak) does not, so only the FP16 split form is paired.  The
+// paired layouts:
+//   amat (forward matrix)  [nl][hi, lo][No][ldk]:  row k = [a[k][0..hn) 0.. | b[k][0..hn) 0..];
+//   T1t (stage-1 product)  [B][V1 hi, V1 lo, V2 hi, V2 lo][No][ldk], for stage 2 (the pupil-y
+//      axis): column R hp + j (R = 0 for S, 1 for D) of row kx holds T1_R[kx][j], the first-stage
+//      product of the y-paired phasor rows, as V1 = Re, V2 = Im for S and V1 = Im, V2 = Re for D;
+//   Pp (phasor)            [B][V1 hi, V1 lo, V2 hi, V2 lo][2 hp][ldk]: row Ry hp + jy, column
+//      Rx hp + jx holds the phasor paired along y (rows) and along x (columns), placed as in T1t
+//      by Rx.
+// Stage 1 applied to the y-paired rows of Pp gives T1_S and T1_D directly (the contraction is
+// linear), so no pass forms the pairs of its output.
+inline int pair_half(int n) { return ((n + 1) / 2 + 15) / 16 * 16; }
 constexpr int kNormParts = 1024;  // maximum blocks of the OPD / pupil-power pass
 
 enum KClass { KC_MATRICES = 0, KC_PROLOGUE, KC_STAGE1, KC_STAGE2, KC_BIN, KC_LOSS, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1,

@@ -75,9 +75,13 @@ __device__ void block_sum(df (&v)[NV], df *sh /* [32][NV] */) {
 // With sr != 0 (BF16x3 forms) A is split stochastically; AH (adjoint) is split by
 // rounding to nearest, or (ah_hi, BF16x3sa form) holds only the stochastically
 // rounded hi parts in two planes (re, im).
+// Paired forward matrix (hp > 0, FP16 split form; pair_layout in dlx_common.cuh): for n < hn
+// the row k of amat holds a = Re A[k][n] at column n and b = Im A[k][n] at column hp + n (times
+// alpha_l), split into two planes (hi, lo) of ldk columns.
 template <int F>
 __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const float *ascale, int nl, int ni,
-                               int no, int ldi, int ldo, double dx, double du, uint32_t sr, int ah_hi) {
+                               int no, int ldi, int ldo, double dx, double du, uint32_t sr, int ah_hi, int hp,
+                               int ldk) {
     const int P = fmt_planes(F), es = fmt_esize(F);
     const size_t per = (size_t)no * ni, total = per * nl;
     const double cN = 0.5 * (ni - 1), cO = 0.5 * (no - 1);
@@ -92,7 +96,22 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const
         const double sc = sqrt(c) * (F == FMT_F16X4 ? (double)ascale[l] : 1.0);
         float re = (float)(sc * co), im = (float)(-sc * s);
         char *a = (char *)amat + (size_t)l * P * no * ldi * es;
-        if constexpr (F == FMT_BF16X4) {
+        if constexpr (F == FMT_F16X4) {
+            if (hp > 0) {
+                if (2 * n < ni) {  // n < hn: a at column n, b at column hp + n (hi, lo planes)
+                    using H = H16<F>;
+                    typename H::T *q = (typename H::T *)amat + (size_t)l * 2 * no * ldk + (size_t)k * ldk + n;
+                    const size_t pl = (size_t)no * ldk;
+                    const typename H::T ah = H::hi(re), bh = H::hi(im);
+                    q[0] = ah;
+                    q[pl] = H::from(re - H::to(ah));
+                    q[hp] = bh;
+                    q[pl + hp] = H::from(im - H::to(bh));
+                }
+            } else {
+                store_cplx<F>(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im);
+            }
+        } else if constexpr (F == FMT_BF16X4) {
             if (sr) {
                 store_cplx_sr(a, (size_t)no * ldi, (size_t)k * ldi + n, re, im, ((size_t)l * no + k) * ldi + n,
                               sr ^ 0x2545f491u);
@@ -125,7 +144,7 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
     DLX_FMT_DISPATCH(p->fmt, F,
                      k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->ascale, p->nl,
                                                                p->ni, p->no, p->ldi, p->ldo, p->dx, p->du, p->sr,
-                                                               p->adj1 ? 1 : 0));
+                                                               p->adj1 ? 1 : 0, p->paired ? p->hp : 0, p->ldk));
     return cudaGetLastError();
 }
 
@@ -352,6 +371,129 @@ __global__ void __launch_bounds__(256, 4) k_phasor(DevParams prm, const float *_
     }
 }
 
+// The phasor of the mirror-paired forward (FP16 split form; pair_layout in dlx_common.cuh).
+// One thread takes a quadrant point jy and four pair indices jx .. jx+3 for one wavelength: the
+// sixteen samples (jy or Ni-1-jy, jx+q or Ni-1-jx-q) of T_hat exp(i 2 pi OPD / lambda), times the
+// tilts of each source and exposure, give (a) the plain phasor P, written as k_phasor writes it
+// (pi_r P; the adjoint 1^T epilogue reads it), and (b) the sums and differences along both axes
+// into Pp, times pi_r / 4 (a sum of four samples of modulus <= 1 stays <= 1).  A mirror that is
+// its own sample (the middle row or column of an odd pupil) counts once: its partner is taken
+// as zero.  Grid: x over (jy, group of four jx), y over (slot, wavelength).
+__device__ __forceinline__ void store_pair4(__half *q, size_t ps, const float (&v1)[4], const float (&v2)[4]) {
+    using H = H16<FMT_F16X4>;
+    __align__(8) __half h1[4], l1[4], h2[4], l2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h1[i] = H::hi(v1[i]);
+        l1[i] = H::from(v1[i] - H::to(h1[i]));
+        h2[i] = H::hi(v2[i]);
+        l2[i] = H::from(v2[i] - H::to(h2[i]));
+    }
+    *(uint2 *)q = *(const uint2 *)h1;
+    *(uint2 *)(q + ps) = *(const uint2 *)l1;
+    *(uint2 *)(q + 2 * ps) = *(const uint2 *)h2;
+    *(uint2 *)(q + 3 * ps) = *(const uint2 *)l2;
+}
+
+__global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const float *__restrict__ opd,
+                                                     const float2 *__restrict__ tilt, const float *__restrict__ invlam,
+                                                     const float *__restrict__ pscale, int B, int nl, int nse, int ne,
+                                                     int ni, int ldi, void *P, void *Pp, int hn, int hp, int ldk,
+                                                     const float *__restrict__ tmap, float tcoef, uint32_t tmask) {
+    pdl_trigger();
+    pdl_wait();
+    constexpr int F = FMT_F16X4;
+    const int npx = ni * ni, ng = (hn + 3) >> 2;
+    const int r = blockIdx.y / nl, l = blockIdx.y - r * nl;
+    const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
+    const float sc = pscale[2 * r] * pscale[2 * r + 1], il = invlam[l];
+    const size_t ps = (size_t)ni * ldi, pps = (size_t)2 * hp * ldk;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < hn * ng; it += gridDim.x * blockDim.x) {
+        const int jy = it / ng, jx0 = 4 * (it - jy * ng);
+        const int ys[2] = {jy, ni - 1 - jy};
+        // T_hat exp(i 2 pi OPD / lambda) and the tangent coefficient at (ys[a], x of (h, q));
+        // h = 1 is the mirror column ni - 1 - (jx0 + q)
+        float br[2][2][4], bi[2][2][4], ta[2][2][4];
+        bool in[2][2][4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int jx = jx0 + q, x = h ? ni - 1 - jx : jx;
+                    in[a][h][q] = jx < hn && !(a == 1 && ys[1] == ys[0]) && !(h == 1 && x == jx);
+                    br[a][h][q] = 0.f;
+                    bi[a][h][q] = 0.f;
+                    ta[a][h][q] = 0.f;
+                    if (!in[a][h][q]) continue;
+                    const size_t o = (size_t)ys[a] * ni + x;
+                    const float tq = __ldg(T + o) * sc;
+                    if (tq != 0.f) {
+                        float ph = __ldg(op + o) * il;
+                        ph -= rintf(ph);
+                        float sn, cs;
+                        sincospif(2.f * ph, &sn, &cs);
+                        br[a][h][q] = tq * cs;
+                        bi[a][h][q] = tq * sn;
+                    }
+                    if (tmap) ta[a][h][q] = tcoef * 6.283185307f * il * __ldg(tmap + o);
+                }
+        for (int se = 0; se < nse; ++se) {
+            const int bg = r * B + l * nse + se;
+            const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
+            const bool tan = tmap && ((tmask >> (se / ne)) & 1u);
+            float pr[2][2][4], pim[2][2][4];
+            char *pb = (char *)P + (size_t)bg * 4 * ps * 2;
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const float2 ey = __ldg(ty + ys[a]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        pr[a][h][q] = 0.f;
+                        pim[a][h][q] = 0.f;
+                        if (!in[a][h][q]) continue;
+                        const int jx = jx0 + q, x = h ? ni - 1 - jx : jx;
+                        float cr = br[a][h][q], ci = bi[a][h][q];
+                        if (tan) {  // times (1 + i a)
+                            const float t = ta[a][h][q], nr = cr - t * ci;
+                            ci = ci + t * cr;
+                            cr = nr;
+                        }
+                        const float2 ex = __ldg(tx + x);
+                        const float xr = ex.x * ey.x - ex.y * ey.y, xi = ex.x * ey.y + ex.y * ey.x;
+                        const float vr = cr * xr - ci * xi, vi = cr * xi + ci * xr;
+                        pr[a][h][q] = vr;
+                        pim[a][h][q] = vi;
+                        // (a) the plain phasor, split as k_phasor splits it
+                        store_cplx<F>(pb, ps, (size_t)ys[a] * ldi + x, vr, vi);
+                    }
+            }
+            // (b) Q[Ry][Rx]: Ry pairs the rows (S = sum, D = difference), Rx the columns; column
+            // block Rx holds (V1, V2) = (Re, Im) for S and (Im, Re) for D
+            __half *qb = (__half *)Pp + (size_t)bg * 4 * pps;
+#pragma unroll
+            for (int ry = 0; ry < 2; ++ry)
+#pragma unroll
+                for (int rx = 0; rx < 2; ++rx) {
+                    float v1[4], v2[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float sy = ry ? -1.f : 1.f, sx = rx ? -1.f : 1.f;
+                        const float qr = (pr[0][0][q] + sx * pr[0][1][q]) + sy * (pr[1][0][q] + sx * pr[1][1][q]);
+                        const float qi = (pim[0][0][q] + sx * pim[0][1][q]) + sy * (pim[1][0][q] + sx * pim[1][1][q]);
+                        v1[q] = 0.25f * (rx ? qi : qr);
+                        v2[q] = 0.25f * (rx ? qr : qi);
+                    }
+                    const int row = ry * hp + jy, col = rx * hp + jx0;
+                    store_pair4(qb + (size_t)row * ldk + col, pps, v1, v2);
+                }
+        }
+    }
+}
+
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
     const int npx = p->ni * p->ni;
     KScope ks(p, KC_PROLOGUE, 2, st);
@@ -361,7 +503,15 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
                                prm, p->nz, npx, p->nl, p->opd, p->npart, p->tpart, p->ncount, p->pscale, p->wnorm,
                                p->lam_d, p->B, p->nse, p->ne, p->ni, p->dx, p->tilt, p->qmax, p->gmax, p->chirp);
     if (e != cudaSuccess) return e;
-    const int groups = p->ni * (p->ldi / 8), nyl = R * p->nl;
+    const int nyl = R * p->nl;
+    if (p->paired) {
+        const int items = p->hn * ((p->hn + 3) / 4);
+        const int px = std::max(1, std::min((items + 255) / 256, (p->sm_count * 16 + nyl - 1) / nyl));
+        return launch_pdl(k_phasor_pair, dim3(px, nyl), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam, p->pscale,
+                          p->B, p->nl, p->nse, p->ne, p->ni, p->ldi, p->P.ptr, p->Pp.ptr, p->hn, p->hp, p->ldk,
+                          p->tan_map, p->tan_coef, p->tan_mask);
+    }
+    const int groups = p->ni * (p->ldi / 8);
     const int px = std::max(1, std::min((groups + 255) / 256, (p->sm_count * 16 + nyl - 1) / nyl));
     DLX_FMT_DISPATCH(p->fmt, F,
                      e = launch_pdl(k_phasor<F>, dim3(px, nyl), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam,

@@ -65,6 +65,18 @@ struct Cfg {
     static constexpr int SMEM = STAGES * STAGE_BYTES + STG_BYTES + 1024 + 256;
 };
 
+// Shared-memory stages of one launch.  Mirror-paired contractions (PR, the FP16 split form;
+// pair_layout in dlx_common.cuh) read a two-plane matrix operand (hi, lo of [Re A | Im A]):
+// the A operand of stage 1 and stage 2, the B operand of the recomputed field.
+template <int F, int PR, int KIND>
+struct Geo {
+    static constexpr int PA = (PR && (KIND == KS1 || KIND == KS2)) ? 2 : Cfg<F>::PL;
+    static constexpr int PB = (PR && KIND == KGE) ? 2 : Cfg<F>::PL;
+    static constexpr int STAGE_BYTES = (PA + PB) * PLANE_BYTES;
+    static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + Cfg<F>::STG_BYTES + 1024 + 256;
+};
+
 // Arguments of one launch.  Per-job operand coordinates come from decode().
 struct TcArgs {
     int M, N, K;   // per-job contraction sizes (complex)
@@ -96,6 +108,7 @@ struct TcArgs {
     int grid;         // CTAs (0: min(units, SMs))
     uint32_t sr;      // BF16x3 forms: stochastic split (seed) of the operand this launch writes, else 0
     int p4;           // BF16x3sa adjoint 1^T: the phasor is a four-plane split
+    int hp;           // mirror-paired contractions: the second half of K starts at hp
     int stall;        // test hook: CTA 0 withholds its first operand copy (its waits expire, bounded)
     int32_t *err;
 };
@@ -542,28 +555,30 @@ __device__ __forceinline__ void store_field_t(const TcArgs &a, int b, int m, int
 }
 
 // ------------------------------------------------------------------ the kernel
-template <int F, int MODE, int KIND>
+template <int F, int MODE, int KIND, int PR>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapC, TcArgs a) {
     using C = Cfg<F>;
+    using G = Geo<F, PR, KIND>;
+    static_assert(!PR || (F == FMT_F16X4 && (KIND == KS1 || KIND == KS2 || KIND == KGE)), "paired: FP16 split forward");
     constexpr uint32_t NBUF = (MODE == FAST) ? 2 : 1;
     // operand-writing contractions of the bf16 forms store through a staged TMA box
     constexpr bool TMA_OUT = C::TMA_STORE && (KIND == KS1 || KIND == KGE || KIND == KGT1);
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *stg = smem + C::STAGES * C::STAGE_BYTES;  // staged output box (TMA_OUT)
+    uint8_t *stg = smem + G::STAGES * G::STAGE_BYTES;  // staged output box (TMA_OUT)
     uint64_t *bars = (uint64_t *)(stg + C::STG_BYTES);
     // bars: full[S], empty[S], tfull[2], tempty[2], drain
-    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * C::STAGES, tfull0 = empty0 + 8 * C::STAGES,
+    const uint32_t full0 = smem_u32(bars), empty0 = full0 + 8 * G::STAGES, tfull0 = empty0 + 8 * G::STAGES,
                    tempty0 = tfull0 + 16, drain = tempty0 + 16;
-    volatile int *abort_flag = (volatile int *)(bars + 2 * C::STAGES + 5);
-    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * C::STAGES + 6);
+    volatile int *abort_flag = (volatile int *)(bars + 2 * G::STAGES + 5);
+    uint32_t *tmem_slot = (uint32_t *)(bars + 2 * G::STAGES + 6);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     pdl_trigger();
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < G::STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
@@ -599,25 +614,25 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 for (int j = 0; j < nj && ok; ++j) {
                     const Job J = decode<KIND>(a, u, j, pc);
                     for (int kb = J.kb0; kb < J.kb1; ++kb, ++it) {
-                        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+                        const uint32_t s = it % G::STAGES, ph = (it / G::STAGES) & 1;
                         if (!mbar_wait(empty0 + 8 * s, ph ^ 1, abort_flag, a.err, 1)) {
                             ok = false;
                             break;
                         }
                         // test hook: the stage is never filled, so the MMA warp's wait for it expires
                         if (a.stall && blockIdx.x == 0 && it == 0) continue;
-                        const uint32_t st = smem_u32(smem + s * C::STAGE_BYTES);
-                        mbar_expect_tx(full0 + 8 * s, C::STAGE_BYTES);
+                        const uint32_t st = smem_u32(smem + s * G::STAGE_BYTES);
+                        mbar_expect_tx(full0 + 8 * s, G::STAGE_BYTES);
                         tma_load4(st, &mapA, kb * C::KB, J.a_row, 0, J.a_batch, full0 + 8 * s);
-                        tma_load4(st + C::PL * PLANE_BYTES, &mapB, kb * C::KB, J.b_row, 0, J.b_batch, full0 + 8 * s);
+                        tma_load4(st + G::PA * PLANE_BYTES, &mapB, kb * C::KB, J.b_row, 0, J.b_batch, full0 + 8 * s);
                     }
                 }
             }
             if (!ok) {
                 // let the copies already issued land before the CTA exits
-                const uint32_t n = it < (uint32_t)C::STAGES ? it : (uint32_t)C::STAGES;
+                const uint32_t n = it < (uint32_t)G::STAGES ? it : (uint32_t)G::STAGES;
                 for (uint32_t q = 0; q < n; ++q) {
-                    const uint32_t k = it - 1 - q, s = k % C::STAGES, ph = (k / C::STAGES) & 1;
+                    const uint32_t k = it - 1 - q, s = k % G::STAGES, ph = (k / G::STAGES) & 1;
                     mbar_wait(full0 + 8 * s, ph, abort_flag, a.err, 2, true, 100000000ull);
                 }
             }
@@ -642,20 +657,49 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     const uint32_t dr = tbase + buf * 256, di = dr + 128;
                     const Job J = decode<KIND>(a, u, j, pc);
                     for (int kb = J.kb0; kb < J.kb1; ++kb, ++it) {
-                        const uint32_t s = it % C::STAGES, ph = (it / C::STAGES) & 1;
+                        const uint32_t s = it % G::STAGES, ph = (it / G::STAGES) & 1;
                         if (!mbar_wait(full0 + 8 * s, ph, abort_flag, a.err, 4)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = smem_u32(smem + s * C::STAGE_BYTES), sb = sa + C::PL * PLANE_BYTES;
+                        const uint32_t sa = smem_u32(smem + s * G::STAGE_BYTES), sb = sa + G::PA * PLANE_BYTES;
 #pragma unroll
                         for (int ks = 0; ks < C::NKSTEP; ++ks) {
                             const uint32_t first = (kb == J.kb0 && ks == 0) ? 0u : 1u;
                             const uint32_t ko = ks * 32;
                             auto A = [&](int p) { return sdesc(sa + p * PLANE_BYTES + ko); };
                             auto Bd = [&](int p) { return sdesc(sb + p * PLANE_BYTES + ko); };
-                            if constexpr (MODE != FAST) {
+                            if constexpr (PR) {
+                                // mirror-paired: matrix planes 0 hi, 1 lo of [a | b]; varying planes
+                                // 0 V1 hi, 1 V1 lo, 2 V2 hi, 3 V2 lo.  Er = M.V1 with the second half
+                                // of K (b . D_im) subtracted, Ei = M.V2
+                                const uint32_t idr = (kb * C::KB + ks * C::KSTEP >= a.hp) ? id_neg : id_pos;
+                                auto pm = [&](uint32_t d, int x, int y, uint32_t id, uint32_t acc) {
+                                    if constexpr (KIND == KGE) mma<F>(d, A(y), Bd(x), id, acc);
+                                    else mma<F>(d, A(x), Bd(y), id, acc);
+                                };
+                                if constexpr (MODE != FAST) {
+                                    const uint32_t cr = tbase + 256, ci = tbase + 384;
+                                    pm(dr, 0, 0, idr, first);
+                                    pm(di, 0, 2, id_pos, first);
+                                    pm(cr, 0, 1, idr, first);
+                                    pm(cr, 1, 0, idr, 1);
+                                    pm(ci, 0, 3, id_pos, first);
+                                    pm(ci, 1, 2, id_pos, 1);
+                                    if constexpr (MODE == SPLIT4) {
+                                        pm(cr, 1, 1, idr, 1);
+                                        pm(ci, 1, 3, id_pos, 1);
+                                    }
+                                } else {
+                                    pm(dr, 0, 0, idr, first);
+                                    pm(dr, 0, 1, idr, 1);
+                                    pm(dr, 1, 0, idr, 1);
+                                    pm(di, 0, 2, id_pos, first);
+                                    pm(di, 0, 3, id_pos, 1);
+                                    pm(di, 1, 2, id_pos, 1);
+                                }
+                            } else if constexpr (MODE != FAST) {
                                 // planes: 0 re_hi, 1 re_lo, 2 im_hi, 3 im_lo; dr/di hold the hi*hi
                                 // products, cr/ci the corrections
                                 const uint32_t cr = tbase + 256, ci = tbase + 384;
@@ -756,7 +800,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     // undo / apply the power-of-two operand scales (exact):
                     // T1t' = alpha pi sigma1 T1t, so the recomputed field carries u^-1
                     const float al = a.ascale[J.l], pi = a.pscale[2 * J.r + 1];
-                    const float u = 1.f / (al * al * pi * a.sig1);
+                    // the paired phasor carries a further 1/4
+                    const float u = (PR ? 4.f : 1.f) / (al * al * pi * a.sig1);
                     if constexpr (KIND == KS1) osc = a.sig1;
                     if constexpr (KIND == KS2) w *= u * u;
                     if constexpr (KIND == KGE) c *= f16_gamma(a, J) * u;
@@ -845,6 +890,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             for (int i = 0; i < CW; ++i) {
                                 er[i] *= osc;
                                 ei[i] *= osc;
+                            }
+                        }
+                        if constexpr (PR && KIND == KS1) {
+                            // paired stage 1: columns hp.. hold the y-differences, stored as (Im, Re)
+                            if (J.n0 + c0 >= a.hp) {
+#pragma unroll
+                                for (int i = 0; i < CW; ++i) {
+                                    const float t = er[i];
+                                    er[i] = ei[i];
+                                    ei[i] = t;
+                                }
                             }
                         }
                         // the previous round's box may be refilled once the TMA has read it; that
@@ -1116,15 +1172,15 @@ bool make_map(dlx_plan *p, Operand &o, std::string *why, bool hi_view = false) {
     return true;
 }
 
-template <int F, int MODE, int KIND>
+template <int F, int MODE, int KIND, int PR = 0>
 cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operand *Cout, TcArgs &a,
                    cudaStream_t st) {
     // the shared-memory attribute is a property of the kernel on each device: set once per device
     static std::atomic<uint64_t> attr_set{0};
     const uint64_t dev_bit = 1ull << (p->device & 63);
     if (!(attr_set.load(std::memory_order_acquire) & dev_bit)) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F, MODE, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             Cfg<F>::SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_tc_gemm<F, MODE, KIND, PR>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Geo<F, PR, KIND>::SMEM);
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(dev_bit, std::memory_order_release);
     }
@@ -1152,6 +1208,7 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
            : (p->adj1 && KIND == KGT1) ? p->sr ^ 0xc2b2ae3du
                                        : 0u;
     a.p4 = (p->adj1 && KIND == KGP) ? 1 : 0;
+    a.hp = PR ? p->hp : 0;
     a.tm = (a.M + BM - 1) / BM;
     a.tn = (a.N + BN - 1) / BN;
     a.KB = Cfg<F>::KB;
@@ -1162,29 +1219,30 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
     const int grid = a.grid > 0 ? a.grid : std::min(a.units, p->sm_count);
     static const int cls_of[5] = {KC_STAGE1, KC_STAGE2, KC_ADJ_FIELD, KC_ADJ2, KC_ADJ1};
     KScope ks(p, cls_of[KIND], 1, st);
-    return launch_pdl(k_tc_gemm<F, MODE, KIND>, dim3(grid), dim3(NTHREADS), Cfg<F>::SMEM, st, A.tmap, B.tmap,
-                      Cout ? Cout->tmap : A.tmap, a);
+    return launch_pdl(k_tc_gemm<F, MODE, KIND, PR>, dim3(grid), dim3(NTHREADS), Geo<F, PR, KIND>::SMEM, st, A.tmap,
+                      B.tmap, Cout ? Cout->tmap : A.tmap, a);
 }
 
 // MODE1 / MODE2: accumulation modes of stage 1 and stage 2
-template <int F, int MODE1, int MODE2>
+template <int F, int MODE1, int MODE2, int PR>
 cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
     TcArgs a{};
-    // stage 1: T1t[b] = A(l) . P[b]^T   (M = No rows kx, N = Ni cols ny, K = Ni)
+    // stage 1: T1t[b] = A(l) . P[b]^T   (M = No rows kx, N = Ni cols ny, K = Ni); mirror-paired:
+    // the paired phasor's 2 hp rows and K = 2 hp, written in the paired layout (pair_layout)
     a.M = p->no;
-    a.N = p->ni;
-    a.K = p->ni;
+    a.N = PR ? 2 * p->hp : p->ni;
+    a.K = PR ? 2 * p->hp : p->ni;
     a.out = p->T1t.ptr;
-    a.out_ld = p->ldi;
-    a.out_ps = (size_t)p->no * p->ldi;
+    a.out_ld = p->T1t.ld;
+    a.out_ps = (size_t)p->no * p->T1t.ld;
     a.units = R * p->B * ((a.M + BM - 1) / BM) * ((a.N + BN - 1) / BN);
-    cudaError_t e = launch<F, MODE1, KS1>(p, p->amat, p->P, &p->T1t, a, st);
+    cudaError_t e = launch<F, MODE1, KS1, PR>(p, p->amat, PR ? p->Pp : p->P, &p->T1t, a, st);
     if (e != cudaSuccess) return e;
-    // stage 2 + intensity: Is[g][rse] = sum_l w |A(l) . T1t[b]^T|^2  (M = N = No, K = Ni)
+    // stage 2 + intensity: Is[g][rse] = sum_l w |A(l) . T1t[b]^T|^2  (M = N = No, K = Ni; paired 2 hp)
     TcArgs c{};
     c.M = p->no;
     c.N = p->no;
-    c.K = p->ni;
+    c.K = PR ? 2 * p->hp : p->ni;
     c.Is = p->Is;
     c.Rnse = R * p->nse;
     const dlx_plan::S2Split &sp = p->s2[R - 1];
@@ -1197,7 +1255,7 @@ cudaError_t forward_impl(dlx_plan *p, int R, cudaStream_t st) {
         c.out_ld = p->ldo;
         c.out_ps = (size_t)p->no * p->ldo;
     }
-    return launch<F, MODE2, KS2>(p, p->amat, p->T1t, nullptr, c, st);
+    return launch<F, MODE2, KS2, PR>(p, p->amat, p->T1t, nullptr, c, st);
 }
 
 template <int F>
@@ -1207,7 +1265,7 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     // recomputed field and dL/dE: GEt[z][kx][ky] = 2 w F GI o (T1t[b] . A(l)^T)
     a.M = p->no;
     a.N = p->no;
-    a.K = p->ni;
+    a.K = p->paired ? 2 * p->hp : p->ni;
     a.b0 = b0;
     a.prm = prm;
     a.GI = p->GI;
@@ -1222,8 +1280,14 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
         Am.tmap = p->amat.tmap_hi;
     }
     // the field kept by stage 2 (BF16 split forms) is scaled and split; otherwise it is recomputed
-    cudaError_t e = p->keep_field ? launch_field_scale(p, prm, b0, nb, st)
-                                  : launch<F, FAST, KGE>(p, T1, Am, &p->GEt, a, st);
+    cudaError_t e;
+    if (p->keep_field) {
+        e = launch_field_scale(p, prm, b0, nb, st);
+    } else if constexpr (F == FMT_F16X4) {
+        e = p->paired ? launch<F, FAST, KGE, 1>(p, T1, Am, &p->GEt, a, st) : launch<F, FAST, KGE>(p, T1, Am, &p->GEt, a, st);
+    } else {
+        e = launch<F, FAST, KGE>(p, T1, Am, &p->GEt, a, st);
+    }
     if (e != cudaSuccess) return e;
     // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No)
     TcArgs b{};
@@ -1270,20 +1334,21 @@ int tc_make_maps(dlx_plan *p, std::string *why) {
     bool ok = make_map(p, p->amat, why) && make_map(p, p->amatH, why) && make_map(p, p->P, why) &&
               make_map(p, p->T1t, why) && make_map(p, p->GEt, why) && make_map(p, p->GT1, why);
     if (ok && p->adj1) ok = make_map(p, p->amat, why, true) && make_map(p, p->T1t, why, true);
+    if (ok && p->paired) ok = make_map(p, p->Pp, why);
     return ok;
 }
 
 cudaError_t tc_forward(dlx_plan *p, int R, cudaStream_t st) {
     switch (p->fmt) {
         case FMT_BF16X4:
-            if (p->prec == DLX_BF16X4) return forward_impl<FMT_BF16X4, SPLIT4, SPLIT4>(p, R, st);
+            if (p->prec == DLX_BF16X4) return forward_impl<FMT_BF16X4, SPLIT4, SPLIT4, 0>(p, R, st);
             // BF16x3 (stochastic split): stage 1 double-buffers its accumulators up to a 256-long
             // contraction; beyond, hi*hi accumulates apart there too (its truncation grows with K)
-            return p->ni <= 256 ? forward_impl<FMT_BF16X4, FAST, SPLIT3>(p, R, st)
-                                : forward_impl<FMT_BF16X4, SPLIT3, SPLIT3>(p, R, st);
-        case FMT_BF16X2: return forward_impl<FMT_BF16X2, FAST, FAST>(p, R, st);
-        case FMT_TF32X4: return forward_impl<FMT_TF32X4, SPLIT3, SPLIT3>(p, R, st);
-        case FMT_F16X4: return forward_impl<FMT_F16X4, SPLIT3, SPLIT3>(p, R, st);
+            return p->ni <= 256 ? forward_impl<FMT_BF16X4, FAST, SPLIT3, 0>(p, R, st)
+                                : forward_impl<FMT_BF16X4, SPLIT3, SPLIT3, 0>(p, R, st);
+        case FMT_BF16X2: return forward_impl<FMT_BF16X2, FAST, FAST, 0>(p, R, st);
+        case FMT_TF32X4: return forward_impl<FMT_TF32X4, SPLIT3, SPLIT3, 0>(p, R, st);
+        case FMT_F16X4: return forward_impl<FMT_F16X4, SPLIT3, SPLIT3, 1>(p, R, st);
         default: return cudaErrorNotSupported;
     }
 }

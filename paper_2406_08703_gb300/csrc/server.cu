@@ -202,6 +202,12 @@ size_t bucket_bytes(const dlx_mft_desc &d, bool has_pix, int cap) {
     const size_t pe = (size_t)dlx::fmt_planes(fmt) * dlx::fmt_esize(fmt);
     size_t b = pe * (nl * no * ldi + nl * ni * ldo + Bt * ni * ldi + Bt * no * ldi + Bt * no * ldo + Bt * ni * ldo);
     b += 4 * (Bt * ni * ni) + 8 * (Bt * 2 * ni) + 4 * (size_t)d.n_src * ne_mft * cap * no * no * 2;
+    // the mirror-paired forward of the FP16 split form: the paired phasor, and first-stage rows of
+    // ldk instead of ldi columns
+    if (fmt == dlx::FMT_F16X4) {
+        const size_t hp = (size_t)dlx::pair_half((int)ni), ldk = dlx::operand_ld((int)(2 * hp));
+        b += pe * (Bt * 2 * hp * ldk + Bt * no * (ldk > ldi ? ldk - ldi : 0));
+    }
     // the fields stage 2 keeps for the adjoint (the bucket's plan takes every PSF in one chunk)
     if (dlx::field_kept(fmt, d.precision == DLX_BF16X3SA, (int)Bt, (int)Bt))
         b += 8 * Bt * no * ldo + 4 * (size_t)cap * ne_mft * (no / d.oversample) * (no / d.oversample);
