@@ -356,7 +356,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     // the fields stage 2 keeps for the adjoint (instead of its recomputation), when the adjoint
     // takes every PSF at once and a workspace limit leaves room for them
     const size_t ef_bytes = sizeof(float) * 2 * (size_t)Bt * p->no * p->ldo;
-    if (e == cudaSuccess && field_kept(p->fmt, p->adj1, p->chunk, Bt) &&
+    if (e == cudaSuccess && field_kept(p->fmt, p->adj1, p->ni, p->chunk, Bt) &&
         (d->workspace_limit_bytes == 0 || d->workspace_limit_bytes >= (size_t)Bt * per_psf + ef_bytes)) {
         e = plan_alloc(p, &p->Ef, ef_bytes);
         if (e == cudaSuccess) e = cudaMemset(p->Ef, 0, ef_bytes);

@@ -395,6 +395,24 @@ __device__ __forceinline__ void store_pair4(__half *q, size_t ps, const float (&
     *(uint2 *)(q + 3 * ps) = *(const uint2 *)l2;
 }
 
+// Four consecutive elements of a four-plane FP16 split operand (8-byte aligned): one 8-byte store
+// per plane.
+__device__ __forceinline__ void store_cplx4_f16(__half *p, size_t ps, const float (&re)[4], const float (&im)[4]) {
+    using H = H16<FMT_F16X4>;
+    __align__(8) __half rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        rh[i] = H::hi(re[i]);
+        rl[i] = H::from(re[i] - H::to(rh[i]));
+        ih[i] = H::hi(im[i]);
+        il[i] = H::from(im[i] - H::to(ih[i]));
+    }
+    *(uint2 *)p = *(const uint2 *)rh;
+    *(uint2 *)(p + ps) = *(const uint2 *)rl;
+    *(uint2 *)(p + 2 * ps) = *(const uint2 *)ih;
+    *(uint2 *)(p + 3 * ps) = *(const uint2 *)il;
+}
+
 __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const float *__restrict__ opd,
                                                      const float2 *__restrict__ tilt, const float *__restrict__ invlam,
                                                      const float *__restrict__ pscale, int B, int nl, int nse, int ne,
@@ -445,6 +463,9 @@ __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const flo
             const bool tan = tmap && ((tmask >> (se / ne)) & 1u);
             float pr[2][2][4], pim[2][2][4];
             char *pb = (char *)P + (size_t)bg * 4 * ps * 2;
+            // four whole pairs of an axis of a multiple of 4 samples: the plain phasor goes out as
+            // 8-byte vectors (the mirror columns ni-4-jx0 .. ni-1-jx0 in increasing order)
+            const bool vec = (ni & 3) == 0 && jx0 + 3 < hn;
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 const float2 ey = __ldg(ty + ys[a]);
@@ -468,8 +489,21 @@ __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const flo
                         pr[a][h][q] = vr;
                         pim[a][h][q] = vi;
                         // (a) the plain phasor, split as k_phasor splits it
-                        store_cplx<F>(pb, ps, (size_t)ys[a] * ldi + x, vr, vi);
+                        if (!vec) store_cplx<F>(pb, ps, (size_t)ys[a] * ldi + x, vr, vi);
                     }
+                if (vec) {
+                    float r0[4], i0[4], r1[4], i1[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        r0[q] = pr[a][0][q];
+                        i0[q] = pim[a][0][q];
+                        r1[q] = pr[a][1][3 - q];
+                        i1[q] = pim[a][1][3 - q];
+                    }
+                    __half *pr0 = (__half *)pb + (size_t)ys[a] * ldi;
+                    store_cplx4_f16(pr0 + jx0, ps, r0, i0);
+                    store_cplx4_f16(pr0 + (ni - 4 - jx0), ps, r1, i1);
+                }
             }
             // (b) Q[Ry][Rx]: Ry pairs the rows (S = sum, D = difference), Rx the columns; column
             // block Rx holds (V1, V2) = (Re, Im) for S and (Im, Re) for D
@@ -1597,28 +1631,35 @@ __global__ void k_grad_final(const float2 *__restrict__ zpart, int nz, int nzb, 
 // The adjoint field from the fields stage 2 kept (the chain rule of the Poisson likelihood,
 // Sec. 4, through I = sum_l w_l F_s |E|^2): GEt[z][kx][ky] = 2 w_l F_s GI[e][ky/os][kx/os] E[kx][ky]
 // for the chunk-local PSF z = b - b0, b = (r, l, s, e), from Ef (fp32, [b][re, im][kx][ky]) into
-// the four-plane BF16 split, rounded to nearest -- the values and the split that the recomputing
-// contraction's epilogue writes.  One warp per row (z, kx) at a time: the row's constants are
-// formed once, and each lane takes 8-element vectors 256 columns apart (two 16-byte loads per
-// plane in, one 16-byte store per plane out, four vectors in flight); padding columns ky >= No
-// get zeros.
-__device__ __forceinline__ void field_scale_vec(const float *er, const float *ei, __nv_bfloat16 *p, size_t ps,
-                                                const float *gi, float c, int k0, int no, int os, int bmax) {
+// the four-plane 16-bit split, rounded to nearest -- the values and the split that the recomputing
+// contraction's epilogue writes.  In the FP16 form Ef holds stage 2's raw accumulators, E times
+// alpha_l^2 pi_r sigma1 (and 1/4 when the forward is mirror-paired), and GEt holds gamma_b G_E:
+// the row constant takes both scales (the recomputing epilogue's u and gamma), and the pass also
+// records max |GEt| of each PSF in gmax for the adjoint 2^T's output scale.  One warp per row
+// (z, kx) at a time: the row's constants are formed once, and each lane takes 8-element vectors
+// 256 columns apart (two 16-byte loads per plane in, one 16-byte store per plane out, four
+// vectors in flight); padding columns ky >= No get zeros.
+template <int F>
+__device__ __forceinline__ float field_scale_vec(const float *er, const float *ei, typename H16<F>::T *p, size_t ps,
+                                                 const float *gi, float c, int k0, int no, int os, int bmax) {
+    using H = H16<F>;
     const float4 a0 = __ldg((const float4 *)(er + k0)), a1 = __ldg((const float4 *)(er + k0) + 1);
     const float4 c0 = __ldg((const float4 *)(ei + k0)), c1 = __ldg((const float4 *)(ei + k0) + 1);
     const float xr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
     const float xi[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
-    __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
+    __align__(16) typename H::T rh[8], rl[8], ih[8], il[8];
     int brow = k0 / os, brem = k0 - brow * os;
+    float mx = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const bool in = k0 + q < no;
         const float f = in ? c * __ldg(gi + min(brow, bmax)) : 0.f;
         const float x = in ? xr[q] * f : 0.f, y = in ? xi[q] * f : 0.f;
-        rh[q] = __float2bfloat16_rn(x);
-        rl[q] = __float2bfloat16_rn(x - __bfloat162float(rh[q]));
-        ih[q] = __float2bfloat16_rn(y);
-        il[q] = __float2bfloat16_rn(y - __bfloat162float(ih[q]));
+        rh[q] = H::hi(x);
+        rl[q] = H::from(x - H::to(rh[q]));
+        ih[q] = H::hi(y);
+        il[q] = H::from(y - H::to(ih[q]));
+        if constexpr (F == FMT_F16X4) mx = fmaxf(mx, fmaxf(fabsf(x), fabsf(y)));
         if (++brem == os) {
             brem = 0;
             ++brow;
@@ -1628,12 +1669,17 @@ __device__ __forceinline__ void field_scale_vec(const float *er, const float *ei
     *(uint4 *)(p + ps + k0) = *(const uint4 *)rl;
     *(uint4 *)(p + 2 * ps + k0) = *(const uint4 *)ih;
     *(uint4 *)(p + 3 * ps + k0) = *(const uint4 *)il;
+    return mx;
 }
 
-__global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ Ef, __nv_bfloat16 *__restrict__ ge,
+template <int F>
+__global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ Ef, typename H16<F>::T *__restrict__ ge,
                                                      const float *__restrict__ GIt, DevParams prm,
                                                      const float *__restrict__ wnorm, int b0, int nb, int B, int nl,
-                                                     int nse, int ne, int no, int ldo, int nd, int os) {
+                                                     int nse, int ne, int no, int ldo, int nd, int os,
+                                                     const unsigned int *__restrict__ qmax,
+                                                     const float *__restrict__ ascale, const float *__restrict__ pscale,
+                                                     float sig1, float pf, unsigned int *gmax) {
     pdl_trigger();
     pdl_wait();
     const int lane = threadIdx.x & 31;
@@ -1643,16 +1689,31 @@ __global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ E
     for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += nwarps) {
         const int z = row / no, kx = row - z * no, b = b0 + z;
         const int r = b / B, rem = b - r * B, l = rem / nse, se = rem - l * nse, s = se / ne, e = se - s * ne;
-        const float c = 2.f * __ldg(wnorm + r * nl + l) * __ldg(slot_ptr(prm, PFLUX, r) + s);
+        const float w = __ldg(wnorm + r * nl + l), fl = __ldg(slot_ptr(prm, PFLUX, r) + s);
+        float c = 2.f * w * fl;
+        if constexpr (F == FMT_F16X4) {
+            // gamma_b = 2^-ceil(log2(2 |F_s| sqrt(w_l) Q_se)) and u = pf / (alpha_l^2 pi_r sigma1)
+            const float Q = __uint_as_float(__ldg(qmax + (size_t)r * nse + se));
+            const float al = __ldg(ascale + l), pi = __ldg(pscale + 2 * r + 1);
+            c *= inv_pow2_ceil(2.f * fabsf(fl) * sqrtf(fabsf(w)) * Q) * (pf / (al * al * pi * sig1));
+        }
         const float *gi = GIt + (((size_t)r * ne + e) * nd + kx / os) * nd;  // row x = kx / os, along y
         const float *er = Ef + (size_t)b * 2 * ps + (size_t)kx * ldo, *ei = er + ps;
-        __nv_bfloat16 *p = ge + (size_t)z * 4 * ps + (size_t)kx * ldo;
+        typename H16<F>::T *p = ge + (size_t)z * 4 * ps + (size_t)kx * ldo;
+        float mx = 0.f;
         int k0 = 8 * lane;
         for (; k0 + 3 * 256 < ldo; k0 += 4 * 256) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) field_scale_vec(er, ei, p, ps, gi, c, k0 + u * 256, no, os, bmax);
+            for (int u = 0; u < 4; ++u)
+                mx = fmaxf(mx, field_scale_vec<F>(er, ei, p, ps, gi, c, k0 + u * 256, no, os, bmax));
         }
-        for (; k0 < ldo; k0 += 256) field_scale_vec(er, ei, p, ps, gi, c, k0, no, os, bmax);
+        for (; k0 < ldo; k0 += 256) mx = fmaxf(mx, field_scale_vec<F>(er, ei, p, ps, gi, c, k0, no, os, bmax));
+        if constexpr (F == FMT_F16X4) {
+            // max |GEt| of the PSF (non-negative floats order as their bits)
+            if (!(mx < 3.0e38f)) mx = 3.0e38f;
+            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            if (lane == 0) atomicMax(gmax + b, __float_as_uint(mx));
+        }
     }
 }
 
@@ -1685,9 +1746,14 @@ cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb
     if (e != cudaSuccess) return e;
     const int rows = nb * p->no;
     const int blocks = std::max(1, std::min((rows + 7) / 8, p->sm_count * 8));
-    return launch_pdl(k_field_scale, dim3(blocks), dim3(256), 0, st, (const float *)p->Ef,
-                      (__nv_bfloat16 *)p->GEt.ptr, (const float *)p->GIt, prm, (const float *)p->wnorm, b0, nb, p->B,
-                      p->nl, p->nse, p->ne, p->no, p->ldo, p->nd, p->os);
+    auto go = [&](auto kern, void *ge) {
+        return launch_pdl(kern, dim3(blocks), dim3(256), 0, st, (const float *)p->Ef, ge, (const float *)p->GIt,
+                          prm, (const float *)p->wnorm, b0, nb, p->B, p->nl, p->nse, p->ne, p->no, p->ldo, p->nd,
+                          p->os, (const unsigned int *)p->qmax, (const float *)p->ascale, (const float *)p->pscale,
+                          inv_pow2_ceil((float)p->ni), p->paired ? 4.f : 1.f, p->gmax);
+    };
+    if (p->fmt == FMT_F16X4) return go(k_field_scale<FMT_F16X4>, p->GEt.ptr);
+    return go(k_field_scale<FMT_BF16X4>, p->GEt.ptr);
 }
 
 cudaError_t launch_grad_reduce(dlx_plan *p, const DevParams &prm, int R, const DevGrads *g, cudaStream_t st) {

@@ -956,7 +956,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
                         for (int i = 0; i < CW; ++i)
                             acc[CW * cc + i] = fmaf(w, er[i] * er[i] + ei[i] * ei[i], acc[CW * cc + i]);
-                        if constexpr (F == FMT_BF16X4) {  // the field kept for the adjoint
+                        // the field kept for the adjoint (FP16 form: the raw accumulators; the scaling
+                        // pass applies the operand scales)
+                        if constexpr (F == FMT_BF16X4 || F == FMT_F16X4) {
                             if (a.out) store_field_t(a, J.b, m, J.n0 + 64 * h + CW * cc, er, ei);
                         }
                     };

@@ -209,7 +209,7 @@ size_t bucket_bytes(const dlx_mft_desc &d, bool has_pix, int cap) {
         b += pe * (Bt * 2 * hp * ldk + Bt * no * (ldk > ldi ? ldk - ldi : 0));
     }
     // the fields stage 2 keeps for the adjoint (the bucket's plan takes every PSF in one chunk)
-    if (dlx::field_kept(fmt, d.precision == DLX_BF16X3SA, (int)Bt, (int)Bt))
+    if (dlx::field_kept(fmt, d.precision == DLX_BF16X3SA, (int)ni, (int)Bt, (int)Bt))
         b += 8 * Bt * no * ldo + 4 * (size_t)cap * ne_mft * (no / d.oversample) * (no / d.oversample);
     b += 16 * (size_t)cap * ni * ni + 8 * (size_t)cap * d.n_exp * nd * nd;
     if (d.dither_px) b += 4 * (size_t)cap * (d.n_exp * nd * nd + 2 * (no / d.oversample) * (no / d.oversample));
