@@ -320,6 +320,12 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     };
     // BF16x3sa: the adjoint-only operands (AH, GEt, GT1) hold the stochastic hi parts alone
     const int adj_planes = p->adj1 ? 2 : p->planes;
+    // the fields stage 2 keeps for the adjoint (instead of its recomputation), when the adjoint
+    // takes every PSF at once and a workspace limit leaves room for them
+    const size_t ef_bytes = sizeof(float) * 2 * (size_t)Bt * p->no * p->ldo;
+    const bool keep_e = field_kept(p->fmt, p->adj1, p->ni, p->chunk, Bt) &&
+                        (d->workspace_limit_bytes == 0 || d->workspace_limit_bytes >= (size_t)Bt * per_psf + ef_bytes);
+    p->padj = p->paired && keep_e;
     if (p->paired) {
         op_alloc(p->amat, p->nl, p->no, p->ldk, 2);
         op_alloc(p->Pp, Bt, 2 * p->hp, p->ldk, p->planes);
@@ -328,10 +334,19 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
         op_alloc(p->amat, p->nl, p->no, p->ldi, p->planes);
         op_alloc(p->T1t, Bt, p->no, p->ldi, p->planes);
     }
-    op_alloc(p->amatH, p->nl, p->ni, p->ldo, adj_planes);
     op_alloc(p->P, Bt, p->ni, p->ldi, p->planes);
-    op_alloc(p->GEt, p->chunk, p->no, p->ldo, adj_planes);
-    op_alloc(p->GT1, p->chunk, p->ni, p->ldo, adj_planes);
+    if (p->padj) {
+        p->hno = (p->no + 1) / 2;
+        p->hpo = pair_half(p->no);
+        p->ldko = operand_ld(2 * p->hpo);
+        op_alloc(p->amatH, p->nl, p->ni, p->ldko, 2);
+        op_alloc(p->GEt, p->chunk, 2 * p->hpo, p->ldko, p->planes);
+        op_alloc(p->GT1, p->chunk, p->ni, p->ldko, p->planes);
+    } else {
+        op_alloc(p->amatH, p->nl, p->ni, p->ldo, adj_planes);
+        op_alloc(p->GEt, p->chunk, p->no, p->ldo, adj_planes);
+        op_alloc(p->GT1, p->chunk, p->ni, p->ldo, adj_planes);
+    }
     const size_t npx = (size_t)p->ni * p->ni, np = (size_t)p->nd * p->nd, nq = (size_t)p->no * p->no;
     const size_t npi = (size_t)p->ndi * p->ndi;
     // blocks of the one-pass binning: up to eight per SM, so that enough loads are in flight
@@ -353,11 +368,7 @@ int make_plan(const dlx_mft_desc *d, int device, int R_max, dlx_plan **out) {
     if (e == cudaSuccess) e = plan_alloc(p, &p->tilt, sizeof(float2) * Bt * 2 * p->ni);
     if (e == cudaSuccess) e = plan_alloc(p, &p->opd, sizeof(float) * npx * R_max);
     if (e == cudaSuccess) e = plan_alloc(p, &p->Is, sizeof(float) * (size_t)p->G * p->nse * R_max * nq);
-    // the fields stage 2 keeps for the adjoint (instead of its recomputation), when the adjoint
-    // takes every PSF at once and a workspace limit leaves room for them
-    const size_t ef_bytes = sizeof(float) * 2 * (size_t)Bt * p->no * p->ldo;
-    if (e == cudaSuccess && field_kept(p->fmt, p->adj1, p->ni, p->chunk, Bt) &&
-        (d->workspace_limit_bytes == 0 || d->workspace_limit_bytes >= (size_t)Bt * per_psf + ef_bytes)) {
+    if (e == cudaSuccess && keep_e) {
         e = plan_alloc(p, &p->Ef, ef_bytes);
         if (e == cudaSuccess) e = cudaMemset(p->Ef, 0, ef_bytes);
         if (e == cudaSuccess) e = plan_alloc(p, &p->GIt, sizeof(float) * p->ne * np * R_max);

@@ -395,6 +395,12 @@ struct dlx_plan {
     int hn = 0, hp = 0;        // pair indices ceil(Ni/2), and that count rounded up to 16
     int ldk = 0;               // row length of the paired operands: operand_ld(2 hp)
     dlx::Operand Pp;
+    // Mirror-paired adjoint (paired plans that keep stage 2's field): the same pairing along the
+    // output axes.  amatH holds [Re A^H | Im A^H] over the first half of the output axis (two
+    // planes), GEt the adjoint field paired along kx (rows) and ky (columns), GT1 the adjoint 2^T
+    // product paired along kx (columns), as Pp and T1t are paired on the pupil axes.
+    bool padj = false;
+    int hno = 0, hpo = 0, ldko = 0;  // ceil(No/2), rounded up to 16, operand_ld(2 hpo)
     double *lam_d = nullptr;   // [nl]
     float *wnorm = nullptr;    // [R][nl] weights / sum(weights)
     float *pscale = nullptr;   // [R][2] 1/sqrt(sum T^2), FP16 phasor scale pi_r
@@ -586,12 +592,11 @@ cudaError_t launch_plane_fold(dlx_plan *p, int R, cudaStream_t st);
 // 16-bit split forms (BF16x3, BF16x4, FP16x3; not BF16x3sa) whose adjoint operand holds every
 // PSF at once allocate Ef.
 inline bool keeps_field(const dlx_plan *p, int R) { return p->Ef != nullptr && p->chunk >= R * p->B; }
-// Whether a plan of this form, pupil size, PSF count and adjoint chunk allocates Ef.  The FP16
-// form's mirror-paired recomputation costs half as much, and below a 384-sample pupil it beat
-// the field's store and scaling pass (binary star, 256^2 pupil: 1184 against 1129 evals/s;
-// calibration, 512^2: 104 against 109).
+// Whether a plan of this form, pupil size, PSF count and adjoint chunk allocates Ef (the FP16
+// form's mirror-paired adjoint needs the kept field: its scaling pass writes the paired operand).
 inline bool field_kept(int fmt, bool adj1, int ni, int chunk, int Bt) {
-    return (fmt == FMT_BF16X4 || (fmt == FMT_F16X4 && ni >= 384)) && !adj1 && chunk >= Bt;
+    (void)ni;
+    return (fmt == FMT_BF16X4 || fmt == FMT_F16X4) && !adj1 && chunk >= Bt;
 }
 // The adjoint field from the kept fields: GEt[z] = split(2 w F GI o Ef[b0 + z]) (z < nb).
 cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st);

@@ -78,10 +78,12 @@ __device__ void block_sum(df (&v)[NV], df *sh /* [32][NV] */) {
 // Paired forward matrix (hp > 0, FP16 split form; pair_layout in dlx_common.cuh): for n < hn
 // the row k of amat holds a = Re A[k][n] at column n and b = Im A[k][n] at column hp + n (times
 // alpha_l), split into two planes (hi, lo) of ldk columns.
+// Paired adjoint matrix (hpo > 0): for k < hno the row n of amatH holds Re A^H[n][k] = Re A[k][n]
+// at column k and Im A^H[n][k] = -Im A[k][n] at column hpo + k, two planes of ldko columns.
 template <int F>
 __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const float *ascale, int nl, int ni,
                                int no, int ldi, int ldo, double dx, double du, uint32_t sr, int ah_hi, int hp,
-                               int ldk) {
+                               int ldk, int hpo, int ldko) {
     const int P = fmt_planes(F), es = fmt_esize(F);
     const size_t per = (size_t)no * ni, total = per * nl;
     const double cN = 0.5 * (ni - 1), cO = 0.5 * (no - 1);
@@ -132,6 +134,21 @@ __global__ void k_mft_matrices(void *amat, void *amatH, const double *lam, const
                 continue;
             }
         }
+        if constexpr (F == FMT_F16X4) {
+            if (hpo > 0) {
+                if (2 * k < no) {
+                    using H = H16<F>;
+                    typename H::T *q = (typename H::T *)amatH + (size_t)l * 2 * ni * ldko + (size_t)n * ldko + k;
+                    const size_t pl = (size_t)ni * ldko;
+                    const typename H::T ah = H::hi(re), bh = H::hi(-im);
+                    q[0] = ah;
+                    q[pl] = H::from(re - H::to(ah));
+                    q[hpo] = bh;
+                    q[pl + hpo] = H::from(-im - H::to(bh));
+                }
+                continue;
+            }
+        }
         char *ah = (char *)amatH + (size_t)l * P * ni * ldo * es;
         store_cplx<F>(ah, (size_t)ni * ldo, (size_t)n * ldo + k, re, -im);
     }
@@ -144,7 +161,8 @@ cudaError_t launch_mft_matrices(dlx_plan *p, cudaStream_t st) {
     DLX_FMT_DISPATCH(p->fmt, F,
                      k_mft_matrices<F><<<blocks, 256, 0, st>>>(p->amat.ptr, p->amatH.ptr, p->lam_d, p->ascale, p->nl,
                                                                p->ni, p->no, p->ldi, p->ldo, p->dx, p->du, p->sr,
-                                                               p->adj1 ? 1 : 0, p->paired ? p->hp : 0, p->ldk));
+                                                               p->adj1 ? 1 : 0, p->paired ? p->hp : 0, p->ldk,
+                                                               p->padj ? p->hpo : 0, p->ldko));
     return cudaGetLastError();
 }
 
@@ -1717,6 +1735,121 @@ __global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ E
     }
 }
 
+// The same pass for the mirror-paired adjoint (FP16 form; pair_layout in dlx_common.cuh): one
+// warp takes the rows jx and No-1-jx of a PSF, each lane four pair indices jy at a time (128 per
+// warp and step); the four values G_E at (jx or No-1-jx, jy or No-1-jy) give the sums and
+// differences along kx (the row block Rx of GEt, for the adjoint 1^T) and along ky (the column
+// block Ry, the adjoint 2^T's contraction), times gamma_b / 4, stored as (V1, V2) = (Re, Im) for
+// Ry = S and (Im, Re) for D.  A mirror that is its own row or column (the middle of an odd axis)
+// counts once.
+__device__ __forceinline__ void load4(const float *p, int c0, bool vec, int n, float (&v)[4]) {
+    if (vec) {
+        const float4 a = __ldg((const float4 *)(p + c0));
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+        v[3] = a.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (c0 + q >= 0 && c0 + q < n) ? __ldg(p + c0 + q) : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(256, 3) k_field_scale_pair(const float *__restrict__ Ef, __half *__restrict__ ge,
+                                                             const float *__restrict__ GIt, DevParams prm,
+                                                             const float *__restrict__ wnorm, int b0, int nb, int B,
+                                                             int nl, int nse, int ne, int no, int ldo, int nd, int os,
+                                                             int hno, int hpo, int ldko,
+                                                             const unsigned int *__restrict__ qmax,
+                                                             const float *__restrict__ ascale,
+                                                             const float *__restrict__ pscale, float sig1, float pf,
+                                                             unsigned int *gmax) {
+    using H = H16<FMT_F16X4>;
+    pdl_trigger();
+    pdl_wait();
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5, nrows = nb * hno;
+    const size_t ps = (size_t)no * ldo, pps = (size_t)2 * hpo * ldko;
+    const int bmax = (no - 1) / os;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += nwarps) {
+        const int z = row / hno, jx = row - z * hno, b = b0 + z;
+        const int r = b / B, rem = b - r * B, l = rem / nse, se = rem - l * nse, s = se / ne, e = se - s * ne;
+        const float w = __ldg(wnorm + r * nl + l), fl = __ldg(slot_ptr(prm, PFLUX, r) + s);
+        const float Q = __uint_as_float(__ldg(qmax + (size_t)r * nse + se));
+        const float al = __ldg(ascale + l), pi = __ldg(pscale + 2 * r + 1);
+        // 2 w F, gamma_b, u, and 1/4 for the sums of four values
+        const float c = 0.25f * 2.f * w * fl * inv_pow2_ceil(2.f * fabsf(fl) * sqrtf(fabsf(w)) * Q) *
+                        (pf / (al * al * pi * sig1));
+        const int kx1 = no - 1 - jx;
+        const bool row1 = kx1 != jx;
+        const float *gi0 = GIt + (((size_t)r * ne + e) * nd + jx / os) * nd;
+        const float *gi1 = GIt + (((size_t)r * ne + e) * nd + kx1 / os) * nd;
+        const float *er0 = Ef + (size_t)b * 2 * ps + (size_t)jx * ldo, *ei0 = er0 + ps;
+        const float *er1 = Ef + (size_t)b * 2 * ps + (size_t)kx1 * ldo, *ei1 = er1 + ps;
+        __half *gz = ge + (size_t)z * 4 * pps;
+        float mx = 0.f;
+        for (int j0 = 4 * lane; j0 < hpo; j0 += 128) {
+            const bool vec = (no & 3) == 0 && j0 + 4 <= no;
+            // row a, direct columns j0 + q (x) and mirror columns no - 1 - j0 - q (y, reversed below)
+            float xr0[4], xi0[4], yr0[4], yi0[4], xr1[4], xi1[4], yr1[4], yi1[4];
+            load4(er0, j0, vec, no, xr0);
+            load4(ei0, j0, vec, no, xi0);
+            load4(er0, no - 4 - j0, vec, no, yr0);
+            load4(ei0, no - 4 - j0, vec, no, yi0);
+            load4(er1, j0, vec, no, xr1);
+            load4(ei1, j0, vec, no, xi1);
+            load4(er1, no - 4 - j0, vec, no, yr1);
+            load4(ei1, no - 4 - j0, vec, no, yi1);
+            // g[a][h]: G_E of row a at the direct (h = 0) and mirror (h = 1) column of pair q
+            float g00r[4], g00i[4], g01r[4], g01i[4], g10r[4], g10i[4], g11r[4], g11i[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int jy = j0 + q, my = no - 1 - jy;
+                const bool in0 = jy < hno, in1 = in0 && my != jy;
+                const int c0 = min(jy / os, bmax), c1 = min(my / os, bmax);
+                const float f00 = in0 ? c * __ldg(gi0 + c0) : 0.f, f01 = in1 ? c * __ldg(gi0 + c1) : 0.f;
+                const float f10 = (in0 && row1) ? c * __ldg(gi1 + c0) : 0.f;
+                const float f11 = (in1 && row1) ? c * __ldg(gi1 + c1) : 0.f;
+                g00r[q] = f00 * xr0[q];
+                g00i[q] = f00 * xi0[q];
+                g01r[q] = f01 * yr0[3 - q];
+                g01i[q] = f01 * yi0[3 - q];
+                g10r[q] = f10 * xr1[q];
+                g10i[q] = f10 * xi1[q];
+                g11r[q] = f11 * yr1[3 - q];
+                g11i[q] = f11 * yi1[3 - q];
+            }
+#pragma unroll
+            for (int rx = 0; rx < 2; ++rx)
+#pragma unroll
+                for (int ry = 0; ry < 2; ++ry) {
+                    const float sx = rx ? -1.f : 1.f, sy = ry ? -1.f : 1.f;
+                    __align__(8) __half h1[4], l1[4], h2[4], l2[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float qr = (g00r[q] + sy * g01r[q]) + sx * (g10r[q] + sy * g11r[q]);
+                        const float qi = (g00i[q] + sy * g01i[q]) + sx * (g10i[q] + sy * g11i[q]);
+                        const float v1 = ry ? qi : qr, v2 = ry ? qr : qi;
+                        mx = fmaxf(mx, fmaxf(fabsf(v1), fabsf(v2)));
+                        h1[q] = H::hi(v1);
+                        l1[q] = H::from(v1 - H::to(h1[q]));
+                        h2[q] = H::hi(v2);
+                        l2[q] = H::from(v2 - H::to(h2[q]));
+                    }
+                    __half *o = gz + (size_t)(rx * hpo + jx) * ldko + ry * hpo + j0;
+                    *(uint2 *)o = *(const uint2 *)h1;
+                    *(uint2 *)(o + pps) = *(const uint2 *)l1;
+                    *(uint2 *)(o + 2 * pps) = *(const uint2 *)h2;
+                    *(uint2 *)(o + 3 * pps) = *(const uint2 *)l2;
+                }
+        }
+        // max |GEt| of the PSF (non-negative floats order as their bits)
+        if (!(mx < 3.0e38f)) mx = 3.0e38f;
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(gmax + b, __float_as_uint(mx));
+    }
+}
+
 // GIt[k][x][y] = GI[k][y][x] for the R * ne weight maps, through 32 x 32 tiles in shared memory
 // (the field scaling reads the weights along y).
 __global__ void k_gi_transpose(const float *__restrict__ GI, float *__restrict__ GIt, int nd) {
@@ -1752,6 +1885,15 @@ cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb
                           p->os, (const unsigned int *)p->qmax, (const float *)p->ascale, (const float *)p->pscale,
                           inv_pow2_ceil((float)p->ni), p->paired ? 4.f : 1.f, p->gmax);
     };
+    if (p->padj) {
+        const int prow = nb * p->hno;
+        const int pblocks = std::max(1, std::min((prow + 7) / 8, p->sm_count * 8));
+        return launch_pdl(k_field_scale_pair, dim3(pblocks), dim3(256), 0, st, (const float *)p->Ef,
+                          (__half *)p->GEt.ptr, (const float *)p->GIt, prm, (const float *)p->wnorm, b0, nb, p->B,
+                          p->nl, p->nse, p->ne, p->no, p->ldo, p->nd, p->os, p->hno, p->hpo, p->ldko,
+                          (const unsigned int *)p->qmax, (const float *)p->ascale, (const float *)p->pscale,
+                          inv_pow2_ceil((float)p->ni), p->paired ? 4.f : 1.f, p->gmax);
+    }
     if (p->fmt == FMT_F16X4) return go(k_field_scale<FMT_F16X4>, p->GEt.ptr);
     return go(k_field_scale<FMT_BF16X4>, p->GEt.ptr);
 }

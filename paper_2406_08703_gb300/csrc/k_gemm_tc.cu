@@ -66,12 +66,13 @@ struct Cfg {
 };
 
 // Shared-memory stages of one launch.  Mirror-paired contractions (PR, the FP16 split form;
-// pair_layout in dlx_common.cuh) read a two-plane matrix operand (hi, lo of [Re A | Im A]):
-// the A operand of stage 1 and stage 2, the B operand of the recomputed field.
+// pair_layout in dlx_common.cuh) read a two-plane matrix operand (hi, lo of [Re A | Im A] or of
+// [Re A^H | Im A^H]): the A operand of stage 1, stage 2 and the adjoint 2^T, the B operand of the
+// recomputed field and the adjoint 1^T.
 template <int F, int PR, int KIND>
 struct Geo {
-    static constexpr int PA = (PR && (KIND == KS1 || KIND == KS2)) ? 2 : Cfg<F>::PL;
-    static constexpr int PB = (PR && KIND == KGE) ? 2 : Cfg<F>::PL;
+    static constexpr int PA = (PR && (KIND == KS1 || KIND == KS2 || KIND == KGT1)) ? 2 : Cfg<F>::PL;
+    static constexpr int PB = (PR && (KIND == KGE || KIND == KGP)) ? 2 : Cfg<F>::PL;
     static constexpr int STAGE_BYTES = (PA + PB) * PLANE_BYTES;
     static constexpr int STAGES = (192 * 1024) / STAGE_BYTES;
     static constexpr int SMEM = STAGES * STAGE_BYTES + Cfg<F>::STG_BYTES + 1024 + 256;
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const __grid_constant__ CUtensorMap mapC, TcArgs a) {
     using C = Cfg<F>;
     using G = Geo<F, PR, KIND>;
-    static_assert(!PR || (F == FMT_F16X4 && (KIND == KS1 || KIND == KS2 || KIND == KGE)), "paired: FP16 split forward");
+    static_assert(!PR || F == FMT_F16X4, "paired: FP16 split form");
     constexpr uint32_t NBUF = (MODE == FAST) ? 2 : 1;
     // operand-writing contractions of the bf16 forms store through a staged TMA box
     constexpr bool TMA_OUT = C::TMA_STORE && (KIND == KS1 || KIND == KGE || KIND == KGT1);
@@ -676,7 +677,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 // of K (b . D_im) subtracted, Ei = M.V2
                                 const uint32_t idr = (kb * C::KB + ks * C::KSTEP >= a.hp) ? id_neg : id_pos;
                                 auto pm = [&](uint32_t d, int x, int y, uint32_t id, uint32_t acc) {
-                                    if constexpr (KIND == KGE) mma<F>(d, A(y), Bd(x), id, acc);
+                                    if constexpr (KIND == KGE || KIND == KGP) mma<F>(d, A(y), Bd(x), id, acc);
                                     else mma<F>(d, A(x), Bd(y), id, acc);
                                 };
                                 if constexpr (MODE != FAST) {
@@ -806,7 +807,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if constexpr (KIND == KS2) w *= u * u;
                     if constexpr (KIND == KGE) c *= f16_gamma(a, J) * u;
                     if constexpr (KIND == KGT1) osc = f16_sigma2(a, J);
-                    if constexpr (KIND == KGP) k2 /= al * al * f16_gamma(a, J) * f16_sigma2(a, J) * pi;
+                    // the paired adjoint field carries gamma_b / 4
+                    if constexpr (KIND == KGP) k2 /= al * al * f16_gamma(a, J) * f16_sigma2(a, J) * pi * (PR ? 0.25f : 1.f);
                 }
                 bool released = false;  // accumulators already handed back to the MMA warp
                 if constexpr (TMA_OUT) {
@@ -892,8 +894,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                                 ei[i] *= osc;
                             }
                         }
-                        if constexpr (PR && KIND == KS1) {
-                            // paired stage 1: columns hp.. hold the y-differences, stored as (Im, Re)
+                        if constexpr (PR && (KIND == KS1 || KIND == KGT1)) {
+                            // paired stage 1 (adjoint 2^T): columns hp.. hold the products of the
+                            // y-differences (kx-differences), stored as (Im, Re)
                             if (J.n0 + c0 >= a.hp) {
 #pragma unroll
                                 for (int i = 0; i < CW; ++i) {
@@ -1210,7 +1213,7 @@ cudaError_t launch(dlx_plan *p, const Operand &A, const Operand &B, const Operan
            : (p->adj1 && KIND == KGT1) ? p->sr ^ 0xc2b2ae3du
                                        : 0u;
     a.p4 = (p->adj1 && KIND == KGP) ? 1 : 0;
-    a.hp = PR ? p->hp : 0;
+    a.hp = PR ? ((KIND == KGT1 || KIND == KGP) ? p->hpo : p->hp) : 0;
     a.tm = (a.M + BM - 1) / BM;
     a.tn = (a.N + BN - 1) / BN;
     a.KB = Cfg<F>::KB;
@@ -1291,25 +1294,30 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
         e = launch<F, FAST, KGE>(p, T1, Am, &p->GEt, a, st);
     }
     if (e != cudaSuccess) return e;
-    // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No)
+    // adjoint stage 2^T: GT1[z][ny][kx] = AH(l) . GEt[z]^T   (M = Ni, N = No, K = No); mirror-paired
+    // (FP16 form with the field kept): N = K = 2 hpo, the paired field from the scaling pass
+    constexpr int PA = (F == FMT_F16X4) ? 1 : 0;
+    const bool pa = PA && p->padj;
+    if (p->padj && !p->keep_field) return cudaErrorInvalidValue;  // the paired operand comes from the pass
     TcArgs b{};
     b.M = p->ni;
-    b.N = p->no;
-    b.K = p->no;
+    b.N = pa ? 2 * p->hpo : p->no;
+    b.K = pa ? 2 * p->hpo : p->no;
     b.b0 = b0;
     b.prm = prm;
     b.out = p->GT1.ptr;
-    b.out_ld = p->ldo;
-    b.out_ps = (size_t)p->ni * p->ldo;
-    b.units = nb * tmi * tmo;
-    e = launch<F, FAST, KGT1>(p, p->amatH, p->GEt, &p->GT1, b, st);
+    b.out_ld = p->GT1.ld;
+    b.out_ps = (size_t)p->ni * p->GT1.ld;
+    b.units = nb * tmi * ((b.N + BN - 1) / BN);
+    e = pa ? launch<F, FAST, KGT1, PA>(p, p->amatH, p->GEt, &p->GT1, b, st)
+           : launch<F, FAST, KGT1>(p, p->amatH, p->GEt, &p->GT1, b, st);
     if (e != cudaSuccess) return e;
     // adjoint stage 1^T + phase gradient: gphi[b][split] = (2 pi/lambda) Im((GT1[z] . AH(l)^T) conj P[b]),
     // the K = No contraction split in gsplit parts (their gphi planes are summed by the reductions)
     TcArgs c{};
     c.M = p->ni;
     c.N = p->ni;
-    c.K = p->no;
+    c.K = pa ? 2 * p->hpo : p->no;
     c.b0 = b0;
     c.prm = prm;
     c.P = p->P.ptr;
@@ -1319,7 +1327,8 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
     c.cNf = 0.5f * (float)(p->ni - 1);
     c.ksplit = p->gsplit;
     c.units = nb * tmi * tmi * p->gsplit;
-    return launch<F, FAST, KGP>(p, p->GT1, p->amatH, nullptr, c, st);
+    return pa ? launch<F, FAST, KGP, PA>(p, p->GT1, p->amatH, nullptr, c, st)
+              : launch<F, FAST, KGP>(p, p->GT1, p->amatH, nullptr, c, st);
 }
 
 }  // namespace
