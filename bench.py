@@ -10,7 +10,7 @@ oversampled grid (1024^2 detector, oversample 2), synthetic seeded inputs.  The
 binary-star fit (256^2 pupil, 32 wavelengths x 2 stars onto 1024^2) is timed
 beside it under the key "binary".
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--form bf16x3] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--form f16x3] [--impl reference]
 
 Prints one JSON line (rank 0).  `value` is device-timed (CUDA events on the
 launching stream, inputs resident); `e2e` times the same call with host inputs
@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--form", default="bf16x3", choices=["bf16x3", "bf16x3sa", "bf16x4", "f16x3", "tf32x3", "bf16", "fp32"])
+    ap.add_argument("--form", default="f16x3", choices=["f16x3", "bf16x3", "bf16x3sa", "bf16x4", "tf32x3", "bf16", "fp32"])
     ap.add_argument("--impl", default="dlx", choices=["dlx", "reference"])
     ap.add_argument("--workload", default=None,
                     help="workload of the main line (default calib) or of --fit / --laplace (default paper)")
@@ -518,7 +518,7 @@ def serving_run(P, reqs, form, n_steps, rate=None, seed=0):
     # algorithmic MFT work of the served evaluations (8 FLOP per complex MAC): forward stage 1 and
     # stage 2 and the adjoint's two stages per PSF, and the recomputed field in the forms whose
     # buckets do not keep stage 2's fields (all but the BF16 split forms)
-    kept = form in ("bf16x3", "bf16x4")
+    kept = form in ("bf16x3", "bf16x4", "f16x3")
     flop = 0.0
     for k, p, d in reqs:
         ni, no = p.n_pupil, p.n_det * p.oversample
@@ -617,7 +617,7 @@ def fit_bench(args):
     i = plan.info
     line = dict(metric=FIT_METRIC, value=secs, unit="s", n_gpus=1, steps=n, warmup=max(args.warmup, 3),
                 ms_per_step=1e3 * secs / n, higher_is_better=False, scaling="weak", vs_baseline=None,
-                dtype={"bf16x3": "bf16x3 split (fp32 accumulate)"}.get(args.form, args.form), data="synthetic",
+                dtype=DTYPES.get(args.form, args.form), data="synthetic",
                 config=dict(workload=workload_name(wl), form=args.form, psfs_per_eval=i.n_psf, pupil=i.n_pupil,
                             mft_out=i.n_mft_out, dithers=dither_mode(crop, start), epochs=[s[0] for s in stages],
                             lr=lr,
@@ -693,7 +693,7 @@ def laplace_bench(args):
     rel_zern = res["sigma_zern"] * (2 * np.pi / lam_c) * np.sqrt(n_s.sum())
     line = dict(metric=LAPLACE_METRIC, value=secs, unit="s", n_gpus=1, steps=max(1, args.steps),
                 warmup=max(args.warmup, 3), ms_per_step=1e3 * secs, higher_is_better=False, scaling="weak",
-                vs_baseline=None, dtype={"bf16x3": "bf16x3 split (fp32 accumulate)"}.get(args.form, args.form),
+                vs_baseline=None, dtype=DTYPES.get(args.form, args.form),
                 data="synthetic", gpu_launches=None,
                 config=dict(workload=workload_name(wl), form=args.form, psfs_per_eval=i.n_psf, pupil=i.n_pupil,
                             mft_out=i.n_mft_out, dithers=dither_mode(crop, truth), n_par=len(lp.labels),
@@ -749,15 +749,14 @@ def contraction_flop(B, ni, no):
             "adjoint_stage1T": 8.0 * B * ni * ni * no}
 
 
-# DRAM bytes (read + written) per launch of the BF16x3 form's contractions, from ncu captures of
-# this build on reduced cases of 16 PSFs (the calibration shapes with 2 of 16 wavelengths, the
-# binary-star shapes with 8 of 32), scaled to a full launch by the PSF count, in which their
-# traffic grows (every PSF's operands are distinct and the A(lambda) blocks are per wavelength);
-# none for a kernel or form without a capture of the current code
+# DRAM bytes (read + written) per launch of a form's contractions, from ncu captures of this
+# build on reduced cases of 16 PSFs (the calibration shapes with 2 of 16 wavelengths), scaled to a
+# full launch by the PSF count, in which their traffic grows (every PSF's operands are distinct
+# and the A(lambda) blocks are per wavelength); none for a kernel, form or workload without a
+# capture of the current code
 TRAFFIC_16 = {
-    "binary": {},
-    "calib": {"stage1": 131.90e6, "stage2_intensity": 1003.46e6, "adjoint_stage2T": 892.43e6,
-              "adjoint_stage1T": 198.76e6},
+    "bf16x3": {"calib": {"stage1": 131.90e6, "stage2_intensity": 1003.46e6, "adjoint_stage2T": 892.43e6,
+                         "adjoint_stage1T": 198.76e6}},
 }
 
 
@@ -771,12 +770,15 @@ def roofline(r, form, workload, clk, peaks):
     alg = contraction_flop(B, ni, no)
     if dom not in alg or classes[dom]["events"] <= 0:
         return None
-    # tensor instructions per algorithmic product: forward contractions of BF16x4 take 4, its adjoint 3
+    # tensor instructions per algorithmic product: forward contractions of BF16x4 take 4, its adjoint 3;
+    # the FP16 form's mirror-paired contractions 1.5 (six real products per 16-wide step over the
+    # paired axis, against eight FLOP per complex MAC over the full one, for axes whose halves are
+    # multiples of 16 as at these workloads)
     adj = dom.startswith("adjoint")
-    split = {"bf16x4": 3.0 if adj else 4.0, "bf16x3sa": 1.0 if adj else 3.0, "f16x3": 3.0, "bf16x3": 3.0,
+    split = {"bf16x4": 3.0 if adj else 4.0, "bf16x3sa": 1.0 if adj else 3.0, "f16x3": 1.5, "bf16x3": 3.0,
              "tf32x3": 3.0, "bf16": 1.0, "fp32": 1.0}[form]
     nom_ratio = {"f16x3": 1.0, "bf16x4": 1.0, "bf16x3": 1.0, "bf16x3sa": 1.0, "bf16": 1.0, "tf32x3": 1.1 / 2.25}
-    t16 = TRAFFIC_16.get(workload, {}).get(dom) if form == "bf16x3" and not N_LAMBDAS else None
+    t16 = TRAFFIC_16.get(form, {}).get(workload, {}).get(dom) if not N_LAMBDAS else None
     traffic = t16 / 16 * B if t16 else None
     per_launch_ms = classes[dom]["ms"] / max(classes[dom]["events"], 1)
     achieved = alg[dom] / (per_launch_ms / 1e3) / 1e12

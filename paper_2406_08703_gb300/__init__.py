@@ -46,7 +46,7 @@ class MftDesc:
     n_src: int
     n_exp: int = 1
     n_zern: int = 0
-    precision: int = DLX_BF16X3
+    precision: int = DLX_F16X3
     psf_chunk: int = 0
     workspace_limit_bytes: int = 0
     prf_prior_sigma: float = 0.0
@@ -107,7 +107,7 @@ def integer_dithers(p) -> Optional[list]:
     return r.astype(int).tolist() if np.all(np.abs(k - r) <= 1e-6) else None
 
 
-def desc_from_problem(p, precision=DLX_BF16X3, crop: bool = False, **kw) -> MftDesc:
+def desc_from_problem(p, precision=DLX_F16X3, crop: bool = False, **kw) -> MftDesc:
     """MftDesc of a workloads.Problem-like object (duck-typed).  crop=True computes integer-pixel
     dithers as windows of one larger detector (raises if a dither is not a whole pixel)."""
     kw.setdefault("prf_prior_sigma", float(getattr(p, "prf_sigma", 0.0) or 0.0))

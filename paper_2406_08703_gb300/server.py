@@ -40,7 +40,7 @@ class Server:
         except Exception:
             pass
 
-    def submit(self, problem, data, n_steps: int = 10, lr: Optional[dict] = None, precision: int = N.DLX_BF16X3,
+    def submit(self, problem, data, n_steps: int = 10, lr: Optional[dict] = None, precision: int = N.DLX_F16X3,
                crop: bool = False, state: Optional[dict] = None) -> int:
         """crop=True serves whole-pixel dithers as windows of one larger detector per source.
         state = a poll result's {"adam_m", "adam_v", "adam_step"} (with the problem's parameters set to
@@ -135,7 +135,7 @@ def dlx_server_create(device: int = 0, hbm_budget: int = 0, max_slots: int = 16)
 
 
 def dlx_submit(server: Server, problem, data, n_steps: int = 10, lr: Optional[dict] = None,
-               precision: int = N.DLX_BF16X3) -> int:
+               precision: int = N.DLX_F16X3) -> int:
     return server.submit(problem, data, n_steps, lr, precision)
 
 

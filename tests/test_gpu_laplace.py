@@ -24,7 +24,8 @@ from laplace_cases import LAM, aberrated_problem, laplace_problem
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": dict(J=1e-4, info=1e-4, hess=1e-4), "bf16x3": dict(J=1e-4, info=1e-4, hess=1e-3)}
+TOL = {"fp32": dict(J=1e-4, info=1e-4, hess=1e-4), "bf16x3": dict(J=1e-4, info=1e-4, hess=1e-3),
+       "f16x3": dict(J=1e-4, info=1e-4, hess=1e-3)}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -60,7 +61,7 @@ def _rel(H, ref):
     return float(np.max(np.abs(H - ref) / s))
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "f16x3"])
 def test_full_period_closed_form(form):
     """Fisher entries of the full-period case: 4 k^2 N <t_i t_j>_A between odd tangents, zero
     with the even defocus term, N / F^2 for the flux and zero between flux and phase."""
@@ -101,7 +102,7 @@ def aberrated():
     return p, data, J, ref, labs
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "f16x3"])
 def test_aberrated_against_oracle(aberrated, form):
     """Three stars, two wavelengths, two exposures (one dithered), a flat field and four Zernike
     terms including the tilts: J, the three curvature matrices and the marginal errors."""
@@ -184,7 +185,7 @@ def test_jvp_rejects_bad_alpha():
             P.dlx_model_jvp(plan, prm, t, 1, a)
 
 
-@pytest.mark.parametrize("form", ["bf16x3"])
+@pytest.mark.parametrize("form", ["bf16x3", "f16x3"])
 def test_paper_full_size_sampled(form):
     """The paper's example (20 stars x 3 wavelengths x 5 images, 512^2 -> 1024^2, Noll 4-10): Jacobian
     entries at sampled pixels against the oracle's differences of direct sums, and properties of the
@@ -225,7 +226,7 @@ def test_paper_full_size_sampled(form):
     assert np.all(res >= (1 - 1e-9) / np.sqrt(np.diag(H)))
 
 
-@pytest.mark.parametrize("form", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("form", ["fp32", "bf16x3", "f16x3"])
 def test_integer_dither_windows_against_oracle(form):
     """The Laplace passes on a window plan (integer dithers, Sec. 3): the tangent forwards, the
     cotangent pass of the window NLL and the one-source plans of the same windows, against the

@@ -136,24 +136,28 @@ def test_adjoint_chunking_is_bitwise_identical():
             assert np.array_equal(o["grads"][k], outs[0]["grads"][k]), k
 
 
-def test_kept_field_matches_recomputed_field():
-    """BF16x3: the adjoint from the field stage 2 keeps (the default when the adjoint takes every PSF
-    at once) against the adjoint that recomputes each PSF's field (a PSF chunk of 1): the same loss and
-    model, and gradients that differ only by the rounding of the two routes to G_E."""
+@pytest.mark.parametrize("form", ["bf16x3", "f16x3"])
+def test_kept_field_matches_recomputed_field(form):
+    """The adjoint from the field stage 2 keeps (the default when the adjoint takes every PSF at
+    once; in the FP16 form also the mirror-paired adjoint contractions) against the adjoint that
+    recomputes each PSF's field (a PSF chunk of 1; unpaired adjoint contractions): the same loss
+    and model, and gradients that differ only by the rounding of the two routes."""
     _, data, start = fit_problem("custom", seed=16, **RAGGED[2])
-    kept = gpu_eval(start, data, "bf16x3", want_psf=False)
-    recomputed = gpu_eval(start, data, "bf16x3", psf_chunk=1, want_psf=False)
+    kept = gpu_eval(start, data, form, want_psf=False)
+    recomputed = gpu_eval(start, data, form, psf_chunk=1, want_psf=False)
     assert kept["loss"] == recomputed["loss"]
     assert np.array_equal(kept["model"], recomputed["model"])
+    bound = {"bf16x3": 2e-4, "f16x3": 1e-4}[form]
     for k, v in kept["grads"].items():
         if v is not None and np.any(v):
-            assert rel_l2(v, recomputed["grads"][k]) < 2e-4, k
+            assert rel_l2(v, recomputed["grads"][k]) < bound, k
 
 
-def test_repeat_is_deterministic():
+@pytest.mark.parametrize("form", ["bf16x3", "f16x3"])
+def test_repeat_is_deterministic(form):
     _, data, start = fit_problem("custom", seed=6, **RAGGED[2])
-    a = gpu_eval(start, data, "bf16x3", want_psf=False)
-    b = gpu_eval(start, data, "bf16x3", want_psf=False)
+    a = gpu_eval(start, data, form, want_psf=False)
+    b = gpu_eval(start, data, form, want_psf=False)
     assert a["loss"] == b["loss"]
     for k in a["grads"]:
         assert np.array_equal(a["grads"][k], b["grads"][k])

@@ -48,11 +48,12 @@ def _serve(P, reqs, n_steps=3, max_slots=8, budget=0, form="bf16x4", crop=False)
     return out, stats
 
 
-def test_same_result_alone_and_in_the_mix(P):
+@pytest.mark.parametrize("form", ["bf16x4", "f16x3"])
+def test_same_result_alone_and_in_the_mix(P, form):
     a = _request(31, **SHAPE_A)
-    alone, _ = _serve(P, [a])
+    alone, _ = _serve(P, [a], form=form)
     mix = [_request(40 + i, **SHAPE_A) for i in range(3)] + [_request(50, **SHAPE_B), _request(51, **SHAPE_B)]
-    mixed, stats = _serve(P, mix[:2] + [a] + mix[2:])
+    mixed, stats = _serve(P, mix[:2] + [a] + mix[2:], form=form)
     x, y = alone[0], mixed[2]
     assert stats["grouped_launches"] > 0  # same-shape requests shared launches
     assert x["loss"] == pytest.approx(y["loss"], rel=1e-9)
@@ -60,9 +61,10 @@ def test_same_result_alone_and_in_the_mix(P):
         assert rel_l2(y[k], x[k]) < 1e-6, k
 
 
-def test_mid_flight_admission_gives_the_solo_result(P):
+@pytest.mark.parametrize("form_name", ["bf16x3", "f16x3"])
+def test_mid_flight_admission_gives_the_solo_result(P, form_name):
     """Continuous batching: six same-shape requests with uneven step counts on a server with two
-    slots, in the default BF16x3 form.  As a request finishes, a queued one is admitted into the
+    slots, in the BF16x3 and FP16x3 forms.  As a request finishes, a queued one is admitted into the
     freed slot while the other slot's request is still stepping, and when the finished request sat
     below the last active slot, that slot's request (inputs, parameters, Adam state) is moved down
     into the freed one mid-fit.  Every request's loss, parameters and gradients equal its run alone
@@ -73,7 +75,7 @@ def test_mid_flight_admission_gives_the_solo_result(P):
 
     ks = [2, 40, 9, 3, 7, 4]
     reqs = [_request(140 + i, **SHAPE_A) for i in range(len(ks))]
-    form = P.PRECISIONS["bf16x3"]
+    form = P.PRECISIONS[form_name]
     keys = ("zern_coeff", "opd_pix", "flux", "pos", "flat", "g_zern", "g_opd_pix", "g_flat", "g_flux", "g_pos")
 
     def run(batch):
@@ -97,12 +99,13 @@ def test_mid_flight_admission_gives_the_solo_result(P):
             assert rel_l2(y[key], alone[key]) < 1e-6, (i, key)
 
 
-def test_single_evaluation_matches_direct_call(P):
+@pytest.mark.parametrize("form", ["bf16x4", "f16x3"])
+def test_single_evaluation_matches_direct_call(P, form):
     import torch
 
     p, d = _request(60, **SHAPE_A)
-    res, _ = _serve(P, [(p, d)], n_steps=0)
-    plan = P.dlx_make_mft(P.desc_from_problem(p, P.DLX_BF16X4))
+    res, _ = _serve(P, [(p, d)], n_steps=0, form=form)
+    plan = P.dlx_make_mft(P.desc_from_problem(p, P.PRECISIONS[form]))
     loss, grads, _ = P.dlx_loss_grad(plan, P.params_from_problem(p), torch.as_tensor(d, device="cuda"))
     torch.cuda.synchronize()
     assert res[0]["loss"] == pytest.approx(loss.item(), rel=1e-9)
