@@ -59,6 +59,26 @@ def test_mft_matrix_is_isometry_at_fft_sampling(oracle_lib):
         assert np.allclose(A.conj().T @ A, np.eye(ni), atol=1e-12)
 
 
+def test_mft_matrix_mirror_symmetry_and_half_axis_contraction(oracle_lib):
+    """On the centred grids (x_{Ni-1-n} = -x_n, u_{No-1-k} = -u_k) the oracle's matrix satisfies
+    A[k][Ni-1-n] = conj(A[k][n]) and A[No-1-k][n] = conj(A[k][n]); hence a contraction over the
+    pupil axis equals one over half of it, sum_j Re(A) (v_j + v_m) + i Im(A) (v_j - v_m), m = Ni-1-j,
+    the middle sample of an odd axis counted once -- the identity the mirror-paired contractions of
+    the FP16 form rely on.  A grid centred one sample off fails the first two checks."""
+    rng = np.random.default_rng(11)
+    for ni, no in ((8, 12), (9, 7), (17, 33)):
+        A = oracle_lib.mft_matrix(no, ni, 0.125 / ni, 1.3e-6, LAM)
+        assert np.allclose(A[:, ::-1], A.conj(), rtol=0, atol=1e-14 * np.abs(A).max())
+        assert np.allclose(A[::-1, :], A.conj(), rtol=0, atol=1e-14 * np.abs(A).max())
+        v = _rand_c(rng, ni)
+        hn = (ni + 1) // 2
+        j = np.arange(hn)
+        vm = np.where(ni - 1 - j != j, v[ni - 1 - j], 0.0)
+        S, D = v[j] + vm, v[j] - vm
+        half = A[:, :hn].real @ S + 1j * (A[:, :hn].imag @ D)
+        assert np.max(np.abs(half - A @ v)) <= 1e-13 * np.max(np.abs(A @ v))
+
+
 def test_parseval(oracle_lib):
     """Unit-power pupil -> unit total intensity at FFT sampling; less on a smaller field."""
     ni = 32
