@@ -287,12 +287,16 @@ __device__ __forceinline__ float2 load_cplx(const void *base, size_t pstride, si
     }
 
 // Programmatic dependent launch.  The kernels of one evaluation run back to back
-// on one stream; each signals at its start that the next may be launched
-// (pdl_trigger) and waits for the previous grid to finish and its writes to be
-// visible (pdl_wait) before it touches global memory, so the next kernel's launch
-// and set-up overlap the tail of the previous one.  Without a programmatic
-// dependency both are no-ops.
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// on one stream, each launched with programmatic stream serialization.  No kernel
+// signals early (griddepcontrol.launch_dependents): a CTA that exits counts as
+// having signalled, so the next grid is launched as the last CTAs of the previous
+// one exit, and its launch overlaps that tail.  Each kernel waits for the previous
+// grid to finish and its writes to be visible (pdl_wait) before it touches global
+// memory.  An early signal at kernel start was measured to cost more than it saved:
+// the dependent grid's CTAs took the SMs freed by a multi-wave grid before its
+// later waves ran (calibration workload 7.53 against 7.14 ms per back-to-back
+// evaluation, binary star 0.766 against 0.699 ms).  Without a programmatic
+// dependency pdl_wait is a no-op.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>

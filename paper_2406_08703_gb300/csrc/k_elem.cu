@@ -184,7 +184,6 @@ __global__ void k_prologue(DevParams prm, int nz, int npx, int nl, float *__rest
                            float *tpart, unsigned int *ncount, float *pscale, float *wnorm,
                            const double *__restrict__ lam, int B, int nse, int ne, int ni, double dx,
                            float2 *__restrict__ tilt, unsigned int *qmax, unsigned int *gmax, double chirp) {
-    pdl_trigger();
     pdl_wait();
     extern __shared__ float c_sh[];
     __shared__ df sh[32];
@@ -298,7 +297,6 @@ __global__ void __launch_bounds__(256, 4) k_phasor(DevParams prm, const float *_
                          const float *__restrict__ invlam, const float *__restrict__ pscale, int B, int nl, int nse,
                          int ne, int ni, int ldi, void *P, uint32_t sr, const float *__restrict__ tmap, float tcoef,
                          uint32_t tmask) {
-    pdl_trigger();
     pdl_wait();
     const int npx = ni * ni, Pl = fmt_planes(F), es = fmt_esize(F), gpr = ldi >> 3;
     const int r = blockIdx.y / nl, l = blockIdx.y - r * nl;
@@ -436,7 +434,6 @@ __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const flo
                                                      const float *__restrict__ pscale, int B, int nl, int nse, int ne,
                                                      int ni, int ldi, void *P, void *Pp, int hn, int hp, int ldk,
                                                      const float *__restrict__ tmap, float tcoef, uint32_t tmask) {
-    pdl_trigger();
     pdl_wait();
     constexpr int F = FMT_F16X4;
     const int npx = ni * ni, ng = (hn + 3) >> 2;
@@ -601,7 +598,6 @@ __global__ void k_bin_nll(const float *__restrict__ Is, int G, int Rnse, int nse
                           float *__restrict__ model, size_t mstride, float *__restrict__ GI, DevGrads g, double *red,
                           unsigned long long *clamped, unsigned int *qmax, double *loss, unsigned int *bcount,
                           float prf_inv, const float *__restrict__ cot, const uint8_t *__restrict__ used, int tn) {
-    pdl_trigger();
     pdl_wait();
     __shared__ df sh[32 * (1 + MAXS)];
     __shared__ unsigned int s_q[kQShared];
@@ -897,7 +893,6 @@ __global__ void __launch_bounds__(256) k_bin_model(const float *__restrict__ Is,
                                                    DevGrads g, double *red_a, unsigned long long *clamped,
                                                    double *loss, unsigned int *bcount, float prf_inv,
                                                    const float *__restrict__ cot) {
-    pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
     __shared__ float s_flux[kMaxSrc];
@@ -994,7 +989,6 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
                                                    int nd, int os_rt, int no, const float *__restrict__ GI,
                                                    DevGrads g, double *red_b, unsigned int *fcount,
                                                    unsigned int *qmax) {
-    pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
     __shared__ unsigned int s_q[kQShared];
@@ -1083,7 +1077,6 @@ __global__ void __launch_bounds__(256) k_flux_grad(const float *__restrict__ Is,
 template <int OS>
 __global__ void __launch_bounds__(128) k_win_sum(const float *__restrict__ Is, int G, int Rnse, int nse, int ns,
                                                  int ndb, int os_rt, int no, DevParams prm, float *__restrict__ S) {
-    pdl_trigger();
     pdl_wait();
     __shared__ float s_flux[kMaxSrc];
     const int r = blockIdx.z, os = OS > 0 ? OS : os_rt;
@@ -1125,7 +1118,6 @@ __global__ void __launch_bounds__(256) k_win_nll(const float *__restrict__ S, in
                                                  DevGrads g, double *red_a, unsigned long long *clamped,
                                                  double *loss, unsigned int *bcount, float prf_inv,
                                                  const float *__restrict__ cot) {
-    pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
     __shared__ bool s_last;
@@ -1217,7 +1209,6 @@ __global__ void __launch_bounds__(128) k_win_flux(const float *__restrict__ Is, 
                                                   int ndb, int os_rt, int no, const float *__restrict__ GI,
                                                   DevGrads g, double *red_b, unsigned int *fcount,
                                                   unsigned int *qmax) {
-    pdl_trigger();
     pdl_wait();
     __shared__ df sh[32];
     __shared__ unsigned int s_q;
@@ -1284,7 +1275,6 @@ __global__ void __launch_bounds__(128) k_win_flux(const float *__restrict__ Is, 
 // planes written)) are added into plane 0 in plane order, so every later reader takes
 // plane 0 alone.  Grid: (segments, 16) blocks stepping over the tile's samples.
 __global__ void k_plane_fold(float *__restrict__ Is, const int2 *__restrict__ fold, int tn, int no, size_t Rnse) {
-    pdl_trigger();
     pdl_wait();
     const int2 f = __ldg(fold + blockIdx.x);
     const int tt = tn * tn, rse = f.x / tt, tile = f.x % tt;
@@ -1313,7 +1303,6 @@ cudaError_t launch_plane_fold(dlx_plan *p, int R, cudaStream_t st) {
 // (fixed order over e)
 __global__ void k_crop_fold(const float *__restrict__ gimg, const int2 *__restrict__ crop, int ne, int nd,
                             float *__restrict__ gi, int nb) {
-    pdl_trigger();
     pdl_wait();
     const int r = blockIdx.y;
     const size_t npb = (size_t)nb * nb, np = (size_t)nd * nd;
@@ -1472,7 +1461,6 @@ constexpr int kGopdTerms = 64;  // Zernike terms per pass of its partial sums
 __global__ void __launch_bounds__(256) k_gopd_zern(const float *__restrict__ gphi, int B, int npx,
                                                    float2 *__restrict__ gopd, DevGrads g, DevParams prm, int nz,
                                                    float2 *__restrict__ zpart) {
-    pdl_trigger();
     pdl_wait();
     __shared__ df sh[4][kGopdPx];
     __shared__ df ts[kGopdPx];
@@ -1599,7 +1587,6 @@ __global__ void k_pos_final(const double *part, int nsplit, int B, int nl, int n
 // exposures of source s.
 __global__ void k_grad_final(const float2 *__restrict__ zpart, int nz, int nzb, const float *__restrict__ mom,
                              int per_psf, int B, int nl, int ns, int ne, DevGrads g) {
-    pdl_trigger();
     pdl_wait();
     __shared__ df sh[32 * 2];
     const int r = blockIdx.y, k = blockIdx.x;
@@ -1698,7 +1685,6 @@ __global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ E
                                                      const unsigned int *__restrict__ qmax,
                                                      const float *__restrict__ ascale, const float *__restrict__ pscale,
                                                      float sig1, float pf, unsigned int *gmax) {
-    pdl_trigger();
     pdl_wait();
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5, nrows = nb * no;
@@ -1765,7 +1751,6 @@ __global__ void __launch_bounds__(256, 3) k_field_scale_pair(const float *__rest
                                                              const float *__restrict__ pscale, float sig1, float pf,
                                                              unsigned int *gmax) {
     using H = H16<FMT_F16X4>;
-    pdl_trigger();
     pdl_wait();
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5, nrows = nb * hno;
@@ -1854,7 +1839,6 @@ __global__ void __launch_bounds__(256, 3) k_field_scale_pair(const float *__rest
 // (the field scaling reads the weights along y).
 __global__ void k_gi_transpose(const float *__restrict__ GI, float *__restrict__ GIt, int nd) {
     __shared__ float t[32][33];
-    pdl_trigger();
     pdl_wait();
     const size_t base = (size_t)blockIdx.z * nd * nd;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;

@@ -576,7 +576,6 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     volatile int *abort_flag = (volatile int *)(bars + 2 * G::STAGES + 5);
     uint32_t *tmem_slot = (uint32_t *)(bars + 2 * G::STAGES + 6);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    pdl_trigger();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < G::STAGES; ++s) {
