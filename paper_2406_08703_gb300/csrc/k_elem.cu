@@ -388,72 +388,87 @@ __global__ void __launch_bounds__(256, 4) k_phasor(DevParams prm, const float *_
 }
 
 // The phasor of the mirror-paired forward (FP16 split form; pair_layout in dlx_common.cuh).
-// One thread takes a quadrant point jy and four pair indices jx .. jx+3 for one wavelength: the
-// sixteen samples (jy or Ni-1-jy, jx+q or Ni-1-jx-q) of T_hat exp(i 2 pi OPD / lambda), times the
+// One thread takes a quadrant point jy and QW pair indices jx .. jx+QW-1 for one wavelength: the
+// 4 QW samples (jy or Ni-1-jy, jx+q or Ni-1-jx-q) of T_hat exp(i 2 pi OPD / lambda), times the
 // tilts of each source and exposure, give (a) the plain phasor P, written as k_phasor writes it
 // (pi_r P; the adjoint 1^T epilogue reads it), and (b) the sums and differences along both axes
 // into Pp, times pi_r / 4 (a sum of four samples of modulus <= 1 stays <= 1).  A mirror that is
 // its own sample (the middle row or column of an odd pupil) counts once: its partner is taken
-// as zero.  Grid: x over (jy, group of four jx), y over (slot, wavelength).
-__device__ __forceinline__ void store_pair4(__half *q, size_t ps, const float (&v1)[4], const float (&v2)[4]) {
+// as zero.  Grid: x over (jy, group of QW jx), y over (slot, wavelength).
+template <int N>
+struct HVec;  // N halves stored as one vector
+template <>
+struct HVec<4> {
+    using T = uint2;
+};
+template <>
+struct HVec<2> {
+    using T = unsigned int;
+};
+template <int N>
+__device__ __forceinline__ void store_pairN(__half *q, size_t ps, const float (&v1)[N], const float (&v2)[N]) {
     using H = H16<FMT_F16X4>;
-    __align__(8) __half h1[4], l1[4], h2[4], l2[4];
+    using V = typename HVec<N>::T;
+    __align__(8) __half h1[N], l1[N], h2[N], l2[N];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < N; ++i) {
         h1[i] = H::hi(v1[i]);
         l1[i] = H::from(v1[i] - H::to(h1[i]));
         h2[i] = H::hi(v2[i]);
         l2[i] = H::from(v2[i] - H::to(h2[i]));
     }
-    *(uint2 *)q = *(const uint2 *)h1;
-    *(uint2 *)(q + ps) = *(const uint2 *)l1;
-    *(uint2 *)(q + 2 * ps) = *(const uint2 *)h2;
-    *(uint2 *)(q + 3 * ps) = *(const uint2 *)l2;
+    *(V *)q = *(const V *)h1;
+    *(V *)(q + ps) = *(const V *)l1;
+    *(V *)(q + 2 * ps) = *(const V *)h2;
+    *(V *)(q + 3 * ps) = *(const V *)l2;
 }
 
-// Four consecutive elements of a four-plane FP16 split operand (8-byte aligned): one 8-byte store
-// per plane.
-__device__ __forceinline__ void store_cplx4_f16(__half *p, size_t ps, const float (&re)[4], const float (&im)[4]) {
+// N consecutive elements of a four-plane FP16 split operand (aligned to 2 N bytes): one 2 N-byte
+// store per plane.
+template <int N>
+__device__ __forceinline__ void store_cplxN_f16(__half *p, size_t ps, const float (&re)[N], const float (&im)[N]) {
     using H = H16<FMT_F16X4>;
-    __align__(8) __half rh[4], rl[4], ih[4], il[4];
+    using V = typename HVec<N>::T;
+    __align__(8) __half rh[N], rl[N], ih[N], il[N];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < N; ++i) {
         rh[i] = H::hi(re[i]);
         rl[i] = H::from(re[i] - H::to(rh[i]));
         ih[i] = H::hi(im[i]);
         il[i] = H::from(im[i] - H::to(ih[i]));
     }
-    *(uint2 *)p = *(const uint2 *)rh;
-    *(uint2 *)(p + ps) = *(const uint2 *)rl;
-    *(uint2 *)(p + 2 * ps) = *(const uint2 *)ih;
-    *(uint2 *)(p + 3 * ps) = *(const uint2 *)il;
+    *(V *)p = *(const V *)rh;
+    *(V *)(p + ps) = *(const V *)rl;
+    *(V *)(p + 2 * ps) = *(const V *)ih;
+    *(V *)(p + 3 * ps) = *(const V *)il;
 }
 
-__global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const float *__restrict__ opd,
+template <int QW>
+__global__ void __launch_bounds__(256, QW == 4 ? 2 : 3) k_phasor_pair(DevParams prm, const float *__restrict__ opd,
                                                      const float2 *__restrict__ tilt, const float *__restrict__ invlam,
                                                      const float *__restrict__ pscale, int B, int nl, int nse, int ne,
                                                      int ni, int ldi, void *P, void *Pp, int hn, int hp, int ldk,
                                                      const float *__restrict__ tmap, float tcoef, uint32_t tmask) {
     pdl_wait();
     constexpr int F = FMT_F16X4;
-    const int npx = ni * ni, ng = (hn + 3) >> 2;
+    const int npx = ni * ni, ng = (hn + QW - 1) / QW;
     const int r = blockIdx.y / nl, l = blockIdx.y - r * nl;
     const float *T = slot_ptr(prm, PT, r), *op = opd + (size_t)r * npx;
     const float sc = pscale[2 * r] * pscale[2 * r + 1], il = invlam[l];
     const size_t ps = (size_t)ni * ldi, pps = (size_t)2 * hp * ldk;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < hn * ng; it += gridDim.x * blockDim.x) {
-        const int jy = it / ng, jx0 = 4 * (it - jy * ng);
+        const int jy = it / ng, jx0 = QW * (it - jy * ng);
         const int ys[2] = {jy, ni - 1 - jy};
         // T_hat exp(i 2 pi OPD / lambda) and the tangent coefficient at (ys[a], x of (h, q));
         // h = 1 is the mirror column ni - 1 - (jx0 + q)
-        float br[2][2][4], bi[2][2][4], ta[2][2][4];
-        bool in[2][2][4];
+        float br[2][2][QW], bi[2][2][QW], ta[2][2][QW];
+        bool in[2][2][QW];
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
+                for (int q = 0; q < QW; ++q) {
                     const int jx = jx0 + q, x = h ? ni - 1 - jx : jx;
                     in[a][h][q] = jx < hn && !(a == 1 && ys[1] == ys[0]) && !(h == 1 && x == jx);
                     br[a][h][q] = 0.f;
@@ -476,18 +491,18 @@ __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const flo
             const int bg = r * B + l * nse + se;
             const float2 *tx = tilt + (size_t)bg * 2 * ni, *ty = tx + ni;
             const bool tan = tmap && ((tmask >> (se / ne)) & 1u);
-            float pr[2][2][4], pim[2][2][4];
+            float pr[2][2][QW], pim[2][2][QW];
             char *pb = (char *)P + (size_t)bg * 4 * ps * 2;
-            // four whole pairs of an axis of a multiple of 4 samples: the plain phasor goes out as
-            // 8-byte vectors (the mirror columns ni-4-jx0 .. ni-1-jx0 in increasing order)
-            const bool vec = (ni & 3) == 0 && jx0 + 3 < hn;
+            // QW whole pairs of an axis of a multiple of QW samples: the plain phasor goes out as
+            // 2 QW-byte vectors (the mirror columns ni-QW-jx0 .. ni-1-jx0 in increasing order)
+            const bool vec = (ni % QW) == 0 && jx0 + QW - 1 < hn;
 #pragma unroll
             for (int a = 0; a < 2; ++a) {
                 const float2 ey = __ldg(ty + ys[a]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < QW; ++q) {
                         pr[a][h][q] = 0.f;
                         pim[a][h][q] = 0.f;
                         if (!in[a][h][q]) continue;
@@ -507,17 +522,17 @@ __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const flo
                         if (!vec) store_cplx<F>(pb, ps, (size_t)ys[a] * ldi + x, vr, vi);
                     }
                 if (vec) {
-                    float r0[4], i0[4], r1[4], i1[4];
+                    float r0[QW], i0[QW], r1[QW], i1[QW];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < QW; ++q) {
                         r0[q] = pr[a][0][q];
                         i0[q] = pim[a][0][q];
-                        r1[q] = pr[a][1][3 - q];
-                        i1[q] = pim[a][1][3 - q];
+                        r1[q] = pr[a][1][QW - 1 - q];
+                        i1[q] = pim[a][1][QW - 1 - q];
                     }
                     __half *pr0 = (__half *)pb + (size_t)ys[a] * ldi;
-                    store_cplx4_f16(pr0 + jx0, ps, r0, i0);
-                    store_cplx4_f16(pr0 + (ni - 4 - jx0), ps, r1, i1);
+                    store_cplxN_f16<QW>(pr0 + jx0, ps, r0, i0);
+                    store_cplxN_f16<QW>(pr0 + (ni - QW - jx0), ps, r1, i1);
                 }
             }
             // (b) Q[Ry][Rx]: Ry pairs the rows (S = sum, D = difference), Rx the columns; column
@@ -527,9 +542,9 @@ __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const flo
             for (int ry = 0; ry < 2; ++ry)
 #pragma unroll
                 for (int rx = 0; rx < 2; ++rx) {
-                    float v1[4], v2[4];
+                    float v1[QW], v2[QW];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < QW; ++q) {
                         const float sy = ry ? -1.f : 1.f, sx = rx ? -1.f : 1.f;
                         const float qr = (pr[0][0][q] + sx * pr[0][1][q]) + sy * (pr[1][0][q] + sx * pr[1][1][q]);
                         const float qi = (pim[0][0][q] + sx * pim[0][1][q]) + sy * (pim[1][0][q] + sx * pim[1][1][q]);
@@ -537,12 +552,15 @@ __global__ void __launch_bounds__(256, 2) k_phasor_pair(DevParams prm, const flo
                         v2[q] = 0.25f * (rx ? qr : qi);
                     }
                     const int row = ry * hp + jy, col = rx * hp + jx0;
-                    store_pair4(qb + (size_t)row * ldk + col, pps, v1, v2);
+                    store_pairN<QW>(qb + (size_t)row * ldk + col, pps, v1, v2);
                 }
         }
     }
 }
 
+// columns per thread of the paired phasor: with two (80 registers, three blocks per SM) the
+// calibration workload's prologue and phasor build took 0.161 ms, with four (128 registers) 0.174
+constexpr int kPhasorQW = 2;
 cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream_t st) {
     const int npx = p->ni * p->ni;
     KScope ks(p, KC_PROLOGUE, 2, st);
@@ -554,9 +572,9 @@ cudaError_t launch_prologue(dlx_plan *p, const DevParams &prm, int R, cudaStream
     if (e != cudaSuccess) return e;
     const int nyl = R * p->nl;
     if (p->paired) {
-        const int items = p->hn * ((p->hn + 3) / 4);
+        const int items = p->hn * ((p->hn + kPhasorQW - 1) / kPhasorQW);
         const int px = std::max(1, std::min((items + 255) / 256, (p->sm_count * 16 + nyl - 1) / nyl));
-        return launch_pdl(k_phasor_pair, dim3(px, nyl), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam, p->pscale,
+        return launch_pdl(k_phasor_pair<kPhasorQW>, dim3(px, nyl), dim3(256), 0, st, prm, p->opd, p->tilt, p->invlam, p->pscale,
                           p->B, p->nl, p->nse, p->ne, p->ni, p->ldi, p->P.ptr, p->Pp.ptr, p->hn, p->hp, p->ldk,
                           p->tan_map, p->tan_coef, p->tan_mask);
     }
