@@ -546,6 +546,18 @@ __device__ __forceinline__ void store_field_t(const TcArgs &a, int b, int m, int
                                               const float (&ei)[CW]) {
     if (m >= a.M) return;
     float *o = (float *)a.out + (size_t)b * 2 * a.out_ps + (size_t)n0 * a.out_ld + m;
+    if (n0 + CW <= a.N) {  // whole chunk: two running pointers, no per-column test
+        float *oi = o + a.out_ps;
+        const size_t ld = a.out_ld;
+#pragma unroll
+        for (int i = 0; i < CW; ++i) {
+            *o = er[i];
+            *oi = ei[i];
+            o += ld;
+            oi += ld;
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < CW; ++i) {
         if (n0 + i < a.N) {
