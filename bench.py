@@ -755,10 +755,9 @@ def contraction_flop(B, ni, no):
 # and the A(lambda) blocks are per wavelength); none for a kernel, form or workload without a
 # capture of the current code
 TRAFFIC_16 = {
-    "f16x3": {"calib": {"stage1": 121.80e6, "stage2_intensity": 906.40e6, "adjoint_stage2T": 851.50e6,
-                        "adjoint_stage1T": 183.30e6}},
-    "bf16x3": {"calib": {"stage1": 131.90e6, "stage2_intensity": 1003.46e6, "adjoint_stage2T": 892.43e6,
-                         "adjoint_stage1T": 198.76e6}},
+    "f16x3": {"calib": {"stage1": 124.86e6, "stage2_intensity": 896.64e6, "adjoint_stage2T": 851.07e6,
+                        "adjoint_stage1T": 183.38e6}},
+    "bf16x3": {"calib": {"stage1": 131.90e6, "adjoint_stage2T": 892.43e6, "adjoint_stage1T": 198.76e6}},
 }
 
 
