@@ -11,6 +11,7 @@
 // floating-point atomics), so results do not depend on scheduling or on which
 // other slots share the launch.
 #include <algorithm>
+#include <type_traits>
 
 #include "dlx_common.cuh"
 
@@ -1695,8 +1696,45 @@ __device__ __forceinline__ float field_scale_vec(const float *er, const float *e
     return mx;
 }
 
+// The same eight columns for the TF32 split form: FP32 planes, hi = the 8-bit split and lo its
+// remainder rounded to TF32, as the recomputing epilogue writes them.
+__device__ __forceinline__ float field_scale_vec_tf32(const float *er, const float *ei, float *p, size_t ps,
+                                                      const float *gi, float c, int k0, int no, int os, int bmax) {
+    const float4 a0 = __ldg((const float4 *)(er + k0)), a1 = __ldg((const float4 *)(er + k0) + 1);
+    const float4 c0 = __ldg((const float4 *)(ei + k0)), c1 = __ldg((const float4 *)(ei + k0) + 1);
+    const float xr[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    const float xi[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+    __align__(16) float rh[8], rl[8], ih[8], il[8];
+    int brow = k0 / os, brem = k0 - brow * os;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const bool in = k0 + q < no;
+        const float f = in ? c * __ldg(gi + min(brow, bmax)) : 0.f;
+        const float x = in ? xr[q] * f : 0.f, y = in ? xi[q] * f : 0.f;
+        rh[q] = split_hi8(x);
+        rl[q] = tf32_round(x - rh[q]);
+        ih[q] = split_hi8(y);
+        il[q] = tf32_round(y - ih[q]);
+        if (++brem == os) {
+            brem = 0;
+            ++brow;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        *(float4 *)(p + k0 + 4 * h) = *(const float4 *)(rh + 4 * h);
+        *(float4 *)(p + ps + k0 + 4 * h) = *(const float4 *)(rl + 4 * h);
+        *(float4 *)(p + 2 * ps + k0 + 4 * h) = *(const float4 *)(ih + 4 * h);
+        *(float4 *)(p + 3 * ps + k0 + 4 * h) = *(const float4 *)(il + 4 * h);
+    }
+    return 0.f;
+}
+
 template <int F>
-__global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ Ef, typename H16<F>::T *__restrict__ ge,
+using FieldOpT = std::conditional_t<F == FMT_TF32X4, float, typename H16<F>::T>;
+
+template <int F>
+__global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ Ef, FieldOpT<F> *__restrict__ ge,
                                                      const float *__restrict__ GIt, DevParams prm,
                                                      const float *__restrict__ wnorm, int b0, int nb, int B, int nl,
                                                      int nse, int ne, int no, int ldo, int nd, int os,
@@ -1721,15 +1759,18 @@ __global__ void __launch_bounds__(256) k_field_scale(const float *__restrict__ E
         }
         const float *gi = GIt + (((size_t)r * ne + e) * nd + kx / os) * nd;  // row x = kx / os, along y
         const float *er = Ef + (size_t)b * 2 * ps + (size_t)kx * ldo, *ei = er + ps;
-        typename H16<F>::T *p = ge + (size_t)z * 4 * ps + (size_t)kx * ldo;
+        FieldOpT<F> *p = ge + (size_t)z * 4 * ps + (size_t)kx * ldo;
+        auto vec8 = [&](int k) {
+            if constexpr (F == FMT_TF32X4) return field_scale_vec_tf32(er, ei, p, ps, gi, c, k, no, os, bmax);
+            else return field_scale_vec<F>(er, ei, p, ps, gi, c, k, no, os, bmax);
+        };
         float mx = 0.f;
         int k0 = 8 * lane;
         for (; k0 + 3 * 256 < ldo; k0 += 4 * 256) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                mx = fmaxf(mx, field_scale_vec<F>(er, ei, p, ps, gi, c, k0 + u * 256, no, os, bmax));
+            for (int u = 0; u < 4; ++u) mx = fmaxf(mx, vec8(k0 + u * 256));
         }
-        for (; k0 < ldo; k0 += 256) mx = fmaxf(mx, field_scale_vec<F>(er, ei, p, ps, gi, c, k0, no, os, bmax));
+        for (; k0 < ldo; k0 += 256) mx = fmaxf(mx, vec8(k0));
         if constexpr (F == FMT_F16X4) {
             // max |GEt| of the PSF (non-negative floats order as their bits)
             if (!(mx < 3.0e38f)) mx = 3.0e38f;
@@ -1897,6 +1938,7 @@ cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb
                           inv_pow2_ceil((float)p->ni), p->paired ? 4.f : 1.f, p->gmax);
     }
     if (p->fmt == FMT_F16X4) return go(k_field_scale<FMT_F16X4>, p->GEt.ptr);
+    if (p->fmt == FMT_TF32X4) return go(k_field_scale<FMT_TF32X4>, p->GEt.ptr);
     return go(k_field_scale<FMT_BF16X4>, p->GEt.ptr);
 }
 

@@ -976,7 +976,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             acc[CW * cc + i] = fmaf(w, er[i] * er[i] + ei[i] * ei[i], acc[CW * cc + i]);
                         // the field kept for the adjoint (FP16 form: the raw accumulators; the scaling
                         // pass applies the operand scales)
-                        if constexpr (F == FMT_BF16X4 || F == FMT_F16X4) {
+                        if constexpr (F == FMT_BF16X4 || F == FMT_F16X4 || F == FMT_TF32X4) {
                             if (a.out) store_field_t(a, J.b, m, J.n0 + 64 * h + CW * cc, er, ei);
                         }
                     };
@@ -1299,7 +1299,7 @@ cudaError_t adjoint_impl(dlx_plan *p, const DevParams &prm, int b0, int nb, cuda
         T1.tmap = p->T1t.tmap_hi;
         Am.tmap = p->amat.tmap_hi;
     }
-    // the field kept by stage 2 (BF16 split forms) is scaled and split; otherwise it is recomputed
+    // the field kept by stage 2 (split forms) is scaled and split; otherwise it is recomputed
     cudaError_t e;
     if (p->keep_field) {
         e = launch_field_scale(p, prm, b0, nb, st);
