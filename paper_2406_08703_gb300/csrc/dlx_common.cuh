@@ -593,14 +593,14 @@ cudaError_t launch_nll_cotangent(const float *m, const int32_t *d, size_t n, flo
 // adds the stage-2 split's extra planes into plane 0 (tensor-core forms; no-op otherwise)
 cudaError_t launch_plane_fold(dlx_plan *p, int R, cudaStream_t st);
 // Whether an evaluation of R slots keeps the fields stage 2 forms for the adjoint: plans of the
-// split forms (BF16x3, BF16x4, FP16x3, TF32x3; not BF16x3sa) whose adjoint operand holds every
-// PSF at once allocate Ef.
+// split forms (BF16x3, BF16x4, FP16x3, TF32x3; not BF16x3sa) and of the FP32 CUDA-core form whose
+// adjoint operand holds every PSF at once allocate Ef.
 inline bool keeps_field(const dlx_plan *p, int R) { return p->Ef != nullptr && p->chunk >= R * p->B; }
 // Whether a plan of this form, pupil size, PSF count and adjoint chunk allocates Ef (the FP16
 // form's mirror-paired adjoint needs the kept field: its scaling pass writes the paired operand).
 inline bool field_kept(int fmt, bool adj1, int ni, int chunk, int Bt) {
     (void)ni;
-    return (fmt == FMT_BF16X4 || fmt == FMT_F16X4 || fmt == FMT_TF32X4) && !adj1 && chunk >= Bt;
+    return (fmt == FMT_BF16X4 || fmt == FMT_F16X4 || fmt == FMT_TF32X4 || fmt == FMT_F32) && !adj1 && chunk >= Bt;
 }
 // The adjoint field from the kept fields: GEt[z] = split(2 w F GI o Ef[b0 + z]) (z < nb).
 cudaError_t launch_field_scale(dlx_plan *p, const DevParams &prm, int b0, int nb, cudaStream_t st);

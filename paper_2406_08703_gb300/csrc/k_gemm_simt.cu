@@ -122,9 +122,10 @@ __global__ void __launch_bounds__(NT, 2) k_simt_stage1(const float *amat, const 
 }
 
 // Stage 2 + intensity: Is[g][r nse + se][ky][kx] = sum_{l in group g} w_l |sum_ny A(l)[ky][ny] T1t[b][kx][ny]|^2.
+// With Ef, every PSF's field is also kept for the adjoint: Ef[b][re, im][ky][kx] (rows of ldo).
 __global__ void __launch_bounds__(NT, 2) k_simt_stage2(const float *amat, const float *T1t, const float *wnorm, float *Is,
                                                     int ni, int no, int ldi, int nse, int nl, int G, int tiles_n,
-                                                    int B) {
+                                                    int B, float *Ef, int ldo) {
     __shared__ SimtSmem sm;
     const int rse = blockIdx.y, r = rse / nse, se = rse % nse, g = blockIdx.z;
     const int m0 = (blockIdx.x / tiles_n) * BM, n0 = (blockIdx.x % tiles_n) * BN;
@@ -144,6 +145,27 @@ __global__ void __launch_bounds__(NT, 2) k_simt_stage2(const float *amat, const 
         for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(w, cr[i][j] * cr[i][j] + ci[i][j] * ci[i][j], acc[i][j]);
+        if (Ef) {
+            const size_t eps = (size_t)no * ldo;
+            float *er = Ef + (size_t)b * 2 * eps, *ei = er + eps;
+            const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int m = m0 + 4 * ty + i, n = n0 + 4 * tx;
+                if (m >= no) continue;
+                if (n + 3 < no && (ldo & 3) == 0) {
+                    *(float4 *)(er + (size_t)m * ldo + n) = make_float4(cr[i][0], cr[i][1], cr[i][2], cr[i][3]);
+                    *(float4 *)(ei + (size_t)m * ldo + n) = make_float4(ci[i][0], ci[i][1], ci[i][2], ci[i][3]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (n + j < no) {
+                            er[(size_t)m * ldo + n + j] = cr[i][j];
+                            ei[(size_t)m * ldo + n + j] = ci[i][j];
+                        }
+                }
+            }
+        }
     }
     float *out = Is + ((size_t)g * gridDim.y + rse) * no * no;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -188,6 +210,40 @@ __global__ void __launch_bounds__(NT, 2) k_simt_grad_field(const float *amat, co
                 out[gps + (size_t)kx * ldo + ky] = f * ci[i][j];
             }
         }
+}
+
+// Adjoint field from the field stage 2 kept: GEt[z][kx][ky] = 2 w_l F_s GI[e][bin(ky,kx)] E[ky][kx],
+// the values k_simt_grad_field computes, transposed through 32 x 32 tiles in shared memory.
+__global__ void k_simt_field_scale(const float *__restrict__ Ef, const float *__restrict__ wnorm, DevParams prm,
+                                   const float *__restrict__ GI, float *GEt, int no, int ldo, int nl, int nse, int ne,
+                                   int nd, int os, int B, int b0) {
+    __shared__ float tr[32][33], ti[32][33];
+    const int z = blockIdx.z, b = b0 + z, r = b / B, bl = b % B, l = bl / nse, se = bl % nse, s = se / ne,
+              e = se % ne;
+    const int kx0 = blockIdx.x * 32, ky0 = blockIdx.y * 32;
+    const size_t ps = (size_t)no * ldo;
+    const float *er = Ef + (size_t)b * 2 * ps, *ei = er + ps;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ky = ky0 + threadIdx.y + 8 * k, kx = kx0 + threadIdx.x;
+        if (ky < no && kx < no) {
+            tr[threadIdx.y + 8 * k][threadIdx.x] = er[(size_t)ky * ldo + kx];
+            ti[threadIdx.y + 8 * k][threadIdx.x] = ei[(size_t)ky * ldo + kx];
+        }
+    }
+    __syncthreads();
+    const float c = 2.f * wnorm[(size_t)r * nl + l] * slot_ptr(prm, PFLUX, r)[s];
+    const float *gi = GI + ((size_t)r * ne + e) * nd * nd;
+    float *gr = GEt + (size_t)z * 2 * ps, *gim = gr + ps;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int kx = kx0 + threadIdx.y + 8 * k, ky = ky0 + threadIdx.x;
+        if (kx < no && ky < no) {
+            const float f = c * gi[(ky / os) * nd + kx / os];
+            gr[(size_t)kx * ldo + ky] = f * tr[threadIdx.x][threadIdx.y + 8 * k];
+            gim[(size_t)kx * ldo + ky] = f * ti[threadIdx.x][threadIdx.y + 8 * k];
+        }
+    }
 }
 
 // Adjoint stage 2^T: GT1[z][ny][kx] = sum_ky AH(l)[ny][ky] GEt[z][kx][ky].
@@ -260,7 +316,7 @@ cudaError_t simt_forward(dlx_plan *p, int R, cudaStream_t st) {
     dim3 g2(cdiv(p->no, BM) * tn, R * p->nse, p->G);
     KScope ks(p, KC_STAGE2, 1, st);
     k_simt_stage2<<<g2, NT, 0, st>>>(amat, (const float *)p->T1t.ptr, p->wnorm, p->Is, p->ni, p->no, p->ldi, p->nse,
-                                     p->nl, p->G, tn, p->B);
+                                     p->nl, p->G, tn, p->B, p->keep_field ? (float *)p->Ef : nullptr, p->ldo);
     return cudaGetLastError();
 }
 
@@ -268,11 +324,17 @@ cudaError_t simt_adjoint_chunk(dlx_plan *p, const DevParams &prm, int b0, int nb
     const float *amat = (const float *)p->amat.ptr, *amatH = (const float *)p->amatH.ptr;
     int tn = cdiv(p->no, BN);
     dim3 ge(cdiv(p->no, BM) * tn, nb);
-    {
-    KScope ks(p, KC_ADJ_FIELD, 1, st);
-    k_simt_grad_field<<<ge, NT, 0, st>>>(amat, (const float *)p->T1t.ptr, p->wnorm, prm, p->GI, (float *)p->GEt.ptr,
-                                         p->ni, p->no, p->ldi, p->ldo, p->nl, p->nse, p->ne, p->nd, p->os, p->B, b0,
-                                         tn);
+    if (p->keep_field) {  // the field stage 2 kept, scaled and transposed
+        KScope ks(p, KC_FIELD_SCALE, 1, st);
+        const int t32 = cdiv(p->no, 32);
+        k_simt_field_scale<<<dim3(t32, t32, nb), dim3(32, 8), 0, st>>>((const float *)p->Ef, p->wnorm, prm, p->GI,
+                                                                       (float *)p->GEt.ptr, p->no, p->ldo, p->nl,
+                                                                       p->nse, p->ne, p->nd, p->os, p->B, b0);
+    } else {
+        KScope ks(p, KC_ADJ_FIELD, 1, st);
+        k_simt_grad_field<<<ge, NT, 0, st>>>(amat, (const float *)p->T1t.ptr, p->wnorm, prm, p->GI,
+                                             (float *)p->GEt.ptr, p->ni, p->no, p->ldi, p->ldo, p->nl, p->nse, p->ne,
+                                             p->nd, p->os, p->B, b0, tn);
     }
     dim3 g2(cdiv(p->ni, BM), cdiv(p->no, BN), nb);
     {

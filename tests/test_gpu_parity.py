@@ -127,16 +127,17 @@ def test_binary_full_size(binary_full, form):
 
 
 def test_adjoint_chunking_is_bitwise_identical():
-    """Per-wavelength recomputation in chunks of 1, 3 or all PSFs gives identical bits."""
+    """Per-wavelength recomputation in chunks of 1, 3 or 5 of the 8 PSFs gives identical bits (a
+    chunk of all PSFs keeps the field instead: test_kept_field_matches_recomputed_field)."""
     _, data, start = fit_problem("custom", seed=5, **RAGGED[0])
-    outs = [gpu_eval(start, data, "fp32", psf_chunk=c, want_psf=False) for c in (1, 3, 0)]
+    outs = [gpu_eval(start, data, "fp32", psf_chunk=c, want_psf=False) for c in (1, 3, 5)]
     for o in outs[1:]:
         assert o["loss"] == outs[0]["loss"]
         for k in o["grads"]:
             assert np.array_equal(o["grads"][k], outs[0]["grads"][k]), k
 
 
-@pytest.mark.parametrize("form", ["bf16x3", "f16x3", "tf32x3"])
+@pytest.mark.parametrize("form", ["bf16x3", "f16x3", "tf32x3", "fp32"])
 def test_kept_field_matches_recomputed_field(form):
     """The adjoint from the field stage 2 keeps (the default when the adjoint takes every PSF at
     once; in the FP16 form also the mirror-paired adjoint contractions) against the adjoint that
@@ -147,7 +148,7 @@ def test_kept_field_matches_recomputed_field(form):
     recomputed = gpu_eval(start, data, form, psf_chunk=1, want_psf=False)
     assert kept["loss"] == recomputed["loss"]
     assert np.array_equal(kept["model"], recomputed["model"])
-    bound = {"bf16x3": 2e-4, "f16x3": 1e-4, "tf32x3": 1e-4}[form]
+    bound = {"bf16x3": 2e-4, "f16x3": 1e-4, "tf32x3": 1e-4, "fp32": 1e-5}[form]
     for k, v in kept["grads"].items():
         if v is not None and np.any(v):
             assert rel_l2(v, recomputed["grads"][k]) < bound, k
